@@ -1,0 +1,190 @@
+"""ctypes front-end of the CPU oracle (test infrastructure only).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
+leg may import this module.  It never imports the product package.
+
+Every routine forwards to ``mf_oracle.c`` (plain FP64 C); the few numpy steps
+here are library primitives (dense matrix products) used as stated steps of a
+definition, with no blocking or reordering beyond the definition.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+GEN_PHILOX_GUE = 0
+GEN_SINC_DVR_HO = 1
+FORM_FP64 = 0
+FORM_FP32 = 1
+
+
+class OrOp(ctypes.Structure):
+    _fields_ = [
+        ("gen", ctypes.c_int32),
+        ("form", ctypes.c_int32),
+        ("seed", ctypes.c_uint64),
+        ("D", ctypes.c_int64),
+        ("L", ctypes.c_double),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        P = ctypes.POINTER
+        d, i64, i32, u64 = ctypes.c_double, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64
+        vp = ctypes.c_void_p
+        L.or_philox4x32_10.argtypes = [vp, vp, vp]
+        L.or_log.argtypes = [d]; L.or_log.restype = d
+        L.or_logf.argtypes = [ctypes.c_float]; L.or_logf.restype = ctypes.c_float
+        L.or_sincos_2pi.argtypes = [d, P(d), P(d)]
+        L.or_sincos_2pif.argtypes = [ctypes.c_float, P(ctypes.c_float), P(ctypes.c_float)]
+        L.or_entry.argtypes = [P(OrOp), i64, i64, P(d), P(d)]
+        L.or_dvr_potential.argtypes = [P(OrOp), i64]; L.or_dvr_potential.restype = d
+        L.or_window.argtypes = [P(OrOp), i64, i64, i64, i64, vp]
+        L.or_window_f32.argtypes = [P(OrOp), i64, i64, i64, i64, vp]
+        L.or_apply.argtypes = [P(OrOp), i64, i64, vp, vp, ctypes.c_int]
+        L.or_apply_rows.argtypes = [P(OrOp), i64, vp, i64, vp, vp, ctypes.c_int]
+        L.or_bessel_j.argtypes = [d, i32, vp]
+        L.or_cheb_terms.argtypes = [d, d]; L.or_cheb_terms.restype = i32
+        L.or_cheb_step.argtypes = [P(OrOp), i64, i64, vp, d, d, d, i32, ctypes.c_int]
+        _lib = L
+    return _lib
+
+
+def dvr_default_L(D):
+    """Grid half-width L = 0.9 sqrt(2D) of the DVR workload."""
+    return 0.9 * np.sqrt(2.0 * float(D))
+
+
+def make_op(gen, D, seed=1, form=FORM_FP64, L=None):
+    if gen == GEN_SINC_DVR_HO and L is None:
+        L = dvr_default_L(D)
+    return OrOp(int(gen), int(form), int(seed) & 0xFFFFFFFFFFFFFFFF, int(D), float(L or 0.0))
+
+
+def philox(ctr, key):
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib().or_philox4x32_10(c.ctypes.data, k.ctypes.data, out.ctypes.data)
+    return out
+
+
+def log64(u):
+    return lib().or_log(float(u))
+
+
+def log32(u):
+    return np.float32(lib().or_logf(ctypes.c_float(np.float32(u))))
+
+
+def sincos64(u):
+    s, c = ctypes.c_double(), ctypes.c_double()
+    lib().or_sincos_2pi(float(u), ctypes.byref(s), ctypes.byref(c))
+    return s.value, c.value
+
+
+def sincos32(u):
+    s, c = ctypes.c_float(), ctypes.c_float()
+    lib().or_sincos_2pif(ctypes.c_float(np.float32(u)), ctypes.byref(s), ctypes.byref(c))
+    return np.float32(s.value), np.float32(c.value)
+
+
+def entry(op, r, c):
+    re, im = ctypes.c_double(), ctypes.c_double()
+    lib().or_entry(ctypes.byref(op), int(r), int(c), ctypes.byref(re), ctypes.byref(im))
+    return complex(re.value, im.value)
+
+
+def potential(op, i):
+    return lib().or_dvr_potential(ctypes.byref(op), int(i))
+
+
+def window(op, r0, c0, rows, cols):
+    """H[r0:r0+rows, c0:c0+cols] as complex128 (entries of op's form)."""
+    out = np.zeros((rows, cols), dtype=np.complex128)
+    lib().or_window(ctypes.byref(op), int(r0), int(c0), int(rows), int(cols), out.ctypes.data)
+    return out
+
+
+def window_native(op, r0, c0, rows, cols):
+    """FP32-form window in its native complex64 (potential not included)."""
+    out = np.zeros((rows, cols), dtype=np.complex64)
+    lib().or_window_f32(ctypes.byref(op), int(r0), int(c0), int(rows), int(cols), out.ctypes.data)
+    return out
+
+
+def dense(op):
+    return window(op, 0, 0, op.D, op.D)
+
+
+def apply(op, x, block=0, nthreads=0):
+    """y = H x (x: [D] or [D, nvec] complex), blockwise FP64 sum."""
+    x = np.asarray(x, dtype=np.complex128)
+    squeeze = x.ndim == 1
+    X = np.ascontiguousarray(x.reshape(op.D, -1))
+    Y = np.zeros_like(X)
+    lib().or_apply(ctypes.byref(op), int(block), int(X.shape[1]), X.ctypes.data, Y.ctypes.data,
+                   int(nthreads))
+    return Y.reshape(-1) if squeeze else Y
+
+
+def apply_rows(op, x, rows, nthreads=0):
+    x = np.asarray(x, dtype=np.complex128)
+    X = np.ascontiguousarray(x.reshape(op.D, -1))
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    Y = np.zeros((rows.size, X.shape[1]), dtype=np.complex128)
+    lib().or_apply_rows(ctypes.byref(op), int(X.shape[1]), X.ctypes.data, int(rows.size),
+                        rows.ctypes.data, Y.ctypes.data, int(nthreads))
+    return Y
+
+
+def bessel_j(x, K):
+    J = np.zeros(K + 1, dtype=np.float64)
+    lib().or_bessel_j(float(x), int(K), J.ctypes.data)
+    return J
+
+
+def cheb_terms(z, tol):
+    return int(lib().or_cheb_terms(float(z), float(tol)))
+
+
+def cheb_coeffs(z, nterms):
+    """a_k = J_0 (k=0), 2 (-i)^k J_k(z) (k>=1), k = 0..nterms-1."""
+    J = bessel_j(z, nterms)
+    a = 2.0 * J[:nterms] * ((-1j) ** np.arange(nterms))
+    a[0] = J[0]
+    return a
+
+
+def cheb_step(op, psi, dt, c, R, nterms, block=0, nthreads=0):
+    """One Chebyshev step of exp(-i dt H) on psi ([D] or [D, nvec])."""
+    psi = np.asarray(psi, dtype=np.complex128)
+    shape = psi.shape
+    P = np.ascontiguousarray(psi.reshape(op.D, -1)).copy()
+    lib().or_cheb_step(ctypes.byref(op), int(block), int(P.shape[1]), P.ctypes.data, float(dt),
+                       float(c), float(R), int(nterms), int(nthreads))
+    return P.reshape(shape)
+
+
+def cheb_step_dense(H, psi, dt, c, R, nterms):
+    """The same recurrence with a materialised H (small D): q_{k+1} =
+    2 (H q_k - c q_k)/R - q_{k-1}, matrix products by numpy."""
+    a = cheb_coeffs(R * dt, nterms)
+    q_prev = None
+    q = np.array(psi, dtype=np.complex128)
+    acc = a[0] * q
+    for k in range(1, nterms):
+        t = (H @ q - c * q) / R
+        qn = t if k == 1 else 2.0 * t - q_prev
+        q_prev, q = q, qn
+        acc = acc + a[k] * q
+    return np.exp(-1j * c * dt) * acc

@@ -1,0 +1,294 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle itself.
+
+Each test names what fixes the expected value: a published known-answer
+vector, a math-library routine, a closed-form spectrum, brute force on a tiny
+input, or an identity of the mathematics.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- Philox ----
+def test_philox_known_answers():
+    """Salmon et al. SC'11 known-answer vectors (tests/golden)."""
+    n = 0
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            w = [int(t, 16) for t in line.split()]
+            out = O.philox(w[0:4], w[4:6])
+            assert list(map(int, out)) == w[6:10]
+            n += 1
+    assert n == 3
+
+
+def test_philox_uniform_moments():
+    """Words mapped to (w + 1/2) 2^-32 are U(0,1): mean 1/2, variance 1/12."""
+    us = []
+    for r in range(4000):
+        w = O.philox([r, 7, 0, 0], [1, 0])
+        us.extend(((int(v) + 0.5) * 2.0 ** -32) for v in w)
+    us = np.array(us)
+    assert abs(us.mean() - 0.5) < 5 * math.sqrt(1 / 12 / us.size)
+    assert abs(us.var() - 1 / 12) < 5e-3
+
+
+# -------------------------------------------------- elementary functions ----
+def _ulps(a, b):
+    return abs(a - b) / np.spacing(abs(b))
+
+
+def test_log64_against_libm():
+    rng = np.random.default_rng(1)
+    us = np.concatenate([rng.random(4000), 2.0 ** -rng.uniform(0, 33, 2000), 1 - rng.random(500) * 1e-6])
+    worst = max(_ulps(O.log64(u), math.log(u)) for u in us if u > 0)
+    assert worst <= 2.0
+
+
+def test_log32_against_libm():
+    rng = np.random.default_rng(2)
+    us = rng.random(4000).astype(np.float32)
+    worst = 0.0
+    for u in us:
+        if u <= 0:
+            continue
+        ref = np.float32(math.log(float(u)))
+        worst = max(worst, abs(float(O.log32(u)) - float(ref)) / float(np.spacing(np.abs(ref))))
+    assert worst <= 3.0
+
+
+def test_sincos_against_multiprecision():
+    """sin/cos(2 pi u) against mpmath at 50 digits (exact angle, no rounding of
+    2 pi u), and the FP32 form against the same."""
+    import mpmath
+    mpmath.mp.dps = 50
+    rng = np.random.default_rng(3)
+    for u in np.concatenate([rng.random(1500), [0.0, 0.125, 0.25, 0.5, 0.75, 0.999999]]):
+        ang = 2 * mpmath.pi * mpmath.mpf(float(u))
+        s, c = O.sincos64(u)
+        assert abs(s - float(mpmath.sin(ang))) < 2.5e-16
+        assert abs(c - float(mpmath.cos(ang))) < 2.5e-16
+        u32 = np.float32(u)
+        ang32 = 2 * mpmath.pi * mpmath.mpf(float(u32))
+        s32, c32 = O.sincos32(u32)
+        assert abs(float(s32) - float(mpmath.sin(ang32))) < 1.5e-7
+        assert abs(float(c32) - float(mpmath.cos(ang32))) < 1.5e-7
+
+
+# ------------------------------------------------------ GUE operator ----
+def test_gue_hermitian_and_real_diagonal():
+    """H_cr = conj(H_rc) bitwise; diagonal real (Sec. III.A partial caching)."""
+    for form in (O.FORM_FP64, O.FORM_FP32):
+        H = O.dense(O.make_op(O.GEN_PHILOX_GUE, 96, seed=5, form=form))
+        assert np.array_equal(H, H.conj().T)
+        assert np.all(H.diagonal().imag == 0)
+
+
+def test_gue_entry_statistics():
+    """Re and Im of off-diagonal entries are N(0, 1/(2D)); diagonal N(0, 1/(2D))."""
+    from scipy import stats
+    D = 512
+    H = O.dense(O.make_op(O.GEN_PHILOX_GUE, D, seed=11))
+    iu = np.triu_indices(D, 1)
+    sig = math.sqrt(1 / (2 * D))
+    for part in (H[iu].real, H[iu].imag, H.diagonal().real):
+        z = part / sig
+        assert abs(z.mean()) < 5 / math.sqrt(z.size)
+        assert abs(z.var() - 1) < 6 * math.sqrt(2 / z.size)
+        assert stats.kstest(z, "norm").pvalue > 1e-4
+
+
+def test_gue_semicircle_edge_and_bulk():
+    """Wigner semicircle on [-2, 2]: extreme eigenvalues near +-2 and
+    P(|lambda| < 1) = (1/2pi) int_{-1}^{1} sqrt(4 - x^2) dx."""
+    H = O.dense(O.make_op(O.GEN_PHILOX_GUE, 2048, seed=1))
+    E = np.linalg.eigvalsh(H)
+    assert 1.9 < E[-1] < 2.1 and -2.1 < E[0] < -1.9
+    frac = (math.sqrt(3) / 2 + 2 * math.asin(0.5)) / math.pi  # closed form of the integral
+    assert abs(np.mean(np.abs(E) < 1) - frac) < 0.02
+
+
+def test_gue_fp32_form_tracks_fp64_form():
+    """The FP32 steps approximate the same entries: typical relative error at
+    single-precision level; worst case bounded by the float resolution of the
+    uniform near 1 (rho = sqrt(-2 ln u) resolves 2^-23.5 there)."""
+    D = 256
+    H64 = O.dense(O.make_op(O.GEN_PHILOX_GUE, D, seed=3))
+    H32 = O.dense(O.make_op(O.GEN_PHILOX_GUE, D, seed=3, form=O.FORM_FP32))
+    rel = np.abs(H32 - H64) / np.abs(H64).max()
+    assert np.median(rel) < 1e-7
+    assert rel.max() < 2e-4
+
+
+def test_seed_changes_operator_and_partition_windows_agree():
+    op1 = O.make_op(O.GEN_PHILOX_GUE, 64, seed=1)
+    op2 = O.make_op(O.GEN_PHILOX_GUE, 64, seed=2)
+    assert not np.allclose(O.dense(op1), O.dense(op2))
+    # windows are cut from global (row, col): any tiling reproduces the dense H
+    H = O.dense(op1)
+    for b in (8, 16, 24):
+        for r0 in range(0, 64, b):
+            for c0 in range(0, 64, b):
+                rows, cols = min(b, 64 - r0), min(b, 64 - c0)
+                assert np.array_equal(O.window(op1, r0, c0, rows, cols), H[r0:r0 + rows, c0:c0 + cols])
+
+
+# ------------------------------------------------------ DVR operator ----
+@pytest.mark.parametrize("D", [256, 384])
+def test_dvr_harmonic_spectrum(D):
+    """Colbert-Miller sinc-DVR + x^2/2 reproduces E_n = n + 1/2."""
+    H = O.dense(O.make_op(O.GEN_SINC_DVR_HO, D))
+    assert np.array_equal(H, H.T) and np.all(H.imag == 0)
+    E = np.linalg.eigvalsh(H.real)
+    n = np.arange(D // 4)
+    assert np.max(np.abs(E[: D // 4] - (n + 0.5))) < 1e-9
+
+
+def test_dvr_fp32_form_tracks_fp64():
+    D = 200
+    T64 = O.dense(O.make_op(O.GEN_SINC_DVR_HO, D)).real
+    T32 = O.dense(O.make_op(O.GEN_SINC_DVR_HO, D, form=O.FORM_FP32)).real
+    assert np.max(np.abs(T32 - T64) / np.abs(T64)) < 3e-7
+
+
+def test_dvr_potential_grid():
+    D = 101
+    op = O.make_op(O.GEN_SINC_DVR_HO, D)
+    L = op.L
+    assert O.potential(op, 0) == pytest.approx(L * L / 2, rel=1e-15)
+    assert O.potential(op, D - 1) == pytest.approx(L * L / 2, rel=1e-12)
+    assert O.potential(op, 50) == pytest.approx(0.0, abs=1e-20)
+
+
+# ------------------------------------------------------ block product ----
+@pytest.mark.parametrize("gen", [O.GEN_PHILOX_GUE, O.GEN_SINC_DVR_HO])
+@pytest.mark.parametrize("form", [O.FORM_FP64, O.FORM_FP32])
+def test_apply_matches_dense_brute_force(gen, form):
+    """Eq. (blockmatvecindex) against a dense numpy product, ragged last block."""
+    D, nvec = 300, 3
+    op = O.make_op(gen, D, seed=9, form=form)
+    rng = np.random.default_rng(4)
+    x = rng.standard_normal((D, nvec)) + 1j * rng.standard_normal((D, nvec))
+    H = O.dense(op)
+    for b in (128, 300):
+        y = O.apply(op, x, block=b)
+        ref = H @ x
+        assert np.max(np.abs(y - ref)) / np.max(np.abs(ref)) < 1e-13
+    rows = np.array([0, 17, 299])
+    assert np.allclose(O.apply_rows(op, x, rows), (H @ x)[rows], rtol=1e-13, atol=0)
+
+
+def test_apply_hermitian_identity():
+    """<x, H y> = <H x, y> for the Hermitian operator."""
+    D = 256
+    op = O.make_op(O.GEN_PHILOX_GUE, D, seed=2)
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal(D) + 1j * rng.standard_normal(D)
+    y = rng.standard_normal(D) + 1j * rng.standard_normal(D)
+    lhs = np.vdot(x, O.apply(op, y))
+    rhs = np.vdot(O.apply(op, x), y)
+    assert abs(lhs - rhs) < 1e-13 * abs(lhs)
+
+
+# --------------------------------------------------------- Bessel / order ----
+@pytest.mark.parametrize("x", [0.5, 2.0, 10.0, 41.3, 200.0])
+def test_bessel_against_scipy(x):
+    from scipy import special
+    K = int(x) + 120
+    J = O.bessel_j(x, K)
+    ref = special.jv(np.arange(K + 1), x)
+    scale = np.max(np.abs(ref))
+    assert np.max(np.abs(J - ref)) < 1e-13 * scale
+    big = np.abs(ref) > 1e-3 * scale
+    assert np.max(np.abs(J[big] - ref[big]) / np.abs(ref[big])) < 1e-10
+
+
+@pytest.mark.parametrize("x,ks", [(1500.0, [0, 700, 1499, 1560]), (10300.0, [1, 5000, 10250, 10400])])
+def test_bessel_large_argument_against_multiprecision(x, ks):
+    """Large R*dt (the DVR workload has R*dt near 1e4): sampled orders against
+    mpmath's series at 25 digits (scipy's own error exceeds 1e-15 there)."""
+    import mpmath
+    mpmath.mp.dps = 25
+    J = O.bessel_j(x, max(ks) + 20)
+    for k in ks:
+        ex = float(mpmath.besselj(k, x, maxterms=10 ** 6, maxprec=20000))
+        assert abs(J[k] - ex) < 1e-15
+
+
+def test_bessel_normalisation_identity():
+    """J_0 + 2 sum J_2k = 1 and J_0^2 + 2 sum J_k^2 = 1 (Neumann identities)."""
+    for x in (3.0, 77.0):
+        J = O.bessel_j(x, int(x) + 100)
+        assert abs(J[0] + 2 * J[2::2].sum() - 1) < 1e-13
+        assert abs(J[0] ** 2 + 2 * (J[1:] ** 2).sum() - 1) < 1e-12
+
+
+def test_cheb_order_matches_paper_run():
+    """Sec. VII: half-width R near 713, tau = 0.1982748544807706 and
+    --cheb-tol 1e-7 gave order 181.  The bounds padding is not printed, so the
+    rule is pinned within the range 0..6 % padding."""
+    tau = 0.1982748544807706
+    lo = O.cheb_terms(713 * tau, 1e-7)
+    hi = O.cheb_terms(713 * 1.06 * tau, 1e-7)
+    assert lo - 12 <= 181 <= hi + 2
+
+
+# --------------------------------------------------------- Chebyshev ----
+def _bounds(H, pad=0.05):
+    E = np.linalg.eigvalsh(H)
+    c = 0.5 * (E[-1] + E[0])
+    R = 0.5 * (E[-1] - E[0]) * (1 + pad)
+    return c, R, E
+
+
+def test_cheb_step_matches_eigendecomposition():
+    """exp(-i t H) psi by numpy eigh vs the oracle recurrence (32 terms, t=1)."""
+    D = 192
+    op = O.make_op(O.GEN_PHILOX_GUE, D, seed=1)
+    H = O.dense(op)
+    c, R, E = _bounds(H)
+    rng = np.random.default_rng(6)
+    psi = rng.standard_normal(D) + 1j * rng.standard_normal(D)
+    psi /= np.linalg.norm(psi)
+    w, V = np.linalg.eigh(H)
+    exact = V @ (np.exp(-1j * w * 1.0) * (V.conj().T @ psi))
+    out = O.cheb_step(op, psi, 1.0, c, R, 32)
+    assert np.max(np.abs(out - exact)) < 1e-12
+    dense_out = O.cheb_step_dense(H, psi, 1.0, c, R, 32)
+    assert np.max(np.abs(dense_out - out)) < 1e-13
+    assert abs(np.linalg.norm(out) - 1) < 1e-12
+    e0 = np.vdot(psi, H @ psi).real
+    e1 = np.vdot(out, H @ out).real
+    assert abs(e1 - e0) < 1e-12
+
+
+def test_dvr_coherent_state_half_period():
+    """Harmonic oscillator closed form: psi(pi)(x) = -i psi0(-x) and
+    psi(2 pi) = -psi0 for psi0 a coherent state at x = 2."""
+    D = 256
+    op = O.make_op(O.GEN_SINC_DVR_HO, D)
+    H = O.dense(op).real
+    dx = 2 * op.L / (D - 1)
+    x = -op.L + dx * np.arange(D)
+    psi0 = np.exp(-0.5 * (x - 2.0) ** 2).astype(np.complex128)
+    psi0 /= np.linalg.norm(psi0)
+    Emin, Emax = 0.0, np.pi ** 2 / (2 * dx * dx) + 0.5 * op.L ** 2
+    c, R = 0.5 * (Emax + Emin), 0.5 * (Emax - Emin)
+    nsteps = 40
+    dt = np.pi / nsteps
+    nterms = O.cheb_terms(R * dt, 1e-14)
+    psi = psi0.copy()
+    for _ in range(nsteps):
+        psi = O.cheb_step_dense(H, psi, dt, c, R, nterms)
+    assert np.max(np.abs(psi - (-1j) * psi0[::-1])) < 1e-9
+    for _ in range(nsteps):
+        psi = O.cheb_step_dense(H, psi, dt, c, R, nterms)
+    assert np.max(np.abs(psi + psi0)) < 1e-9
