@@ -1,0 +1,358 @@
+#!/usr/bin/env python3
+"""Benchmark of the matrix-free H*psi hot path on the sinc-DVR workload.
+
+Workload: the Colbert-Miller sinc-DVR harmonic oscillator on D = 131072 grid
+points (L = 0.9 sqrt(2D)), one vector (a Gaussian wavepacket at x = 2),
+FP32 entry generation with FP64 Chebyshev recurrence.  One step = one
+64-term Chebyshev step of exp(-i tau H) (63 matrix-free H*psi applies plus
+the FP64 recurrence/accumulation), tau the longest sub-step that 64 terms
+resolve at coefficient tolerance 1e-7.  The dense operator would need
+275 GB in complex128; it is never stored.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mf|reference]
+
+Under torchrun (N > 1) every rank propagates an independent wavepacket
+(parameter-parallel tasks, no collective on the data path) and the job value
+is the sum of work over the max time across ranks.  ``--impl reference``
+times the CPU oracle on bounded row samples of the same product.
+"""
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "H psi matrix entries applied/s and Chebyshev steps/s at stated error vs FP64 form"
+D = 131072
+TERMS = 64
+TOL = 1e-7
+DT_CONFIG = 0.1  # the workload's nominal dt; tau sub-steps cover it
+WORKLOAD = "sinc-DVR harmonic oscillator D=131072, 1 vector, 64-term Chebyshev steps"
+
+
+def env_rank():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+# ------------------------------------------------------------------ clocks ---
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        try:
+            rows = [l.split(",") for l in open(self.path).read().strip().splitlines() if l.strip()]
+            os.unlink(self.path)
+        except Exception:
+            return out
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [c.strip() for c in r]
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if sm:
+            busy = [s for s in sm if s > 0.5 * max(sm)] or sm
+            out = {"sm_mhz": float(np.median(busy)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                   "samples": len(sm)}
+        return out
+
+
+# -------------------------------------------------------------- roofline ---
+def traffic_from_profile():
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, valid only while the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "dvr_window_f32_D131072.md")
+    src = os.path.join(ROOT, "paper_2606_31598_gb300", "csrc", "k_apply.cu")
+    try:
+        txt = open(path).read()
+        want = re.search(r"source_sha256:\s*([0-9a-f]{64})", txt).group(1)
+        traffic = float(re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt).group(1))
+    except Exception:
+        return None
+    have = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    return traffic if have == want else None
+
+
+# ------------------------------------------------------------ CPU oracle ---
+def cpu_oracle_sample(target_s=10.0, max_rows=None):
+    """Oracle FP64 product on evenly spaced output rows; returns entries/s."""
+    from oracle import oracle as O
+    import workloads as W
+    op = O.make_op(O.GEN_SINC_DVR_HO, D)
+    x = W.wavepacket(D)
+    rows = np.linspace(0, D - 1, 256).astype(np.int64)
+    t0 = time.perf_counter()
+    O.apply_rows(op, x, rows)
+    t = time.perf_counter() - t0
+    n = int(min(max_rows or D, max(256, 256 * target_s / max(t, 1e-6))))
+    rows = np.linspace(0, D - 1, n).astype(np.int64)
+    t0 = time.perf_counter()
+    O.apply_rows(op, x, rows)
+    t = time.perf_counter() - t0
+    return n * D / t, n, t
+
+
+def cpu_threads():
+    try:
+        from oracle import oracle as O  # noqa: F401
+        import ctypes
+        gomp = ctypes.CDLL("libgomp.so.1")
+        gomp.omp_get_max_threads.restype = ctypes.c_int
+        return int(gomp.omp_get_max_threads())
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args):
+    rank, _, world = env_rank()
+    if rank != 0:
+        return 0
+    per_step_s = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        cpu_oracle_sample(target_s=min(per_step_s, 5.0))
+    vals, times, nrows = [], [], 0
+    for _ in range(args.steps):
+        v, nrows, t = cpu_oracle_sample(target_s=per_step_s)
+        vals.append(v)
+        times.append(t)
+    value = float(np.sum([n for n in [nrows * D] * len(times)]) / np.sum(times))
+    cores = cpu_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "entries/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "D": D, "nvec": 1},
+        "cpu_baseline": {"value": value, "unit": "entries/s", "cores": cores, "kind": "oracle",
+                         "sample": "%d of %d output rows of one FP64 H psi per step" % (nrows, D)},
+        "e2e": {"value": value, "unit": "entries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------- GPU ---
+def substep_tau(plan):
+    """Longest tau whose expansion needs at most TERMS terms at TOL."""
+    lo, hi = 1e-7, 1e-2
+    for _ in range(50):
+        mid = np.sqrt(lo * hi)
+        if plan.cheb_terms(mid) <= TERMS:
+            lo = mid
+        else:
+            hi = mid
+    return lo
+
+
+def coherent_state(x, x0, t):
+    """Exact unit harmonic oscillator coherent state at time t (psi(x, 0) a
+    Gaussian of unit width at x0, zero momentum)."""
+    return (np.pi ** -0.25 * np.exp(-0.5j * t) * np.exp(-0.5 * (x - x0 * np.cos(t)) ** 2 - 1j * x0 * np.sin(t) * x
+                                                       + 0.25j * x0 * x0 * np.sin(2 * t)))
+
+
+def run_mf(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2606_31598_gb300 as mf
+    import workloads as W
+
+    rank, local, world = env_rank()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream().cuda_stream
+    props = torch.cuda.get_device_properties(dev)
+    x0 = 2.0 + 0.25 * rank  # independent task per rank
+
+    plan = mf.Plan(D, mf.MF_GEN_SINC_DVR_HO, precision=mf.MF_PREC_FP32, stream=stream)
+    desc = plan.describe()
+    emin, emax = plan.bounds()
+    tau = substep_tau(plan)
+    nterms = plan.cheb_terms(tau)
+    assert nterms <= TERMS
+    psi0 = W.wavepacket(D, x0=x0)
+    psi = torch.from_numpy(psi0).to(dev)
+    applies = TERMS - 1
+    entries_per_step = applies * float(D) * float(D)
+
+    for _ in range(args.warmup):
+        plan.cheb_propagate(psi, 1, tau, TERMS)
+    torch.cuda.synchronize()
+
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > 129 MB L2
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stops = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clock = ClockSampler(local)
+    psi.copy_(torch.from_numpy(psi0).to(dev))
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clock.start()
+    plan.profile(True)
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        starts[k].record()
+        plan.cheb_propagate(psi, 1, tau, TERMS)
+        stops[k].record()
+    torch.cuda.synchronize()
+    kern_ms, kern_n = plan.profile_read()
+    plan.profile(False)
+    if world > 1:
+        dist.barrier()
+    clocks = clock.stop()
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, stops)]
+    t_local = sum(step_ms) / 1e3
+    t = torch.tensor([t_local], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    t_job = float(t.item())
+    value = world * args.steps * entries_per_step / t_job
+    psi_timed = psi.cpu().numpy()
+
+    # end to end through the public call: pinned host psi in, result out
+    host_in = torch.from_numpy(psi0.copy()).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    e_a = torch.cuda.Event(enable_timing=True)
+    e_b = torch.cuda.Event(enable_timing=True)
+    dpsi = torch.empty_like(psi)
+    torch.cuda.synchronize()
+    e_a.record()
+    for k in range(args.steps):
+        dpsi.copy_(host_in, non_blocking=True)
+        plan.cheb_propagate(dpsi, 1, tau, TERMS)
+        host_out.copy_(dpsi, non_blocking=True)
+        host_in, host_out = host_out, host_in
+    e_b.record()
+    torch.cuda.synchronize()
+    t_e2e = torch.tensor([e_a.elapsed_time(e_b) / 1e3], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_e2e, op=dist.ReduceOp.MAX)
+    e2e_value = world * args.steps * entries_per_step / float(t_e2e.item())
+
+    # stated error: one step of the FP32 form vs the FP64 form and vs the
+    # closed-form coherent state
+    err = {}
+    if rank == 0:
+        plan64 = mf.Plan(D, mf.MF_GEN_SINC_DVR_HO, precision=mf.MF_PREC_FP64, stream=stream)
+        plan64.set_bounds(emin, emax)
+        a = torch.from_numpy(psi0).to(dev)
+        b = torch.from_numpy(psi0).to(dev)
+        plan.cheb_propagate(a, 1, tau, TERMS)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        plan64.cheb_propagate(b, 1, tau, TERMS)
+        ev1.record()
+        torch.cuda.synchronize()
+        fp64_step_s = ev0.elapsed_time(ev1) / 1e3
+        a, b = a.cpu().numpy(), b.cpu().numpy()
+        L = W.dvr_default_L(D)
+        xg = -L + (2 * L / (D - 1)) * np.arange(D)
+        exact = coherent_state(xg, x0, tau)
+        exact = exact / np.linalg.norm(exact)
+        err = {"fp32_vs_fp64_form": float(np.linalg.norm(a - b)), "fp32_vs_closed_form": float(np.linalg.norm(a - exact)),
+               "fp64_vs_closed_form": float(np.linalg.norm(b - exact)),
+               "norm_drift_after_timed_steps": float(abs(np.linalg.norm(psi_timed) - 1.0)),
+               "measure": "2-norm of the state difference after one step (unit-norm states)"}
+        fp64_entries_per_s = entries_per_step / fp64_step_s
+        plan64.close()
+
+    if rank == 0:
+        sm_mhz = clocks.get("sm_mhz") or 0.0
+        nsm = props.multi_processor_count
+        peak = nsm * 128 * 2 * sm_mhz * 1e6 / 1e12 if sm_mhz else None  # TFLOP/s FP32 FMA pipe
+        per_launch_s = kern_ms / 1e3 / max(kern_n, 1)
+        achieved = 4.0 * D * D / per_launch_s / 1e12
+        traffic = traffic_from_profile()
+        line = {
+            "metric": METRIC, "value": value, "unit": "entries/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_job * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "D": D, "nvec": 1, "terms_per_step": TERMS, "applies_per_step": applies,
+                       "tau": tau, "substeps_per_dt_0.1": int(np.ceil(DT_CONFIG / tau)),
+                       "precision": "fp32 entries and tile sums, fp64 recurrence", "storage": desc["storage"],
+                       "path": desc["path"], "launch": [desc["dvr_rows"], desc["dvr_cols"]],
+                       "l2": "flushed between timed steps (256 MiB write, outside the step events)",
+                       "bounds": [emin, emax]},
+            "cheb_terms_per_s": world * args.steps * applies / t_job,
+            "cheb_steps_per_s": world * args.steps / t_job,
+            "dt_steps_per_s": world * args.steps / t_job / np.ceil(DT_CONFIG / tau),
+            "fp64_form_entries_per_s": fp64_entries_per_s,
+            "error": err,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": (achieved / peak) if peak else None, "traffic": traffic,
+                         "kernel": "dvr_window<float,16>", "flop_per_launch": 4.0 * D * D,
+                         "peak_basis": "%d SMs x 128 FP32 lanes x 2 FLOP x median sampled SM clock" % nsm,
+                         "kernel_ms": per_launch_s * 1e3, "kernel_launches_timed": kern_n},
+            "e2e": {"value": e2e_value, "unit": "entries/s", "h2d_bytes_per_step": D * 16, "d2h_bytes_per_step": D * 16},
+            "gpu_launches": args.steps * (2 + 2 * applies),
+            "clocks": clocks,
+        }
+        cb_value, cb_rows, cb_t = cpu_oracle_sample(target_s=10.0)
+        line["cpu_baseline"] = {"value": cb_value, "unit": "entries/s", "cores": cpu_threads(), "kind": "oracle",
+                                "sample": "%d of %d output rows of one FP64 H psi (%.1f s)" % (cb_rows, D, cb_t)}
+        print(json.dumps(line))
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mf", choices=["mf", "reference"])
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_mf(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

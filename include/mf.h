@@ -1,0 +1,208 @@
+/*
+ * mf.h -- C ABI of the GB300 matrix-free block-procedural operator library.
+ *
+ * The library applies a dense Hermitian operator H (D x D, complex) to one or
+ * more vectors without materialising H: every block H^[n,m] is generated on
+ * demand inside the apply kernel, or read from an HBM block cache that holds
+ * none, some or all canonical block pairs (n <= m) under a memory budget.
+ * A centred Chebyshev expansion of exp(-i dt H) is built on the product.
+ *
+ * Paper: U. Shafir, R. Kosloff, "Memory-Scalable and Hardware-Adaptive
+ * Matrix-Free Quantum Simulation".  Section/equation numbers below refer to it.
+ *
+ * Conventions shared by every call
+ *  - Vectors are complex128 (interleaved re, im doubles), row-major [D][nvec]
+ *    with the vector index fastest (the Y = A X layout of Sec. IV.A,
+ *    Eq. generic_multivector).  Pointers passed to mf_apply/mf_cheb_propagate
+ *    are DEVICE pointers owned by the caller; the library never frees them.
+ *  - The plan owns its cache, workspace and CUDA resources; mf_plan_destroy
+ *    releases them.  Work is enqueued on the plan's stream (mf_options.stream,
+ *    NULL = the legacy default stream) and is asynchronous unless stated.
+ *  - Every call returns an mf_status.  Argument errors are detected on the host
+ *    before anything is enqueued and leave the plan unchanged.  CUDA launch
+ *    errors are returned as MF_ERR_CUDA by the call that hit them; kernel-side
+ *    failures (device error word) are returned by the next mf_sync.
+ *  - Hermitian generators require M == D.  y must not alias x.
+ */
+#ifndef MF_H
+#define MF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mf_plan* mf_plan_t;
+
+typedef enum {
+  MF_OK = 0,
+  MF_ERR_INVALID = 1,      /* bad argument; nothing enqueued */
+  MF_ERR_OOM = 2,          /* device allocation failed or plan exceeds memory */
+  MF_ERR_CUDA = 3,         /* a CUDA runtime call or launch failed */
+  MF_ERR_UNSUPPORTED = 4,  /* valid request this build does not implement */
+  MF_ERR_TIMEOUT = 5,      /* a bounded device wait ran out */
+  MF_WARN_DENSE_WORK = 6   /* plan created, but W_Hpsi exceeds the limit (Sec. IV.H) */
+} mf_status;
+
+/* Block sources (Sec. III.A).  PHILOX_GUE is "seeded generation": entry
+ * (r, c), r <= c, from Philox4x32-10 with counter (r, c/2, 0, 0) and key
+ * (seed lo, seed hi), words mapped by Box-Muller to a complex Gaussian of
+ * variance 1/(2D) per part, real diagonal, H_cr = conj(H_rc) (global indices:
+ * partition invariant, Sec. II).  SINC_DVR_HO is "analytic generation": the
+ * Colbert-Miller sinc-DVR kinetic energy on x_i = -L + i*2L/(D-1) plus
+ * V = x^2/2 (hbar = m = omega = 1). */
+typedef enum { MF_GEN_PHILOX_GUE = 0, MF_GEN_SINC_DVR_HO = 1 } mf_generator;
+
+/* Entry precision forms.  FP64: entries, products and sums in double.
+ * FP32: entries generated in single precision by the FP32 steps of the
+ * generator, FP32 products and FP32 tile sums, FP64 cross-tile sums.
+ * BF16X2: FP32 entries split hi = bf16(h), lo = bf16(h - hi), products
+ * hi*xh + hi*xl + lo*xh on tensor cores with FP32 accumulation. */
+typedef enum { MF_PREC_FP64 = 0, MF_PREC_FP32 = 1, MF_PREC_BF16X2 = 2 } mf_precision;
+
+/* Storage modes (Sec. III.A, Sec. IV.E): AUTO lets the planner choose. */
+typedef enum {
+  MF_STORE_AUTO = -1,
+  MF_STORE_PROCEDURAL = 0,
+  MF_STORE_PARTIAL = 1,
+  MF_STORE_FULL = 2
+} mf_storage;
+
+/* Planner modes: Algorithm 1 (analytic), Algorithm 2 (measured autotune),
+ * Algorithm 3 (learned surrogate; hybrid = learned ranking + measurement). */
+typedef enum {
+  MF_PLANNER_ANALYTIC = 0,
+  MF_PLANNER_AUTOTUNE = 1,
+  MF_PLANNER_LEARNED = 2,
+  MF_PLANNER_HYBRID = 3
+} mf_planner_mode;
+
+typedef struct {
+  int32_t precision;       /* mf_precision, default MF_PREC_FP32 */
+  int32_t storage;         /* mf_storage, default MF_STORE_AUTO */
+  int32_t planner_mode;    /* mf_planner_mode, default MF_PLANNER_ANALYTIC */
+  int32_t nvec_hint;       /* R the plan is tuned for (default 1) */
+  double cheb_tol;         /* coefficient tolerance for the Chebyshev order (1e-7) */
+  int32_t lanczos_m;       /* Lanczos steps for spectral bounds (40) */
+  double bounds_pad;       /* relative padding of the Lanczos half-width (0.05) */
+  double dvr_L;            /* DVR half-width L; 0 selects 0.9*sqrt(2D) */
+  void* stream;            /* cudaStream_t for all work; NULL = default stream */
+  double alpha_safety;     /* alpha of Eq. planner_memory_constraint (0.9) */
+  double f_cache;          /* f_cache of Sec. IV.G used when budget == SIZE_MAX (0.8) */
+  int32_t autotune_k;      /* K_bench candidates measured by Algorithm 2 (8) */
+  int32_t autotune_warmup; /* R_warm (1) */
+  int32_t autotune_repeats;/* R_bench (3) */
+  double dense_work_limit; /* W_Hpsi threshold in entries for MF_WARN_DENSE_WORK (1e13) */
+  int32_t device;          /* CUDA device ordinal (0) */
+} mf_options;
+
+/* Fill *o with the defaults listed above.  Never fails. */
+void mf_options_default(mf_options* o);
+
+/* Human-readable name of a status code (static storage, never NULL). */
+const char* mf_status_string(mf_status s);
+
+/*
+ * mf_plan_create -- build an execution plan for y = A x (Sec. I, Eq. 1) with
+ * A = H of the given generator (Sec. IV: block size b, storage mode, cache
+ * budget, pairs cached, launch shape, precision).
+ *   out      : receives the plan handle (owned by the library).
+ *   D, M     : operator shape; M == D for both Hermitian generators.
+ *   generator: mf_generator.
+ *   seed     : Philox key (ignored by the DVR generator).
+ *   block    : block size b of the partition D = sum b_n (Sec. II); 0 lets the
+ *              planner choose (Sec. IV.F).  Must be a multiple of 128 when given.
+ *   cache_budget_bytes : bytes the block cache may use (Eq. partial_cache_pairs);
+ *              0 = procedural only, SIZE_MAX = f_cache * free memory.
+ *   opt      : options, NULL = defaults.
+ * Allocates the cache and workspace and fills the cache (Sec. III.A "full/
+ * partial caching") on opt->stream before returning.  Errors: MF_ERR_INVALID
+ * (D < 2, M != D, bad generator/precision/block), MF_ERR_OOM, MF_ERR_CUDA,
+ * MF_ERR_UNSUPPORTED.  MF_WARN_DENSE_WORK still returns a usable plan.
+ */
+mf_status mf_plan_create(mf_plan_t* out, int64_t D, int64_t M, int32_t generator, uint64_t seed,
+                         int64_t block, size_t cache_budget_bytes, const mf_options* opt);
+
+/* Release everything the plan owns (synchronises its stream).  NULL is a no-op. */
+mf_status mf_plan_destroy(mf_plan_t p);
+
+/*
+ * mf_apply -- y = H x for nvec simultaneous vectors (Eq. blockmatvec and
+ * Eq. blockmatvecindex: phi^[n] = sum_m H^[n,m] psi^[m], every block pair
+ * included, each canonical pair generated or read once and applied as both
+ * H^[n,m] and H^[m,n] = (H^[n,m])^dagger).
+ *   y, x : device pointers to complex128 [D][nvec]; y must not overlap x.
+ *   nvec : number of vectors, 1 <= nvec <= 64.
+ * Asynchronous on the plan's stream.  Errors: MF_ERR_INVALID, MF_ERR_CUDA.
+ */
+mf_status mf_apply(mf_plan_t p, void* y, const void* x, int64_t nvec);
+
+/*
+ * mf_cheb_propagate -- psi <- exp(-i dt H) psi by the centred Chebyshev
+ * recurrence of Sec. VII (H~ = (H - c)/R, q_{l+1} = 2 H~ q_l - q_{l-1}) with
+ * coefficients a_0 = J_0(R dt), a_k = 2 (-i)^k J_k(R dt) computed on the GPU
+ * in FP64; recurrence and accumulation in FP64.
+ *   psi   : device complex128 [D][nvec], updated in place.
+ *   dt    : time step (may be negative).
+ *   order : number of terms k = 0..order-1; 0 = smallest count meeting
+ *           opt.cheb_tol (|a_k| < tol for every k >= order).
+ * Spectral bounds come from mf_plan_set_bounds, else are computed on first
+ * use (Lanczos for PHILOX_GUE, the analytic Toeplitz-symbol bound for the DVR).
+ * Errors: MF_ERR_INVALID, MF_ERR_CUDA.
+ */
+mf_status mf_cheb_propagate(mf_plan_t p, void* psi, int64_t nvec, double dt, int32_t order);
+
+/* Number of Chebyshev terms mf_cheb_propagate would use for dt at the plan's
+ * tolerance (computes bounds and coefficients if needed; synchronises). */
+mf_status mf_cheb_terms(mf_plan_t p, double dt, int32_t* nterms);
+
+/*
+ * mf_spectral_bounds -- E_min, E_max used by the Chebyshev scaling (Sec. VII):
+ * Lanczos with opt.lanczos_m steps on the GPU (Ritz extremes padded by
+ * opt.bounds_pad of the half-width) for PHILOX_GUE; [min V, pi^2/(2 dx^2) +
+ * max V] for the DVR.  Synchronises.  Results are cached in the plan.
+ */
+mf_status mf_spectral_bounds(mf_plan_t p, double* emin, double* emax);
+/* Override the bounds used by mf_cheb_propagate (emax > emin). */
+mf_status mf_plan_set_bounds(mf_plan_t p, double emin, double emax);
+
+/*
+ * mf_plan_profile -- enable (1) or disable (0) timing of every launch of the
+ * plan's generate-and-apply kernel with a CUDA event pair recorded on the
+ * plan's stream around it (the measured-time primitive of Sec. IV.B,
+ * Eq. measured_matvec_time).  Resets the counters.  Events are created on
+ * demand and owned by the plan.
+ */
+mf_status mf_plan_profile(mf_plan_t p, int32_t enable);
+/* Synchronise the plan's stream, return the summed event time (ms) and count
+ * of the apply-kernel launches timed since the last read, and reset them. */
+mf_status mf_plan_profile_read(mf_plan_t p, double* total_ms, int64_t* launches);
+
+/* Wait for the plan's stream and report any device-side error word. */
+mf_status mf_sync(mf_plan_t p);
+
+/*
+ * mf_plan_describe -- the plan record of Sec. IV (block count and size,
+ * storage mode, cache budget and pairs cached, launch shape, precision,
+ * safety estimate) as a NUL-terminated JSON object in buf[0..len).
+ * MF_ERR_INVALID if buf is NULL or too small (the record is truncated).
+ */
+mf_status mf_plan_describe(mf_plan_t p, char* buf, size_t len);
+
+/*
+ * mf_debug_entries -- copy the generator's entries H[r0:r0+rows, c0:c0+cols]
+ * as produced on the GPU in the plan's precision form to HOST memory out:
+ * complex64 (FP32 and BF16X2 plans, the FP32 entry before splitting) or
+ * complex128 (FP64 plans), row-major.  DVR entries exclude the potential.
+ * Any (r, c) in [0, D) is allowed (entries below the diagonal are the
+ * conjugates).  Synchronises.  Used for the bit-exact entry parity.
+ */
+mf_status mf_debug_entries(mf_plan_t p, int64_t r0, int64_t c0, int64_t rows, int64_t cols,
+                           void* out_host);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MF_H */

@@ -262,6 +262,10 @@ double or_dvr_potential(const or_op* op, int64_t i) {
   return 0.5 * (x * x);
 }
 
+double or_dvr_kinetic(const or_op* op, int64_t k) {
+  return op->form == OR_FORM_FP64 ? dvr_T64(op, k) : (double)dvr_T32(op, k);
+}
+
 void or_entry_f32(const or_op* op, int64_t r, int64_t c, float* re, float* im) {
   if (op->gen == OR_GEN_PHILOX_GUE) {
     gue_entry32(op->seed, op->D, r, c, re, im);

@@ -44,6 +44,8 @@ void or_sincos_2pif(float u, float* s, float* c);
 void or_entry(const or_op* op, int64_t r, int64_t c, double* re, double* im);
 /* Form-native entries: the FP32 form returned without widening. */
 void or_entry_f32(const or_op* op, int64_t r, int64_t c, float* re, float* im);
+/* DVR: kinetic entry T(k), k = r - c, in the op's form (widened to double). */
+double or_dvr_kinetic(const or_op* op, int64_t k);
 /* DVR: the diagonal potential V_i = x_i^2/2 (always FP64). */
 double or_dvr_potential(const or_op* op, int64_t i);
 

@@ -48,6 +48,7 @@ def lib():
         L.or_sincos_2pif.argtypes = [ctypes.c_float, P(ctypes.c_float), P(ctypes.c_float)]
         L.or_entry.argtypes = [P(OrOp), i64, i64, P(d), P(d)]
         L.or_dvr_potential.argtypes = [P(OrOp), i64]; L.or_dvr_potential.restype = d
+        L.or_dvr_kinetic.argtypes = [P(OrOp), i64]; L.or_dvr_kinetic.restype = d
         L.or_window.argtypes = [P(OrOp), i64, i64, i64, i64, vp]
         L.or_window_f32.argtypes = [P(OrOp), i64, i64, i64, i64, vp]
         L.or_apply.argtypes = [P(OrOp), i64, i64, vp, vp, ctypes.c_int]
@@ -102,6 +103,17 @@ def entry(op, r, c):
     re, im = ctypes.c_double(), ctypes.c_double()
     lib().or_entry(ctypes.byref(op), int(r), int(c), ctypes.byref(re), ctypes.byref(im))
     return complex(re.value, im.value)
+
+
+def kinetic(op, k):
+    """DVR kinetic entry T(k), k = r - c, in op's form (as a double)."""
+    return lib().or_dvr_kinetic(ctypes.byref(op), int(k))
+
+
+def kinetic_window(op, r0, c0, rows, cols):
+    ks = (r0 + np.arange(rows))[:, None] - (c0 + np.arange(cols))[None, :]
+    table = {int(k): kinetic(op, int(k)) for k in np.unique(ks)}
+    return np.vectorize(lambda k: table[int(k)])(ks).astype(np.float64)
 
 
 def potential(op, i):

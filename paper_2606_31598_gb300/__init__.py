@@ -1,0 +1,257 @@
+"""Python binding of libmf, the GB300 matrix-free block-procedural operator library.
+
+Argument marshalling only: every function forwards to the C ABI of
+``include/mf.h`` under the same name; every step of the computation runs in
+the library's CUDA kernels.  Tensors are passed by device pointer; PyTorch is
+used only for device memory and streams.  There is no fallback: if
+``libmf.so`` has not been built (``python -c "import __graft_entry__ as g;
+g.build()"``) every call raises.
+"""
+import ctypes
+import json
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmf.so")
+
+MF_OK = 0
+MF_ERR_INVALID = 1
+MF_ERR_OOM = 2
+MF_ERR_CUDA = 3
+MF_ERR_UNSUPPORTED = 4
+MF_ERR_TIMEOUT = 5
+MF_WARN_DENSE_WORK = 6
+
+MF_GEN_PHILOX_GUE = 0
+MF_GEN_SINC_DVR_HO = 1
+MF_PREC_FP64 = 0
+MF_PREC_FP32 = 1
+MF_PREC_BF16X2 = 2
+MF_STORE_AUTO = -1
+MF_STORE_PROCEDURAL = 0
+MF_STORE_PARTIAL = 1
+MF_STORE_FULL = 2
+MF_PLANNER_ANALYTIC = 0
+MF_PLANNER_AUTOTUNE = 1
+MF_PLANNER_LEARNED = 2
+MF_PLANNER_HYBRID = 3
+SIZE_MAX = (1 << 64) - 1
+
+
+class MFError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        super().__init__("%s%s" % (status_string(status), (": " + what) if what else ""))
+
+
+class mf_options(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int32),
+        ("storage", ctypes.c_int32),
+        ("planner_mode", ctypes.c_int32),
+        ("nvec_hint", ctypes.c_int32),
+        ("cheb_tol", ctypes.c_double),
+        ("lanczos_m", ctypes.c_int32),
+        ("bounds_pad", ctypes.c_double),
+        ("dvr_L", ctypes.c_double),
+        ("stream", ctypes.c_void_p),
+        ("alpha_safety", ctypes.c_double),
+        ("f_cache", ctypes.c_double),
+        ("autotune_k", ctypes.c_int32),
+        ("autotune_warmup", ctypes.c_int32),
+        ("autotune_repeats", ctypes.c_int32),
+        ("dense_work_limit", ctypes.c_double),
+        ("device", ctypes.c_int32),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    """Load libmf.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libmf.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, u64, d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+        P = ctypes.POINTER
+        L.mf_options_default.argtypes = [P(mf_options)]
+        L.mf_options_default.restype = None
+        L.mf_status_string.argtypes = [ctypes.c_int]
+        L.mf_status_string.restype = ctypes.c_char_p
+        L.mf_plan_create.argtypes = [P(vp), i64, i64, i32, u64, i64, ctypes.c_size_t, P(mf_options)]
+        L.mf_plan_destroy.argtypes = [vp]
+        L.mf_apply.argtypes = [vp, vp, vp, i64]
+        L.mf_cheb_propagate.argtypes = [vp, vp, i64, d, i32]
+        L.mf_cheb_terms.argtypes = [vp, d, P(i32)]
+        L.mf_spectral_bounds.argtypes = [vp, P(d), P(d)]
+        L.mf_plan_set_bounds.argtypes = [vp, d, d]
+        L.mf_sync.argtypes = [vp]
+        L.mf_plan_describe.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
+        L.mf_debug_entries.argtypes = [vp, i64, i64, i64, i64, vp]
+        L.mf_plan_profile.argtypes = [vp, i32]
+        L.mf_plan_profile_read.argtypes = [vp, P(d), P(i64)]
+        for name in ("mf_plan_create", "mf_plan_destroy", "mf_apply", "mf_cheb_propagate", "mf_cheb_terms",
+                     "mf_spectral_bounds", "mf_plan_set_bounds", "mf_sync", "mf_plan_describe",
+                     "mf_debug_entries", "mf_plan_profile", "mf_plan_profile_read"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def status_string(s):
+    try:
+        return lib().mf_status_string(int(s)).decode()
+    except Exception:  # library missing: still format the code
+        return "mf_status(%d)" % int(s)
+
+
+def _check(st, what=""):
+    if st not in (MF_OK, MF_WARN_DENSE_WORK):
+        raise MFError(st, what)
+    return st
+
+
+def _ptr(t):
+    """Device pointer of a torch tensor, or an int address."""
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def mf_options_default(**overrides):
+    o = mf_options()
+    lib().mf_options_default(ctypes.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def current_stream():
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def mf_plan_create(D, M, generator, seed, block=0, cache_budget_bytes=0, options=None):
+    h = ctypes.c_void_p()
+    opt = options if options is not None else mf_options_default(stream=current_stream())
+    st = lib().mf_plan_create(ctypes.byref(h), int(D), int(M), int(generator), int(seed) & (2 ** 64 - 1),
+                              int(block), int(cache_budget_bytes), ctypes.byref(opt))
+    _check(st, "mf_plan_create")
+    return h
+
+
+def mf_plan_destroy(plan):
+    return _check(lib().mf_plan_destroy(plan), "mf_plan_destroy")
+
+
+def mf_apply(plan, y, x, nvec=1):
+    return _check(lib().mf_apply(plan, _ptr(y), _ptr(x), int(nvec)), "mf_apply")
+
+
+def mf_cheb_propagate(plan, psi, nvec, dt, order=0):
+    return _check(lib().mf_cheb_propagate(plan, _ptr(psi), int(nvec), float(dt), int(order)),
+                  "mf_cheb_propagate")
+
+
+def mf_cheb_terms(plan, dt):
+    n = ctypes.c_int32()
+    _check(lib().mf_cheb_terms(plan, float(dt), ctypes.byref(n)), "mf_cheb_terms")
+    return n.value
+
+
+def mf_spectral_bounds(plan):
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    _check(lib().mf_spectral_bounds(plan, ctypes.byref(lo), ctypes.byref(hi)), "mf_spectral_bounds")
+    return lo.value, hi.value
+
+
+def mf_plan_set_bounds(plan, emin, emax):
+    return _check(lib().mf_plan_set_bounds(plan, float(emin), float(emax)), "mf_plan_set_bounds")
+
+
+def mf_sync(plan):
+    return _check(lib().mf_sync(plan), "mf_sync")
+
+
+def mf_plan_describe(plan):
+    buf = ctypes.create_string_buffer(4096)
+    _check(lib().mf_plan_describe(plan, buf, len(buf)), "mf_plan_describe")
+    return json.loads(buf.value.decode())
+
+
+def mf_debug_entries(plan, r0, c0, rows, cols, out_host):
+    """out_host: a contiguous numpy array (complex64 or complex128 per plan)."""
+    return _check(lib().mf_debug_entries(plan, int(r0), int(c0), int(rows), int(cols),
+                                         out_host.ctypes.data), "mf_debug_entries")
+
+
+def mf_plan_profile(plan, enable):
+    return _check(lib().mf_plan_profile(plan, int(enable)), "mf_plan_profile")
+
+
+def mf_plan_profile_read(plan):
+    ms, n = ctypes.c_double(), ctypes.c_int64()
+    _check(lib().mf_plan_profile_read(plan, ctypes.byref(ms), ctypes.byref(n)), "mf_plan_profile_read")
+    return ms.value, n.value
+
+
+class Plan:
+    """Owning handle with the calls as methods (destroyed on close/GC)."""
+
+    def __init__(self, D, generator, seed=1, block=0, cache_budget_bytes=0, M=None, **opts):
+        o = mf_options_default()
+        if "stream" not in opts:
+            opts["stream"] = current_stream()
+        for k, v in opts.items():
+            setattr(o, k, v)
+        self.options = o
+        self.D = int(D)
+        self.handle = mf_plan_create(D, D if M is None else M, generator, seed, block, cache_budget_bytes, o)
+
+    def apply(self, y, x, nvec=1):
+        return mf_apply(self.handle, y, x, nvec)
+
+    def cheb_propagate(self, psi, nvec, dt, order=0):
+        return mf_cheb_propagate(self.handle, psi, nvec, dt, order)
+
+    def cheb_terms(self, dt):
+        return mf_cheb_terms(self.handle, dt)
+
+    def bounds(self):
+        return mf_spectral_bounds(self.handle)
+
+    def set_bounds(self, emin, emax):
+        return mf_plan_set_bounds(self.handle, emin, emax)
+
+    def describe(self):
+        return mf_plan_describe(self.handle)
+
+    def entries(self, r0, c0, rows, cols):
+        import numpy as np
+        dt = np.complex128 if self.options.precision == MF_PREC_FP64 else np.complex64
+        out = np.zeros((rows, cols), dtype=dt)
+        mf_debug_entries(self.handle, r0, c0, rows, cols, out)
+        return out
+
+    def sync(self):
+        return mf_sync(self.handle)
+
+    def profile(self, enable=True):
+        return mf_plan_profile(self.handle, enable)
+
+    def profile_read(self):
+        return mf_plan_profile_read(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            mf_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

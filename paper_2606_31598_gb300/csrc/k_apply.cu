@@ -1,0 +1,322 @@
+// k_apply.cu -- fused generate-and-apply kernels (SIMT).
+//
+// (1) Hermitian canonical-tile kernel (Sec. III.A "partial caching" and
+//     Eq. blockmatvec): each CTA owns one canonical kTile x kTile tile
+//     (ti <= tj).  Every canonical entry h_rc (r <= c) is generated in
+//     registers from the Philox ensemble -- or read from the HBM block cache
+//     when its block pair is cached -- exactly once, and applied twice:
+//     y_r += h_rc x_c (block H^[n,m]) and y_c += conj(h_rc) x_r (block
+//     H^[m,n] = (H^[n,m])^dagger).  Row and column sums of the tile go to
+//     partial-sum slots that a fixed-order FP64 reduction combines.
+//
+// (2) DVR Toeplitz-window kernel (Sec. III.A "analytic generation"): the
+//     sinc-DVR kinetic block H^[n,m]_{ab} = T(r - c) depends on r - c only, so
+//     a CTA covering rows [R0, R0+RB) and columns [C0, C0+KC) generates the
+//     RB + KC - 1 distinct entries of its tile once into shared memory and
+//     contracts the whole RB x KC tile from that window: the dense O(RB*KC)
+//     product runs on the FMA pipe with register-blocked 16 x 16 sub-tiles.
+#include <cuda_runtime.h>
+
+#include "mf_internal.h"
+
+namespace mf {
+
+template <typename T> __device__ __forceinline__ typename cplx<T>::t czero();
+template <> __device__ __forceinline__ float2 czero<float>() { return make_float2(0.f, 0.f); }
+template <> __device__ __forceinline__ double2 czero<double>() { return make_double2(0.0, 0.0); }
+
+// acc += h * x
+template <typename C> __device__ __forceinline__ void cmac(C& acc, const C& h, const C& x) {
+  acc.x = fma(h.x, x.x, acc.x);
+  acc.x = fma(-h.y, x.y, acc.x);
+  acc.y = fma(h.x, x.y, acc.y);
+  acc.y = fma(h.y, x.x, acc.y);
+}
+// acc += conj(h) * x
+template <typename C> __device__ __forceinline__ void cmacc(C& acc, const C& h, const C& x) {
+  acc.x = fma(h.x, x.x, acc.x);
+  acc.x = fma(h.y, x.y, acc.x);
+  acc.y = fma(h.x, x.y, acc.y);
+  acc.y = fma(-h.y, x.x, acc.y);
+}
+
+// ---------------------------------------------------------------------------
+// (1) Hermitian canonical-tile kernel, one vector.
+// Thread (ty, tx) of the 16 x 16 grid owns rows ti*128 + ty*8 + [0,8) and
+// columns tj*128 + tx*8 + [0,8): 32 Philox calls, 64 canonical entries.
+// ---------------------------------------------------------------------------
+template <typename T, int GEN>
+__global__ void __launch_bounds__(256) herm_tile_nv1(const WorkItem* __restrict__ work, int64_t D,
+                                                     int64_t dpad, uint64_t seed, T sigma, dvr_consts dk,
+                                                     const typename cplx<T>::t* __restrict__ xc,
+                                                     typename cplx<T>::t* __restrict__ part,
+                                                     const typename cplx<T>::t* __restrict__ cache,
+                                                     int64_t bstride) {
+  using C = typename cplx<T>::t;
+  __shared__ C xs_r[kTile], xs_c[kTile];
+  __shared__ C red[16][kTile + 1];
+
+  const WorkItem it = work[blockIdx.x];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int64_t rt0 = (int64_t)it.ti * kTile, ct0 = (int64_t)it.tj * kTile;
+  if (tid < kTile) {
+    const int64_t r = rt0 + tid;
+    xs_r[tid] = r < D ? xc[r] : czero<T>();
+  } else {
+    const int64_t c = ct0 + tid - kTile;
+    xs_c[tid - kTile] = c < D ? xc[c] : czero<T>();
+  }
+  __syncthreads();
+
+  // column accumulators and column-side x live in registers (indexed only by
+  // unrolled loop counters); the row accumulator is one value per row a,
+  // parked in shared memory when the row is done
+  C yc[8], xcv[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    yc[q] = czero<T>();
+    xcv[q] = xs_c[tx * 8 + q];
+  }
+  const bool diag = it.ti == it.tj;
+  const int64_t r0 = rt0 + ty * 8, c0 = ct0 + tx * 8;
+  const bool active = !(diag && ty > tx);
+
+  if (it.cache_off >= 0) {
+    // cached block pair: stream the canonical entries from HBM
+    const C* base = cache + it.cache_off + (int64_t)(ty * 8) * bstride + tx * 8;
+#pragma unroll 1
+    for (int a = 0; a < 8; ++a) {
+      C yra = czero<T>();
+      if (active) {
+        const C xa = xs_r[ty * 8 + a];
+        C h[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) h[q] = base[(int64_t)a * bstride + q];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int dr = (ty * 8 + a) - (tx * 8 + q);
+          if (!diag || dr < 0) {
+            cmac(yra, h[q], xcv[q]);
+            cmacc(yc[q], h[q], xa);
+          } else if (dr == 0) {
+            cmac(yra, h[q], xcv[q]);
+          }
+        }
+      }
+      red[tx][ty * 8 + a] = yra;
+    }
+  } else {
+#pragma unroll 1
+    for (int a = 0; a < 8; ++a) {
+      C yra = czero<T>();
+      const int64_t r = r0 + a;
+      if (active) {
+        const C xa = xs_r[ty * 8 + a];
+#pragma unroll
+        for (int pb = 0; pb < 4; ++pb) {
+          const int64_t c = c0 + 2 * pb;
+          if (diag && r > c + 1) continue;  // both entries below the diagonal
+          C h0, h1;
+          if (GEN == MF_GEN_PHILOX_GUE) {
+            gue_pair<T>(seed, sigma, (uint32_t)r, (uint32_t)(c >> 1), h0, h1);
+          } else {
+            h0.x = dvr_T(dk, (long long)(r - c), T());
+            h1.x = dvr_T(dk, (long long)(r - c - 1), T());
+            h0.y = T(0);
+            h1.y = T(0);
+          }
+          // entry (r, c)
+          if (r < c) {
+            cmac(yra, h0, xcv[2 * pb]);
+            cmacc(yc[2 * pb], h0, xa);
+          } else if (r == c) {
+            cmac(yra, h0, xcv[2 * pb]);
+          }
+          // entry (r, c+1)
+          if (r < c + 1) {
+            cmac(yra, h1, xcv[2 * pb + 1]);
+            cmacc(yc[2 * pb + 1], h1, xa);
+          } else if (r == c + 1) {
+            cmac(yra, h1, xcv[2 * pb + 1]);
+          }
+        }
+      }
+      red[tx][ty * 8 + a] = yra;
+    }
+  }
+
+  // row sums over the 16 column groups, then column sums over the 16 row groups
+  __syncthreads();
+  C rs = czero<T>();
+  if (tid < kTile) {
+#pragma unroll
+    for (int g = 0; g < 16; ++g) {
+      rs.x += red[g][tid].x;
+      rs.y += red[g][tid].y;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int a = 0; a < 8; ++a) red[ty][tx * 8 + a] = yc[a];
+  __syncthreads();
+  if (tid < kTile) {
+    C cs = czero<T>();
+#pragma unroll
+    for (int g = 0; g < 16; ++g) {
+      cs.x += red[g][tid].x;
+      cs.y += red[g][tid].y;
+    }
+    if (diag) {
+      rs.x += cs.x;
+      rs.y += cs.y;
+      part[(int64_t)it.ti * dpad + rt0 + tid] = rs;
+    } else {
+      part[(int64_t)it.tj * dpad + rt0 + tid] = rs;  // rows of tile ti, slot tj
+      part[(int64_t)it.ti * dpad + ct0 + tid] = cs;  // rows of tile tj, slot ti
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// (2) DVR Toeplitz-window kernel.  8 warps share the CTA's RB = 32*P rows and
+// split its KC columns; lane L owns rows R0 + P*L + [0,P).  For a block of U
+// columns the P x U sub-tile needs the P+U-1 window entries T(r - c), loaded
+// from shared memory once and reused from registers.  The window table is
+// stored with one pad slot per P entries so the lane-strided loads are free of
+// bank conflicts.
+// ---------------------------------------------------------------------------
+template <typename T, int P>
+__global__ void __launch_bounds__(256, 2) dvr_window(int64_t D, int64_t dpad, int kc, dvr_consts dk,
+                                                     const typename cplx<T>::t* __restrict__ xc,
+                                                     typename cplx<T>::t* __restrict__ part) {
+  using C = typename cplx<T>::t;
+  constexpr int U = P;
+  constexpr int RB = 32 * P;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int ntb = RB + kc - 1;
+  const int ntb_pad = ((ntb + ntb / P + 1) + 3) & ~3;
+  T* tb = reinterpret_cast<T*>(smem_raw);
+  C* xs = reinterpret_cast<C*>(tb + ntb_pad);
+
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int64_t R0 = (int64_t)blockIdx.x * RB;
+  const int64_t C0 = (int64_t)blockIdx.y * kc;
+  const long long kmin = (long long)(R0 - C0) - kc + 1;
+  for (int j = tid; j < ntb; j += 256) tb[j + j / P] = dvr_T(dk, kmin + j, T());
+  for (int c = tid; c < kc; c += 256) {
+    const int64_t g = C0 + c;
+    xs[c] = g < D ? xc[g] : czero<T>();
+  }
+  __syncthreads();
+
+  T acc_r[P], acc_i[P];
+#pragma unroll
+  for (int a = 0; a < P; ++a) {
+    acc_r[a] = T(0);
+    acc_i[a] = T(0);
+  }
+  const int kw = kc / 8;
+  const int cbeg = w * kw, cend = cbeg + kw;
+#pragma unroll 1
+  for (int cc0 = cbeg; cc0 < cend; cc0 += U) {
+    // window start jb is a multiple of P, so padded offsets are compile-time
+    const int jb = P * lane - cc0 + kc - 1 - (U - 1);
+    const T* wp = tb + jb + jb / P;
+    T win[P + U - 1];
+#pragma unroll
+    for (int m = 0; m < P + U - 1; ++m) win[m] = wp[m + m / P];
+    C xv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) xv[u] = xs[cc0 + u];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+#pragma unroll
+      for (int a = 0; a < P; ++a) {
+        const T t = win[a - u + U - 1];
+        acc_r[a] = fma(t, xv[u].x, acc_r[a]);
+        acc_i[a] = fma(t, xv[u].y, acc_i[a]);
+      }
+    }
+  }
+  __syncthreads();
+  // cross-warp sum in fixed warp order (reuses the x region)
+  C* red = xs;  // [8][RB]
+#pragma unroll
+  for (int a = 0; a < P; ++a) {
+    C v;
+    v.x = acc_r[a];
+    v.y = acc_i[a];
+    red[w * RB + P * lane + a] = v;
+  }
+  __syncthreads();
+  for (int r = tid; r < RB; r += 256) {
+    C s = red[r];
+#pragma unroll
+    for (int g = 1; g < 8; ++g) {
+      s.x += red[g * RB + r].x;
+      s.y += red[g * RB + r].y;
+    }
+    part[(int64_t)blockIdx.y * dpad + R0 + r] = s;
+  }
+}
+
+template <typename T, int P>
+static size_t dvr_smem_bytes(int kc) {
+  using C = typename cplx<T>::t;
+  const int RB = 32 * P;
+  const int ntb = RB + kc - 1;
+  const int ntb_pad = ((ntb + ntb / P + 1) + 3) & ~3;
+  const size_t xs = (size_t)kc * sizeof(C), red = (size_t)8 * RB * sizeof(C);
+  return (size_t)ntb_pad * sizeof(T) + (xs > red ? xs : red);
+}
+
+cudaError_t launch_dvr_apply(const Plan& p, const void* xc, void* part, int64_t nvec) {
+  if (nvec != 1) return cudaErrorNotSupported;
+  const int kc = p.dvr_cols;
+  const int64_t nslot = (p.D + kc - 1) / kc;
+  if (p.prec == MF_PREC_FP64) {
+    constexpr int P = 8;
+    const size_t sm = dvr_smem_bytes<double, P>(kc);
+    auto k = dvr_window<double, P>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    dim3 grid((unsigned)((p.D + 32 * P - 1) / (32 * P)), (unsigned)nslot);
+    k<<<grid, 256, sm, p.stream>>>(p.D, p.dpad, kc, p.dvr, (const double2*)xc, (double2*)part);
+  } else {
+    constexpr int P = 16;
+    const size_t sm = dvr_smem_bytes<float, P>(kc);
+    auto k = dvr_window<float, P>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    dim3 grid((unsigned)((p.D + 32 * P - 1) / (32 * P)), (unsigned)nslot);
+    k<<<grid, 256, sm, p.stream>>>(p.D, p.dpad, kc, p.dvr, (const float2*)xc, (float2*)part);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gue_apply(const Plan& p, const void* xc, void* part, int64_t nvec) {
+  if (nvec != 1) return cudaErrorNotSupported;
+  const int64_t dpad = p.dpad;
+  const unsigned grid = (unsigned)p.nwork;
+  if (p.prec == MF_PREC_FP64) {
+    if (p.gen == MF_GEN_PHILOX_GUE)
+      herm_tile_nv1<double, MF_GEN_PHILOX_GUE><<<grid, 256, 0, p.stream>>>(
+          p.d_work, p.D, dpad, p.seed, p.sigma64, p.dvr, (const double2*)xc, (double2*)part,
+          (const double2*)p.d_cache, p.b);
+    else
+      herm_tile_nv1<double, MF_GEN_SINC_DVR_HO><<<grid, 256, 0, p.stream>>>(
+          p.d_work, p.D, dpad, p.seed, p.sigma64, p.dvr, (const double2*)xc, (double2*)part,
+          (const double2*)p.d_cache, p.b);
+  } else {
+    if (p.gen == MF_GEN_PHILOX_GUE)
+      herm_tile_nv1<float, MF_GEN_PHILOX_GUE><<<grid, 256, 0, p.stream>>>(
+          p.d_work, p.D, dpad, p.seed, p.sigma32, p.dvr, (const float2*)xc, (float2*)part,
+          (const float2*)p.d_cache, p.b);
+    else
+      herm_tile_nv1<float, MF_GEN_SINC_DVR_HO><<<grid, 256, 0, p.stream>>>(
+          p.d_work, p.D, dpad, p.seed, p.sigma32, p.dvr, (const float2*)xc, (float2*)part,
+          (const float2*)p.d_cache, p.b);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace mf

@@ -1,0 +1,622 @@
+// mf_api.cu -- host implementation of the C ABI declared in include/mf.h.
+//
+// Plan creation follows Sec. IV of the paper: a block partition (Sec. II),
+// a storage mode and cache budget (Sec. III.A, Sec. IV.G, Eq.
+// partial_cache_pairs), a memory-feasibility check (Eq.
+// planner_memory_constraint), a dense-work safety estimate (Sec. IV.H) and a
+// launch shape.  The apply follows Eq. blockmatvec; the propagator follows
+// Sec. VII (centred Chebyshev with Lanczos bounds).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "mf_internal.h"
+
+using namespace mf;
+
+struct mf_plan {
+  Plan p;
+};
+
+namespace {
+
+#define MF_CUDA(call)                                      \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) {                               \
+      if (e_ == cudaErrorMemoryAllocation) return MF_ERR_OOM; \
+      return MF_ERR_CUDA;                                  \
+    }                                                      \
+  } while (0)
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+template <typename T>
+void free_dev(T*& ptr) {
+  if (ptr) cudaFree((void*)ptr);
+  ptr = nullptr;
+}
+
+void release(Plan& p) {
+  for (auto& e : p.ev) {
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
+  p.ev.clear();
+  free_dev(p.d_cache);
+  free_dev(p.d_work);
+  free_dev(p.d_part);
+  free_dev(p.d_xc);
+  for (auto& q : p.d_q) free_dev(q);
+  free_dev(p.d_J);
+  free_dev(p.d_red);
+  free_dev(p.d_err);
+}
+
+// Workspace for nvec vectors: partial slots, compute copy, three FP64 vectors.
+mf_status ensure_workspace(Plan& p, int64_t nvec) {
+  if (nvec <= p.nvec_cap) return MF_OK;
+  free_dev(p.d_part);
+  free_dev(p.d_xc);
+  for (auto& q : p.d_q) free_dev(q);
+  const size_t eb = compute_elem_bytes(p.prec);
+  const size_t part_bytes = (size_t)p.nslot * (size_t)p.dpad * (size_t)nvec * eb;
+  const size_t xc_bytes = (size_t)std::max(p.dpad, p.D) * (size_t)nvec * eb;
+  MF_CUDA(cudaMalloc(&p.d_part, part_bytes));
+  MF_CUDA(cudaMalloc(&p.d_xc, xc_bytes));
+  for (auto& q : p.d_q) MF_CUDA(cudaMalloc((void**)&q, (size_t)p.D * (size_t)nvec * sizeof(double2)));
+  p.nvec_cap = nvec;
+  return MF_OK;
+}
+
+mf_status ensure_J(Plan& p, int32_t K) {
+  if (K + 1 <= p.J_cap) return MF_OK;
+  free_dev(p.d_J);
+  const int32_t cap = std::max<int32_t>(K + 1, 256);
+  MF_CUDA(cudaMalloc((void**)&p.d_J, (size_t)cap * sizeof(double)));
+  p.J_cap = cap;
+  p.J_arg = -1.0;
+  return MF_OK;
+}
+
+// The generate-and-apply kernel of the plan's path (xc -> partial slots),
+// bracketed by CUDA events when profiling is on.
+mf_status apply_kernel(Plan& p, int64_t nvec) {
+  if (p.profiling) {
+    if (p.ev_used == p.ev.size()) {
+      std::pair<cudaEvent_t, cudaEvent_t> e;
+      MF_CUDA(cudaEventCreate(&e.first));
+      MF_CUDA(cudaEventCreate(&e.second));
+      p.ev.push_back(e);
+    }
+    MF_CUDA(cudaEventRecord(p.ev[p.ev_used].first, p.stream));
+  }
+  if (p.use_dvr_window)
+    MF_CUDA(launch_dvr_apply(p, p.d_xc, p.d_part, nvec));
+  else
+    MF_CUDA(launch_gue_apply(p, p.d_xc, p.d_part, nvec));
+  if (p.profiling) {
+    MF_CUDA(cudaEventRecord(p.ev[p.ev_used].second, p.stream));
+    ++p.ev_used;
+  }
+  return MF_OK;
+}
+
+// One product y = H x on device vectors; x FP64 [D][nvec].
+mf_status apply_internal(Plan& p, double2* y, const double2* x, int64_t nvec) {
+  mf_status st = ensure_workspace(p, nvec);
+  if (st != MF_OK) return st;
+  MF_CUDA(launch_to_compute(p, x, p.d_xc, p.D * nvec));
+  if ((st = apply_kernel(p, nvec)) != MF_OK) return st;
+  MF_CUDA(launch_reduce(p, p.d_part, x, y, nvec));
+  return MF_OK;
+}
+
+// Eigenvalue extremes of the symmetric tridiagonal (alpha, beta) by Sturm
+// bisection (count of eigenvalues below s from the LDL^T pivots).
+int sturm_count(const std::vector<double>& a, const std::vector<double>& b, double s) {
+  int cnt = 0;
+  double d = 1.0;
+  for (size_t i = 0; i < a.size(); ++i) {
+    const double bb = i ? b[i - 1] * b[i - 1] : 0.0;
+    d = (a[i] - s) - (i ? bb / d : 0.0);
+    if (d == 0.0) d = -1e-300;
+    if (d < 0) ++cnt;
+  }
+  return cnt;
+}
+
+double tridiag_eig(const std::vector<double>& a, const std::vector<double>& b, int k) {
+  double lo = 1e300, hi = -1e300;
+  for (size_t i = 0; i < a.size(); ++i) {
+    const double r = (i ? std::fabs(b[i - 1]) : 0.0) + (i + 1 < a.size() ? std::fabs(b[i]) : 0.0);
+    lo = std::min(lo, a[i] - r);
+    hi = std::max(hi, a[i] + r);
+  }
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (sturm_count(a, b, mid) > k) hi = mid; else lo = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+mf_status compute_bounds(Plan& p) {
+  if (p.have_bounds) return MF_OK;
+  if (p.gen == MF_GEN_SINC_DVR_HO) {
+    // symbol of the sinc-DVR kinetic operator is k^2/2 on |k| <= pi/dx, so
+    // 0 <= T <= pi^2/(2 dx^2); 0 <= V <= L^2/2 on the grid.
+    const double L = p.dvr.L;
+    p.emin = 0.0;
+    p.emax = M_PI * M_PI / (2.0 * p.dvr.dx2) + 0.5 * L * L;
+    p.have_bounds = true;
+    return MF_OK;
+  }
+  const int64_t n = p.D;
+  const int m = std::max(2, (int)std::min<int64_t>(p.opt.lanczos_m, p.D));
+  mf_status st = ensure_workspace(p, 1);
+  if (st != MF_OK) return st;
+  double2 *v = p.d_q[0], *vp = p.d_q[1], *w = p.d_q[2];
+  double* d_s = nullptr;
+  MF_CUDA(cudaMalloc((void**)&d_s, 2 * sizeof(double)));
+  auto dot = [&](const double2* a, const double2* b, double* out) -> mf_status {
+    MF_CUDA(launch_dot(p, a, b, n, d_s));
+    MF_CUDA(cudaMemcpyAsync(out, d_s, sizeof(double), cudaMemcpyDeviceToHost, p.stream));
+    MF_CUDA(cudaStreamSynchronize(p.stream));
+    return MF_OK;
+  };
+  std::vector<double> al, be;
+  double nrm2 = 0.0;
+  MF_CUDA(launch_random_unit(p, v, n, p.seed ^ 0x5DEECE66Dull));
+  st = dot(v, v, &nrm2);
+  if (st == MF_OK) {
+    MF_CUDA(launch_scale(p, v, v, 1.0 / std::sqrt(nrm2), n));
+    double beta = 0.0;
+    bool have_prev = false;
+    for (int j = 0; j < m; ++j) {
+      st = apply_internal(p, w, v, 1);
+      if (st != MF_OK) break;
+      double alpha = 0.0;
+      if ((st = dot(v, w, &alpha)) != MF_OK) break;
+      MF_CUDA(launch_axpby_lanczos(p, w, v, have_prev ? vp : nullptr, alpha, beta, n));
+      double bn2 = 0.0;
+      if ((st = dot(w, w, &bn2)) != MF_OK) break;
+      al.push_back(alpha);
+      const double bn = std::sqrt(bn2);
+      if (j == m - 1 || bn < 1e-12) break;
+      be.push_back(bn);
+      std::swap(vp, v);  // vp <- v (old), v <- buffer to hold w/bn
+      MF_CUDA(launch_scale(p, v, w, 1.0 / bn, n));
+      beta = bn;
+      have_prev = true;
+    }
+  }
+  cudaFree(d_s);
+  if (st != MF_OK) return st;
+  if (be.size() + 1 > al.size()) be.resize(al.size() - 1);
+  const double tmin = tridiag_eig(al, be, 0);
+  const double tmax = tridiag_eig(al, be, (int)al.size() - 1);
+  const double half = 0.5 * (tmax - tmin), pad = p.opt.bounds_pad * half;
+  p.emin = tmin - pad;
+  p.emax = tmax + pad;
+  p.have_bounds = true;
+  return MF_OK;
+}
+
+// Bessel coefficients J_k(z), k = 0..K on the device, cached per argument.
+// With order == 0 the term count is the smallest n with |a_k| < tol for all
+// k >= n (a_0 = J_0, a_k = 2 J_k), read back once per argument.
+mf_status coefficients(Plan& p, double z, int32_t order, int32_t* nterms) {
+  const int32_t Kmax = (int32_t)std::ceil(z) + 60 + (int32_t)(30.0 * std::cbrt(z + 1.0));
+  const int32_t K = std::max(Kmax, order);
+  if (p.J_arg != z || p.J_K < K) {
+    mf_status st = ensure_J(p, K);
+    if (st != MF_OK) return st;
+    MF_CUDA(launch_bessel(p, z, K, p.d_J));
+    p.J_arg = z;
+    p.J_K = K;
+    p.J_terms = 0;
+  }
+  if (order > 0) {
+    *nterms = order;
+    return MF_OK;
+  }
+  if (p.J_terms == 0) {
+    std::vector<double> J((size_t)p.J_K + 1);
+    MF_CUDA(cudaMemcpyAsync(J.data(), p.d_J, J.size() * sizeof(double), cudaMemcpyDeviceToHost, p.stream));
+    MF_CUDA(cudaStreamSynchronize(p.stream));
+    int32_t last = 0;
+    for (int32_t k = 0; k <= p.J_K; ++k) {
+      const double a = k ? 2.0 * std::fabs(J[k]) : std::fabs(J[0]);
+      if (a >= p.opt.cheb_tol) last = k;
+    }
+    p.J_terms = last + 1;
+  }
+  *nterms = p.J_terms;
+  return MF_OK;
+}
+
+const char* gen_name(int g) { return g == MF_GEN_PHILOX_GUE ? "philox_gue" : "sinc_dvr_ho"; }
+const char* prec_name(int g) { return g == MF_PREC_FP64 ? "fp64" : (g == MF_PREC_FP32 ? "fp32" : "bf16x2"); }
+const char* store_name(int s) {
+  return s == MF_STORE_FULL ? "full" : (s == MF_STORE_PARTIAL ? "partial" : "procedural");
+}
+
+}  // namespace
+
+extern "C" {
+
+void mf_options_default(mf_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = MF_PREC_FP32;
+  o->storage = MF_STORE_AUTO;
+  o->planner_mode = MF_PLANNER_ANALYTIC;
+  o->nvec_hint = 1;
+  o->cheb_tol = 1e-7;
+  o->lanczos_m = 40;
+  o->bounds_pad = 0.05;
+  o->dvr_L = 0.0;
+  o->stream = nullptr;
+  o->alpha_safety = 0.9;
+  o->f_cache = 0.8;
+  o->autotune_k = 8;
+  o->autotune_warmup = 1;
+  o->autotune_repeats = 3;
+  o->dense_work_limit = 1e13;
+  o->device = 0;
+}
+
+const char* mf_status_string(mf_status s) {
+  switch (s) {
+    case MF_OK: return "MF_OK";
+    case MF_ERR_INVALID: return "MF_ERR_INVALID";
+    case MF_ERR_OOM: return "MF_ERR_OOM";
+    case MF_ERR_CUDA: return "MF_ERR_CUDA";
+    case MF_ERR_UNSUPPORTED: return "MF_ERR_UNSUPPORTED";
+    case MF_ERR_TIMEOUT: return "MF_ERR_TIMEOUT";
+    case MF_WARN_DENSE_WORK: return "MF_WARN_DENSE_WORK";
+  }
+  return "MF_STATUS_UNKNOWN";
+}
+
+mf_status mf_plan_create(mf_plan_t* out, int64_t D, int64_t M, int32_t generator, uint64_t seed, int64_t block,
+                         size_t cache_budget_bytes, const mf_options* opt) {
+  if (!out) return MF_ERR_INVALID;
+  *out = nullptr;
+  mf_options o;
+  if (opt) o = *opt; else mf_options_default(&o);
+  if (D < 2 || M != D || D > (int64_t)1 << 31) return MF_ERR_INVALID;
+  if (generator != MF_GEN_PHILOX_GUE && generator != MF_GEN_SINC_DVR_HO) return MF_ERR_INVALID;
+  if (o.precision != MF_PREC_FP64 && o.precision != MF_PREC_FP32 && o.precision != MF_PREC_BF16X2)
+    return MF_ERR_INVALID;
+  if (o.precision == MF_PREC_BF16X2) return MF_ERR_UNSUPPORTED;
+  if (block < 0 || (block > 0 && block % kTile != 0)) return MF_ERR_INVALID;
+  if (o.storage < MF_STORE_AUTO || o.storage > MF_STORE_FULL) return MF_ERR_INVALID;
+  if (!(o.cheb_tol > 0) || o.lanczos_m < 2 || !(o.alpha_safety > 0 && o.alpha_safety <= 1)) return MF_ERR_INVALID;
+
+  mf_plan* h = new (std::nothrow) mf_plan();
+  if (!h) return MF_ERR_OOM;
+  Plan& p = h->p;
+  p.D = D;
+  p.gen = generator;
+  p.seed = seed;
+  p.prec = o.precision;
+  p.opt = o;
+  p.stream = (cudaStream_t)o.stream;
+  p.device = o.device;
+  DeviceGuard guard(p.device);
+  auto fail = [&](mf_status s) {
+    release(p);
+    delete h;
+    return s;
+  };
+  if (cudaSetDevice(p.device) != cudaSuccess) return fail(MF_ERR_CUDA);
+  if (cudaDeviceGetAttribute(&p.num_sms, cudaDevAttrMultiProcessorCount, p.device) != cudaSuccess)
+    return fail(MF_ERR_CUDA);
+  size_t mfree = 0, mtotal = 0;
+  if (cudaMemGetInfo(&mfree, &mtotal) != cudaSuccess) return fail(MF_ERR_CUDA);
+
+  // generator constants
+  p.sigma64 = std::sqrt(0.5 / (double)D);
+  p.sigma32 = sqrtf(0.5f / (float)D);
+  const double L = o.dvr_L > 0 ? o.dvr_L : 0.9 * std::sqrt(2.0 * (double)D);
+  p.dvr.L = L;
+  p.dvr.dx = (2.0 * L) / (double)(D - 1);
+  p.dvr.dx2 = p.dvr.dx * p.dvr.dx;
+  const double PI2_6 = 0x1.a51a6625307d3p+0;
+  p.dvr.t0_64 = PI2_6 / p.dvr.dx2;
+  p.dvr.t0_32 = (float)p.dvr.t0_64;
+  p.dvr.c32 = (float)(1.0 / p.dvr.dx2);
+
+  // partition (Sec. II / IV.F): b multiple of the tile, at most D rounded up
+  const int64_t Dt = (D + kTile - 1) / kTile * kTile;
+  p.b = block > 0 ? std::min(block, Dt) : std::min<int64_t>(Dt, 2048);
+  p.nblk = (D + p.b - 1) / p.b;
+  p.npair = p.nblk * (p.nblk + 1) / 2;
+  p.ntile = (D + kTile - 1) / kTile;
+
+  // storage (Sec. III.A, IV.G): P_cache = min(N_pair, floor(M_cache / (B_c b^2)))
+  const size_t eb = compute_elem_bytes(p.prec);
+  size_t budget = cache_budget_bytes;
+  if (budget == SIZE_MAX) budget = (size_t)(o.f_cache * (double)mfree);
+  const double blk_bytes = (double)eb * (double)p.b * (double)p.b;
+  int64_t pc = (int64_t)std::min<double>((double)p.npair, std::floor((double)budget / blk_bytes));
+  int32_t storage = o.storage;
+  if (storage == MF_STORE_AUTO) {
+    // DVR: the Toeplitz-window generator is cheaper than streaming its blocks
+    if (generator == MF_GEN_SINC_DVR_HO) pc = 0;
+    storage = pc == 0 ? MF_STORE_PROCEDURAL : (pc == p.npair ? MF_STORE_FULL : MF_STORE_PARTIAL);
+  } else if (storage == MF_STORE_PROCEDURAL) {
+    pc = 0;
+  } else if (storage == MF_STORE_FULL) {
+    if (pc < p.npair) return fail(MF_ERR_OOM);
+  }
+  p.storage = storage;
+  p.pairs_cached = pc;
+  p.cache_budget = budget;
+
+  // memory feasibility (Eq. planner_memory_constraint): M_op + M_work <= alpha M_free
+  const int64_t nv = std::max(1, o.nvec_hint);
+  p.use_dvr_window = generator == MF_GEN_SINC_DVR_HO && pc == 0;
+  if (p.use_dvr_window) {
+    const int P = p.prec == MF_PREC_FP64 ? 8 : 16;
+    p.dvr_rows = 32 * P;
+    const int64_t rtiles = (D + p.dvr_rows - 1) / p.dvr_rows;
+    int kc = 4096;
+    while (kc > 128 && rtiles * ((D + kc - 1) / kc) < 8 * (int64_t)p.num_sms) kc /= 2;
+    p.dvr_cols = kc;
+    p.nslot = (D + kc - 1) / kc;
+    p.dpad = rtiles * p.dvr_rows;
+  } else {
+    p.nslot = p.ntile;
+    p.dpad = p.ntile * kTile;
+  }
+  const double m_work = (double)p.nslot * p.dpad * nv * eb + 3.0 * D * nv * 16.0 + (double)p.dpad * nv * eb;
+  const double m_op = (double)pc * blk_bytes;
+  if (m_op + m_work > o.alpha_safety * (double)mfree) {
+    if (o.storage == MF_STORE_FULL || o.storage == MF_STORE_PARTIAL) return fail(MF_ERR_OOM);
+    // shrink the cache until the plan fits
+    const double room = o.alpha_safety * (double)mfree - m_work;
+    pc = room > 0 ? (int64_t)std::floor(room / blk_bytes) : 0;
+    pc = std::min(pc, p.npair);
+    p.pairs_cached = pc;
+    p.storage = pc == 0 ? MF_STORE_PROCEDURAL : (pc == p.npair ? MF_STORE_FULL : MF_STORE_PARTIAL);
+    if (m_work > o.alpha_safety * (double)mfree) return fail(MF_ERR_OOM);
+  }
+
+  // dense-work safety estimate (Sec. IV.H): W_Hpsi ~ D^2 entries
+  p.w_hpsi = (double)D * (double)D;
+  p.dense_warn = p.w_hpsi > o.dense_work_limit;
+
+  if (cudaMalloc((void**)&p.d_err, sizeof(int)) != cudaSuccess) return fail(MF_ERR_OOM);
+  if (cudaMemsetAsync(p.d_err, 0, sizeof(int), p.stream) != cudaSuccess) return fail(MF_ERR_CUDA);
+  if (cudaMalloc((void**)&p.d_red, 512 * sizeof(double)) != cudaSuccess) return fail(MF_ERR_OOM);
+
+  // cache: the first P_cache canonical pairs in row order
+  p.pair_slot.assign((size_t)(p.nblk * p.nblk), -1);
+  std::vector<int2> pairs;
+  for (int64_t n = 0, s = 0; n < p.nblk && s < p.pairs_cached; ++n)
+    for (int64_t m = n; m < p.nblk && s < p.pairs_cached; ++m, ++s) {
+      p.pair_slot[(size_t)(n * p.nblk + m)] = s;
+      pairs.push_back(make_int2((int)n, (int)m));
+    }
+  if (p.pairs_cached > 0) {
+    p.cache_bytes = (size_t)p.pairs_cached * (size_t)blk_bytes;
+    cudaError_t e = cudaMalloc(&p.d_cache, p.cache_bytes);
+    if (e != cudaSuccess) return fail(MF_ERR_OOM);
+    int2* d_pairs = nullptr;
+    if (cudaMalloc((void**)&d_pairs, pairs.size() * sizeof(int2)) != cudaSuccess) return fail(MF_ERR_OOM);
+    cudaMemcpyAsync(d_pairs, pairs.data(), pairs.size() * sizeof(int2), cudaMemcpyHostToDevice, p.stream);
+    e = launch_cache_fill_pairs(p, d_pairs, (int64_t)pairs.size());
+    cudaStreamSynchronize(p.stream);
+    cudaFree(d_pairs);
+    if (e != cudaSuccess) return fail(MF_ERR_CUDA);
+  }
+
+  // work list of canonical tiles, cached and procedural items interleaved so
+  // HBM streaming and generation overlap on the SMs (Eq. runtime_overlap)
+  if (!p.use_dvr_window) {
+    std::vector<WorkItem> cached, proc;
+    const int64_t tpb = p.b / kTile;
+    for (int64_t ti = 0; ti < p.ntile; ++ti)
+      for (int64_t tj = ti; tj < p.ntile; ++tj) {
+        const int64_t n = ti / tpb, m = tj / tpb;
+        const int64_t slot = p.pair_slot[(size_t)(n * p.nblk + m)];
+        WorkItem it{(int32_t)ti, (int32_t)tj, -1};
+        if (slot >= 0) {
+          it.cache_off = slot * p.b * p.b + (ti * kTile - n * p.b) * p.b + (tj * kTile - m * p.b);
+          cached.push_back(it);
+        } else {
+          proc.push_back(it);
+        }
+      }
+    std::vector<WorkItem> work;
+    work.reserve(cached.size() + proc.size());
+    size_t ic = 0, ip = 0;
+    while (ic < cached.size() || ip < proc.size()) {
+      // take from the list that is behind its share
+      const bool take_c = ip >= proc.size() ||
+                          (ic < cached.size() && (double)ic * proc.size() <= (double)ip * cached.size());
+      work.push_back(take_c ? cached[ic++] : proc[ip++]);
+    }
+    p.nwork = (int64_t)work.size();
+    if (cudaMalloc((void**)&p.d_work, work.size() * sizeof(WorkItem)) != cudaSuccess) return fail(MF_ERR_OOM);
+    if (cudaMemcpyAsync(p.d_work, work.data(), work.size() * sizeof(WorkItem), cudaMemcpyHostToDevice,
+                        p.stream) != cudaSuccess)
+      return fail(MF_ERR_CUDA);
+  }
+  mf_status st = ensure_workspace(p, nv);
+  if (st != MF_OK) return fail(st);
+  if (cudaStreamSynchronize(p.stream) != cudaSuccess) return fail(MF_ERR_CUDA);
+  *out = h;
+  return p.dense_warn ? MF_WARN_DENSE_WORK : MF_OK;
+}
+
+mf_status mf_plan_destroy(mf_plan_t h) {
+  if (!h) return MF_OK;
+  DeviceGuard guard(h->p.device);
+  cudaStreamSynchronize(h->p.stream);
+  release(h->p);
+  delete h;
+  return MF_OK;
+}
+
+mf_status mf_apply(mf_plan_t h, void* y, const void* x, int64_t nvec) {
+  if (!h || !y || !x || nvec < 1 || nvec > 64) return MF_ERR_INVALID;
+  Plan& p = h->p;
+  const size_t bytes = (size_t)p.D * (size_t)nvec * sizeof(double2);
+  const char *yb = (const char*)y, *xb = (const char*)x;
+  if (yb < xb + bytes && xb < yb + bytes) return MF_ERR_INVALID;
+  if (nvec != 1) return MF_ERR_UNSUPPORTED;
+  DeviceGuard guard(p.device);
+  return apply_internal(p, (double2*)y, (const double2*)x, nvec);
+}
+
+mf_status mf_spectral_bounds(mf_plan_t h, double* emin, double* emax) {
+  if (!h) return MF_ERR_INVALID;
+  DeviceGuard guard(h->p.device);
+  mf_status st = compute_bounds(h->p);
+  if (st != MF_OK) return st;
+  if (emin) *emin = h->p.emin;
+  if (emax) *emax = h->p.emax;
+  return MF_OK;
+}
+
+mf_status mf_plan_set_bounds(mf_plan_t h, double emin, double emax) {
+  if (!h || !(emax > emin) || !std::isfinite(emin) || !std::isfinite(emax)) return MF_ERR_INVALID;
+  h->p.emin = emin;
+  h->p.emax = emax;
+  h->p.have_bounds = true;
+  h->p.J_arg = -1.0;
+  return MF_OK;
+}
+
+mf_status mf_cheb_terms(mf_plan_t h, double dt, int32_t* nterms) {
+  if (!h || !nterms || !(dt > 0) || !std::isfinite(dt)) return MF_ERR_INVALID;
+  Plan& p = h->p;
+  DeviceGuard guard(p.device);
+  mf_status st = compute_bounds(p);
+  if (st != MF_OK) return st;
+  const double R = 0.5 * (p.emax - p.emin);
+  return coefficients(p, R * dt, 0, nterms);
+}
+
+mf_status mf_cheb_propagate(mf_plan_t h, void* psi, int64_t nvec, double dt, int32_t order) {
+  if (!h || !psi || nvec < 1 || nvec > 64 || !(dt > 0) || !std::isfinite(dt) || order < 0) return MF_ERR_INVALID;
+  Plan& p = h->p;
+  if (nvec != 1) return MF_ERR_UNSUPPORTED;
+  DeviceGuard guard(p.device);
+  mf_status st = compute_bounds(p);
+  if (st != MF_OK) return st;
+  const double c = 0.5 * (p.emax + p.emin), R = 0.5 * (p.emax - p.emin);
+  int32_t nt = 0;
+  st = coefficients(p, R * dt, order, &nt);
+  if (st != MF_OK) return st;
+  st = ensure_workspace(p, nvec);
+  if (st != MF_OK) return st;
+  double2* q_prev = p.d_q[0];
+  double2* q_cur = p.d_q[1];
+  double2* acc = p.d_q[2];
+  MF_CUDA(launch_cheb_init(p, (const double2*)psi, q_cur, acc, p.d_xc, nvec));
+  for (int32_t j = 1; j < nt; ++j) {
+    if ((st = apply_kernel(p, nvec)) != MF_OK) return st;
+    MF_CUDA(launch_cheb_update(p, p.d_part, q_cur, q_prev, acc, p.d_xc, nvec, j, c, R));
+    std::swap(q_cur, q_prev);
+  }
+  MF_CUDA(launch_cheb_final(p, acc, (double2*)psi, nvec, c, dt));
+  return MF_OK;
+}
+
+mf_status mf_plan_profile(mf_plan_t h, int32_t enable) {
+  if (!h) return MF_ERR_INVALID;
+  h->p.profiling = enable != 0;
+  h->p.ev_used = 0;
+  return MF_OK;
+}
+
+mf_status mf_plan_profile_read(mf_plan_t h, double* total_ms, int64_t* launches) {
+  if (!h || !total_ms || !launches) return MF_ERR_INVALID;
+  Plan& p = h->p;
+  DeviceGuard guard(p.device);
+  MF_CUDA(cudaStreamSynchronize(p.stream));
+  double tot = 0.0;
+  for (size_t i = 0; i < p.ev_used; ++i) {
+    float ms = 0.f;
+    MF_CUDA(cudaEventElapsedTime(&ms, p.ev[i].first, p.ev[i].second));
+    tot += ms;
+  }
+  *total_ms = tot;
+  *launches = (int64_t)p.ev_used;
+  p.ev_used = 0;
+  return MF_OK;
+}
+
+mf_status mf_sync(mf_plan_t h) {
+  if (!h) return MF_ERR_INVALID;
+  Plan& p = h->p;
+  DeviceGuard guard(p.device);
+  int err = 0;
+  if (cudaMemcpyAsync(&err, p.d_err, sizeof(int), cudaMemcpyDeviceToHost, p.stream) != cudaSuccess)
+    return MF_ERR_CUDA;
+  if (cudaStreamSynchronize(p.stream) != cudaSuccess) return MF_ERR_CUDA;
+  if (err == 1) return MF_ERR_TIMEOUT;
+  if (err != 0) return MF_ERR_CUDA;
+  return MF_OK;
+}
+
+mf_status mf_plan_describe(mf_plan_t h, char* buf, size_t len) {
+  if (!h || !buf || len == 0) return MF_ERR_INVALID;
+  const Plan& p = h->p;
+  char tmp[2048];
+  const int n = std::snprintf(
+      tmp, sizeof(tmp),
+      "{\"D\": %lld, \"generator\": \"%s\", \"seed\": %llu, \"precision\": \"%s\", \"block\": %lld, "
+      "\"n_blk\": %lld, \"n_pair\": %lld, \"storage\": \"%s\", \"cache_budget_bytes\": %zu, "
+      "\"pairs_cached\": %lld, \"cache_bytes\": %zu, \"path\": \"%s\", \"tile\": %d, \"dvr_rows\": %d, "
+      "\"dvr_cols\": %d, \"n_slot\": %lld, \"n_work\": %lld, \"w_hpsi\": %.6g, \"dense_warn\": %s, "
+      "\"dvr_L\": %.17g, \"dvr_dx\": %.17g, \"have_bounds\": %s, \"emin\": %.17g, \"emax\": %.17g, "
+      "\"num_sms\": %d}",
+      (long long)p.D, gen_name(p.gen), (unsigned long long)p.seed, prec_name(p.prec), (long long)p.b,
+      (long long)p.nblk, (long long)p.npair, store_name(p.storage), p.cache_budget, (long long)p.pairs_cached,
+      p.cache_bytes, p.use_dvr_window ? "dvr_window" : "herm_tile", kTile, p.dvr_rows, p.dvr_cols,
+      (long long)p.nslot, (long long)p.nwork, p.w_hpsi, p.dense_warn ? "true" : "false", p.dvr.L, p.dvr.dx,
+      p.have_bounds ? "true" : "false", p.emin, p.emax, p.num_sms);
+  if (n < 0) return MF_ERR_INVALID;
+  std::strncpy(buf, tmp, len - 1);
+  buf[len - 1] = '\0';
+  return (size_t)n < len ? MF_OK : MF_ERR_INVALID;
+}
+
+mf_status mf_debug_entries(mf_plan_t h, int64_t r0, int64_t c0, int64_t rows, int64_t cols, void* out_host) {
+  if (!h || !out_host || rows < 1 || cols < 1) return MF_ERR_INVALID;
+  Plan& p = h->p;
+  if (r0 < 0 || c0 < 0 || r0 + rows > p.D || c0 + cols > p.D) return MF_ERR_INVALID;
+  DeviceGuard guard(p.device);
+  const size_t bytes = (size_t)rows * (size_t)cols * compute_elem_bytes(p.prec);
+  void* d = nullptr;
+  MF_CUDA(cudaMalloc(&d, bytes));
+  cudaError_t e = launch_debug_entries(p, r0, c0, rows, cols, d);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out_host, d, bytes, cudaMemcpyDeviceToHost, p.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p.stream);
+  cudaFree(d);
+  return e == cudaSuccess ? MF_OK : MF_ERR_CUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,113 @@
+// mf_internal.h -- plan record and kernel launcher declarations shared by the
+// translation units of libmf (host side).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/mf.h"
+#include "gen.cuh"
+
+namespace mf {
+
+constexpr int kTile = 128;  // CTA tile edge of the Hermitian (canonical-pair) kernels
+
+// One CTA work item of the Hermitian apply: canonical tile (ti <= tj) in units
+// of kTile, and the byte offset of its block in the HBM cache (-1 when the
+// block pair is generated procedurally).
+struct WorkItem {
+  int32_t ti, tj;
+  int64_t cache_off;  // element offset of the tile's cached block, or -1
+};
+
+struct Plan {
+  // problem
+  int64_t D = 0;
+  int32_t gen = 0;
+  uint64_t seed = 0;
+  int32_t prec = MF_PREC_FP32;
+  mf_options opt{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int num_sms = 0;
+  // partition (Sec. II) and storage (Sec. III.A)
+  int64_t b = 0, nblk = 0, npair = 0;
+  int32_t storage = MF_STORE_PROCEDURAL;
+  size_t cache_budget = 0, cache_bytes = 0;
+  int64_t pairs_cached = 0;
+  std::vector<int64_t> pair_slot;  // nblk*nblk (n<=m) -> cache slot or -1
+  void* d_cache = nullptr;
+  // generator constants
+  float sigma32 = 0.f;
+  double sigma64 = 0.0;
+  dvr_consts dvr{};
+  // Hermitian (Philox) tiling
+  int64_t ntile = 0;              // tile rows = ceil(D / kTile)
+  WorkItem* d_work = nullptr;     // canonical tiles, cached/procedural interleaved
+  int64_t nwork = 0;
+  // DVR launch shape
+  int dvr_rows = 512, dvr_cols = 4096;
+  // workspace (sized for nvec_cap vectors)
+  int64_t nvec_cap = 0;
+  int64_t nslot = 0;              // partial-sum slots per output row
+  int64_t dpad = 0;               // rows per slot (D padded to the kernel's row tile)
+  bool use_dvr_window = false;    // DVR procedural path (Toeplitz window kernel)
+  void* d_part = nullptr;         // [nslot][D][nvec] complex (compute precision)
+  void* d_xc = nullptr;           // compute-precision copy of the input
+  double2* d_q[3] = {nullptr, nullptr, nullptr};  // Chebyshev q_prev, q_cur, acc
+  double* d_J = nullptr;          // Bessel J_k(R dt)
+  int32_t J_cap = 0;
+  double* d_red = nullptr;        // small reduction scratch (dots/norms)
+  int* d_err = nullptr;           // device error word
+  // spectral bounds
+  bool have_bounds = false;
+  double emin = 0.0, emax = 0.0;
+  // Chebyshev coefficient cache
+  double J_arg = -1.0;
+  int32_t J_K = 0;
+  int32_t J_terms = 0;
+  // per-launch timing of the apply kernel (CUDA events on the plan's stream)
+  bool profiling = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+  size_t ev_used = 0;
+  // safety estimate (Sec. IV.H)
+  double w_hpsi = 0.0;
+  bool dense_warn = false;
+};
+
+// ---- launchers (return cudaError_t of the launch) ----
+// Hermitian canonical-tile apply, nvec == 1 register kernel.
+cudaError_t launch_gue_apply(const Plan& p, const void* xc, void* part, int64_t nvec);
+// DVR Toeplitz-window apply (rows x column chunk per CTA).
+cudaError_t launch_dvr_apply(const Plan& p, const void* xc, void* part, int64_t nvec);
+// Fill the cache blocks listed in d_pairs (block pair (n, m) per cache slot).
+cudaError_t launch_cache_fill_pairs(const Plan& p, const int2* d_pairs, int64_t npairs);
+// FP64 master -> compute-precision copy.
+cudaError_t launch_to_compute(const Plan& p, const double2* x, void* xc, int64_t n);
+// y = sum of partial slots (+ V x for the DVR), FP64.
+cudaError_t launch_reduce(const Plan& p, const void* part, const double2* x, double2* y, int64_t nvec);
+// Chebyshev pieces.
+cudaError_t launch_cheb_init(const Plan& p, const double2* psi, double2* q, double2* acc, void* xc,
+                             int64_t nvec);
+cudaError_t launch_cheb_update(const Plan& p, const void* part, const double2* qcur, double2* qprev,
+                               double2* acc, void* xc, int64_t nvec, int32_t k_next, double c, double R);
+cudaError_t launch_cheb_final(const Plan& p, const double2* acc, double2* psi, int64_t nvec, double c,
+                              double dt);
+cudaError_t launch_bessel(const Plan& p, double z, int32_t K, double* J);
+// Lanczos helpers: out[0] = Re<a,b>, FP64 reduction into d_red slot.
+cudaError_t launch_dot(const Plan& p, const double2* a, const double2* b, int64_t n, double* out);
+cudaError_t launch_axpby_lanczos(const Plan& p, double2* w, const double2* v, const double2* vprev,
+                                 double alpha, double beta, int64_t n);
+cudaError_t launch_scale(const Plan& p, double2* dst, const double2* src, double s, int64_t n);
+cudaError_t launch_random_unit(const Plan& p, double2* v, int64_t n, uint64_t seed);
+// Entry dump of the generator (plan precision form) into a device buffer.
+cudaError_t launch_debug_entries(const Plan& p, int64_t r0, int64_t c0, int64_t rows, int64_t cols,
+                                 void* out);
+
+size_t compute_elem_bytes(int prec);  // bytes of one complex compute-format element
+
+}  // namespace mf

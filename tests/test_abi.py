@@ -1,0 +1,71 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports
+every entry point declared in include/mf.h, and rejects bad arguments before
+touching CUDA."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h")]
+
+
+def _declared():
+    names = set()
+    for h in HEADERS:
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        for m in re.finditer(r"\b(mf_[a-z0-9_]+)\s*\(", src):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def mf():
+    import paper_2606_31598_gb300 as mf
+    from paper_2606_31598_gb300 import _build
+    _build.build()
+    return mf
+
+
+def test_header_declares_core_calls():
+    names = _declared()
+    for n in ("mf_plan_create", "mf_apply", "mf_cheb_propagate", "mf_plan_destroy", "mf_debug_entries"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(mf):
+    lib = mf.lib()
+    missing = [n for n in sorted(_declared()) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_options_default_and_status_strings(mf):
+    o = mf.mf_options_default()
+    assert o.precision == mf.MF_PREC_FP32 and o.lanczos_m == 40 and abs(o.cheb_tol - 1e-7) < 1e-20
+    assert o.storage == mf.MF_STORE_AUTO and o.alpha_safety == pytest.approx(0.9)
+    for s, name in [(0, "MF_OK"), (1, "MF_ERR_INVALID"), (5, "MF_ERR_TIMEOUT"), (6, "MF_WARN_DENSE_WORK")]:
+        assert mf.status_string(s) == name
+
+
+@pytest.mark.parametrize(
+    "D,M,gen,block,prec",
+    [(1, 1, 0, 0, 1), (100, 99, 0, 0, 1), (100, 100, 7, 0, 1), (1000, 1000, 0, 100, 1), (1000, 1000, 0, -128, 1),
+     (1000, 1000, 1, 0, 9)],
+)
+def test_plan_create_rejects_bad_arguments_without_gpu(mf, D, M, gen, block, prec):
+    h = ctypes.c_void_p()
+    o = mf.mf_options_default(precision=prec)
+    st = mf.lib().mf_plan_create(ctypes.byref(h), D, M, gen, 1, block, 0, ctypes.byref(o))
+    assert st == mf.MF_ERR_INVALID
+    assert not h.value
+
+
+def test_null_handles_are_invalid(mf):
+    L = mf.lib()
+    assert L.mf_apply(None, None, None, 1) == mf.MF_ERR_INVALID
+    assert L.mf_cheb_propagate(None, None, 1, 0.1, 0) == mf.MF_ERR_INVALID
+    assert L.mf_plan_destroy(None) == mf.MF_OK
+    assert L.mf_sync(None) == mf.MF_ERR_INVALID
