@@ -187,7 +187,7 @@ def test_cheb_step_matches_oracle_gue(mf, prec):
 def test_cheb_dvr_half_period_closed_form(mf):
     """Harmonic oscillator: psi(pi)(x) = -i psi0(-x) for the coherent state."""
     D = 256
-    p = _plan(mf, D, 1, 0)
+    p = _plan(mf, D, 1, 0, cheb_tol=1e-14)
     psi0 = W.wavepacket(D)
     d = _dev(psi0)
     nsteps = 40
