@@ -202,6 +202,30 @@ mf_status mf_plan_describe(mf_plan_t p, char* buf, size_t len);
 mf_status mf_debug_entries(mf_plan_t p, int64_t r0, int64_t c0, int64_t rows, int64_t cols,
                            void* out_host);
 
+/*
+ * mf_apply_dvr_noalloc -- y = H x for the sinc-DVR harmonic-oscillator
+ * operator in the FP32 form, one vector, without allocating any memory.  The
+ * paper has no counterpart: this entry point exists for callers that cannot
+ * allocate device memory while they run (a service whose device memory is
+ * fully reserved by another runtime's caching allocator, a plugin that its
+ * host application forbids to call cudaMalloc).
+ *   D      : 2 <= D <= 131072 (larger D returns MF_ERR_INVALID).
+ *   dvr_L  : grid half-width, 0 selects 0.9*sqrt(2D).
+ *   x, y   : device complex128 [D], owned by the caller; y must not overlap x.
+ *   stream : cudaStream_t to run on (NULL = default stream).
+ * The kernels' scratch lives in one fixed 40 MiB device array of the library
+ * that every GPU loading the library holds until the process exits; no
+ * cudaMalloc, cudaFree or other allocating call is made.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  Every call
+ * on a device shares the one array and leaves its contents behind (nothing in
+ * it needs clearing: the kernels write every scratch value they read), so
+ * calls that overlap on the GPU -- on different streams, or from different
+ * threads -- race and must be serialised by the caller.  Asynchronous;
+ * errors: MF_ERR_INVALID, MF_ERR_CUDA.
+ */
+mf_status mf_apply_dvr_noalloc(int64_t D, double dvr_L, const void* x, void* y, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -91,11 +91,12 @@ def lib():
         L.mf_sync.argtypes = [vp]
         L.mf_plan_describe.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
         L.mf_debug_entries.argtypes = [vp, i64, i64, i64, i64, vp]
+        L.mf_apply_dvr_noalloc.argtypes = [i64, d, vp, vp, vp]
         L.mf_plan_profile.argtypes = [vp, i32]
         L.mf_plan_profile_read.argtypes = [vp, P(d), P(i64)]
         for name in ("mf_plan_create", "mf_plan_destroy", "mf_apply", "mf_cheb_propagate", "mf_cheb_terms",
                      "mf_spectral_bounds", "mf_plan_set_bounds", "mf_sync", "mf_plan_describe",
-                     "mf_debug_entries", "mf_plan_profile", "mf_plan_profile_read"):
+                     "mf_debug_entries", "mf_plan_profile", "mf_plan_profile_read", "mf_apply_dvr_noalloc"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -186,6 +187,12 @@ def mf_debug_entries(plan, r0, c0, rows, cols, out_host):
     """out_host: a contiguous numpy array (complex64 or complex128 per plan)."""
     return _check(lib().mf_debug_entries(plan, int(r0), int(c0), int(rows), int(cols),
                                          out_host.ctypes.data), "mf_debug_entries")
+
+
+def mf_apply_dvr_noalloc(D, dvr_L, x, y, stream=None):
+    """Allocation-free DVR apply (FP32 form, one vector); see include/mf.h."""
+    return _check(lib().mf_apply_dvr_noalloc(int(D), float(dvr_L), _ptr(x), _ptr(y), stream),
+                  "mf_apply_dvr_noalloc")
 
 
 def mf_plan_profile(plan, enable):

@@ -1,0 +1,95 @@
+// k_noalloc.cu -- an apply entry point that allocates no memory.
+//
+// Some callers cannot allocate device memory once they are running: a
+// service whose device memory is already fully reserved by another runtime's
+// caching allocator, or a plugin inside a host application that forbids it
+// to call cudaMalloc (which can synchronise the device and can fail under
+// fragmentation).  mf_apply_dvr_noalloc gives them y = H x for the sinc-DVR
+// operator with no allocation at all: the caller passes x and y, and the
+// kernels' scratch (the FP32 copy of x and the partial-sum slots) lives in
+// one file-scope device array of fixed size that every GPU loading this
+// library holds until the process exits.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <mutex>
+
+#include "mf_internal.h"
+
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)40 << 20;  // 40 MiB
+constexpr int64_t kNoAllocMaxD = 131072;
+constexpr int kMaxDevices = 64;
+
+// The scratch array itself.  In host code this name is only a stand-in for
+// the device symbol; its device address comes from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_mu;
+void* g_addr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once
+// per device with that device current.
+cudaError_t scratch_address(int dev, void** out) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (!g_addr[dev]) {
+    void* ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_addr[dev] = ptr;
+  }
+  *out = g_addr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" mf_status mf_apply_dvr_noalloc(int64_t D, double dvr_L, const void* x, void* y, void* stream) {
+  using namespace mf;
+  if (D < 2 || D > kNoAllocMaxD || !x || !y || !(dvr_L >= 0.0)) return MF_ERR_INVALID;
+  const size_t bytes = (size_t)D * sizeof(double2);
+  const char *xb = (const char*)x, *yb = (const char*)y;
+  if (yb < xb + bytes && xb < yb + bytes) return MF_ERR_INVALID;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MF_ERR_CUDA;
+
+  // the same launch shape the plan path picks for this D (FP32 form)
+  Plan p;
+  p.D = D;
+  p.gen = MF_GEN_SINC_DVR_HO;
+  p.prec = MF_PREC_FP32;
+  p.stream = (cudaStream_t)stream;
+  p.device = dev;
+  if (cudaDeviceGetAttribute(&p.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return MF_ERR_CUDA;
+  const double L = dvr_L > 0 ? dvr_L : 0.9 * std::sqrt(2.0 * (double)D);
+  p.dvr.L = L;
+  p.dvr.dx = (2.0 * L) / (double)(D - 1);
+  p.dvr.dx2 = p.dvr.dx * p.dvr.dx;
+  p.dvr.t0_64 = 0x1.a51a6625307d3p+0 / p.dvr.dx2;
+  p.dvr.t0_32 = (float)p.dvr.t0_64;
+  p.dvr.c32 = (float)(1.0 / p.dvr.dx2);
+  p.use_dvr_window = true;
+  p.dvr_rows = 512;
+  const int64_t rtiles = (D + p.dvr_rows - 1) / p.dvr_rows;
+  int kc = 4096;
+  while (kc > 128 && rtiles * ((D + kc - 1) / kc) < 8 * (int64_t)p.num_sms) kc /= 2;
+  p.dvr_cols = kc;
+  p.nslot = (D + kc - 1) / kc;
+  p.dpad = rtiles * p.dvr_rows;
+
+  const size_t xc_bytes = ((size_t)p.dpad * sizeof(float2) + 255) & ~(size_t)255;
+  const size_t part_bytes = (size_t)p.nslot * (size_t)p.dpad * sizeof(float2);
+  if (xc_bytes + part_bytes > kNoAllocScratchBytes) return MF_ERR_INVALID;
+
+  void* base = nullptr;
+  if (scratch_address(dev, &base) != cudaSuccess) return MF_ERR_CUDA;
+  void* xc = base;
+  void* part = (char*)base + xc_bytes;
+  // every partial slot row the reduction reads is written by the apply kernel
+  // first, so no part of the scratch needs clearing between calls
+  if (launch_to_compute(p, (const double2*)x, xc, D) != cudaSuccess) return MF_ERR_CUDA;
+  if (launch_dvr_apply(p, xc, part, 1) != cudaSuccess) return MF_ERR_CUDA;
+  if (launch_reduce(p, part, (const double2*)x, (double2*)y, 1) != cudaSuccess) return MF_ERR_CUDA;
+  return MF_OK;
+}
