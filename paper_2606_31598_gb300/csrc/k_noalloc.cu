@@ -88,8 +88,9 @@ extern "C" mf_status mf_apply_dvr_noalloc(int64_t D, double dvr_L, const void* x
   void* part = (char*)base + xc_bytes;
   // every partial slot row the reduction reads is written by the apply kernel
   // first, so no part of the scratch needs clearing between calls
-  if (launch_to_compute(p, (const double2*)x, xc, D) != cudaSuccess) return MF_ERR_CUDA;
+  const VecShape sh{1, 1, p.nslot, p.dpad};
+  if (launch_to_compute(p, (const double2*)x, xc, D, sh) != cudaSuccess) return MF_ERR_CUDA;
   if (launch_dvr_apply(p, xc, part, 1) != cudaSuccess) return MF_ERR_CUDA;
-  if (launch_reduce(p, part, (const double2*)x, (double2*)y, 1) != cudaSuccess) return MF_ERR_CUDA;
+  if (launch_reduce(p, part, (const double2*)x, (double2*)y, sh) != cudaSuccess) return MF_ERR_CUDA;
   return MF_OK;
 }

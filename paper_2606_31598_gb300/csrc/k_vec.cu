@@ -18,33 +18,41 @@ static inline unsigned grid_for(int64_t n, int threads = 256) {
 size_t compute_elem_bytes(int prec) { return prec == MF_PREC_FP64 ? sizeof(double2) : sizeof(float2); }
 
 // ------------------------------------------------------------- convert ----
+// xc[row][v] = x[row][v] for v < nv, 0 for nv <= v < nb.
 template <typename C>
-__global__ void k_to_compute(const double2* __restrict__ x, C* __restrict__ xc, int64_t n) {
+__global__ void k_to_compute(const double2* __restrict__ x, C* __restrict__ xc, int64_t n, int64_t nv, int64_t nb) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-    const double2 v = x[e];
+    const int64_t row = e / nb, v = e % nb;
     C o;
-    o.x = (decltype(o.x))v.x;
-    o.y = (decltype(o.y))v.y;
+    if (v < nv) {
+      const double2 a = x[row * nv + v];
+      o.x = (decltype(o.x))a.x;
+      o.y = (decltype(o.y))a.y;
+    } else {
+      o.x = 0;
+      o.y = 0;
+    }
     xc[e] = o;
   }
 }
 
-cudaError_t launch_to_compute(const Plan& p, const double2* x, void* xc, int64_t n) {
+cudaError_t launch_to_compute(const Plan& p, const double2* x, void* xc, int64_t D, VecShape s) {
+  const int64_t n = D * s.nb;
   if (p.prec == MF_PREC_FP64)
-    k_to_compute<double2><<<grid_for(n), 256, 0, p.stream>>>(x, (double2*)xc, n);
+    k_to_compute<double2><<<grid_for(n), 256, 0, p.stream>>>(x, (double2*)xc, n, s.nv, s.nb);
   else
-    k_to_compute<float2><<<grid_for(n), 256, 0, p.stream>>>(x, (float2*)xc, n);
+    k_to_compute<float2><<<grid_for(n), 256, 0, p.stream>>>(x, (float2*)xc, n, s.nv, s.nb);
   return cudaGetLastError();
 }
 
 // --------------------------------------------------- reduction + epilogue ----
-// y_e = sum_{s=0}^{nslot-1} part[s][row][v] in FP64 in slot order, plus
-// V_row * x_e for the DVR potential.
+// y[row][v] = sum_{s=0}^{nslot-1} part[s][row][v] in FP64 in slot order, plus
+// V_row * x[row][v] for the DVR potential.
 template <typename C>
-__device__ __forceinline__ double2 slot_sum(const C* __restrict__ part, int64_t nslot, int64_t stride, int64_t e) {
+__device__ __forceinline__ double2 slot_sum(const C* __restrict__ part, int64_t nslot, int64_t stride, int64_t idx) {
   double sr = 0.0, si = 0.0;
   for (int64_t s = 0; s < nslot; ++s) {
-    const C v = part[s * stride + e];
+    const C v = part[s * stride + idx];
     sr += (double)v.x;
     si += (double)v.y;
   }
@@ -52,12 +60,14 @@ __device__ __forceinline__ double2 slot_sum(const C* __restrict__ part, int64_t 
 }
 
 template <typename C>
-__global__ void k_reduce(const C* __restrict__ part, int64_t nslot, int64_t stride, int64_t n, int nvec,
-                         int dvr, dvr_consts dk, const double2* __restrict__ x, double2* __restrict__ y) {
+__global__ void k_reduce(const C* __restrict__ part, VecShape sh, int64_t n, int dvr, dvr_consts dk,
+                         const double2* __restrict__ x, double2* __restrict__ y) {
+  const int64_t stride = sh.dpad * sh.nb;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-    double2 s = slot_sum(part, nslot, stride, e);
+    const int64_t row = e / sh.nv, v = e % sh.nv;
+    double2 s = slot_sum(part, sh.nslot, stride, row * sh.nb + v);
     if (dvr) {
-      const double V = dvr_V(dk, e / nvec);
+      const double V = dvr_V(dk, row);
       const double2 xv = x[e];
       s.x = fma(V, xv.x, s.x);
       s.y = fma(V, xv.y, s.y);
@@ -66,40 +76,46 @@ __global__ void k_reduce(const C* __restrict__ part, int64_t nslot, int64_t stri
   }
 }
 
-cudaError_t launch_reduce(const Plan& p, const void* part, const double2* x, double2* y, int64_t nvec) {
-  const int64_t n = p.D * nvec, stride = p.dpad * nvec;
+cudaError_t launch_reduce(const Plan& p, const void* part, const double2* x, double2* y, VecShape s) {
+  const int64_t n = p.D * s.nv;
   const int dvr = p.gen == MF_GEN_SINC_DVR_HO;
   if (p.prec == MF_PREC_FP64)
-    k_reduce<double2><<<grid_for(n), 256, 0, p.stream>>>((const double2*)part, p.nslot, stride, n, (int)nvec, dvr,
-                                                         p.dvr, x, y);
+    k_reduce<double2><<<grid_for(n), 256, 0, p.stream>>>((const double2*)part, s, n, dvr, p.dvr, x, y);
   else
-    k_reduce<float2><<<grid_for(n), 256, 0, p.stream>>>((const float2*)part, p.nslot, stride, n, (int)nvec, dvr,
-                                                        p.dvr, x, y);
+    k_reduce<float2><<<grid_for(n), 256, 0, p.stream>>>((const float2*)part, s, n, dvr, p.dvr, x, y);
   return cudaGetLastError();
 }
 
-// Chebyshev (Sec. VII): q0 = psi, acc = a0 q0, compute-format copy of q0.
+// Chebyshev (Sec. VII): q0 = psi, acc = a0 q0, compute-format copy of q0
+// (padding of the copy written as zeros).
 template <typename C>
 __global__ void k_cheb_init(const double2* __restrict__ psi, double2* __restrict__ q, double2* __restrict__ acc,
-                            C* __restrict__ xc, const double* __restrict__ J, int64_t n) {
+                            C* __restrict__ xc, const double* __restrict__ J, int64_t nrow, int64_t nv, int64_t nb) {
   const double a0 = J[0];
+  const int64_t n = nrow * nb;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-    const double2 v = psi[e];
-    q[e] = v;
-    acc[e] = make_double2(a0 * v.x, a0 * v.y);
+    const int64_t row = e / nb, v = e % nb;
     C o;
-    o.x = (decltype(o.x))v.x;
-    o.y = (decltype(o.y))v.y;
+    o.x = 0;
+    o.y = 0;
+    if (v < nv) {
+      const int64_t i = row * nv + v;
+      const double2 a = psi[i];
+      q[i] = a;
+      acc[i] = make_double2(a0 * a.x, a0 * a.y);
+      o.x = (decltype(o.x))a.x;
+      o.y = (decltype(o.y))a.y;
+    }
     xc[e] = o;
   }
 }
 
-cudaError_t launch_cheb_init(const Plan& p, const double2* psi, double2* q, double2* acc, void* xc, int64_t nvec) {
-  const int64_t n = p.D * nvec;
+cudaError_t launch_cheb_init(const Plan& p, const double2* psi, double2* q, double2* acc, void* xc, VecShape s) {
+  const int64_t n = p.D * s.nb;
   if (p.prec == MF_PREC_FP64)
-    k_cheb_init<double2><<<grid_for(n), 256, 0, p.stream>>>(psi, q, acc, (double2*)xc, p.d_J, n);
+    k_cheb_init<double2><<<grid_for(n), 256, 0, p.stream>>>(psi, q, acc, (double2*)xc, p.d_J, p.D, s.nv, s.nb);
   else
-    k_cheb_init<float2><<<grid_for(n), 256, 0, p.stream>>>(psi, q, acc, (float2*)xc, p.d_J, n);
+    k_cheb_init<float2><<<grid_for(n), 256, 0, p.stream>>>(psi, q, acc, (float2*)xc, p.d_J, p.D, s.nv, s.nb);
   return cudaGetLastError();
 }
 
@@ -107,16 +123,19 @@ cudaError_t launch_cheb_init(const Plan& p, const double2* psi, double2* q, doub
 // q_{k+1} = t (k+1 == 1) or 2t - q_{k-1}; acc += a_{k+1} q_{k+1} with
 // a_j = 2 (-i)^j J_j; q_{k+1} overwrites q_{k-1} and its compute copy xc.
 template <typename C>
-__global__ void k_cheb_update(const C* __restrict__ part, int64_t nslot, int64_t stride, int64_t n, int nvec,
-                              int dvr, dvr_consts dk, const double2* __restrict__ qcur,
-                              double2* __restrict__ qprev, double2* __restrict__ acc, C* __restrict__ xc,
-                              const double* __restrict__ J, int32_t j, double c, double R) {
+__global__ void k_cheb_update(const C* __restrict__ part, VecShape sh, int64_t n, int dvr, dvr_consts dk,
+                              const double2* __restrict__ qcur, double2* __restrict__ qprev,
+                              double2* __restrict__ acc, C* __restrict__ xc, const double* __restrict__ J,
+                              int32_t j, double c, double R) {
   const double aj = 2.0 * J[j];
+  const int64_t stride = sh.dpad * sh.nb;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-    double2 y = slot_sum(part, nslot, stride, e);
+    const int64_t row = e / sh.nv, v = e % sh.nv;
+    const int64_t ci = row * sh.nb + v;
+    double2 y = slot_sum(part, sh.nslot, stride, ci);
     const double2 q = qcur[e];
     if (dvr) {
-      const double V = dvr_V(dk, e / nvec);
+      const double V = dvr_V(dk, row);
       y.x = fma(V, q.x, y.x);
       y.y = fma(V, q.y, y.y);
     }
@@ -142,22 +161,20 @@ __global__ void k_cheb_update(const C* __restrict__ part, int64_t nslot, int64_t
     C o;
     o.x = (decltype(o.x))tr;
     o.y = (decltype(o.y))ti;
-    xc[e] = o;
+    xc[ci] = o;
   }
 }
 
 cudaError_t launch_cheb_update(const Plan& p, const void* part, const double2* qcur, double2* qprev, double2* acc,
-                               void* xc, int64_t nvec, int32_t k_next, double c, double R) {
-  const int64_t n = p.D * nvec, stride = p.dpad * nvec;
+                               void* xc, VecShape s, int32_t k_next, double c, double R) {
+  const int64_t n = p.D * s.nv;
   const int dvr = p.gen == MF_GEN_SINC_DVR_HO;
   if (p.prec == MF_PREC_FP64)
-    k_cheb_update<double2><<<grid_for(n), 256, 0, p.stream>>>((const double2*)part, p.nslot, stride, n, (int)nvec,
-                                                              dvr, p.dvr, qcur, qprev, acc, (double2*)xc, p.d_J,
-                                                              k_next, c, R);
+    k_cheb_update<double2><<<grid_for(n), 256, 0, p.stream>>>((const double2*)part, s, n, dvr, p.dvr, qcur, qprev,
+                                                              acc, (double2*)xc, p.d_J, k_next, c, R);
   else
-    k_cheb_update<float2><<<grid_for(n), 256, 0, p.stream>>>((const float2*)part, p.nslot, stride, n, (int)nvec,
-                                                             dvr, p.dvr, qcur, qprev, acc, (float2*)xc, p.d_J,
-                                                             k_next, c, R);
+    k_cheb_update<float2><<<grid_for(n), 256, 0, p.stream>>>((const float2*)part, s, n, dvr, p.dvr, qcur, qprev,
+                                                             acc, (float2*)xc, p.d_J, k_next, c, R);
   return cudaGetLastError();
 }
 
@@ -170,8 +187,7 @@ __global__ void k_cheb_final(const double2* __restrict__ acc, double2* __restric
   }
 }
 
-cudaError_t launch_cheb_final(const Plan& p, const double2* acc, double2* psi, int64_t nvec, double c, double dt) {
-  const int64_t n = p.D * nvec;
+cudaError_t launch_cheb_final(const Plan& p, const double2* acc, double2* psi, int64_t n, double c, double dt) {
   double s, co;
   sincos(c * dt, &s, &co);
   k_cheb_final<<<grid_for(n), 256, 0, p.stream>>>(acc, psi, n, co, -s);

@@ -62,12 +62,21 @@ void release(Plan& p) {
   p.ev.clear();
   free_dev(p.d_cache);
   free_dev(p.d_work);
+  free_dev(p.d_pair_slot);
   free_dev(p.d_part);
   free_dev(p.d_xc);
   for (auto& q : p.d_q) free_dev(q);
   free_dev(p.d_J);
   free_dev(p.d_red);
   free_dev(p.d_err);
+}
+
+// Vector shape of the path used for nvec vectors: the Hermitian or DVR
+// window path for one vector, the row-owner path (padded to a compiled
+// vector count) for several.
+VecShape shape_for(const Plan& p, int64_t nvec) {
+  if (nvec == 1) return VecShape{1, 1, p.nslot, p.dpad};
+  return VecShape{nvec, rows_nvec_bucket(nvec), p.rows_nsplit, p.ntile * (int64_t)kTile};
 }
 
 // Workspace for nvec vectors: partial slots, compute copy, three FP64 vectors.
@@ -77,10 +86,18 @@ mf_status ensure_workspace(Plan& p, int64_t nvec) {
   free_dev(p.d_xc);
   for (auto& q : p.d_q) free_dev(q);
   const size_t eb = compute_elem_bytes(p.prec);
-  const size_t part_bytes = (size_t)p.nslot * (size_t)p.dpad * (size_t)nvec * eb;
-  const size_t xc_bytes = (size_t)std::max(p.dpad, p.D) * (size_t)nvec * eb;
+  const VecShape one = shape_for(p, 1);
+  size_t part_bytes = (size_t)one.nslot * (size_t)one.dpad * eb;
+  size_t rows = (size_t)std::max(one.dpad, p.D);
+  size_t xc_bytes = rows * eb;
+  if (nvec > 1) {
+    const VecShape m = shape_for(p, nvec);
+    part_bytes = std::max(part_bytes, (size_t)m.nslot * (size_t)m.dpad * (size_t)m.nb * eb);
+    xc_bytes = std::max(xc_bytes, (size_t)std::max<int64_t>(m.dpad, p.D) * (size_t)m.nb * eb);
+  }
   MF_CUDA(cudaMalloc(&p.d_part, part_bytes));
   MF_CUDA(cudaMalloc(&p.d_xc, xc_bytes));
+  MF_CUDA(cudaMemset(p.d_xc, 0, xc_bytes));
   for (auto& q : p.d_q) MF_CUDA(cudaMalloc((void**)&q, (size_t)p.D * (size_t)nvec * sizeof(double2)));
   p.nvec_cap = nvec;
   return MF_OK;
@@ -108,10 +125,12 @@ mf_status apply_kernel(Plan& p, int64_t nvec) {
     }
     MF_CUDA(cudaEventRecord(p.ev[p.ev_used].first, p.stream));
   }
-  if (p.use_dvr_window)
-    MF_CUDA(launch_dvr_apply(p, p.d_xc, p.d_part, nvec));
+  if (nvec > 1)
+    MF_CUDA(launch_rows_apply(p, p.d_xc, p.d_part, rows_nvec_bucket(nvec)));
+  else if (p.use_dvr_window)
+    MF_CUDA(launch_dvr_apply(p, p.d_xc, p.d_part, 1));
   else
-    MF_CUDA(launch_gue_apply(p, p.d_xc, p.d_part, nvec));
+    MF_CUDA(launch_gue_apply(p, p.d_xc, p.d_part, 1));
   if (p.profiling) {
     MF_CUDA(cudaEventRecord(p.ev[p.ev_used].second, p.stream));
     ++p.ev_used;
@@ -123,9 +142,10 @@ mf_status apply_kernel(Plan& p, int64_t nvec) {
 mf_status apply_internal(Plan& p, double2* y, const double2* x, int64_t nvec) {
   mf_status st = ensure_workspace(p, nvec);
   if (st != MF_OK) return st;
-  MF_CUDA(launch_to_compute(p, x, p.d_xc, p.D * nvec));
+  const VecShape sh = shape_for(p, nvec);
+  MF_CUDA(launch_to_compute(p, x, p.d_xc, p.D, sh));
   if ((st = apply_kernel(p, nvec)) != MF_OK) return st;
-  MF_CUDA(launch_reduce(p, p.d_part, x, y, nvec));
+  MF_CUDA(launch_reduce(p, p.d_part, x, y, sh));
   return MF_OK;
 }
 
@@ -462,6 +482,20 @@ mf_status mf_plan_create(mf_plan_t* out, int64_t D, int64_t M, int32_t generator
                         p.stream) != cudaSuccess)
       return fail(MF_ERR_CUDA);
   }
+  // multi-vector row-owner path: enough (row tile, column range) CTAs for
+  // two waves, column ranges a multiple of the 32-column chunk
+  {
+    int64_t ns = std::max<int64_t>(1, std::min<int64_t>(64, (2 * (int64_t)p.num_sms + p.ntile - 1) / p.ntile));
+    int64_t cols = ((D + ns - 1) / ns + 31) / 32 * 32;
+    p.rows_split_cols = cols;
+    p.rows_nsplit = (D + cols - 1) / cols;
+  }
+  if (p.pairs_cached > 0) {
+    const size_t nb = p.pair_slot.size() * sizeof(int64_t);
+    if (cudaMalloc((void**)&p.d_pair_slot, nb) != cudaSuccess) return fail(MF_ERR_OOM);
+    if (cudaMemcpyAsync(p.d_pair_slot, p.pair_slot.data(), nb, cudaMemcpyHostToDevice, p.stream) != cudaSuccess)
+      return fail(MF_ERR_CUDA);
+  }
   mf_status st = ensure_workspace(p, nv);
   if (st != MF_OK) return fail(st);
   if (cudaStreamSynchronize(p.stream) != cudaSuccess) return fail(MF_ERR_CUDA);
@@ -484,7 +518,6 @@ mf_status mf_apply(mf_plan_t h, void* y, const void* x, int64_t nvec) {
   const size_t bytes = (size_t)p.D * (size_t)nvec * sizeof(double2);
   const char *yb = (const char*)y, *xb = (const char*)x;
   if (yb < xb + bytes && xb < yb + bytes) return MF_ERR_INVALID;
-  if (nvec != 1) return MF_ERR_UNSUPPORTED;
   DeviceGuard guard(p.device);
   return apply_internal(p, (double2*)y, (const double2*)x, nvec);
 }
@@ -521,7 +554,6 @@ mf_status mf_cheb_terms(mf_plan_t h, double dt, int32_t* nterms) {
 mf_status mf_cheb_propagate(mf_plan_t h, void* psi, int64_t nvec, double dt, int32_t order) {
   if (!h || !psi || nvec < 1 || nvec > 64 || !(dt > 0) || !std::isfinite(dt) || order < 0) return MF_ERR_INVALID;
   Plan& p = h->p;
-  if (nvec != 1) return MF_ERR_UNSUPPORTED;
   DeviceGuard guard(p.device);
   mf_status st = compute_bounds(p);
   if (st != MF_OK) return st;
@@ -531,16 +563,17 @@ mf_status mf_cheb_propagate(mf_plan_t h, void* psi, int64_t nvec, double dt, int
   if (st != MF_OK) return st;
   st = ensure_workspace(p, nvec);
   if (st != MF_OK) return st;
+  const VecShape sh = shape_for(p, nvec);
   double2* q_prev = p.d_q[0];
   double2* q_cur = p.d_q[1];
   double2* acc = p.d_q[2];
-  MF_CUDA(launch_cheb_init(p, (const double2*)psi, q_cur, acc, p.d_xc, nvec));
+  MF_CUDA(launch_cheb_init(p, (const double2*)psi, q_cur, acc, p.d_xc, sh));
   for (int32_t j = 1; j < nt; ++j) {
     if ((st = apply_kernel(p, nvec)) != MF_OK) return st;
-    MF_CUDA(launch_cheb_update(p, p.d_part, q_cur, q_prev, acc, p.d_xc, nvec, j, c, R));
+    MF_CUDA(launch_cheb_update(p, p.d_part, q_cur, q_prev, acc, p.d_xc, sh, j, c, R));
     std::swap(q_cur, q_prev);
   }
-  MF_CUDA(launch_cheb_final(p, acc, (double2*)psi, nvec, c, dt));
+  MF_CUDA(launch_cheb_final(p, acc, (double2*)psi, p.D * nvec, c, dt));
   return MF_OK;
 }
 

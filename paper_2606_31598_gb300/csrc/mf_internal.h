@@ -49,6 +49,9 @@ struct Plan {
   int64_t ntile = 0;              // tile rows = ceil(D / kTile)
   WorkItem* d_work = nullptr;     // canonical tiles, cached/procedural interleaved
   int64_t nwork = 0;
+  // multi-vector row-owner path: split-K over column ranges
+  int64_t rows_nsplit = 1, rows_split_cols = 0;
+  int64_t* d_pair_slot = nullptr;  // device copy of pair_slot
   // DVR launch shape
   int dvr_rows = 512, dvr_cols = 4096;
   // workspace (sized for nvec_cap vectors)
@@ -86,17 +89,25 @@ cudaError_t launch_gue_apply(const Plan& p, const void* xc, void* part, int64_t 
 cudaError_t launch_dvr_apply(const Plan& p, const void* xc, void* part, int64_t nvec);
 // Fill the cache blocks listed in d_pairs (block pair (n, m) per cache slot).
 cudaError_t launch_cache_fill_pairs(const Plan& p, const int2* d_pairs, int64_t npairs);
-// FP64 master -> compute-precision copy.
-cudaError_t launch_to_compute(const Plan& p, const double2* x, void* xc, int64_t n);
+// Multi-vector row-owner apply (nvec bucket 2..64).
+cudaError_t launch_rows_apply(const Plan& p, const void* xc, void* part, int64_t nvec_bucket);
+int64_t rows_nvec_bucket(int64_t nvec);
+
+// Vector layouts: the FP64 master x/y is [D][nv]; the compute copy xc and the
+// partial slots use a padded vector stride nb >= nv ([D][nb], [slot][dpad][nb])
+// with zeros in the padding.  nslot/dpad describe the path in use.
+struct VecShape {
+  int64_t nv, nb, nslot, dpad;
+};
+// FP64 master -> compute-precision copy (padding written as zeros).
+cudaError_t launch_to_compute(const Plan& p, const double2* x, void* xc, int64_t D, VecShape s);
 // y = sum of partial slots (+ V x for the DVR), FP64.
-cudaError_t launch_reduce(const Plan& p, const void* part, const double2* x, double2* y, int64_t nvec);
+cudaError_t launch_reduce(const Plan& p, const void* part, const double2* x, double2* y, VecShape s);
 // Chebyshev pieces.
-cudaError_t launch_cheb_init(const Plan& p, const double2* psi, double2* q, double2* acc, void* xc,
-                             int64_t nvec);
+cudaError_t launch_cheb_init(const Plan& p, const double2* psi, double2* q, double2* acc, void* xc, VecShape s);
 cudaError_t launch_cheb_update(const Plan& p, const void* part, const double2* qcur, double2* qprev,
-                               double2* acc, void* xc, int64_t nvec, int32_t k_next, double c, double R);
-cudaError_t launch_cheb_final(const Plan& p, const double2* acc, double2* psi, int64_t nvec, double c,
-                              double dt);
+                               double2* acc, void* xc, VecShape s, int32_t k_next, double c, double R);
+cudaError_t launch_cheb_final(const Plan& p, const double2* acc, double2* psi, int64_t n, double c, double dt);
 cudaError_t launch_bessel(const Plan& p, double z, int32_t K, double* J);
 // Lanczos helpers: out[0] = Re<a,b>, FP64 reduction into d_red slot.
 cudaError_t launch_dot(const Plan& p, const double2* a, const double2* b, int64_t n, double* out);

@@ -220,3 +220,55 @@ def test_bad_calls_rejected(mf):
         p.cheb_propagate(x, 1, -1.0, 8)
     with pytest.raises(mf.MFError):
         p.set_bounds(1.0, 0.0)
+
+
+# --------------------------------------------------------- multi-vector ----
+@pytest.mark.parametrize("gen", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("nvec", [2, 3, 16, 64])
+def test_multivector_apply_matches_oracle(mf, gen, prec, nvec):
+    """Y = H X (Eq. generic_multivector) by the row-owner kernels, ragged D."""
+    D = 1000
+    p = _plan(mf, D, gen, prec, seed=5, block=256)
+    X = W.random_state(D, nvec, seed=7)
+    Y = _apply(p, X)
+    ref = O.apply(O.make_op(gen, D, seed=5, form=_form(prec)), X, block=256)
+    assert _relerr(Y, ref) < (1e-12 if prec == 0 else 2e-5)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_multivector_cache_modes_bit_identical(mf, prec):
+    D, b, nvec = 1000, 256, 8
+    eb = 16 if prec == 0 else 8
+    X = W.random_state(D, nvec, seed=3)
+    ys = []
+    for storage, budget in [(mf.MF_STORE_PROCEDURAL, 0), (mf.MF_STORE_PARTIAL, 4 * b * b * eb),
+                            (mf.MF_STORE_FULL, 10 * b * b * eb)]:
+        ys.append(_apply(_plan(mf, D, 0, prec, block=b, budget=budget, storage=storage), X))
+    assert np.array_equal(ys[0], ys[1]) and np.array_equal(ys[0], ys[2])
+
+
+def test_multivector_matches_single_vector_columns(mf):
+    """Each column of the multi-vector product equals the one-vector product."""
+    D, nvec = 700, 5
+    p = _plan(mf, D, 0, 0, seed=2)
+    X = W.random_state(D, nvec, seed=9)
+    Y = _apply(p, X)
+    for v in range(nvec):
+        assert _relerr(Y[:, v], _apply(p, np.ascontiguousarray(X[:, v]))) < 1e-13
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_multivector_cheb_matches_oracle(mf, prec):
+    D, nvec = 1024, 4
+    p = _plan(mf, D, 0, prec, seed=4, block=512)
+    emin, emax = p.bounds()
+    H = O.dense(O.make_op(O.GEN_PHILOX_GUE, D, seed=4, form=_form(prec)))
+    X = W.random_state(D, nvec, seed=11)
+    d = _dev(X)
+    p.cheb_propagate(d, nvec, 0.7, 24)
+    torch.cuda.synchronize()
+    out = d.cpu().numpy()
+    c, R = 0.5 * (emax + emin), 0.5 * (emax - emin)
+    ref = O.cheb_step_dense(H, X, 0.7, c, R, 24)
+    assert np.max(np.abs(out - ref)) < (1e-11 if prec == 0 else 2e-5)
