@@ -35,6 +35,7 @@ extern "C" {
 #endif
 
 typedef struct mf_plan* mf_plan_t;
+typedef struct mf_mlp* mf_mlp_t;
 
 typedef enum {
   MF_OK = 0,
@@ -96,7 +97,58 @@ typedef struct {
   int32_t autotune_repeats;/* R_bench (3) */
   double dense_work_limit; /* W_Hpsi threshold in entries for MF_WARN_DENSE_WORK (1e13) */
   int32_t device;          /* CUDA device ordinal (0) */
+  mf_mlp_t model;          /* trained surrogate for MF_PLANNER_LEARNED/_HYBRID (NULL) */
 } mf_options;
+
+/* Generic planning instance P_mv of Sec. IV.A (Y = A X with A of size
+ * D_out x D_in, R simultaneous vectors, n_op operators, N_task independent
+ * tasks, B_c bytes per complex scalar, M_free smallest free memory, N_GPU). */
+typedef struct {
+  int64_t D_out, D_in, R, n_op, N_task;
+  double B_c;
+  double M_free;
+  int32_t N_gpu;
+} mf_problem;
+
+/* One candidate plan of Algorithm 1 (Sec. IV.B). */
+typedef struct {
+  int64_t block;         /* b; 0 = one block of D_in */
+  int32_t storage;       /* MF_STORE_PROCEDURAL, _PARTIAL or _FULL */
+  int64_t pairs_cached;  /* P_cache; -1 derives it from the budget (Eq. partial_cache_pairs) */
+  int32_t p_row;         /* row-group size of Eq. planner_full_cache */
+  int32_t groups;        /* C(p), groups working on independent tasks (Eq. planner_waves) */
+  int32_t r_arrays;      /* r temporaries of size D_in x R (Eq. planner_workspace) */
+} mf_candidate;
+
+/* Throughputs of the runtime model; a zero disables that term. */
+typedef struct {
+  double flops_per_s;       /* contraction rate */
+  double hbm_bytes_per_s;   /* cached-block streaming rate */
+  double gen_entries_per_s; /* procedural entry generation rate */
+} mf_device_model;
+
+/* Algorithm 1 quantities of one candidate. */
+typedef struct {
+  int64_t n_blk, n_pair, pairs_cached, waves;
+  double M_block;  /* B_c b^2 */
+  double M_work;   /* Eq. planner_workspace */
+  double M_op;     /* 0, Eq. planner_partial_cache or Eq. planner_full_cache */
+  double M_tot;    /* Eq. planner_total_memory */
+  double F_mv;     /* Eq. generic_matvec_flops */
+  double T_model;  /* max(generation, streaming, contraction) time, Eq. runtime_overlap */
+  double S_model;  /* W T_model Pi_mem, Eq. planner_cost_score */
+  int32_t feasible;/* Eq. planner_memory_constraint */
+} mf_estimate;
+
+/*
+ * mf_planner_estimate -- evaluate one candidate of the analytic planner
+ * (Algorithm 1) for a planning instance: memory terms, feasibility against
+ * alpha * M_free, arithmetic scale, waves and model score.  Host only, no GPU
+ * needed.  model may be NULL (T_model and S_model are then 0).  Errors:
+ * MF_ERR_INVALID for NULL pointers or out-of-range fields.
+ */
+mf_status mf_planner_estimate(const mf_problem* prob, const mf_candidate* cand, const mf_device_model* model,
+                              double alpha, double cache_budget_bytes, mf_estimate* out);
 
 /* Fill *o with the defaults listed above.  Never fails. */
 void mf_options_default(mf_options* o);
@@ -179,6 +231,53 @@ mf_status mf_plan_profile(mf_plan_t p, int32_t enable);
 /* Synchronise the plan's stream, return the summed event time (ms) and count
  * of the apply-kernel launches timed since the last read, and reset them. */
 mf_status mf_plan_profile_read(mf_plan_t p, double* total_ms, int64_t* launches);
+
+/*
+ * mf_plan_trials -- the plan-trial log of Algorithm 2/3 (Sec. IV.C: hardware
+ * metadata, plan features x(p) and measured t_mv) as JSON lines, one per
+ * candidate considered (measured candidates carry t_mv > 0; the analytic
+ * planner logs its choice with t_mv = -1).  *needed receives the buffer size
+ * including the terminating NUL; buf may be NULL to query it.  MF_ERR_INVALID
+ * when buf is too small (the text is truncated).
+ */
+mf_status mf_plan_trials(mf_plan_t p, char* buf, size_t len, size_t* needed);
+
+/*
+ * Learned surrogate (Sec. IV.C, Algorithm 3): a multilayer perceptron
+ * f(x) = tanh(tanh(z W1 + b1) W2 + b2) W3 + b3, z = (x - mu)/sigma, FP32,
+ * forward/backward/Adam in the library's kernels.  Parameters are one flat
+ * array: W1 [n_in][n_hidden], b1, W2 [n_hidden][n_hidden], b2,
+ * W3 [n_hidden][n_out], b3 (row-major).  Targets are natural logs of
+ * measured times, one output per storage strategy (procedural, partial,
+ * full) for the planner; mask[i][o] = 0 drops an unmeasured target from the
+ * mean-squared error (Eq. nn_loss).  All arrays are HOST memory; calls are
+ * synchronous on the legacy default stream.
+ */
+mf_status mf_mlp_create(mf_mlp_t* out, int32_t n_in, int32_t n_hidden, int32_t n_out, uint64_t seed);
+mf_status mf_mlp_destroy(mf_mlp_t m);
+mf_status mf_mlp_param_count(mf_mlp_t m, int64_t* n);
+/* Copy parameters / normalisation (mu, sigma: n_in floats each) out or in;
+ * any pointer may be NULL. */
+mf_status mf_mlp_get_params(mf_mlp_t m, float* params, float* mu, float* sigma);
+mf_status mf_mlp_set_params(mf_mlp_t m, const float* params, const float* mu, const float* sigma);
+/* Y[n][n_out] = f(X[n][n_in]). */
+mf_status mf_mlp_predict(mf_mlp_t m, const float* X, int64_t n, float* Y);
+/* Masked MSE loss and its gradient (flat, like the parameters) at the
+ * current parameters; mask may be NULL (all ones). */
+mf_status mf_mlp_loss_grad(mf_mlp_t m, const float* X, const float* Y, const float* mask, int64_t n, float* loss,
+                           float* grad);
+/* Full-batch Adam (beta 0.9/0.999, eps 1e-8) for `epochs` steps at rate lr;
+ * set_normalization != 0 first sets mu/sigma to the z-score statistics of X;
+ * loss_curve (epochs floats, may be NULL) receives the loss before each step. */
+mf_status mf_mlp_train(mf_mlp_t m, const float* X, const float* Y, const float* mask, int64_t n, int32_t epochs,
+                       float lr, int32_t set_normalization, float* loss_curve);
+/* The 10-entry feature vector the planner feeds the surrogate for
+ * (generator, precision, D, b, R = nvec, cache budget):
+ * log2 D, log2 b, log2 R, one-hot precision (fp32, bf16x2, fp64), one-hot
+ * generator (philox, dvr), budget / full-cache bytes (capped at 1),
+ * log10(1 + budget/1e9). */
+mf_status mf_mlp_features(int32_t generator, int32_t precision, int64_t D, int64_t block, int64_t nvec,
+                          double cache_budget_bytes, float* out10);
 
 /* Wait for the plan's stream and report any device-side error word. */
 mf_status mf_sync(mf_plan_t p);

@@ -62,7 +62,31 @@ class mf_options(ctypes.Structure):
         ("autotune_repeats", ctypes.c_int32),
         ("dense_work_limit", ctypes.c_double),
         ("device", ctypes.c_int32),
+        ("model", ctypes.c_void_p),
     ]
+
+
+class mf_problem(ctypes.Structure):
+    _fields_ = [("D_out", ctypes.c_int64), ("D_in", ctypes.c_int64), ("R", ctypes.c_int64),
+                ("n_op", ctypes.c_int64), ("N_task", ctypes.c_int64), ("B_c", ctypes.c_double),
+                ("M_free", ctypes.c_double), ("N_gpu", ctypes.c_int32)]
+
+
+class mf_candidate(ctypes.Structure):
+    _fields_ = [("block", ctypes.c_int64), ("storage", ctypes.c_int32), ("pairs_cached", ctypes.c_int64),
+                ("p_row", ctypes.c_int32), ("groups", ctypes.c_int32), ("r_arrays", ctypes.c_int32)]
+
+
+class mf_device_model(ctypes.Structure):
+    _fields_ = [("flops_per_s", ctypes.c_double), ("hbm_bytes_per_s", ctypes.c_double),
+                ("gen_entries_per_s", ctypes.c_double)]
+
+
+class mf_estimate(ctypes.Structure):
+    _fields_ = [("n_blk", ctypes.c_int64), ("n_pair", ctypes.c_int64), ("pairs_cached", ctypes.c_int64),
+                ("waves", ctypes.c_int64), ("M_block", ctypes.c_double), ("M_work", ctypes.c_double),
+                ("M_op", ctypes.c_double), ("M_tot", ctypes.c_double), ("F_mv", ctypes.c_double),
+                ("T_model", ctypes.c_double), ("S_model", ctypes.c_double), ("feasible", ctypes.c_int32)]
 
 
 _lib = None
@@ -93,6 +117,22 @@ def lib():
         L.mf_debug_entries.argtypes = [vp, i64, i64, i64, i64, vp]
         L.mf_apply_dvr_noalloc.argtypes = [i64, d, vp, vp, vp]
         L.mf_plan_profile.argtypes = [vp, i32]
+        L.mf_planner_estimate.argtypes = [P(mf_problem), P(mf_candidate), P(mf_device_model), d, d, P(mf_estimate)]
+        L.mf_plan_trials.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t, P(ctypes.c_size_t)]
+        fp = P(ctypes.c_float)
+        L.mf_mlp_create.argtypes = [P(vp), i32, i32, i32, u64]
+        L.mf_mlp_destroy.argtypes = [vp]
+        L.mf_mlp_param_count.argtypes = [vp, P(i64)]
+        L.mf_mlp_get_params.argtypes = [vp, vp, vp, vp]
+        L.mf_mlp_set_params.argtypes = [vp, vp, vp, vp]
+        L.mf_mlp_predict.argtypes = [vp, vp, i64, vp]
+        L.mf_mlp_loss_grad.argtypes = [vp, vp, vp, vp, i64, vp, vp]
+        L.mf_mlp_train.argtypes = [vp, vp, vp, vp, i64, i32, ctypes.c_float, i32, vp]
+        L.mf_mlp_features.argtypes = [i32, i32, i64, i64, i64, d, vp]
+        for name in ("mf_planner_estimate", "mf_plan_trials", "mf_mlp_create", "mf_mlp_destroy", "mf_mlp_param_count",
+                     "mf_mlp_get_params", "mf_mlp_set_params", "mf_mlp_predict", "mf_mlp_loss_grad", "mf_mlp_train",
+                     "mf_mlp_features"):
+            getattr(L, name).restype = ctypes.c_int
         L.mf_plan_profile_read.argtypes = [vp, P(d), P(i64)]
         for name in ("mf_plan_create", "mf_plan_destroy", "mf_apply", "mf_cheb_propagate", "mf_cheb_terms",
                      "mf_spectral_bounds", "mf_plan_set_bounds", "mf_sync", "mf_plan_describe",
@@ -195,6 +235,102 @@ def mf_apply_dvr_noalloc(D, dvr_L, x, y, stream=None):
                   "mf_apply_dvr_noalloc")
 
 
+def mf_planner_estimate(problem, candidate, model=None, alpha=0.9, cache_budget_bytes=0.0):
+    """Algorithm 1 quantities of one candidate (host only)."""
+    out = mf_estimate()
+    _check(lib().mf_planner_estimate(ctypes.byref(problem), ctypes.byref(candidate),
+                                     ctypes.byref(model) if model is not None else None, float(alpha),
+                                     float(cache_budget_bytes), ctypes.byref(out)), "mf_planner_estimate")
+    return out
+
+
+def mf_plan_trials(plan):
+    """The plan-trial log as a list of dicts (one per candidate)."""
+    need = ctypes.c_size_t()
+    _check(lib().mf_plan_trials(plan, None, 0, ctypes.byref(need)), "mf_plan_trials")
+    buf = ctypes.create_string_buffer(max(1, need.value))
+    _check(lib().mf_plan_trials(plan, buf, len(buf), None), "mf_plan_trials")
+    return [json.loads(l) for l in buf.value.decode().splitlines() if l.strip()]
+
+
+def _fptr(a):
+    return None if a is None else a.ctypes.data
+
+
+class MLP:
+    """The learned planner's surrogate network (host arrays in, host arrays out)."""
+
+    def __init__(self, n_in=10, n_hidden=64, n_out=3, seed=0):
+        import numpy as np
+        self._np = np
+        self.handle = ctypes.c_void_p()
+        _check(lib().mf_mlp_create(ctypes.byref(self.handle), n_in, n_hidden, n_out, seed), "mf_mlp_create")
+        self.n_in, self.n_hidden, self.n_out = n_in, n_hidden, n_out
+        n = ctypes.c_int64()
+        _check(lib().mf_mlp_param_count(self.handle, ctypes.byref(n)), "mf_mlp_param_count")
+        self.n_params = n.value
+
+    def _f32(self, a, shape=None):
+        a = self._np.ascontiguousarray(a, dtype=self._np.float32)
+        return a if shape is None else a.reshape(shape)
+
+    def params(self):
+        np = self._np
+        p = np.zeros(self.n_params, np.float32)
+        mu = np.zeros(self.n_in, np.float32)
+        sd = np.zeros(self.n_in, np.float32)
+        _check(lib().mf_mlp_get_params(self.handle, p.ctypes.data, mu.ctypes.data, sd.ctypes.data), "get_params")
+        return p, mu, sd
+
+    def set_params(self, params=None, mu=None, sd=None):
+        a = [None if v is None else self._f32(v) for v in (params, mu, sd)]
+        _check(lib().mf_mlp_set_params(self.handle, *[_fptr(v) for v in a]), "set_params")
+
+    def predict(self, X):
+        X = self._f32(X, (-1, self.n_in))
+        Y = self._np.zeros((X.shape[0], self.n_out), self._np.float32)
+        _check(lib().mf_mlp_predict(self.handle, X.ctypes.data, X.shape[0], Y.ctypes.data), "predict")
+        return Y
+
+    def loss_grad(self, X, Y, mask=None):
+        X = self._f32(X, (-1, self.n_in))
+        Y = self._f32(Y, (-1, self.n_out))
+        M = None if mask is None else self._f32(mask, (-1, self.n_out))
+        loss = self._np.zeros(1, self._np.float32)
+        g = self._np.zeros(self.n_params, self._np.float32)
+        _check(lib().mf_mlp_loss_grad(self.handle, X.ctypes.data, Y.ctypes.data, _fptr(M), X.shape[0],
+                                      loss.ctypes.data, g.ctypes.data), "loss_grad")
+        return float(loss[0]), g
+
+    def train(self, X, Y, mask=None, epochs=1000, lr=1e-3, set_normalization=True):
+        X = self._f32(X, (-1, self.n_in))
+        Y = self._f32(Y, (-1, self.n_out))
+        M = None if mask is None else self._f32(mask, (-1, self.n_out))
+        curve = self._np.zeros(max(1, epochs), self._np.float32)
+        _check(lib().mf_mlp_train(self.handle, X.ctypes.data, Y.ctypes.data, _fptr(M), X.shape[0], int(epochs),
+                                  float(lr), int(bool(set_normalization)), curve.ctypes.data), "train")
+        return curve[:epochs]
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib().mf_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mf_mlp_features(generator, precision, D, block, nvec, cache_budget_bytes):
+    import numpy as np
+    out = np.zeros(10, np.float32)
+    _check(lib().mf_mlp_features(int(generator), int(precision), int(D), int(block), int(nvec),
+                                 float(cache_budget_bytes), out.ctypes.data), "mf_mlp_features")
+    return out
+
+
 def mf_plan_profile(plan, enable):
     return _check(lib().mf_plan_profile(plan, int(enable)), "mf_plan_profile")
 
@@ -213,6 +349,8 @@ class Plan:
         if "stream" not in opts:
             opts["stream"] = current_stream()
         for k, v in opts.items():
+            if k == "model" and hasattr(v, "handle"):
+                v = v.handle.value
             setattr(o, k, v)
         self.options = o
         self.D = int(D)
@@ -235,6 +373,9 @@ class Plan:
 
     def describe(self):
         return mf_plan_describe(self.handle)
+
+    def trials(self):
+        return mf_plan_trials(self.handle)
 
     def entries(self, r0, c0, rows, cols):
         import numpy as np

@@ -272,64 +272,12 @@ mf_status coefficients(Plan& p, double z, int32_t order, int32_t* nterms) {
   return MF_OK;
 }
 
-const char* gen_name(int g) { return g == MF_GEN_PHILOX_GUE ? "philox_gue" : "sinc_dvr_ho"; }
-const char* prec_name(int g) { return g == MF_PREC_FP64 ? "fp64" : (g == MF_PREC_FP32 ? "fp32" : "bf16x2"); }
-const char* store_name(int s) {
-  return s == MF_STORE_FULL ? "full" : (s == MF_STORE_PARTIAL ? "partial" : "procedural");
-}
-
-}  // namespace
-
-extern "C" {
-
-void mf_options_default(mf_options* o) {
-  if (!o) return;
-  std::memset(o, 0, sizeof(*o));
-  o->precision = MF_PREC_FP32;
-  o->storage = MF_STORE_AUTO;
-  o->planner_mode = MF_PLANNER_ANALYTIC;
-  o->nvec_hint = 1;
-  o->cheb_tol = 1e-7;
-  o->lanczos_m = 40;
-  o->bounds_pad = 0.05;
-  o->dvr_L = 0.0;
-  o->stream = nullptr;
-  o->alpha_safety = 0.9;
-  o->f_cache = 0.8;
-  o->autotune_k = 8;
-  o->autotune_warmup = 1;
-  o->autotune_repeats = 3;
-  o->dense_work_limit = 1e13;
-  o->device = 0;
-}
-
-const char* mf_status_string(mf_status s) {
-  switch (s) {
-    case MF_OK: return "MF_OK";
-    case MF_ERR_INVALID: return "MF_ERR_INVALID";
-    case MF_ERR_OOM: return "MF_ERR_OOM";
-    case MF_ERR_CUDA: return "MF_ERR_CUDA";
-    case MF_ERR_UNSUPPORTED: return "MF_ERR_UNSUPPORTED";
-    case MF_ERR_TIMEOUT: return "MF_ERR_TIMEOUT";
-    case MF_WARN_DENSE_WORK: return "MF_WARN_DENSE_WORK";
-  }
-  return "MF_STATUS_UNKNOWN";
-}
-
-mf_status mf_plan_create(mf_plan_t* out, int64_t D, int64_t M, int32_t generator, uint64_t seed, int64_t block,
-                         size_t cache_budget_bytes, const mf_options* opt) {
-  if (!out) return MF_ERR_INVALID;
+// Build a plan for one explicit candidate: block size b (> 0, multiple of the
+// tile) and storage mode (procedural, partial or full; partial takes
+// P_cache from the budget).  Arguments are validated by the caller.
+mf_status create_fixed(mf_plan_t* out, int64_t D, int32_t generator, uint64_t seed, int64_t block,
+                       size_t cache_budget_bytes, const mf_options& o) {
   *out = nullptr;
-  mf_options o;
-  if (opt) o = *opt; else mf_options_default(&o);
-  if (D < 2 || M != D || D > (int64_t)1 << 31) return MF_ERR_INVALID;
-  if (generator != MF_GEN_PHILOX_GUE && generator != MF_GEN_SINC_DVR_HO) return MF_ERR_INVALID;
-  if (o.precision != MF_PREC_FP64 && o.precision != MF_PREC_FP32 && o.precision != MF_PREC_BF16X2)
-    return MF_ERR_INVALID;
-  if (o.precision == MF_PREC_BF16X2) return MF_ERR_UNSUPPORTED;
-  if (block < 0 || (block > 0 && block % kTile != 0)) return MF_ERR_INVALID;
-  if (o.storage < MF_STORE_AUTO || o.storage > MF_STORE_FULL) return MF_ERR_INVALID;
-  if (!(o.cheb_tol > 0) || o.lanczos_m < 2 || !(o.alpha_safety > 0 && o.alpha_safety <= 1)) return MF_ERR_INVALID;
 
   mf_plan* h = new (std::nothrow) mf_plan();
   if (!h) return MF_ERR_OOM;
@@ -367,7 +315,7 @@ mf_status mf_plan_create(mf_plan_t* out, int64_t D, int64_t M, int32_t generator
 
   // partition (Sec. II / IV.F): b multiple of the tile, at most D rounded up
   const int64_t Dt = (D + kTile - 1) / kTile * kTile;
-  p.b = block > 0 ? std::min(block, Dt) : std::min<int64_t>(Dt, 2048);
+  p.b = std::min(block, Dt);
   p.nblk = (D + p.b - 1) / p.b;
   p.npair = p.nblk * (p.nblk + 1) / 2;
   p.ntile = (D + kTile - 1) / kTile;
@@ -379,15 +327,13 @@ mf_status mf_plan_create(mf_plan_t* out, int64_t D, int64_t M, int32_t generator
   const double blk_bytes = (double)eb * (double)p.b * (double)p.b;
   int64_t pc = (int64_t)std::min<double>((double)p.npair, std::floor((double)budget / blk_bytes));
   int32_t storage = o.storage;
-  if (storage == MF_STORE_AUTO) {
-    // DVR: the Toeplitz-window generator is cheaper than streaming its blocks
-    if (generator == MF_GEN_SINC_DVR_HO) pc = 0;
-    storage = pc == 0 ? MF_STORE_PROCEDURAL : (pc == p.npair ? MF_STORE_FULL : MF_STORE_PARTIAL);
-  } else if (storage == MF_STORE_PROCEDURAL) {
+  if (storage == MF_STORE_PROCEDURAL) {
     pc = 0;
   } else if (storage == MF_STORE_FULL) {
     if (pc < p.npair) return fail(MF_ERR_OOM);
   }
+  if (pc == 0) storage = MF_STORE_PROCEDURAL;
+  else if (pc == p.npair) storage = MF_STORE_FULL;
   p.storage = storage;
   p.pairs_cached = pc;
   p.cache_budget = budget;
@@ -408,7 +354,19 @@ mf_status mf_plan_create(mf_plan_t* out, int64_t D, int64_t M, int32_t generator
     p.nslot = p.ntile;
     p.dpad = p.ntile * kTile;
   }
-  const double m_work = (double)p.nslot * p.dpad * nv * eb + 3.0 * D * nv * 16.0 + (double)p.dpad * nv * eb;
+  // multi-vector row-owner path: enough (row tile, column range) CTAs for
+  // two waves, column ranges a multiple of the 32-column chunk
+  {
+    int64_t ns = std::max<int64_t>(1, std::min<int64_t>(64, (2 * (int64_t)p.num_sms + p.ntile - 1) / p.ntile));
+    int64_t cols = ((D + ns - 1) / ns + 31) / 32 * 32;
+    p.rows_split_cols = cols;
+    p.rows_nsplit = (D + cols - 1) / cols;
+  }
+  const int64_t nbk = nv > 1 ? rows_nvec_bucket(nv) : 1;
+  const double part_b = nv > 1 ? std::max((double)p.nslot * p.dpad, (double)p.rows_nsplit * p.ntile * kTile * nbk)
+                               : (double)p.nslot * p.dpad;
+  const double m_work = part_b * eb + 3.0 * D * nv * 16.0 + (double)std::max(p.dpad, p.ntile * kTile) * nbk * eb;
+  p.m_work = m_work;
   const double m_op = (double)pc * blk_bytes;
   if (m_op + m_work > o.alpha_safety * (double)mfree) {
     if (o.storage == MF_STORE_FULL || o.storage == MF_STORE_PARTIAL) return fail(MF_ERR_OOM);
@@ -482,14 +440,6 @@ mf_status mf_plan_create(mf_plan_t* out, int64_t D, int64_t M, int32_t generator
                         p.stream) != cudaSuccess)
       return fail(MF_ERR_CUDA);
   }
-  // multi-vector row-owner path: enough (row tile, column range) CTAs for
-  // two waves, column ranges a multiple of the 32-column chunk
-  {
-    int64_t ns = std::max<int64_t>(1, std::min<int64_t>(64, (2 * (int64_t)p.num_sms + p.ntile - 1) / p.ntile));
-    int64_t cols = ((D + ns - 1) / ns + 31) / 32 * 32;
-    p.rows_split_cols = cols;
-    p.rows_nsplit = (D + cols - 1) / cols;
-  }
   if (p.pairs_cached > 0) {
     const size_t nb = p.pair_slot.size() * sizeof(int64_t);
     if (cudaMalloc((void**)&p.d_pair_slot, nb) != cudaSuccess) return fail(MF_ERR_OOM);
@@ -501,6 +451,294 @@ mf_status mf_plan_create(mf_plan_t* out, int64_t D, int64_t M, int32_t generator
   if (cudaStreamSynchronize(p.stream) != cudaSuccess) return fail(MF_ERR_CUDA);
   *out = h;
   return p.dense_warn ? MF_WARN_DENSE_WORK : MF_OK;
+}
+
+
+const char* gen_name(int g) { return g == MF_GEN_PHILOX_GUE ? "philox_gue" : "sinc_dvr_ho"; }
+const char* prec_name(int g) { return g == MF_PREC_FP64 ? "fp64" : (g == MF_PREC_FP32 ? "fp32" : "bf16x2"); }
+const char* store_name(int s) {
+  return s == MF_STORE_FULL ? "full" : (s == MF_STORE_PARTIAL ? "partial" : "procedural");
+}
+
+// Measured time of one application (Eq. measured_matvec_time): R_warm
+// untimed applies, then the mean of R_bench applies each bracketed by CUDA
+// events on the plan's stream (synchronised before and after).
+mf_status measure_plan(Plan& p, int64_t nvec, int warm, int reps, double* t_mean) {
+  double2 *x = nullptr, *y = nullptr;
+  const size_t bytes = (size_t)p.D * (size_t)nvec * sizeof(double2);
+  if (cudaMalloc((void**)&x, bytes) != cudaSuccess) return MF_ERR_OOM;
+  if (cudaMalloc((void**)&y, bytes) != cudaSuccess) {
+    cudaFree(x);
+    return MF_ERR_OOM;
+  }
+  cudaEvent_t a = nullptr, b = nullptr;
+  mf_status st = MF_OK;
+  double tot = 0.0;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) st = MF_ERR_CUDA;
+  if (st == MF_OK && launch_random_unit(p, x, p.D * nvec, p.seed + 17) != cudaSuccess) st = MF_ERR_CUDA;
+  for (int i = 0; st == MF_OK && i < warm; ++i) st = apply_internal(p, y, x, nvec);
+  if (st == MF_OK && cudaStreamSynchronize(p.stream) != cudaSuccess) st = MF_ERR_CUDA;
+  for (int i = 0; st == MF_OK && i < reps; ++i) {
+    cudaEventRecord(a, p.stream);
+    st = apply_internal(p, y, x, nvec);
+    cudaEventRecord(b, p.stream);
+    float ms = 0.f;
+    if (st == MF_OK && (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&ms, a, b) != cudaSuccess))
+      st = MF_ERR_CUDA;
+    tot += ms * 1e-3;
+  }
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  cudaFree(x);
+  cudaFree(y);
+  if (st == MF_OK) *t_mean = tot / std::max(1, reps);
+  return st;
+}
+
+// Device throughputs assumed by Algorithm 1 before any measurement: FMA
+// pipe rate of the precision, measured-class HBM rate, and per-generator
+// entry rates (the DVR window makes generation nearly free).
+mf_device_model device_model(int prec, int gen, int num_sms) {
+  mf_device_model m{};
+  const double clk = 1.9e9;
+  m.flops_per_s = prec == MF_PREC_FP64 ? 1.2e12 : (double)num_sms * 128.0 * 2.0 * clk;
+  m.hbm_bytes_per_s = 6.7e12;
+  if (gen == MF_GEN_SINC_DVR_HO) m.gen_entries_per_s = 1e15;
+  else m.gen_entries_per_s = prec == MF_PREC_FP64 ? 1.5e10 : 4.0e11;
+  return m;
+}
+
+std::string trial_json(const Plan& p, const mf_problem& pr, const mf_candidate& c, const mf_estimate& e,
+                       double t_mv, double budget, double gpu_mem) {
+  const char* sn = store_name(c.storage);
+  const double lg = 1.0 / std::log(10.0);
+  char buf[2048];
+  std::snprintf(buf, sizeof(buf),
+                "{\"generator\": \"%s\", \"precision\": \"%s\", \"D\": %lld, \"R\": %lld, \"block\": %lld, "
+                "\"storage\": \"%s\", \"pairs_cached\": %lld, \"n_pair\": %lld, \"budget_bytes\": %.6g, "
+                "\"t_mv\": %.9g, \"T_model\": %.9g, \"S_model\": %.9g, \"M_work\": %.6g, \"M_op\": %.6g, "
+                "\"M_tot\": %.6g, \"M_free\": %.6g, \"F_mv\": %.6g, \"waves\": %lld, \"sms\": %d, "
+                "\"features\": [%.6g, %.6g, %.6g, %.6g, %.6g, %.6g, %d, %lld, %d, %d, %d, 1, 0, 0, %.6g, %.6g, %.6g, "
+                "%.6g, %.6g, %d]}",
+                gen_name(p.gen), prec_name(p.prec), (long long)pr.D_in, (long long)pr.R, (long long)c.block, sn,
+                (long long)e.pairs_cached, (long long)e.n_pair, budget, t_mv, e.T_model, e.S_model, e.M_work,
+                e.M_op, e.M_tot, pr.M_free, e.F_mv, (long long)e.waves, p.num_sms, std::log((double)pr.D_in) * lg,
+                std::log((double)pr.D_out) * lg, std::log((double)pr.R) * lg, std::log((double)e.n_blk) * lg,
+                std::log((double)c.block) * lg, std::log((double)pr.N_task) * lg, c.p_row, (long long)e.waves,
+                c.storage == MF_STORE_FULL, c.storage == MF_STORE_PARTIAL, c.storage == MF_STORE_PROCEDURAL,
+                std::log(e.F_mv) * lg, e.M_op / pr.M_free, e.M_work / pr.M_free, e.M_tot / pr.M_free,
+                gpu_mem / 1e9, p.num_sms);
+  return std::string(buf);
+}
+
+}  // namespace
+
+extern "C" {
+
+void mf_options_default(mf_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = MF_PREC_FP32;
+  o->storage = MF_STORE_AUTO;
+  o->planner_mode = MF_PLANNER_ANALYTIC;
+  o->nvec_hint = 1;
+  o->cheb_tol = 1e-7;
+  o->lanczos_m = 40;
+  o->bounds_pad = 0.05;
+  o->dvr_L = 0.0;
+  o->stream = nullptr;
+  o->alpha_safety = 0.9;
+  o->f_cache = 0.8;
+  o->autotune_k = 8;
+  o->autotune_warmup = 1;
+  o->autotune_repeats = 3;
+  o->dense_work_limit = 1e13;
+  o->device = 0;
+  o->model = nullptr;
+}
+
+const char* mf_status_string(mf_status s) {
+  switch (s) {
+    case MF_OK: return "MF_OK";
+    case MF_ERR_INVALID: return "MF_ERR_INVALID";
+    case MF_ERR_OOM: return "MF_ERR_OOM";
+    case MF_ERR_CUDA: return "MF_ERR_CUDA";
+    case MF_ERR_UNSUPPORTED: return "MF_ERR_UNSUPPORTED";
+    case MF_ERR_TIMEOUT: return "MF_ERR_TIMEOUT";
+    case MF_WARN_DENSE_WORK: return "MF_WARN_DENSE_WORK";
+  }
+  return "MF_STATUS_UNKNOWN";
+}
+
+mf_status mf_plan_create(mf_plan_t* out, int64_t D, int64_t M, int32_t generator, uint64_t seed, int64_t block,
+                         size_t cache_budget_bytes, const mf_options* opt) {
+  if (!out) return MF_ERR_INVALID;
+  *out = nullptr;
+  mf_options o;
+  if (opt) o = *opt; else mf_options_default(&o);
+  if (D < 2 || M != D || D > (int64_t)1 << 31) return MF_ERR_INVALID;
+  if (generator != MF_GEN_PHILOX_GUE && generator != MF_GEN_SINC_DVR_HO) return MF_ERR_INVALID;
+  if (o.precision != MF_PREC_FP64 && o.precision != MF_PREC_FP32 && o.precision != MF_PREC_BF16X2)
+    return MF_ERR_INVALID;
+  if (o.precision == MF_PREC_BF16X2) return MF_ERR_UNSUPPORTED;
+  if (block < 0 || (block > 0 && block % kTile != 0)) return MF_ERR_INVALID;
+  if (o.storage < MF_STORE_AUTO || o.storage > MF_STORE_FULL) return MF_ERR_INVALID;
+  if (o.planner_mode < MF_PLANNER_ANALYTIC || o.planner_mode > MF_PLANNER_HYBRID) return MF_ERR_INVALID;
+  if (!(o.cheb_tol > 0) || o.lanczos_m < 2 || !(o.alpha_safety > 0 && o.alpha_safety <= 1)) return MF_ERR_INVALID;
+  if (o.nvec_hint < 1 || o.nvec_hint > 64 || o.autotune_k < 1 || o.autotune_repeats < 1 || o.autotune_warmup < 0)
+    return MF_ERR_INVALID;
+  if ((o.planner_mode == MF_PLANNER_LEARNED || o.planner_mode == MF_PLANNER_HYBRID) && !o.model)
+    return MF_ERR_INVALID;
+
+  // one explicit candidate: no planning
+  if (block > 0 && o.storage != MF_STORE_AUTO && o.planner_mode == MF_PLANNER_ANALYTIC)
+    return create_fixed(out, D, generator, seed, block, cache_budget_bytes, o);
+
+  DeviceGuard guard(o.device);
+  if (cudaSetDevice(o.device) != cudaSuccess) return MF_ERR_CUDA;
+  int num_sms = 0;
+  if (cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, o.device) != cudaSuccess) return MF_ERR_CUDA;
+  size_t mfree = 0, mtotal = 0;
+  if (cudaMemGetInfo(&mfree, &mtotal) != cudaSuccess) return MF_ERR_CUDA;
+  const double budget = cache_budget_bytes == SIZE_MAX ? o.f_cache * (double)mfree : (double)cache_budget_bytes;
+  const size_t eb = compute_elem_bytes(o.precision);
+
+  // candidate block sizes (Sec. IV.F) and storage modes (Sec. IV.G)
+  const int64_t Dt = (D + kTile - 1) / kTile * kTile;
+  std::vector<int64_t> blocks;
+  if (block > 0) blocks.push_back(std::min(block, Dt));
+  else
+    for (int64_t b = 256; b <= 4096; b *= 2)
+      if (b <= Dt) blocks.push_back(b);
+  if (blocks.empty()) blocks.push_back(Dt);
+  std::vector<int32_t> stores;
+  if (o.storage != MF_STORE_AUTO) stores.push_back(o.storage);
+  else stores = {MF_STORE_PROCEDURAL, MF_STORE_PARTIAL, MF_STORE_FULL};
+
+  mf_problem pr{D, D, o.nvec_hint, 1, 1, (double)eb, (double)mfree, 1};
+  const mf_device_model dm = device_model(o.precision, generator, num_sms);
+  struct Ranked {
+    mf_candidate c;
+    mf_estimate e;
+  };
+  std::vector<Ranked> ranked;
+  for (int64_t b : blocks)
+    for (int32_t st : stores) {
+      mf_candidate c{b, st, -1, 1, 1, 4};
+      mf_estimate e{};
+      planner_estimate(pr, c, dm, o.alpha_safety, budget, e);
+      if (st == MF_STORE_PARTIAL && (e.pairs_cached == 0 || e.pairs_cached == e.n_pair)) continue;
+      if (st == MF_STORE_FULL && (double)e.n_pair * e.M_block > budget) continue;
+      if (!e.feasible && st != MF_STORE_PROCEDURAL) continue;
+      ranked.push_back({c, e});
+    }
+  if (ranked.empty()) return MF_ERR_OOM;
+  std::stable_sort(ranked.begin(), ranked.end(),
+                   [](const Ranked& a, const Ranked& b) { return a.e.S_model < b.e.S_model; });
+
+  auto budget_for = [&](const Ranked& r) -> size_t {
+    if (r.c.storage == MF_STORE_PROCEDURAL) return 0;
+    return (size_t)((double)r.e.pairs_cached * r.e.M_block);
+  };
+  auto build = [&](const Ranked& r, mf_plan_t* h) {
+    mf_options oc = o;
+    oc.storage = r.c.storage;
+    return create_fixed(h, D, generator, seed, r.c.block, budget_for(r), oc);
+  };
+
+  if (o.planner_mode == MF_PLANNER_ANALYTIC) {
+    mf_status st = MF_ERR_OOM;
+    for (const Ranked& r : ranked) {  // best feasible by the model
+      st = build(r, out);
+      if (st == MF_OK || st == MF_WARN_DENSE_WORK) {
+        (*out)->p.s_model = r.e.S_model;
+        (*out)->p.trials.push_back(trial_json((*out)->p, pr, r.c, r.e, -1.0, budget, (double)mtotal));
+        return st;
+      }
+    }
+    return st;
+  }
+
+  // Algorithm 2: measure the K_bench best candidates, keep the fastest job
+  // score S_bench = W t_mv (Eq. bench_score, Eq. bench_argmin); Algorithm 3
+  // (learned/hybrid) reorders the candidates by the surrogate first.
+  if (o.planner_mode == MF_PLANNER_LEARNED || o.planner_mode == MF_PLANNER_HYBRID) {
+    std::vector<double> pred(ranked.size(), 0.0);
+    for (size_t i = 0; i < ranked.size(); ++i) {
+      double t = 0.0;
+      mf_status st = surrogate_predict(o.model, generator, o.precision, pr, ranked[i].c, ranked[i].e, budget,
+                                       (double)mtotal, num_sms, &t);
+      if (st != MF_OK) return st;
+      pred[i] = t * (double)ranked[i].e.waves;
+    }
+    std::vector<size_t> idx(ranked.size());
+    for (size_t i = 0; i < idx.size(); ++i) idx[i] = i;
+    std::stable_sort(idx.begin(), idx.end(), [&](size_t a, size_t b) { return pred[a] < pred[b]; });
+    std::vector<Ranked> re;
+    for (size_t i : idx) re.push_back(ranked[i]);
+    ranked.swap(re);
+    if (o.planner_mode == MF_PLANNER_LEARNED) {
+      mf_status st = MF_ERR_OOM;
+      for (const Ranked& r : ranked) {
+        st = build(r, out);
+        if (st == MF_OK || st == MF_WARN_DENSE_WORK) {
+          (*out)->p.planner_used = MF_PLANNER_LEARNED;
+          (*out)->p.s_model = r.e.S_model;
+          return st;
+        }
+      }
+      return st;
+    }
+  }
+  const size_t K = std::min<size_t>((size_t)o.autotune_k, ranked.size());
+  mf_plan_t best = nullptr;
+  mf_status best_st = MF_ERR_OOM;
+  double best_score = 1e300;
+  std::vector<std::string> log;
+  for (size_t i = 0; i < K; ++i) {
+    mf_plan_t h = nullptr;
+    mf_status st = build(ranked[i], &h);
+    if (st != MF_OK && st != MF_WARN_DENSE_WORK) continue;
+    double t = 0.0;
+    mf_status ms = measure_plan(h->p, o.nvec_hint, o.autotune_warmup, o.autotune_repeats, &t);
+    if (ms != MF_OK) {
+      mf_plan_destroy(h);
+      if (ms == MF_ERR_CUDA) return ms;
+      continue;
+    }
+    log.push_back(trial_json(h->p, pr, ranked[i].c, ranked[i].e, t, budget, (double)mtotal));
+    const double score = (double)ranked[i].e.waves * t;
+    if (score < best_score) {
+      if (best) mf_plan_destroy(best);
+      best = h;
+      best_st = st;
+      best_score = score;
+      best->p.s_model = ranked[i].e.S_model;
+      best->p.t_measured = t;
+    } else {
+      mf_plan_destroy(h);
+    }
+  }
+  if (!best) return MF_ERR_OOM;
+  best->p.trials = log;
+  best->p.planner_used = o.planner_mode;
+  *out = best;
+  return best_st;
+}
+
+mf_status mf_plan_trials(mf_plan_t h, char* buf, size_t len, size_t* needed) {
+  if (!h) return MF_ERR_INVALID;
+  std::string all;
+  for (const auto& t : h->p.trials) {
+    all += t;
+    all += "\n";
+  }
+  if (needed) *needed = all.size() + 1;
+  if (!buf) return MF_OK;
+  if (len == 0) return MF_ERR_INVALID;
+  std::strncpy(buf, all.c_str(), len - 1);
+  buf[len - 1] = '\0';
+  return all.size() + 1 <= len ? MF_OK : MF_ERR_INVALID;
 }
 
 mf_status mf_plan_destroy(mf_plan_t h) {

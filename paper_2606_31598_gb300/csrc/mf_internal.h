@@ -77,6 +77,12 @@ struct Plan {
   bool profiling = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
   size_t ev_used = 0;
+  // planner record: Algorithm 1 score, measured time, trial log (JSON lines)
+  double m_work = 0.0;
+  double s_model = 0.0;
+  double t_measured = -1.0;
+  int32_t planner_used = MF_PLANNER_ANALYTIC;
+  std::vector<std::string> trials;
   // safety estimate (Sec. IV.H)
   double w_hpsi = 0.0;
   bool dense_warn = false;
@@ -120,5 +126,16 @@ cudaError_t launch_debug_entries(const Plan& p, int64_t r0, int64_t c0, int64_t 
                                  void* out);
 
 size_t compute_elem_bytes(int prec);  // bytes of one complex compute-format element
+
+// Surrogate prediction of one candidate's time (k_mlp.cu); model is an mf_mlp.
+mf_status surrogate_predict(void* model, int32_t generator, int32_t precision, const mf_problem& pr,
+                            const mf_candidate& c, const mf_estimate& e, double budget, double gpu_mem, int sms,
+                            double* t);
+void mlp_features(int32_t generator, int32_t precision, const mf_problem& pr, const mf_candidate& c,
+                  const mf_estimate& e, double budget, float* x);
+
+// Algorithm 1 estimate of one candidate (planner.cu).
+void planner_estimate(const mf_problem& pr, const mf_candidate& c, const mf_device_model& dm, double alpha,
+                      double cache_budget, mf_estimate& e);
 
 }  // namespace mf

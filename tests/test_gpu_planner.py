@@ -1,0 +1,98 @@
+"""GPU checks of the planners: the surrogate network's kernels against the FP64
+oracle (gradients, training curve, predictions), the measured autotuner
+(Algorithm 2) and the learned selection (Algorithm 3)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import mlp_oracle as MO
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def mf():
+    import paper_2606_31598_gb300 as mf
+    mf.lib()
+    return mf
+
+
+def _data(n=257, F=10, O=3, seed=0):
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((n, F)).astype(np.float32) * 2 + 1
+    Y = np.stack([np.sin(X[:, 0]) + 0.1 * X[:, 1], X[:, 2] * 0.3 - X[:, 3] * 0.2, np.tanh(X[:, 4])], 1)
+    M = (rng.random((n, O)) > 0.25).astype(np.float32)
+    return X, Y.astype(np.float32), M
+
+
+def test_mlp_gradient_matches_oracle(mf):
+    X, Y, M = _data()
+    net = mf.MLP(10, 64, 3, seed=3)
+    mu, sd = MO.zscore(X)
+    net.set_params(mu=mu, sd=sd)
+    p, mu32, sd32 = net.params()
+    loss, g = net.loss_grad(X, Y, M)
+    lo, go = MO.loss_grad(p.astype(np.float64), mu32.astype(np.float64), sd32.astype(np.float64), X, Y, M, 10, 64, 3)
+    assert abs(loss - lo) < 1e-5 * max(1.0, lo)
+    assert np.max(np.abs(g - go)) < 1e-5 * max(1.0, np.max(np.abs(go)))
+
+
+def test_mlp_prediction_matches_oracle(mf):
+    X, _, _ = _data(seed=4)
+    net = mf.MLP(10, 64, 3, seed=5)
+    p, mu, sd = net.params()
+    ref = MO.forward(p, mu, sd, X, 10, 64, 3)[3]
+    assert np.max(np.abs(net.predict(X) - ref)) < 1e-5
+
+
+def test_mlp_training_curve_matches_oracle(mf):
+    """Same initial parameters and normalisation: the GPU Adam trajectory
+    follows the FP64 trainer within FP32 rounding."""
+    X, Y, M = _data(seed=6)
+    net = mf.MLP(10, 64, 3, seed=7)
+    mu, sd = MO.zscore(X)
+    net.set_params(mu=mu, sd=sd)
+    p0, mu32, sd32 = net.params()
+    curve = net.train(X, Y, M, epochs=150, lr=3e-3, set_normalization=False)
+    _, ref = MO.train_adam(p0, mu32.astype(np.float64), sd32.astype(np.float64), X, Y, M, 10, 64, 3, 150, 3e-3)
+    assert np.max(np.abs(curve - ref) / np.maximum(ref, 1e-3)) < 2e-3
+    assert curve[-1] < 0.2 * curve[0]
+
+
+def test_autotune_measures_and_keeps_the_fastest(mf):
+    D = 4096
+    budget = 10 * 1024 * 1024 * 8  # room for some cached 1024-blocks
+    p = mf.Plan(D, mf.MF_GEN_PHILOX_GUE, seed=1, cache_budget_bytes=budget, precision=mf.MF_PREC_FP32,
+                planner_mode=mf.MF_PLANNER_AUTOTUNE, autotune_k=4, autotune_repeats=2)
+    tr = p.trials()
+    measured = [t for t in tr if t["t_mv"] > 0]
+    assert len(measured) >= 2
+    d = p.describe()
+    best = min(measured, key=lambda t: t["t_mv"])
+    assert (d["block"], d["storage"]) == (best["block"], best["storage"])
+    for t in measured:
+        assert len(t["features"]) == 20
+    # the tuned plan computes the same product as a fixed one
+    x = torch.from_numpy(W.random_state(D, 1, seed=1)).cuda()
+    y1 = torch.empty_like(x)
+    y2 = torch.empty_like(x)
+    p.apply(y1, x, 1)
+    q = mf.Plan(D, mf.MF_GEN_PHILOX_GUE, seed=1, block=512, precision=mf.MF_PREC_FP32, storage=mf.MF_STORE_PROCEDURAL)
+    q.apply(y2, x, 1)
+    torch.cuda.synchronize()
+    a, b = y1.cpu().numpy(), y2.cpu().numpy()
+    assert np.max(np.abs(a - b)) / np.max(np.abs(b)) < 2e-5
+
+
+def test_learned_planner_uses_the_surrogate(mf):
+    """A surrogate that predicts 'procedural is fast, caching is slow' makes
+    the learned planner choose a procedural plan even with budget to spare."""
+    net = mf.MLP(10, 64, 3, seed=11)
+    rng = np.random.default_rng(0)
+    X = rng.uniform(0, 1, (64, 10)).astype(np.float32)
+    Y = np.tile(np.array([[-5.0, 2.0, 2.0]], np.float32), (64, 1))
+    net.train(X, Y, None, epochs=300, lr=1e-2)
+    p = mf.Plan(2048, mf.MF_GEN_PHILOX_GUE, seed=1, cache_budget_bytes=2 ** 30, precision=mf.MF_PREC_FP32,
+                planner_mode=mf.MF_PLANNER_LEARNED, model=net.handle.value)
+    assert p.describe()["storage"] == "procedural"

@@ -1,0 +1,135 @@
+"""Analytic planner (Algorithm 1) and surrogate oracle pins; host only.
+
+Expected values are the paper's printed numbers for its 18-qubit run
+(Sec. VII: block 4096 = 128 MiB in complex64, 32 GiB of operator per GPU in
+a two-GPU row group for two operators, 2.749e11 real FLOP per application,
+20 coupling values over 4 GPU groups = 5 waves, score 5 x 0.104089 s) and the
+definitions of Sec. IV (Eq. partial_cache_pairs and the memory constraint).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import mlp_oracle as MO
+
+
+@pytest.fixture(scope="module")
+def mf():
+    import paper_2606_31598_gb300 as mf
+    from paper_2606_31598_gb300 import _build
+    _build.build()
+    return mf
+
+
+def _est(mf, pr, c, budget=0.0, alpha=0.9, model=None):
+    return mf.mf_planner_estimate(pr, c, model, alpha, budget)
+
+
+def test_paper_18_qubit_storage_flops_and_waves(mf):
+    # d_B = 2^16 bath dimension, R = d_S = 4, n_op = 2 (H_B and B_1), complex64
+    pr = mf.mf_problem(2 ** 16, 2 ** 16, 4, 2, 20, 8.0, 43.97 * 2 ** 30, 8)
+    c = mf.mf_candidate(4096, mf.MF_STORE_FULL, -1, 2, 4, 3)
+    e = _est(mf, pr, c)
+    assert e.n_blk == 16
+    assert e.M_block == 128 * 2 ** 20                 # 4096^2 x 8 B
+    assert e.M_op == 32 * 2 ** 30                     # 2 operators x 16 GiB row slice
+    assert abs(e.F_mv - 2.749e11) / 2.749e11 < 1e-3   # 2 d_S d_B^2 8
+    assert e.waves == 5                               # ceil(20 / 4)
+    assert abs(e.waves * 0.104089 - 0.520447) < 5e-6  # S_bench = W t_mv
+    assert e.feasible == 1
+    # one 16 GiB row slice per operator: 32768 x 65536 x 8 B
+    one = _est(mf, mf.mf_problem(2 ** 16, 2 ** 16, 4, 1, 1, 8.0, 1e12, 1), mf.mf_candidate(4096, 2, -1, 2, 1, 3))
+    assert one.M_op == 32768 * 65536 * 8
+
+
+def test_explicit_dense_sizes(mf):
+    # complex64 D = 2^18: 8 D^2 = 2^39 bytes; complex128: 1 TiB
+    for bc, want in [(8.0, 2 ** 39), (16.0, 2 ** 40)]:
+        pr = mf.mf_problem(2 ** 18, 2 ** 18, 1, 1, 1, bc, 1e15, 1)
+        e = _est(mf, pr, mf.mf_candidate(0, mf.MF_STORE_FULL, -1, 1, 1, 0))
+        assert e.M_op == want and e.M_tot == want
+
+
+def test_partial_cache_pairs_equation(mf):
+    """P_cache = min(N_pair, floor(M_cache / (B_c b^2))) for D = 262144,
+    b = 2048, 120 GB at 8 B per entry: N_pair = 128*129/2 = 8256, 3576 pairs."""
+    pr = mf.mf_problem(262144, 262144, 64, 1, 1, 8.0, 280e9, 1)
+    e = _est(mf, pr, mf.mf_candidate(2048, mf.MF_STORE_PARTIAL, -1, 1, 1, 4), budget=120e9)
+    assert e.n_blk == 128 and e.n_pair == 8256
+    assert e.pairs_cached == math.floor(120e9 / (8 * 2048 ** 2)) == 3576
+    assert e.M_op == 3576 * 2048 ** 2 * 8
+    # budget larger than the operator: all pairs
+    e2 = _est(mf, pr, mf.mf_candidate(2048, mf.MF_STORE_PARTIAL, -1, 1, 1, 4), budget=1e15)
+    assert e2.pairs_cached == 8256
+
+
+def test_memory_constraint_boundary(mf):
+    """Accept iff M_tot <= alpha min M_free (Eq. planner_memory_constraint)."""
+    D, R, bc = 10000, 2, 8.0
+    m_work = 4 * D * R * bc
+    c = mf.mf_candidate(0, mf.MF_STORE_PROCEDURAL, -1, 1, 1, 4)
+    ok = _est(mf, mf.mf_problem(D, D, R, 1, 1, bc, m_work / 0.9, 1), c)
+    bad = _est(mf, mf.mf_problem(D, D, R, 1, 1, bc, m_work / 0.9 * (1 - 1e-9), 1), c)
+    assert ok.M_work == m_work and ok.feasible == 1 and bad.feasible == 0
+
+
+def test_model_score_prefers_cache_for_seeded_and_window_for_dvr(mf):
+    pr = mf.mf_problem(65536, 65536, 1, 1, 1, 8.0, 200e9, 1)
+    gue = mf.mf_device_model(7.4e13, 6.7e12, 4e11)
+    proc = _est(mf, pr, mf.mf_candidate(2048, 0, -1, 1, 1, 4), model=gue, budget=100e9)
+    full = _est(mf, pr, mf.mf_candidate(2048, 2, -1, 1, 1, 4), model=gue, budget=100e9)
+    assert full.S_model < proc.S_model
+    dvr = mf.mf_device_model(7.4e13, 6.7e12, 1e15)
+    proc_d = _est(mf, pr, mf.mf_candidate(2048, 0, -1, 1, 1, 4), model=dvr, budget=100e9)
+    full_d = _est(mf, pr, mf.mf_candidate(2048, 2, -1, 1, 1, 4), model=dvr, budget=100e9)
+    assert proc_d.S_model < full_d.S_model
+
+
+def test_estimate_rejects_bad_input(mf):
+    import ctypes
+    L = mf.lib()
+    e = mf.mf_estimate()
+    pr = mf.mf_problem(0, 10, 1, 1, 1, 8.0, 1e9, 1)
+    c = mf.mf_candidate(0, 0, -1, 1, 1, 1)
+    assert L.mf_planner_estimate(ctypes.byref(pr), ctypes.byref(c), None, 0.9, 0.0, ctypes.byref(e)) == 1
+    pr = mf.mf_problem(10, 10, 1, 1, 1, 8.0, 1e9, 1)
+    assert L.mf_planner_estimate(ctypes.byref(pr), ctypes.byref(c), None, 1.5, 0.0, ctypes.byref(e)) == 1
+
+
+def test_features_vector(mf):
+    f = mf.mf_mlp_features(0, 1, 65536, 2048, 16, 30e9)
+    assert f[0] == 16 and f[1] == 11 and f[2] == 4
+    assert list(f[3:8]) == [1, 0, 0, 1, 0]
+    full = (32 * 33 / 2) * 8 * 2048 ** 2
+    assert abs(f[8] - min(1.0, 30e9 / full)) < 1e-6
+    assert abs(f[9] - math.log10(31.0)) < 1e-6
+
+
+# ------------------------------------------------ surrogate oracle pins ----
+def test_mlp_oracle_gradient_against_finite_differences():
+    rng = np.random.default_rng(0)
+    F, H, O, n = 5, 7, 3, 13
+    p = rng.standard_normal(F * H + H + H * H + H + H * O + O) * 0.4
+    X = rng.standard_normal((n, F))
+    Y = rng.standard_normal((n, O))
+    M = (rng.random((n, O)) > 0.3).astype(float)
+    mu, sd = MO.zscore(X)
+    _, g = MO.loss_grad(p, mu, sd, X, Y, M, F, H, O)
+    h = 1e-6
+    for i in rng.choice(p.size, 40, replace=False):
+        e = np.zeros_like(p)
+        e[i] = h
+        num = (MO.loss_grad(p + e, mu, sd, X, Y, M, F, H, O)[0] - MO.loss_grad(p - e, mu, sd, X, Y, M, F, H, O)[0]) / (2 * h)
+        assert abs(num - g[i]) < 1e-7 * max(1.0, abs(num))
+
+
+def test_mlp_oracle_adam_fits_a_smooth_map():
+    rng = np.random.default_rng(1)
+    F, H, O = 3, 16, 2
+    X = rng.uniform(-1, 1, (200, F))
+    Y = np.stack([np.sin(X[:, 0]) + X[:, 1] ** 2, X[:, 2] * X[:, 0]], 1)
+    p0 = rng.standard_normal(F * H + H + H * H + H + H * O + O) * 0.3
+    mu, sd = MO.zscore(X)
+    _, curve = MO.train_adam(p0, mu, sd, X, Y, None, F, H, O, 600, 1e-2)
+    assert curve[-1] < 0.02 * curve[0]
