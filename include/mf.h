@@ -36,6 +36,7 @@ extern "C" {
 
 typedef struct mf_plan* mf_plan_t;
 typedef struct mf_mlp* mf_mlp_t;
+typedef struct mf_batch* mf_batch_t;
 
 typedef enum {
   MF_OK = 0,
@@ -278,6 +279,34 @@ mf_status mf_mlp_train(mf_mlp_t m, const float* X, const float* Y, const float* 
  * log10(1 + budget/1e9). */
 mf_status mf_mlp_features(int32_t generator, int32_t precision, int64_t D, int64_t block, int64_t nvec,
                           double cache_budget_bytes, float* out10);
+
+/*
+ * Batched independent problems (parameter-parallel execution, Sec. IV.H):
+ * nprob Hermitian problems of the same generator with their own D[i]
+ * (>= 2), nvec[i] (1..16) and seeds[i] are propagated together.  Each
+ * problem is a plan chosen by opt->planner_mode with a share of
+ * cache_budget_bytes proportional to its full canonical cache; its bounds
+ * come from its own Lanczos run.  One persistent kernel per Chebyshev term
+ * applies every problem (work list of (problem, 128-row tile) items drained
+ * through an atomic counter), and the whole propagation is captured once in
+ * a CUDA graph that later calls with the same (psi, dt, nsteps, order)
+ * replay.  psi is ONE device buffer of complex128 holding the problems'
+ * [D[i]][nvec[i]] blocks back to back (element offsets from
+ * mf_batch_offsets, nprob + 1 entries).  The graph runs on the batch's own
+ * stream, ordered after and before opt->stream by events.
+ */
+mf_status mf_batch_create(mf_batch_t* out, int32_t nprob, const int64_t* D, const int32_t* nvec,
+                          const uint64_t* seeds, int32_t generator, size_t cache_budget_bytes,
+                          const mf_options* opt);
+mf_status mf_batch_destroy(mf_batch_t b);
+mf_status mf_batch_offsets(mf_batch_t b, int64_t* offsets);
+/* nsteps Chebyshev steps of dt (order as in mf_cheb_propagate; the largest
+ * per-problem term count is used for all); *nterms_out (may be NULL)
+ * receives the term count.  Asynchronous. */
+mf_status mf_batch_propagate(mf_batch_t b, void* psi, double dt, int32_t nsteps, int32_t order, int32_t* nterms_out);
+/* The plan of problem i (owned by the batch) and launch facts. */
+mf_status mf_batch_plan(mf_batch_t b, int32_t i, mf_plan_t* plan);
+mf_status mf_batch_info(mf_batch_t b, int32_t* n_items, int32_t* persist_grid);
 
 /* Wait for the plan's stream and report any device-side error word. */
 mf_status mf_sync(mf_plan_t p);

@@ -129,6 +129,15 @@ def lib():
         L.mf_mlp_loss_grad.argtypes = [vp, vp, vp, vp, i64, vp, vp]
         L.mf_mlp_train.argtypes = [vp, vp, vp, vp, i64, i32, ctypes.c_float, i32, vp]
         L.mf_mlp_features.argtypes = [i32, i32, i64, i64, i64, d, vp]
+        L.mf_batch_create.argtypes = [P(vp), i32, vp, vp, vp, i32, ctypes.c_size_t, P(mf_options)]
+        L.mf_batch_destroy.argtypes = [vp]
+        L.mf_batch_offsets.argtypes = [vp, vp]
+        L.mf_batch_propagate.argtypes = [vp, vp, d, i32, i32, P(i32)]
+        L.mf_batch_plan.argtypes = [vp, i32, P(vp)]
+        L.mf_batch_info.argtypes = [vp, P(i32), P(i32)]
+        for name in ("mf_batch_create", "mf_batch_destroy", "mf_batch_offsets", "mf_batch_propagate",
+                     "mf_batch_plan", "mf_batch_info"):
+            getattr(L, name).restype = ctypes.c_int
         for name in ("mf_planner_estimate", "mf_plan_trials", "mf_mlp_create", "mf_mlp_destroy", "mf_mlp_param_count",
                      "mf_mlp_get_params", "mf_mlp_set_params", "mf_mlp_predict", "mf_mlp_loss_grad", "mf_mlp_train",
                      "mf_mlp_features"):
@@ -329,6 +338,56 @@ def mf_mlp_features(generator, precision, D, block, nvec, cache_budget_bytes):
     _check(lib().mf_mlp_features(int(generator), int(precision), int(D), int(block), int(nvec),
                                  float(cache_budget_bytes), out.ctypes.data), "mf_mlp_features")
     return out
+
+
+class Batch:
+    """Batched independent problems sharing one persistent launch per term."""
+
+    def __init__(self, Ds, nvecs, seeds, generator, cache_budget_bytes=0, **opts):
+        import numpy as np
+        self._np = np
+        o = mf_options_default()
+        if "stream" not in opts:
+            opts["stream"] = current_stream()
+        for k, v in opts.items():
+            setattr(o, k, v)
+        self.options = o
+        self.Ds = np.ascontiguousarray(Ds, dtype=np.int64)
+        self.nvecs = np.ascontiguousarray(nvecs, dtype=np.int32)
+        sd = np.ascontiguousarray(seeds, dtype=np.uint64)
+        self.handle = ctypes.c_void_p()
+        _check(lib().mf_batch_create(ctypes.byref(self.handle), len(self.Ds), self.Ds.ctypes.data,
+                                     self.nvecs.ctypes.data, sd.ctypes.data, int(generator), int(cache_budget_bytes),
+                                     ctypes.byref(o)), "mf_batch_create")
+        self.offsets = np.zeros(len(self.Ds) + 1, dtype=np.int64)
+        _check(lib().mf_batch_offsets(self.handle, self.offsets.ctypes.data), "mf_batch_offsets")
+
+    def propagate(self, psi, dt, nsteps=1, order=0):
+        nt = ctypes.c_int32()
+        _check(lib().mf_batch_propagate(self.handle, _ptr(psi), float(dt), int(nsteps), int(order), ctypes.byref(nt)),
+               "mf_batch_propagate")
+        return nt.value
+
+    def plan(self, i):
+        h = ctypes.c_void_p()
+        _check(lib().mf_batch_plan(self.handle, int(i), ctypes.byref(h)), "mf_batch_plan")
+        return h
+
+    def info(self):
+        a, b = ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().mf_batch_info(self.handle, ctypes.byref(a), ctypes.byref(b)), "mf_batch_info")
+        return a.value, b.value
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib().mf_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def mf_plan_profile(plan, enable):

@@ -20,10 +20,6 @@
 
 using namespace mf;
 
-struct mf_plan {
-  Plan p;
-};
-
 namespace {
 
 #define MF_CUDA(call)                                      \
@@ -459,6 +455,18 @@ const char* prec_name(int g) { return g == MF_PREC_FP64 ? "fp64" : (g == MF_PREC
 const char* store_name(int s) {
   return s == MF_STORE_FULL ? "full" : (s == MF_STORE_PARTIAL ? "partial" : "procedural");
 }
+
+}  // namespace
+
+namespace mf {
+mf_status plan_workspace(Plan& p, int64_t nvec) { return ensure_workspace(p, nvec); }
+mf_status plan_bounds(Plan& p) { return compute_bounds(p); }
+mf_status plan_coefficients(Plan& p, double z, int32_t order, int32_t* nterms) {
+  return coefficients(p, z, order, nterms);
+}
+}  // namespace mf
+
+namespace {
 
 // Measured time of one application (Eq. measured_matvec_time): R_warm
 // untimed applies, then the mean of R_bench applies each bracketed by CUDA

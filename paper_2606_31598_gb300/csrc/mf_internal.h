@@ -88,6 +88,11 @@ struct Plan {
   bool dense_warn = false;
 };
 
+// Plan services shared with the batched path (mf_api.cu).
+mf_status plan_workspace(Plan& p, int64_t nvec);
+mf_status plan_bounds(Plan& p);
+mf_status plan_coefficients(Plan& p, double z, int32_t order, int32_t* nterms);
+
 // ---- launchers (return cudaError_t of the launch) ----
 // Hermitian canonical-tile apply, nvec == 1 register kernel.
 cudaError_t launch_gue_apply(const Plan& p, const void* xc, void* part, int64_t nvec);
@@ -139,3 +144,8 @@ void planner_estimate(const mf_problem& pr, const mf_candidate& c, const mf_devi
                       double cache_budget, mf_estimate& e);
 
 }  // namespace mf
+
+// The opaque handle of the C ABI.
+struct mf_plan {
+  mf::Plan p;
+};

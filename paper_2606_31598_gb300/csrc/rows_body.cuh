@@ -1,0 +1,174 @@
+// rows_body.cuh -- the row-owner generate-and-apply tile (device code) shared
+// by the split-K launcher (k_rows.cu) and the batched persistent kernel
+// (k_batch.cu): CTAs own a 128-row output tile and sweep a column range in
+// chunks of 32 columns; each chunk of H is generated (canonical entries,
+// conjugates below the diagonal, DVR window table) or copied from the block
+// cache into shared memory and contracted with the chunk's rows of X.
+#pragma once
+#include "mf_internal.h"
+
+namespace mf {
+
+namespace rows {
+
+constexpr int RT = 128;   // rows per CTA
+constexpr int KCH = 32;   // columns per chunk
+constexpr int HPAD = 1;   // pad of the chunk rows (complex elements)
+
+template <typename T> __device__ __forceinline__ typename cplx<T>::t zc() {
+  typename cplx<T>::t z;
+  z.x = T(0);
+  z.y = T(0);
+  return z;
+}
+
+}  // namespace rows
+using namespace rows;
+
+// Generate (or load) H[R0 : R0+RT, c0 : c0+KCH] into hs[RT][KCH+HPAD].
+template <typename T, int GEN, int NT>
+__device__ __forceinline__ void fill_chunk(typename cplx<T>::t* hs, T* win, int64_t R0, int64_t c0, int64_t D,
+                                           uint64_t seed, T sigma, const dvr_consts& dk,
+                                           const typename cplx<T>::t* __restrict__ cache,
+                                           const int64_t* __restrict__ slot_of_pair, int64_t b, int64_t nblk) {
+  using C = typename cplx<T>::t;
+  const int tid = threadIdx.x;
+  constexpr int LD = KCH + HPAD;
+  // cached block pair?  (the chunk lies inside one block pair since b is a
+  // multiple of 128 and chunks are 32-aligned)
+  int64_t slot = -1;
+  bool transposed = false;
+  int64_t n = R0 / b, m = c0 / b;
+  if (cache) {
+    if (n <= m) {
+      slot = slot_of_pair[n * nblk + m];
+    } else {
+      slot = slot_of_pair[m * nblk + n];
+      transposed = true;
+    }
+  }
+  if (slot >= 0) {
+    const int64_t bb = b * b;
+    for (int e = tid; e < RT * KCH; e += NT) {
+      const int r = e / KCH, c = e % KCH;
+      C h;
+      if (!transposed) {
+        h = cache[slot * bb + (R0 + r - n * b) * b + (c0 + c - m * b)];
+      } else {
+        h = cache[slot * bb + (c0 + c - m * b) * b + (R0 + r - n * b)];
+        h.y = -h.y;
+      }
+      hs[r * LD + c] = h;
+    }
+    return;
+  }
+  if (GEN == MF_GEN_SINC_DVR_HO) {
+    // window table: T(k) for k = r - c in (R0 - c0 - KCH, R0 - c0 + RT)
+    const long long kmin = (long long)(R0 - c0) - (KCH - 1);
+    for (int j = tid; j < RT + KCH - 1; j += NT) win[j] = dvr_T(dk, kmin + j, T());
+    __syncthreads();
+    for (int e = tid; e < RT * KCH; e += NT) {
+      const int r = e / KCH, c = e % KCH;
+      C h;
+      h.x = win[r - c + KCH - 1];
+      h.y = T(0);
+      hs[r * LD + c] = h;
+    }
+    return;
+  }
+  if (c0 >= R0 + RT) {
+    // strictly above the diagonal: canonical pairs along rows
+    for (int e = tid; e < RT * (KCH / 2); e += NT) {
+      const int r = e / (KCH / 2), pc = e % (KCH / 2);
+      C h0, h1;
+      gue_pair<T>(seed, sigma, (uint32_t)(R0 + r), (uint32_t)((c0 >> 1) + pc), h0, h1);
+      hs[r * LD + 2 * pc] = h0;
+      hs[r * LD + 2 * pc + 1] = h1;
+    }
+  } else if (c0 + KCH <= R0) {
+    // strictly below: H[r][c] = conj(H[c][r]); canonical row c holds the
+    // pair of columns (rows here) r = 2p, 2p + 1
+    for (int e = tid; e < KCH * (RT / 2); e += NT) {
+      const int c = e / (RT / 2), pr = e % (RT / 2);
+      C h0, h1;
+      gue_pair<T>(seed, sigma, (uint32_t)(c0 + c), (uint32_t)((R0 >> 1) + pr), h0, h1);
+      h0.y = -h0.y;
+      h1.y = -h1.y;
+      hs[(2 * pr) * LD + c] = h0;
+      hs[(2 * pr + 1) * LD + c] = h1;
+    }
+  } else {
+    for (int e = tid; e < RT * KCH; e += NT) {
+      const int r = e / KCH, c = e % KCH;
+      hs[r * LD + c] = gue_entry<T>(seed, sigma, R0 + r, c0 + c);
+    }
+  }
+}
+
+// Y[R0 : R0+RT, :] over columns [cbeg, cend) -> out[row][v] (row-major,
+// NV vectors per row).  Called by all NT threads of the CTA; smem_raw holds
+// rows_smem_bytes<T, NV>() bytes.
+template <typename T, int GEN, int NV, int TR, int TV, int NT>
+__device__ __forceinline__ void row_tile(unsigned char* smem_raw, int64_t R0, int64_t cbeg, int64_t cend, int64_t D,
+                                         uint64_t seed, T sigma, const dvr_consts& dk,
+                                         const typename cplx<T>::t* __restrict__ xc,
+                                         typename cplx<T>::t* __restrict__ out,
+                                         const typename cplx<T>::t* __restrict__ cache,
+                                         const int64_t* __restrict__ slot_of_pair, int64_t b, int64_t nblk) {
+  using C = typename cplx<T>::t;
+  static_assert((RT / TR) * (NV / TV) == NT, "thread blocking must cover the tile");
+  constexpr int LD = KCH + HPAD;
+  C* hs = reinterpret_cast<C*>(smem_raw);      // [RT][LD]
+  C* xs = hs + RT * LD;                         // [KCH][NV]
+  T* win = reinterpret_cast<T*>(xs + KCH * NV);  // [RT + KCH]
+
+  const int tid = threadIdx.x;
+  const int tv = tid % (NV / TV), tr = tid / (NV / TV);
+  const int r0 = tr * TR;  // thread rows r0..r0+TR-1, vectors tv + j*(NV/TV)
+
+  C acc[TR][TV];
+#pragma unroll
+  for (int i = 0; i < TR; ++i)
+#pragma unroll
+    for (int j = 0; j < TV; ++j) acc[i][j] = zc<T>();
+
+  for (int64_t c0 = cbeg; c0 < cend; c0 += KCH) {
+    fill_chunk<T, GEN, NT>(hs, win, R0, c0, D, seed, sigma, dk, cache, slot_of_pair, b, nblk);
+    for (int e = tid; e < KCH * NV; e += NT) {
+      const int64_t c = c0 + e / NV;
+      xs[e] = c < cend ? xc[c * NV + e % NV] : zc<T>();
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int k = 0; k < KCH; ++k) {
+      C h[TR], x[TV];
+#pragma unroll
+      for (int i = 0; i < TR; ++i) h[i] = hs[(r0 + i) * LD + k];
+#pragma unroll
+      for (int j = 0; j < TV; ++j) x[j] = xs[k * NV + tv + j * (NV / TV)];
+#pragma unroll
+      for (int i = 0; i < TR; ++i)
+#pragma unroll
+        for (int j = 0; j < TV; ++j) {
+          acc[i][j].x = fma(h[i].x, x[j].x, acc[i][j].x);
+          acc[i][j].x = fma(-h[i].y, x[j].y, acc[i][j].x);
+          acc[i][j].y = fma(h[i].x, x[j].y, acc[i][j].y);
+          acc[i][j].y = fma(h[i].y, x[j].x, acc[i][j].y);
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < TR; ++i)
+#pragma unroll
+    for (int j = 0; j < TV; ++j) out[(r0 + i) * NV + tv + j * (NV / TV)] = acc[i][j];
+}
+
+template <typename T, int NV>
+__host__ __device__ constexpr size_t rows_smem_bytes() {
+  return sizeof(typename cplx<T>::t) * ((size_t)RT * (KCH + HPAD) + (size_t)KCH * NV) + sizeof(T) * (RT + KCH);
+}
+
+}  // namespace mf
+
+

@@ -1,0 +1,72 @@
+"""Batched independent problems in one persistent launch per term, captured in
+a CUDA graph: every problem's slice must match its own plan's propagation
+and the oracle's recurrence."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def mf():
+    import paper_2606_31598_gb300 as mf
+    mf.lib()
+    return mf
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 3e-5)])
+def test_batch_matches_per_problem_and_oracle(mf, prec, tol):
+    Ds = [1000, 2048, 700, 130, 1536]
+    nv = [1, 3, 16, 2, 5]
+    seeds = [0, 1, 2, 3, 4]
+    b = mf.Batch(Ds, nv, seeds, mf.MF_GEN_PHILOX_GUE, precision=prec)
+    total = int(b.offsets[-1])
+    rng = np.random.default_rng(0)
+    parts = [W.random_state(D, k, seed=10 + i).reshape(D, k) for i, (D, k) in enumerate(zip(Ds, nv))]
+    packed = np.concatenate([p.ravel() for p in parts])
+    assert packed.size == total
+    d = torch.from_numpy(packed.copy()).cuda()
+    dt, nsteps = 0.6, 2
+    nt = b.propagate(d, dt, nsteps)
+    nt2 = b.propagate(d, dt, nsteps)  # graph replay: two more steps
+    torch.cuda.synchronize()
+    assert nt == nt2 and nt > 2
+    out = d.cpu().numpy()
+    for i, (D, k) in enumerate(zip(Ds, nv)):
+        got = out[b.offsets[i]:b.offsets[i + 1]].reshape(D, k)
+        h = b.plan(i)
+        emin, emax = mf.mf_spectral_bounds(h)
+        c, R = 0.5 * (emax + emin), 0.5 * (emax - emin)
+        H = O.dense(O.make_op(O.GEN_PHILOX_GUE, D, seed=seeds[i], form=O.FORM_FP64 if prec == 0 else O.FORM_FP32))
+        ref = parts[i].copy()
+        for _ in range(2 * nsteps):
+            ref = O.cheb_step_dense(H, ref, dt, c, R, nt)
+        assert np.max(np.abs(got - ref)) < tol, (i, np.max(np.abs(got - ref)))
+
+
+def test_batch_dvr_and_workload_draw(mf):
+    """DVR problems and the uneven-problem recipe (a slice of it)."""
+    probs = W.batch_problems(256)
+    Ds = [p[0] for p in probs[:6]]
+    nv = [p[1] for p in probs[:6]]
+    assert all(1024 <= D <= 32768 and D % 128 == 0 for D, _, _ in probs)
+    assert all(1 <= k <= 16 for _, k, _ in probs)
+    b = mf.Batch(Ds, nv, list(range(6)), mf.MF_GEN_SINC_DVR_HO, precision=mf.MF_PREC_FP64)
+    n_items, grid = b.info()
+    assert n_items == sum((D + 127) // 128 for D in Ds) and grid > 0
+    parts = [W.random_state(D, k, seed=i).reshape(D, k) for i, (D, k) in enumerate(zip(Ds, nv))]
+    d = torch.from_numpy(np.concatenate([p.ravel() for p in parts])).cuda()
+    b.propagate(d, 1e-4, 1, 12)
+    torch.cuda.synchronize()
+    out = d.cpu().numpy()
+    for i, (D, k) in enumerate(zip(Ds, nv)):
+        got = out[b.offsets[i]:b.offsets[i + 1]].reshape(D, k)
+        h = b.plan(i)
+        emin, emax = mf.mf_spectral_bounds(h)
+        c, R = 0.5 * (emax + emin), 0.5 * (emax - emin)
+        ref = O.cheb_step(O.make_op(O.GEN_SINC_DVR_HO, D), parts[i], 1e-4, c, R, 12)
+        assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < 1e-11
