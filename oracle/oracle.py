@@ -200,3 +200,48 @@ def cheb_step_dense(H, psi, dt, c, R, nterms):
         q_prev, q = q, qn
         acc = acc + a[k] * q
     return np.exp(-1j * c * dt) * acc
+
+
+# ------------------------------------------------------------- BF16X2 form --
+def bf16_rn(a):
+    """Round float32 values to the nearest bfloat16 (ties to even), returned
+    as float32 (the bfloat16 value widened)."""
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    u = a.view(np.uint32).astype(np.uint64)
+    r = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return r.astype(np.uint32).view(np.float32)
+
+
+def split_bf16(a):
+    """hi = bf16(a), lo = bf16(a - hi), a in float32."""
+    a = np.asarray(a, dtype=np.float32)
+    hi = bf16_rn(a)
+    lo = bf16_rn((a - hi).astype(np.float32))
+    return hi, lo
+
+
+def apply_bf16x2(op, x, H32=None):
+    """y = H x in the BF16X2 form: FP32-form entries and the FP32 copy of x
+    are split into bf16 hi + lo; each real product a*b is taken as
+    a_hi b_hi + a_hi b_lo + a_lo b_hi (the lo*lo term dropped), summed exactly
+    in FP64; the DVR potential is applied in FP64 to the FP64 x.  H32: the
+    FP32-form window of the whole operator (complex64), computed if None."""
+    x = np.asarray(x, dtype=np.complex128)
+    X = x.reshape(op.D, -1)
+    if H32 is None:
+        H32 = window_native(make_op(op.gen, op.D, seed=op.seed, form=FORM_FP32, L=op.L or None), 0, 0, op.D, op.D)
+    Ar_h, Ar_l = split_bf16(H32.real)
+    Ai_h, Ai_l = split_bf16(H32.imag)
+    X32 = X.astype(np.complex64)
+    Xr_h, Xr_l = split_bf16(X32.real)
+    Xi_h, Xi_l = split_bf16(X32.imag)
+    f = lambda a: a.astype(np.float64)
+    def prod(ah, al, bh, bl):
+        return f(ah) @ f(bh) + f(ah) @ f(bl) + f(al) @ f(bh)
+    yr = prod(Ar_h, Ar_l, Xr_h, Xr_l) - prod(Ai_h, Ai_l, Xi_h, Xi_l)
+    yi = prod(Ar_h, Ar_l, Xi_h, Xi_l) + prod(Ai_h, Ai_l, Xr_h, Xr_l)
+    Y = yr + 1j * yi
+    if op.gen == GEN_SINC_DVR_HO:
+        V = np.array([potential(op, i) for i in range(op.D)])
+        Y = Y + V[:, None] * X
+    return Y.reshape(x.shape)

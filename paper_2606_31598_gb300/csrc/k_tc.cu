@@ -1,0 +1,437 @@
+// k_tc.cu -- multi-vector generate-and-apply on the 5th-generation tensor
+// cores (tcgen05, TMEM accumulators), BF16 hi+lo split form.
+//
+// Row-owner form of Y = H X (Sec. IV.A, Eq. generic_multivector; output
+// block rows as in Sec. III.B): a CTA owns 128 output rows and sweeps its
+// column range in chunks of 32 columns.  For every chunk
+//   * all warps generate H[128 x 32] (Philox canonical entries, conjugates
+//     below the diagonal, DVR window table) or read it from the FP32 block
+//     cache, split each real part into bf16 hi + lo and store the four planes
+//     (re hi, re lo, im hi, im lo) straight into shared memory in the
+//     canonical no-swizzle K-major layout the tensor core reads;
+//   * one thread streams the chunk's operand tiles of X (pre-split per apply
+//     into the same layout: B1 = [Re X | Im X], B2 = [-Im X | Re X], hi and
+//     lo) with bulk asynchronous copies completing on an mbarrier;
+//   * the same thread issues twelve tcgen05.mma (two K steps of 16, six split
+//     products each: A_re_hi B1_hi, A_re_hi B1_lo, A_re_lo B1_hi and the same
+//     for A_im with B2) accumulating D[128 x 2 NV] = [Re Y | Im Y] in TMEM;
+//     tcgen05.commit arrives on the stage's mbarrier when they finish.
+// Two shared-memory stages let the generation of chunk k+1 run on the SIMT
+// pipes while the tensor core works on chunk k.  The epilogue reads TMEM
+// with tcgen05.ld and writes the split-K partial slot.  Every wait is
+// bounded; on time-out the kernel records the stage in the plan's error word,
+// drains its own outstanding work (again bounded), frees TMEM and returns.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "rows_body.cuh"
+
+namespace mf {
+namespace tc {
+
+constexpr int RT = 128;          // rows per CTA (MMA M)
+constexpr int KC = 32;           // columns per chunk
+constexpr int NTHREADS = 512;
+constexpr int A_PLANE = RT * KC * 2;  // bytes of one bf16 plane of the chunk (8 KB)
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// byte offset of element (row, k) in a canonical no-swizzle K-major tile
+// whose core matrices (8 rows x 16 bytes) are laid out K-core-fastest:
+// LBO (next K core) = 128 B, SBO (next 8-row group) = 4 * 128 B.
+__device__ __forceinline__ uint32_t kmajor_off(int row, int k) {
+  return (uint32_t)((row >> 3) * 512 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+  const uint64_t lbo = 128 >> 4, sbo = 512 >> 4;
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | (lbo << 16) | (sbo << 32) | (1ull << 46);
+}
+
+// kind::f16 instruction descriptor: D f32, A and B bf16, both K-major,
+// N = n, M = 128.
+__host__ __device__ constexpr uint32_t idesc_bf16(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait; false on time-out
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (uint32_t i = 0; i < kSpinLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+template <int NCOL>
+__device__ __forceinline__ void tmem_load(uint32_t taddr, float* v);
+
+template <>
+__device__ __forceinline__ void tmem_load<4>(uint32_t taddr, float* v) {
+  uint32_t r[4];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <>
+__device__ __forceinline__ void tmem_load<8>(uint32_t taddr, float* v) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <>
+__device__ __forceinline__ void tmem_load<16>(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <>
+__device__ __forceinline__ void tmem_load<32>(uint32_t taddr, float* v) {
+  tmem_load<16>(taddr, v);
+  tmem_load<16>(taddr + 16, v + 16);
+}
+
+// split one complex entry into the four planes at byte offset off
+__device__ __forceinline__ void put_entry(unsigned char* A, uint32_t off, float2 h) {
+  const __nv_bfloat16 rh = __float2bfloat16_rn(h.x);
+  const __nv_bfloat16 rl = __float2bfloat16_rn(h.x - __bfloat162float(rh));
+  const __nv_bfloat16 ih = __float2bfloat16_rn(h.y);
+  const __nv_bfloat16 il = __float2bfloat16_rn(h.y - __bfloat162float(ih));
+  *reinterpret_cast<__nv_bfloat16*>(A + 0 * A_PLANE + off) = rh;
+  *reinterpret_cast<__nv_bfloat16*>(A + 1 * A_PLANE + off) = rl;
+  *reinterpret_cast<__nv_bfloat16*>(A + 2 * A_PLANE + off) = ih;
+  *reinterpret_cast<__nv_bfloat16*>(A + 3 * A_PLANE + off) = il;
+}
+
+// Fill the four A planes of chunk [R0, R0+128) x [c0, c0+32).
+template <int GEN>
+__device__ __forceinline__ void fill_a(unsigned char* A, float* win, int64_t R0, int64_t c0, uint64_t seed,
+                                       float sigma, const dvr_consts& dk, const float2* __restrict__ cache,
+                                       const int64_t* __restrict__ slot_of_pair, int64_t b, int64_t nblk) {
+  const int tid = threadIdx.x;
+  int64_t slot = -1;
+  bool transposed = false;
+  const int64_t n = R0 / b, m = c0 / b;
+  if (cache) {
+    if (n <= m) slot = slot_of_pair[n * nblk + m];
+    else {
+      slot = slot_of_pair[m * nblk + n];
+      transposed = true;
+    }
+  }
+  if (slot >= 0) {
+    const int64_t bb = b * b;
+    if (!transposed) {
+      for (int e = tid; e < RT * KC; e += NTHREADS) {
+        const int r = e / KC, k = e % KC;
+        put_entry(A, kmajor_off(r, k), cache[slot * bb + (R0 + r - n * b) * b + (c0 + k - m * b)]);
+      }
+    } else {
+      for (int e = tid; e < RT * KC; e += NTHREADS) {
+        const int k = e / RT, r = e % RT;  // consecutive threads read consecutive cached columns
+        float2 h = cache[slot * bb + (c0 + k - m * b) * b + (R0 + r - n * b)];
+        h.y = -h.y;
+        put_entry(A, kmajor_off(r, k), h);
+      }
+    }
+    return;
+  }
+  if (GEN == MF_GEN_SINC_DVR_HO) {
+    const long long kmin = (long long)(R0 - c0) - (KC - 1);
+    for (int j = tid; j < RT + KC - 1; j += NTHREADS) win[j] = dvr_T_f32(dk, kmin + j);
+    __syncthreads();
+    for (int e = tid; e < RT * KC; e += NTHREADS) {
+      const int r = e / KC, k = e % KC;
+      put_entry(A, kmajor_off(r, k), make_float2(win[r - k + KC - 1], 0.f));
+    }
+    return;
+  }
+  if (c0 >= R0 + RT) {
+    for (int e = tid; e < RT * (KC / 2); e += NTHREADS) {
+      const int r = e / (KC / 2), pc = e % (KC / 2);
+      float2 h0, h1;
+      gue_pair<float>(seed, sigma, (uint32_t)(R0 + r), (uint32_t)((c0 >> 1) + pc), h0, h1);
+      put_entry(A, kmajor_off(r, 2 * pc), h0);
+      put_entry(A, kmajor_off(r, 2 * pc + 1), h1);
+    }
+  } else if (c0 + KC <= R0) {
+    for (int e = tid; e < KC * (RT / 2); e += NTHREADS) {
+      const int k = e % KC, pr = e / KC;
+      float2 h0, h1;
+      gue_pair<float>(seed, sigma, (uint32_t)(c0 + k), (uint32_t)((R0 >> 1) + pr), h0, h1);
+      h0.y = -h0.y;
+      h1.y = -h1.y;
+      put_entry(A, kmajor_off(2 * pr, k), h0);
+      put_entry(A, kmajor_off(2 * pr + 1, k), h1);
+    }
+  } else {
+    for (int e = tid; e < RT * KC; e += NTHREADS) {
+      const int r = e / KC, k = e % KC;
+      put_entry(A, kmajor_off(r, k), gue_entry<float>(seed, sigma, R0 + r, c0 + k));
+    }
+  }
+}
+
+// Y[R0:R0+128, :] over columns [cbeg, cend) into part[slot][row][NV].
+template <int GEN, int NV>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    tc_rows(int64_t D, int64_t dpad, int64_t split_cols, uint64_t seed, float sigma, dvr_consts dk,
+            const unsigned char* __restrict__ gB, float2* __restrict__ part, const float2* __restrict__ cache,
+            const int64_t* __restrict__ slot_of_pair, int64_t b, int64_t nblk, int* __restrict__ err) {
+  constexpr int N = 2 * NV;             // MMA N: [Re | Im] of NV vectors
+  constexpr int B_TILE = N * KC * 2;    // bytes of one bf16 B tile
+  constexpr int B_CHUNK = 4 * B_TILE;   // B1 hi, B1 lo, B2 hi, B2 lo
+  constexpr int STAGE = 4 * A_PLANE + B_CHUNK;
+  constexpr uint32_t TMEM_COLS = N < 32 ? 32 : N;
+  constexpr uint32_t IDESC = idesc_bf16(N);
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ uint64_t full_bar[2], mma_bar[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+  __shared__ float win[RT + KC];
+
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int64_t R0 = (int64_t)blockIdx.x * RT;
+  const int64_t cbeg = (int64_t)blockIdx.y * split_cols;
+  const int64_t cend = cbeg + split_cols < D ? cbeg + split_cols : D;
+  const int nchunk = (int)((cend - cbeg + KC - 1) / KC);
+
+  if (tid == 0) {
+    mbar_init(&full_bar[0], 1);
+    mbar_init(&full_bar[1], 1);
+    mbar_init(&mma_bar[0], 1);
+    mbar_init(&mma_bar[1], 1);
+    abort_flag = 0;
+    fence_async_smem();
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+
+  int issued = 0;  // chunks whose MMAs were committed (thread 0's view)
+  for (int kc = 0; kc < nchunk; ++kc) {
+    const int s = kc & 1;
+    unsigned char* A = smem + s * STAGE;
+    unsigned char* B = A + 4 * A_PLANE;
+    const int64_t c0 = cbeg + (int64_t)kc * KC;
+    // the stage's previous MMAs (chunk kc - 2) must be done before overwriting
+    if (kc >= 2 && tid == 0) {
+      if (!mbar_wait(&mma_bar[s], (uint32_t)(((kc - 2) >> 1) & 1))) {
+        atomicCAS(err, 0, 100 + s);
+        abort_flag = 1;
+      }
+    }
+    __syncthreads();
+    if (abort_flag) break;
+    if (tid == 0) {
+      mbar_expect_tx(&full_bar[s], (uint32_t)B_CHUNK);
+      bulk_g2s(B, gB + (c0 / KC) * (int64_t)B_CHUNK, (uint32_t)B_CHUNK, &full_bar[s]);
+    }
+    fill_a<GEN>(A, win, R0, c0, seed, sigma, dk, cache, slot_of_pair, b, nblk);
+    fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      if (!mbar_wait(&full_bar[s], (uint32_t)((kc >> 1) & 1))) {
+        atomicCAS(err, 0, 110 + s);
+        abort_flag = 1;
+        mbar_wait(&full_bar[s], (uint32_t)((kc >> 1) & 1));  // one more bounded wait for the copy in flight
+      } else {
+        tc_fence_after();
+        const uint32_t a0 = smem_u32(A), b0 = smem_u32(B);
+#pragma unroll
+        for (int ks = 0; ks < KC / 16; ++ks) {
+          const uint32_t ko = (uint32_t)ks * 256;  // two 8-element K cores of 128 B
+          const uint64_t are_h = smem_desc(a0 + 0 * A_PLANE + ko), are_l = smem_desc(a0 + 1 * A_PLANE + ko);
+          const uint64_t aim_h = smem_desc(a0 + 2 * A_PLANE + ko), aim_l = smem_desc(a0 + 3 * A_PLANE + ko);
+          const uint64_t b1_h = smem_desc(b0 + 0 * B_TILE + ko), b1_l = smem_desc(b0 + 1 * B_TILE + ko);
+          const uint64_t b2_h = smem_desc(b0 + 2 * B_TILE + ko), b2_l = smem_desc(b0 + 3 * B_TILE + ko);
+          const uint32_t acc0 = (kc > 0 || ks > 0) ? 1u : 0u;
+          mma_bf16(tmem, are_h, b1_h, IDESC, acc0);
+          mma_bf16(tmem, are_h, b1_l, IDESC, 1u);
+          mma_bf16(tmem, are_l, b1_h, IDESC, 1u);
+          mma_bf16(tmem, aim_h, b2_h, IDESC, 1u);
+          mma_bf16(tmem, aim_h, b2_l, IDESC, 1u);
+          mma_bf16(tmem, aim_l, b2_h, IDESC, 1u);
+        }
+        mma_commit(&mma_bar[s]);
+        issued = kc + 1;
+      }
+    }
+  }
+  // wait for the last committed chunk (MMAs complete in issue order)
+  __shared__ int s_issued;
+  if (tid == 0) {
+    s_issued = issued;
+    if (issued > 0) {
+      const int last = issued - 1;
+      if (!mbar_wait(&mma_bar[last & 1], (uint32_t)((last >> 1) & 1))) {
+        atomicCAS(err, 0, 120);
+        abort_flag = 1;
+      }
+    }
+  }
+  __syncthreads();
+  tc_fence_after();
+  if (!abort_flag && s_issued == nchunk && nchunk > 0) {
+    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31, columns
+    // (w / 4) * N/4 .. +N/4 of D = [Re Y | Im Y]
+    constexpr int QC = N / 4;
+    const int lane_grp = warp & 3, quarter = warp >> 2;
+    const int row = lane_grp * 32 + (tid & 31);
+    float v[QC];
+    tmem_load<QC>(tmem + ((uint32_t)(lane_grp * 32) << 16) + (uint32_t)(quarter * QC), v);
+    float* out = reinterpret_cast<float*>(part + ((int64_t)blockIdx.y * dpad + R0 + row) * NV);
+#pragma unroll
+    for (int i = 0; i < QC; ++i) {
+      const int col = quarter * QC + i;
+      const int vec = col < NV ? col : col - NV;
+      out[2 * vec + (col < NV ? 0 : 1)] = v[i];
+    }
+  } else if (!abort_flag && nchunk == 0) {
+    // empty column range: the slot is zero
+    for (int e = tid; e < RT * NV; e += NTHREADS)
+      part[((int64_t)blockIdx.y * dpad + R0) * NV + e] = make_float2(0.f, 0.f);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
+// Operand tiles of X for every 32-row chunk: B1 = [Re X | Im X],
+// B2 = [-Im X | Re X] (N = 2 NV columns, row = vector part), split into
+// bf16 hi and lo, K-major canonical layout; rows of X beyond D are zero.
+template <int NV>
+__global__ void tc_split_x(const float2* __restrict__ xc, int64_t D, int64_t nchunk, unsigned char* __restrict__ gB) {
+  constexpr int N = 2 * NV;
+  constexpr int B_TILE = N * KC * 2;
+  const int64_t total = nchunk * KC * N;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = e / (KC * N);
+    const int rem = (int)(e % (KC * N));
+    const int n = rem / KC, k = rem % KC;
+    const int64_t c = q * KC + k;
+    float2 xv = make_float2(0.f, 0.f);
+    const int vec = n < NV ? n : n - NV;
+    if (c < D) xv = xc[c * NV + vec];
+    const float v1 = n < NV ? xv.x : xv.y;   // B1: [Re | Im]
+    const float v2 = n < NV ? -xv.y : xv.x;  // B2: [-Im | Re]
+    unsigned char* base = gB + q * 4 * B_TILE;
+    const uint32_t off = kmajor_off(n, k);
+    const __nv_bfloat16 h1 = __float2bfloat16_rn(v1), h2 = __float2bfloat16_rn(v2);
+    *reinterpret_cast<__nv_bfloat16*>(base + 0 * B_TILE + off) = h1;
+    *reinterpret_cast<__nv_bfloat16*>(base + 1 * B_TILE + off) = __float2bfloat16_rn(v1 - __bfloat162float(h1));
+    *reinterpret_cast<__nv_bfloat16*>(base + 2 * B_TILE + off) = h2;
+    *reinterpret_cast<__nv_bfloat16*>(base + 3 * B_TILE + off) = __float2bfloat16_rn(v2 - __bfloat162float(h2));
+  }
+}
+
+template <int GEN, int NV>
+cudaError_t launch_tc_t(const Plan& p, const void* xc, void* part, void* gB, int* err) {
+  constexpr int N = 2 * NV;
+  constexpr size_t STAGE = 4 * (size_t)A_PLANE + 4 * (size_t)N * KC * 2;
+  const size_t smem = 2 * STAGE;
+  const int64_t nchunk = (p.D + KC - 1) / KC;
+  tc_split_x<NV><<<(unsigned)std::min<int64_t>((nchunk * KC * N + 255) / 256, 65535), 256, 0, p.stream>>>(
+      (const float2*)xc, p.D, nchunk, (unsigned char*)gB);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  auto k = tc_rows<GEN, NV>;
+  e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((unsigned)p.ntile, (unsigned)p.rows_nsplit);
+  k<<<grid, NTHREADS, smem, p.stream>>>(p.D, p.ntile * (int64_t)kTile, p.rows_split_cols, p.seed, p.sigma32, p.dvr,
+                                        (const unsigned char*)gB, (float2*)part,
+                                        p.pairs_cached > 0 ? (const float2*)p.d_cache : nullptr, p.d_pair_slot, p.b,
+                                        p.nblk, err);
+  return cudaGetLastError();
+}
+
+}  // namespace tc
+
+size_t tc_operand_bytes(int64_t D, int64_t nv_bucket) {
+  const int64_t nchunk = (D + tc::KC - 1) / tc::KC;
+  return (size_t)nchunk * 4 * (size_t)(2 * nv_bucket) * tc::KC * 2;
+}
+
+int64_t tc_nvec_bucket(int64_t nvec) {
+  int64_t b = 8;
+  while (b < nvec) b *= 2;
+  return b;
+}
+
+cudaError_t launch_tc_apply(const Plan& p, const void* xc, void* part, void* gB, int64_t nv_bucket) {
+  if (p.rows_split_cols % tc::KC != 0) return cudaErrorInvalidValue;
+  const bool dvr = p.gen == MF_GEN_SINC_DVR_HO;
+  switch (nv_bucket) {
+    case 8: return dvr ? tc::launch_tc_t<MF_GEN_SINC_DVR_HO, 8>(p, xc, part, gB, p.d_err)
+                       : tc::launch_tc_t<MF_GEN_PHILOX_GUE, 8>(p, xc, part, gB, p.d_err);
+    case 16: return dvr ? tc::launch_tc_t<MF_GEN_SINC_DVR_HO, 16>(p, xc, part, gB, p.d_err)
+                        : tc::launch_tc_t<MF_GEN_PHILOX_GUE, 16>(p, xc, part, gB, p.d_err);
+    case 32: return dvr ? tc::launch_tc_t<MF_GEN_SINC_DVR_HO, 32>(p, xc, part, gB, p.d_err)
+                        : tc::launch_tc_t<MF_GEN_PHILOX_GUE, 32>(p, xc, part, gB, p.d_err);
+    case 64: return dvr ? tc::launch_tc_t<MF_GEN_SINC_DVR_HO, 64>(p, xc, part, gB, p.d_err)
+                        : tc::launch_tc_t<MF_GEN_PHILOX_GUE, 64>(p, xc, part, gB, p.d_err);
+  }
+  return cudaErrorNotSupported;
+}
+
+}  // namespace mf

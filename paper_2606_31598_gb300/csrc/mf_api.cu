@@ -61,6 +61,7 @@ void release(Plan& p) {
   free_dev(p.d_pair_slot);
   free_dev(p.d_part);
   free_dev(p.d_xc);
+  free_dev(p.d_tcb);
   for (auto& q : p.d_q) free_dev(q);
   free_dev(p.d_J);
   free_dev(p.d_red);
@@ -71,6 +72,8 @@ void release(Plan& p) {
 // window path for one vector, the row-owner path (padded to a compiled
 // vector count) for several.
 VecShape shape_for(const Plan& p, int64_t nvec) {
+  if (p.prec == MF_PREC_BF16X2)
+    return VecShape{nvec, tc_nvec_bucket(nvec), p.rows_nsplit, p.ntile * (int64_t)kTile};
   if (nvec == 1) return VecShape{1, 1, p.nslot, p.dpad};
   return VecShape{nvec, rows_nvec_bucket(nvec), p.rows_nsplit, p.ntile * (int64_t)kTile};
 }
@@ -80,19 +83,21 @@ mf_status ensure_workspace(Plan& p, int64_t nvec) {
   if (nvec <= p.nvec_cap) return MF_OK;
   free_dev(p.d_part);
   free_dev(p.d_xc);
+  free_dev(p.d_tcb);
   for (auto& q : p.d_q) free_dev(q);
   const size_t eb = compute_elem_bytes(p.prec);
   const VecShape one = shape_for(p, 1);
   size_t part_bytes = (size_t)one.nslot * (size_t)one.dpad * eb;
   size_t rows = (size_t)std::max(one.dpad, p.D);
   size_t xc_bytes = rows * eb;
-  if (nvec > 1) {
+  if (nvec > 1 || p.prec == MF_PREC_BF16X2) {
     const VecShape m = shape_for(p, nvec);
     part_bytes = std::max(part_bytes, (size_t)m.nslot * (size_t)m.dpad * (size_t)m.nb * eb);
     xc_bytes = std::max(xc_bytes, (size_t)std::max<int64_t>(m.dpad, p.D) * (size_t)m.nb * eb);
   }
   MF_CUDA(cudaMalloc(&p.d_part, part_bytes));
   MF_CUDA(cudaMalloc(&p.d_xc, xc_bytes));
+  if (p.prec == MF_PREC_BF16X2) MF_CUDA(cudaMalloc(&p.d_tcb, tc_operand_bytes(p.D, shape_for(p, nvec).nb)));
   MF_CUDA(cudaMemset(p.d_xc, 0, xc_bytes));
   for (auto& q : p.d_q) MF_CUDA(cudaMalloc((void**)&q, (size_t)p.D * (size_t)nvec * sizeof(double2)));
   p.nvec_cap = nvec;
@@ -121,7 +126,9 @@ mf_status apply_kernel(Plan& p, int64_t nvec) {
     }
     MF_CUDA(cudaEventRecord(p.ev[p.ev_used].first, p.stream));
   }
-  if (nvec > 1)
+  if (p.prec == MF_PREC_BF16X2)
+    MF_CUDA(launch_tc_apply(p, p.d_xc, p.d_part, p.d_tcb, tc_nvec_bucket(nvec)));
+  else if (nvec > 1)
     MF_CUDA(launch_rows_apply(p, p.d_xc, p.d_part, rows_nvec_bucket(nvec)));
   else if (p.use_dvr_window)
     MF_CUDA(launch_dvr_apply(p, p.d_xc, p.d_part, 1));
@@ -336,7 +343,7 @@ mf_status create_fixed(mf_plan_t* out, int64_t D, int32_t generator, uint64_t se
 
   // memory feasibility (Eq. planner_memory_constraint): M_op + M_work <= alpha M_free
   const int64_t nv = std::max(1, o.nvec_hint);
-  p.use_dvr_window = generator == MF_GEN_SINC_DVR_HO && pc == 0;
+  p.use_dvr_window = generator == MF_GEN_SINC_DVR_HO && pc == 0 && p.prec != MF_PREC_BF16X2;
   if (p.use_dvr_window) {
     const int P = p.prec == MF_PREC_FP64 ? 8 : 16;
     p.dvr_rows = 32 * P;
@@ -358,8 +365,8 @@ mf_status create_fixed(mf_plan_t* out, int64_t D, int32_t generator, uint64_t se
     p.rows_split_cols = cols;
     p.rows_nsplit = (D + cols - 1) / cols;
   }
-  const int64_t nbk = nv > 1 ? rows_nvec_bucket(nv) : 1;
-  const double part_b = nv > 1 ? std::max((double)p.nslot * p.dpad, (double)p.rows_nsplit * p.ntile * kTile * nbk)
+  const int64_t nbk = p.prec == MF_PREC_BF16X2 ? tc_nvec_bucket(nv) : (nv > 1 ? rows_nvec_bucket(nv) : 1);
+  const double part_b = (nv > 1 || p.prec == MF_PREC_BF16X2) ? std::max((double)p.nslot * p.dpad, (double)p.rows_nsplit * p.ntile * kTile * nbk)
                                : (double)p.nslot * p.dpad;
   const double m_work = part_b * eb + 3.0 * D * nv * 16.0 + (double)std::max(p.dpad, p.ntile * kTile) * nbk * eb;
   p.m_work = m_work;
@@ -588,7 +595,6 @@ mf_status mf_plan_create(mf_plan_t* out, int64_t D, int64_t M, int32_t generator
   if (generator != MF_GEN_PHILOX_GUE && generator != MF_GEN_SINC_DVR_HO) return MF_ERR_INVALID;
   if (o.precision != MF_PREC_FP64 && o.precision != MF_PREC_FP32 && o.precision != MF_PREC_BF16X2)
     return MF_ERR_INVALID;
-  if (o.precision == MF_PREC_BF16X2) return MF_ERR_UNSUPPORTED;
   if (block < 0 || (block > 0 && block % kTile != 0)) return MF_ERR_INVALID;
   if (o.storage < MF_STORE_AUTO || o.storage > MF_STORE_FULL) return MF_ERR_INVALID;
   if (o.planner_mode < MF_PLANNER_ANALYTIC || o.planner_mode > MF_PLANNER_HYBRID) return MF_ERR_INVALID;

@@ -61,6 +61,7 @@ struct Plan {
   bool use_dvr_window = false;    // DVR procedural path (Toeplitz window kernel)
   void* d_part = nullptr;         // [nslot][D][nvec] complex (compute precision)
   void* d_xc = nullptr;           // compute-precision copy of the input
+  void* d_tcb = nullptr;          // BF16X2: split operand tiles of X
   double2* d_q[3] = {nullptr, nullptr, nullptr};  // Chebyshev q_prev, q_cur, acc
   double* d_J = nullptr;          // Bessel J_k(R dt)
   int32_t J_cap = 0;
@@ -103,6 +104,11 @@ cudaError_t launch_cache_fill_pairs(const Plan& p, const int2* d_pairs, int64_t 
 // Multi-vector row-owner apply (nvec bucket 2..64).
 cudaError_t launch_rows_apply(const Plan& p, const void* xc, void* part, int64_t nvec_bucket);
 int64_t rows_nvec_bucket(int64_t nvec);
+// Tensor-core BF16X2 apply (k_tc.cu): vector buckets 8..64, operand tiles of
+// X in gB (tc_operand_bytes bytes).
+cudaError_t launch_tc_apply(const Plan& p, const void* xc, void* part, void* gB, int64_t nv_bucket);
+size_t tc_operand_bytes(int64_t D, int64_t nv_bucket);
+int64_t tc_nvec_bucket(int64_t nvec);
 
 // Vector layouts: the FP64 master x/y is [D][nv]; the compute copy xc and the
 // partial slots use a padded vector stride nb >= nv ([D][nb], [slot][dpad][nb])
