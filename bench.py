@@ -342,15 +342,104 @@ def run_mf(args):
     return 0
 
 
+def time_applies(plan, x, y, nvec, reps):
+    """Mean seconds of one apply (CUDA events on the current stream)."""
+    import torch
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    plan.apply(y, x, nvec)
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(reps):
+        plan.apply(y, x, nvec)
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / 1e3 / reps
+
+
+def run_multivector(args):
+    """Philox ensemble D = 262144, 64 vectors, block 2048, 120 GB partial
+    cache (P_cache = 3576 of 8256 canonical pairs): BF16X2 on tcgen05 against
+    the FP32 and FP64 SIMT forms; Chebyshev steps of dt = 1 (order from tol
+    1e-12) in the BF16X2 form."""
+    import torch
+    import paper_2606_31598_gb300 as mf
+    import workloads as W
+    D, R, B = args.mv_dim, 64, 2048
+    nblk = (D + B - 1) // B
+    # the same cached fraction of canonical pairs as 120 GB at D = 262144
+    BUDGET = int(120e9 if D == 262144 else 3576 / 8256 * nblk * (nblk + 1) / 2 * B * B * 8 + 1)
+    stream = torch.cuda.current_stream().cuda_stream
+    X = torch.from_numpy(W.random_state(D, R, seed=2)).cuda()
+    Y = torch.empty_like(X)
+    out = {"workload": "Philox GUE D=%d, 64 vectors, block 2048, %.1f GB partial cache" % (D, BUDGET / 1e9)}
+    plan = mf.Plan(D, mf.MF_GEN_PHILOX_GUE, seed=1, block=B, cache_budget_bytes=BUDGET, precision=mf.MF_PREC_BF16X2,
+                   storage=mf.MF_STORE_PARTIAL, nvec_hint=R, stream=stream, cheb_tol=1e-12)
+    desc = plan.describe()
+    t_bf = time_applies(plan, X, Y, R, 3)
+    Ybf = Y.clone()
+    plan.profile(True)
+    psi = X.clone()
+    for _ in range(args.warmup):
+        plan.cheb_propagate(psi, R, 1.0, 0)
+    torch.cuda.synchronize()
+    plan.profile_read()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        plan.cheb_propagate(psi, R, 1.0, 0)
+    e1.record()
+    torch.cuda.synchronize()
+    kern_ms, kern_n = plan.profile_read()
+    t_steps = e0.elapsed_time(e1) / 1e3
+    nterms = plan.cheb_terms(1.0)
+    plan.close()
+    p32 = mf.Plan(D, mf.MF_GEN_PHILOX_GUE, seed=1, block=B, cache_budget_bytes=BUDGET, precision=mf.MF_PREC_FP32,
+                  storage=mf.MF_STORE_PARTIAL, nvec_hint=R, stream=stream)
+    t_32 = time_applies(p32, X, Y, R, 1)
+    Y32 = Y.clone()
+    p32.close()
+    entries = float(D) * D * R
+    flops_tc = 24.0 * D * D * R  # 3 split products x 8 real FLOP per complex MAC
+    out.update({
+        "plan": desc, "nterms_per_step": nterms,
+        "bf16x2": {"apply_s": t_bf, "entries_per_s": entries / t_bf, "tensor_tflops": flops_tc / t_bf / 1e12,
+                   "kernel_ms": kern_ms / max(1, kern_n),
+                   "cheb_steps_per_s": args.steps / t_steps, "cheb_terms_per_s": args.steps * (nterms - 1) / t_steps},
+        "fp32": {"apply_s": t_32, "entries_per_s": entries / t_32},
+        "speedup_bf16x2_vs_fp32": t_32 / t_bf,
+        "bf16x2_vs_fp32_rel": float((Ybf - Y32).abs().max() / Y32.abs().max()),
+    })
+    if args.fp64:
+        p64 = mf.Plan(D, mf.MF_GEN_PHILOX_GUE, seed=1, block=B, precision=mf.MF_PREC_FP64,
+                      storage=mf.MF_STORE_PROCEDURAL, nvec_hint=R, stream=stream)
+        t_64 = time_applies(p64, X, Y, R, 1)
+        p64.close()
+        m = Y.abs().max()
+        out["fp64_procedural"] = {"apply_s": t_64, "entries_per_s": entries / t_64}
+        out["bf16x2"]["err_vs_fp64_form"] = float((Ybf - Y).abs().max() / m)
+        out["fp32"]["err_vs_fp64_form"] = float((Y32 - Y).abs().max() / m)
+        out["speedup_bf16x2_vs_fp64_procedural"] = t_64 / t_bf
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mf", choices=["mf", "reference"])
+    ap.add_argument("--workload", default="dvr", choices=["dvr", "multivector"],
+                    help="dvr: the benchmark line; multivector: the 64-vector tensor-core workload report")
+    ap.add_argument("--fp64", action="store_true", help="multivector: also time the FP64 procedural form")
+    ap.add_argument("--mv-dim", type=int, default=262144, help="multivector: D (smaller D keeps the cached fraction)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "multivector":
+        return run_multivector(args)
     return run_mf(args)
 
 

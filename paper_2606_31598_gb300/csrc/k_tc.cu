@@ -34,6 +34,11 @@ constexpr int KC = 32;           // columns per chunk
 constexpr int NTHREADS = 512;
 constexpr int A_PLANE = RT * KC * 2;  // bytes of one bf16 plane of the chunk (8 KB)
 constexpr uint32_t kSpinLimit = 1u << 22;
+// The tensor core's FP32 accumulation is not round-to-nearest over long
+// chains, so TMEM accumulates SEG chunks (SEG * 12 MMAs) at a time and is
+// then drained into an FP32 accumulator in shared memory with ordinary
+// round-to-nearest adds.
+constexpr int SEG = 32;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -143,24 +148,57 @@ __device__ __forceinline__ void tmem_load<32>(uint32_t taddr, float* v) {
   tmem_load<16>(taddr + 16, v + 16);
 }
 
-// split one complex entry into the four planes at byte offset off
-__device__ __forceinline__ void put_entry(unsigned char* A, uint32_t off, float2 h) {
-  const __nv_bfloat16 rh = __float2bfloat16_rn(h.x);
-  const __nv_bfloat16 rl = __float2bfloat16_rn(h.x - __bfloat162float(rh));
-  const __nv_bfloat16 ih = __float2bfloat16_rn(h.y);
-  const __nv_bfloat16 il = __float2bfloat16_rn(h.y - __bfloat162float(ih));
-  *reinterpret_cast<__nv_bfloat16*>(A + 0 * A_PLANE + off) = rh;
-  *reinterpret_cast<__nv_bfloat16*>(A + 1 * A_PLANE + off) = rl;
-  *reinterpret_cast<__nv_bfloat16*>(A + 2 * A_PLANE + off) = ih;
-  *reinterpret_cast<__nv_bfloat16*>(A + 3 * A_PLANE + off) = il;
+// Split two complex entries into bf16 hi + lo of their real and imaginary
+// parts; plane p of the pair is word[p] (lower address = first entry).
+__device__ __forceinline__ void split_pair(float2 h0, float2 h1, uint32_t* w) {
+  const __nv_bfloat16 a_rh = __float2bfloat16_rn(h0.x), b_rh = __float2bfloat16_rn(h1.x);
+  const __nv_bfloat16 a_ih = __float2bfloat16_rn(h0.y), b_ih = __float2bfloat16_rn(h1.y);
+  const __nv_bfloat16 a_rl = __float2bfloat16_rn(h0.x - __bfloat162float(a_rh));
+  const __nv_bfloat16 b_rl = __float2bfloat16_rn(h1.x - __bfloat162float(b_rh));
+  const __nv_bfloat16 a_il = __float2bfloat16_rn(h0.y - __bfloat162float(a_ih));
+  const __nv_bfloat16 b_il = __float2bfloat16_rn(h1.y - __bfloat162float(b_ih));
+  auto pk = [](__nv_bfloat16 a, __nv_bfloat16 b) {
+    return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+  };
+  w[0] = pk(a_rh, b_rh);
+  w[1] = pk(a_rl, b_rl);
+  w[2] = pk(a_ih, b_ih);
+  w[3] = pk(a_il, b_il);
 }
 
-// Fill the four A planes of chunk [R0, R0+128) x [c0, c0+32).
+// entries (r, k) and (r, k + 1), k even: one 32-bit store per plane
+__device__ __forceinline__ void put_hpair(unsigned char* A, int r, int k, float2 h0, float2 h1) {
+  uint32_t w[4];
+  split_pair(h0, h1, w);
+  const uint32_t off = kmajor_off(r, k);
+#pragma unroll
+  for (int pl = 0; pl < 4; ++pl) *reinterpret_cast<uint32_t*>(A + pl * A_PLANE + off) = w[pl];
+}
+
+// entries (r, k) and (r + 1, k), r even: two 16-bit stores per plane
+__device__ __forceinline__ void put_vpair(unsigned char* A, int r, int k, float2 h0, float2 h1) {
+  uint32_t w[4];
+  split_pair(h0, h1, w);
+  const uint32_t off = kmajor_off(r, k);
+#pragma unroll
+  for (int pl = 0; pl < 4; ++pl) {
+    *reinterpret_cast<uint16_t*>(A + pl * A_PLANE + off) = (uint16_t)(w[pl] & 0xFFFFu);
+    *reinterpret_cast<uint16_t*>(A + pl * A_PLANE + off + 16) = (uint16_t)(w[pl] >> 16);
+  }
+}
+
+// Fill the four A planes of chunk [R0, R0+128) x [c0, c0+32).  Warp w covers
+// the 8-row group w (16 groups) and, per K core kc (4 cores of 8 columns),
+// one 8 x 8 core matrix: horizontal pairs with lane -> (row lane/4, columns
+// 2 (lane%4), +1), vertical pairs with lane -> (rows 2 (lane%4), +1, column
+// lane/4); both keep a warp's stores inside one 128-byte core matrix.
 template <int GEN>
 __device__ __forceinline__ void fill_a(unsigned char* A, float* win, int64_t R0, int64_t c0, uint64_t seed,
                                        float sigma, const dvr_consts& dk, const float2* __restrict__ cache,
                                        const int64_t* __restrict__ slot_of_pair, int64_t b, int64_t nblk) {
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, g = tid >> 5;
+  const int hr = 8 * g + (lane >> 2), hk = 2 * (lane & 3);   // horizontal pair origin within a K core
+  const int vr = 8 * g + 2 * (lane & 3), vk = lane >> 2;     // vertical pair origin within a K core
   int64_t slot = -1;
   bool transposed = false;
   const int64_t n = R0 / b, m = c0 / b;
@@ -172,19 +210,24 @@ __device__ __forceinline__ void fill_a(unsigned char* A, float* win, int64_t R0,
     }
   }
   if (slot >= 0) {
-    const int64_t bb = b * b;
+    const float2* blk = cache + slot * b * b;
+    float4 q[4];
     if (!transposed) {
-      for (int e = tid; e < RT * KC; e += NTHREADS) {
-        const int r = e / KC, k = e % KC;
-        put_entry(A, kmajor_off(r, k), cache[slot * bb + (R0 + r - n * b) * b + (c0 + k - m * b)]);
-      }
+      // H[r][k], H[r][k+1] adjacent in the cached row: one 16-byte load
+#pragma unroll
+      for (int kc = 0; kc < 4; ++kc)
+        q[kc] = *reinterpret_cast<const float4*>(blk + (R0 + hr - n * b) * b + (c0 + 8 * kc + hk - m * b));
+#pragma unroll
+      for (int kc = 0; kc < 4; ++kc)
+        put_hpair(A, hr, 8 * kc + hk, make_float2(q[kc].x, q[kc].y), make_float2(q[kc].z, q[kc].w));
     } else {
-      for (int e = tid; e < RT * KC; e += NTHREADS) {
-        const int k = e / RT, r = e % RT;  // consecutive threads read consecutive cached columns
-        float2 h = cache[slot * bb + (c0 + k - m * b) * b + (R0 + r - n * b)];
-        h.y = -h.y;
-        put_entry(A, kmajor_off(r, k), h);
-      }
+      // H[r][k] = conj(C[k][r]): rows r, r+1 adjacent in the cached row k
+#pragma unroll
+      for (int kc = 0; kc < 4; ++kc)
+        q[kc] = *reinterpret_cast<const float4*>(blk + (c0 + 8 * kc + vk - m * b) * b + (R0 + vr - n * b));
+#pragma unroll
+      for (int kc = 0; kc < 4; ++kc)
+        put_vpair(A, vr, 8 * kc + vk, make_float2(q[kc].x, -q[kc].y), make_float2(q[kc].z, -q[kc].w));
     }
     return;
   }
@@ -192,34 +235,39 @@ __device__ __forceinline__ void fill_a(unsigned char* A, float* win, int64_t R0,
     const long long kmin = (long long)(R0 - c0) - (KC - 1);
     for (int j = tid; j < RT + KC - 1; j += NTHREADS) win[j] = dvr_T_f32(dk, kmin + j);
     __syncthreads();
-    for (int e = tid; e < RT * KC; e += NTHREADS) {
-      const int r = e / KC, k = e % KC;
-      put_entry(A, kmajor_off(r, k), make_float2(win[r - k + KC - 1], 0.f));
+#pragma unroll
+    for (int kc = 0; kc < 4; ++kc) {
+      const int k = 8 * kc + hk;
+      put_hpair(A, hr, k, make_float2(win[hr - k + KC - 1], 0.f), make_float2(win[hr - k - 1 + KC - 1], 0.f));
     }
     return;
   }
   if (c0 >= R0 + RT) {
-    for (int e = tid; e < RT * (KC / 2); e += NTHREADS) {
-      const int r = e / (KC / 2), pc = e % (KC / 2);
+    // above the diagonal: canonical pairs along rows
+#pragma unroll
+    for (int kc = 0; kc < 4; ++kc) {
+      const int k = 8 * kc + hk;
       float2 h0, h1;
-      gue_pair<float>(seed, sigma, (uint32_t)(R0 + r), (uint32_t)((c0 >> 1) + pc), h0, h1);
-      put_entry(A, kmajor_off(r, 2 * pc), h0);
-      put_entry(A, kmajor_off(r, 2 * pc + 1), h1);
+      gue_pair<float>(seed, sigma, (uint32_t)(R0 + hr), (uint32_t)((c0 + k) >> 1), h0, h1);
+      put_hpair(A, hr, k, h0, h1);
     }
   } else if (c0 + KC <= R0) {
-    for (int e = tid; e < KC * (RT / 2); e += NTHREADS) {
-      const int k = e % KC, pr = e / KC;
+    // below: the canonical row c0 + k holds the pair of columns R0 + r, +1
+#pragma unroll
+    for (int kc = 0; kc < 4; ++kc) {
+      const int k = 8 * kc + vk;
       float2 h0, h1;
-      gue_pair<float>(seed, sigma, (uint32_t)(c0 + k), (uint32_t)((R0 >> 1) + pr), h0, h1);
+      gue_pair<float>(seed, sigma, (uint32_t)(c0 + k), (uint32_t)((R0 + vr) >> 1), h0, h1);
       h0.y = -h0.y;
       h1.y = -h1.y;
-      put_entry(A, kmajor_off(2 * pr, k), h0);
-      put_entry(A, kmajor_off(2 * pr + 1, k), h1);
+      put_vpair(A, vr, k, h0, h1);
     }
   } else {
-    for (int e = tid; e < RT * KC; e += NTHREADS) {
-      const int r = e / KC, k = e % KC;
-      put_entry(A, kmajor_off(r, k), gue_entry<float>(seed, sigma, R0 + r, c0 + k));
+#pragma unroll
+    for (int kc = 0; kc < 4; ++kc) {
+      const int k = 8 * kc + hk;
+      put_hpair(A, hr, k, gue_entry<float>(seed, sigma, R0 + hr, c0 + k),
+                gue_entry<float>(seed, sigma, R0 + hr, c0 + k + 1));
     }
   }
 }
@@ -234,6 +282,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   constexpr int B_TILE = N * KC * 2;    // bytes of one bf16 B tile
   constexpr int B_CHUNK = 4 * B_TILE;   // B1 hi, B1 lo, B2 hi, B2 lo
   constexpr int STAGE = 4 * A_PLANE + B_CHUNK;
+  constexpr int QC = N / 4;  // TMEM columns per thread in the drains
   constexpr uint32_t TMEM_COLS = N < 32 ? 32 : N;
   constexpr uint32_t IDESC = idesc_bf16(N);
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -243,6 +292,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __shared__ float win[RT + KC];
 
   const int tid = threadIdx.x, warp = tid >> 5;
+  // drain mapping: warp w reads TMEM lanes 32 (w % 4) .. +31 (rows) and
+  // columns (w / 4) * QC .. +QC of D = [Re Y | Im Y]
+  const int lane_grp = warp & 3, quarter = warp >> 2;
+  const int drow = lane_grp * 32 + (tid & 31);
+  float* accs = reinterpret_cast<float*>(smem + 2 * STAGE);  // [N][RT], column-major
+  for (int e = tid; e < N * RT; e += NTHREADS) accs[e] = 0.f;
   const int64_t R0 = (int64_t)blockIdx.x * RT;
   const int64_t cbeg = (int64_t)blockIdx.y * split_cols;
   const int64_t cend = cbeg + split_cols < D ? cbeg + split_cols : D;
@@ -304,7 +359,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           const uint64_t aim_h = smem_desc(a0 + 2 * A_PLANE + ko), aim_l = smem_desc(a0 + 3 * A_PLANE + ko);
           const uint64_t b1_h = smem_desc(b0 + 0 * B_TILE + ko), b1_l = smem_desc(b0 + 1 * B_TILE + ko);
           const uint64_t b2_h = smem_desc(b0 + 2 * B_TILE + ko), b2_l = smem_desc(b0 + 3 * B_TILE + ko);
-          const uint32_t acc0 = (kc > 0 || ks > 0) ? 1u : 0u;
+          const uint32_t acc0 = ((kc % SEG) != 0 || ks > 0) ? 1u : 0u;
           mma_bf16(tmem, are_h, b1_h, IDESC, acc0);
           mma_bf16(tmem, are_h, b1_l, IDESC, 1u);
           mma_bf16(tmem, are_l, b1_h, IDESC, 1u);
@@ -315,6 +370,24 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         mma_commit(&mma_bar[s]);
         issued = kc + 1;
       }
+    }
+    // end of a segment (not the last chunk): drain TMEM into the shared accumulator
+    if ((kc + 1) % SEG == 0 && kc + 1 < nchunk) {
+      if (tid == 0 && !abort_flag) {
+        if (!mbar_wait(&mma_bar[s], (uint32_t)((kc >> 1) & 1))) {
+          atomicCAS(err, 0, 130);
+          abort_flag = 1;
+        }
+      }
+      __syncthreads();
+      if (abort_flag) break;
+      tc_fence_after();
+      float v[QC];
+      tmem_load<QC>(tmem + ((uint32_t)(lane_grp * 32) << 16) + (uint32_t)(quarter * QC), v);
+#pragma unroll
+      for (int i = 0; i < QC; ++i) accs[(quarter * QC + i) * RT + drow] += v[i];
+      tc_fence_before();
+      __syncthreads();
     }
   }
   // wait for the last committed chunk (MMAs complete in issue order)
@@ -332,24 +405,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __syncthreads();
   tc_fence_after();
   if (!abort_flag && s_issued == nchunk && nchunk > 0) {
-    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31, columns
-    // (w / 4) * N/4 .. +N/4 of D = [Re Y | Im Y]
-    constexpr int QC = N / 4;
-    const int lane_grp = warp & 3, quarter = warp >> 2;
-    const int row = lane_grp * 32 + (tid & 31);
+    // last segment, then the sums to the partial slot
     float v[QC];
     tmem_load<QC>(tmem + ((uint32_t)(lane_grp * 32) << 16) + (uint32_t)(quarter * QC), v);
-    float* out = reinterpret_cast<float*>(part + ((int64_t)blockIdx.y * dpad + R0 + row) * NV);
+    float* out = reinterpret_cast<float*>(part + ((int64_t)blockIdx.y * dpad + R0 + drow) * NV);
 #pragma unroll
     for (int i = 0; i < QC; ++i) {
       const int col = quarter * QC + i;
       const int vec = col < NV ? col : col - NV;
-      out[2 * vec + (col < NV ? 0 : 1)] = v[i];
+      out[2 * vec + (col < NV ? 0 : 1)] = accs[col * RT + drow] + v[i];
     }
-  } else if (!abort_flag && nchunk == 0) {
-    // empty column range: the slot is zero
-    for (int e = tid; e < RT * NV; e += NTHREADS)
-      part[((int64_t)blockIdx.y * dpad + R0) * NV + e] = make_float2(0.f, 0.f);
   }
   tc_fence_before();
   __syncthreads();
@@ -388,7 +453,7 @@ template <int GEN, int NV>
 cudaError_t launch_tc_t(const Plan& p, const void* xc, void* part, void* gB, int* err) {
   constexpr int N = 2 * NV;
   constexpr size_t STAGE = 4 * (size_t)A_PLANE + 4 * (size_t)N * KC * 2;
-  const size_t smem = 2 * STAGE;
+  const size_t smem = 2 * STAGE + (size_t)N * RT * sizeof(float);
   const int64_t nchunk = (p.D + KC - 1) / KC;
   tc_split_x<NV><<<(unsigned)std::min<int64_t>((nchunk * KC * N + 255) / 256, 65535), 256, 0, p.stream>>>(
       (const float2*)xc, p.D, nchunk, (unsigned char*)gB);

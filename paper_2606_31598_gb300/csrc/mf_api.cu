@@ -596,6 +596,8 @@ mf_status mf_plan_create(mf_plan_t* out, int64_t D, int64_t M, int32_t generator
   if (o.precision != MF_PREC_FP64 && o.precision != MF_PREC_FP32 && o.precision != MF_PREC_BF16X2)
     return MF_ERR_INVALID;
   if (block < 0 || (block > 0 && block % kTile != 0)) return MF_ERR_INVALID;
+  // the FP32 steps of the DVR generator square an exact float(i - j)
+  if (generator == MF_GEN_SINC_DVR_HO && o.precision != MF_PREC_FP64 && D > ((int64_t)1 << 24)) return MF_ERR_INVALID;
   if (o.storage < MF_STORE_AUTO || o.storage > MF_STORE_FULL) return MF_ERR_INVALID;
   if (o.planner_mode < MF_PLANNER_ANALYTIC || o.planner_mode > MF_PLANNER_HYBRID) return MF_ERR_INVALID;
   if (!(o.cheb_tol > 0) || o.lanczos_m < 2 || !(o.alpha_safety > 0 && o.alpha_safety <= 1)) return MF_ERR_INVALID;
