@@ -1,0 +1,220 @@
+"""Measured planner sweep and learned-planner evaluation (Sec. IV.B-C,
+Algorithms 2 and 3).
+
+A *problem* is (generator, precision, D, nvec, cache budget); its candidate
+plans are every block size b with every storage mode the budget allows
+(procedural; partial with P_cache from Eq. partial_cache_pairs; full when the
+whole canonical cache fits).  Each distinct plan is built and timed once
+(R_warm warm-up applies, then the mean of R_bench applies, Eq.
+measured_matvec_time); budgets that lead to the same plan share that
+measurement.  Every (problem, candidate) becomes one JSON record with the
+surrogate's features, the strategy (procedural/partial/full), the measured
+time and the analytic model score.
+
+The surrogate (the library's MLP: 10 features -> 64 -> 64 -> 3 log-times,
+one per strategy) is trained on the GPU on the records of 80 % of the
+problems; on the held-out 20 % the learned planner's choice (lowest predicted
+time) and the analytic planner's choice (lowest model score) are compared
+with the exhaustive measured best: regret = t(choice) / t(best) - 1.
+
+    python -m paper_2606_31598_gb300.planner_sweep --out records.jsonl [--small]
+"""
+import argparse
+import json
+import math
+import os
+import sys
+import time
+
+import numpy as np
+
+STRATEGIES = ("procedural", "partial", "full")
+
+
+def _mf():
+    import paper_2606_31598_gb300 as mf
+    return mf
+
+
+def candidates(mf, gen, prec, D, nvec, budget, blocks):
+    """(b, storage) candidates of one problem with their analytic estimates."""
+    eb = 16.0 if prec == mf.MF_PREC_FP64 else 8.0
+    pr = mf.mf_problem(D, D, nvec, 1, 1, eb, 250e9, 1)
+    out = []
+    for b in blocks:
+        if b > D:
+            continue
+        nblk = -(-D // b)
+        npair = nblk * (nblk + 1) // 2
+        full_bytes = npair * eb * b * b
+        modes = [mf.MF_STORE_PROCEDURAL]
+        pc = min(npair, int(math.floor(budget / (eb * b * b)))) if budget > 0 else 0
+        if 0 < pc < npair:
+            modes.append(mf.MF_STORE_PARTIAL)
+        if budget >= full_bytes:
+            modes.append(mf.MF_STORE_FULL)
+        for st in modes:
+            c = mf.mf_candidate(b, st, -1, 1, 1, 4)
+            e = mf.mf_planner_estimate(pr, c, _device_model(mf, prec, gen), 0.9, budget)
+            if not e.feasible and st != mf.MF_STORE_PROCEDURAL:
+                continue
+            out.append({"block": b, "storage": STRATEGIES[st], "pairs_cached": int(e.pairs_cached),
+                        "S_model": e.S_model, "budget_used": 0.0 if st == 0 else e.pairs_cached * e.M_block})
+    return out
+
+
+def _device_model(mf, prec, gen):
+    # the same throughputs the library's analytic planner assumes
+    clk, sms = 1.9e9, 152
+    fl = 1.2e12 if prec == mf.MF_PREC_FP64 else sms * 128 * 2 * clk
+    g = 1e15 if gen == mf.MF_GEN_SINC_DVR_HO else (1.5e10 if prec == mf.MF_PREC_FP64 else 4e11)
+    return mf.mf_device_model(fl, 6.7e12, g)
+
+
+def measure(mf, torch, gen, prec, D, nvec, b, storage, budget_used, warm, reps):
+    st = STRATEGIES.index(storage)
+    plan = mf.Plan(D, gen, seed=1, block=b, cache_budget_bytes=int(budget_used) + (1 if st else 0), precision=prec,
+                   storage=st, nvec_hint=nvec)
+    x = torch.randn(D, nvec, dtype=torch.complex128, device="cuda")
+    y = torch.empty_like(x)
+    for _ in range(warm):
+        plan.apply(y, x, nvec)
+    a = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(reps):
+        plan.apply(y, x, nvec)
+    e.record()
+    torch.cuda.synchronize()
+    plan.sync()
+    desc = plan.describe()
+    plan.close()
+    del x, y
+    return a.elapsed_time(e) / 1e3 / reps, desc
+
+
+def grid(small):
+    if small:
+        return dict(Ds=[4096, 8192], nvecs=[1, 16], blocks=[256, 512, 1024], precs=[1, 2], budgets_gb=[0, 0.05, 1.0],
+                    gens=[0, 1])
+    return dict(Ds=[16384, 32768, 65536, 131072, 262144, 524288], nvecs=[1, 4, 16, 64],
+                blocks=[256, 512, 1024, 2048, 4096], precs=[1, 2], budgets_gb=[0, 30, 60, 120, 160], gens=[0, 1])
+
+
+def run_sweep(out_path, small=False, warm=1, reps=3, max_minutes=1e9, log=print):
+    """Measure every problem of the grid (cheapest first); returns records."""
+    import torch
+    mf = _mf()
+    g = grid(small)
+    problems = [(gen, prec, D, nv, bud) for gen in g["gens"] for prec in g["precs"] for D in g["Ds"]
+                for nv in g["nvecs"] for bud in g["budgets_gb"]]
+    problems.sort(key=lambda p: (p[2] * p[2] * max(p[3], 4), p))
+    cache = {}
+    records = []
+    t0 = time.time()
+    n_measured = 0
+    with open(out_path, "w") as f:
+        for (gen, prec, D, nv, bud_gb) in problems:
+            if (time.time() - t0) / 60.0 > max_minutes:
+                log("time cap reached after %d problems" % len({r['problem'] for r in records}))
+                break
+            budget = bud_gb * 1e9
+            pid = "%d/%d/%d/%d/%g" % (gen, prec, D, nv, bud_gb)
+            for c in candidates(mf, gen, prec, D, nv, budget, g["blocks"]):
+                # procedural plans do not depend on b (it only sets the cache
+                # granularity): one measurement serves every block size
+                kb = 0 if c["storage"] == "procedural" else c["block"]
+                key = (gen, prec, D, nv, kb, c["storage"], c["pairs_cached"])
+                if key not in cache:
+                    t, desc = measure(mf, torch, gen, prec, D, nv, c["block"], c["storage"], c["budget_used"], warm,
+                                      reps)
+                    cache[key] = t
+                    n_measured += 1
+                feats = [float(v) for v in mf.mf_mlp_features(gen, prec, D, c["block"], nv, budget)]
+                rec = {"problem": pid, "generator": gen, "precision": prec, "D": D, "nvec": nv, "budget_gb": bud_gb,
+                       "block": c["block"], "storage": c["storage"], "pairs_cached": c["pairs_cached"],
+                       "S_model": c["S_model"], "t_mv": cache[key], "features": feats}
+                records.append(rec)
+                f.write(json.dumps(rec) + "\n")
+            f.flush()
+    log("measured %d distinct plans, %d records, %d problems in %.1f min" %
+        (n_measured, len(records), len({r['problem'] for r in records}), (time.time() - t0) / 60))
+    return records
+
+
+def load(path):
+    with open(path) as f:
+        return [json.loads(l) for l in f if l.strip()]
+
+
+def split(records, frac=0.2, seed=0):
+    probs = sorted({r["problem"] for r in records})
+    rng = np.random.default_rng(seed)
+    test = set(rng.choice(probs, size=max(1, int(round(frac * len(probs)))), replace=False))
+    return [r for r in records if r["problem"] not in test], [r for r in records if r["problem"] in test]
+
+
+def train_surrogate(records, epochs=3000, lr=3e-3, seed=0):
+    mf = _mf()
+    X = np.array([r["features"] for r in records], np.float32)
+    Y = np.zeros((len(records), 3), np.float32)
+    M = np.zeros((len(records), 3), np.float32)
+    for i, r in enumerate(records):
+        k = STRATEGIES.index(r["storage"])
+        Y[i, k] = math.log(r["t_mv"])
+        M[i, k] = 1.0
+    net = mf.MLP(10, 64, 3, seed=seed)
+    curve = net.train(X, Y, M, epochs=epochs, lr=lr, set_normalization=True)
+    return net, curve
+
+
+def regret(records, net=None):
+    """Mean and max regret of the learned (net) or analytic (net=None)
+    choice against the measured best, per problem."""
+    by = {}
+    for r in records:
+        by.setdefault(r["problem"], []).append(r)
+    regs = []
+    for pid, rs in by.items():
+        best = min(r["t_mv"] for r in rs)
+        if net is None:
+            pick = min(rs, key=lambda r: r["S_model"])
+        else:
+            pred = net.predict(np.array([r["features"] for r in rs], np.float32))
+            pick = rs[int(np.argmin([pred[i, STRATEGIES.index(r["storage"])] for i, r in enumerate(rs)]))]
+        regs.append(pick["t_mv"] / best - 1.0)
+    regs = np.array(regs)
+    return {"problems": int(len(regs)), "mean": float(regs.mean()), "median": float(np.median(regs)),
+            "max": float(regs.max()), "zero_regret_frac": float(np.mean(regs < 1e-9))}
+
+
+def evaluate(records, epochs=3000, seed=0):
+    train, test = split(records, 0.2, seed)
+    net, curve = train_surrogate(train, epochs=epochs, seed=seed)
+    out = {"records": len(records), "train_records": len(train), "test_records": len(test),
+           "loss_first": float(curve[0]), "loss_last": float(curve[-1]),
+           "learned_test": regret(test, net), "analytic_test": regret(test, None),
+           "learned_train": regret(train, net), "analytic_train": regret(train, None)}
+    net.close()
+    return out
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", default="planner_records.jsonl")
+    ap.add_argument("--small", action="store_true")
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--warm", type=int, default=1)
+    ap.add_argument("--max-minutes", type=float, default=1e9)
+    ap.add_argument("--evaluate-only", action="store_true")
+    ap.add_argument("--epochs", type=int, default=3000)
+    a = ap.parse_args(argv)
+    recs = load(a.out) if a.evaluate_only else run_sweep(a.out, a.small, a.warm, a.reps, a.max_minutes)
+    res = evaluate(recs, epochs=a.epochs)
+    print(json.dumps(res))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
