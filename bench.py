@@ -425,13 +425,153 @@ def run_multivector(args):
     return 0
 
 
+def run_philox(args):
+    """Seeded generation and cached streaming, one vector: the Philox ensemble
+    at D = 131072 (FP32 form) procedural (every canonical entry generated
+    once per apply, used for H and H^dagger) and fully cached (each canonical
+    entry read once from HBM, 8 bytes); Chebyshev steps of dt = 1."""
+    import torch
+    import paper_2606_31598_gb300 as mf
+    import workloads as W
+    D = args.philox_dim
+    stream = torch.cuda.current_stream().cuda_stream
+    x = torch.from_numpy(W.random_state(D, 1, seed=3)).cuda()
+    y = torch.empty_like(x)
+    canon = D * (D + 1) / 2.0
+    out = {"workload": "Philox GUE D=%d, 1 vector, FP32 form" % D}
+    props = torch.cuda.get_device_properties(0)
+    for name, storage, budget in [("procedural", mf.MF_STORE_PROCEDURAL, 0),
+                                  ("full_cache", mf.MF_STORE_FULL, int(canon * 8 * 1.02) + (1 << 30))]:
+        plan = mf.Plan(D, mf.MF_GEN_PHILOX_GUE, seed=1, block=2048, cache_budget_bytes=budget,
+                       precision=mf.MF_PREC_FP32, storage=storage, stream=stream)
+        desc = plan.describe()
+        clock = ClockSampler(0)
+        clock.start()
+        plan.profile(True)
+        t = time_applies(plan, x, y, 1, args.steps)
+        kern_ms, kern_n = plan.profile_read()
+        clk = clock.stop()
+        plan.profile(False)
+        per = kern_ms / 1e3 / max(1, kern_n)
+        res = {"apply_s": t, "kernel_s": per, "entries_per_s": D * float(D) / t, "canonical_entries_per_s": canon / per,
+               "pairs_cached": desc["pairs_cached"], "clocks": clk}
+        if storage == mf.MF_STORE_FULL:
+            gbs = canon * 8 / per / 1e9
+            res["roofline"] = {"bound": "hbm", "achieved": gbs, "peak": 6781.4, "unit": "GB/s", "frac": gbs / 6781.4,
+                               "note": "8 B per canonical entry read once per apply; peak of measured copy"}
+        else:
+            mhz = clk.get("sm_mhz") or 1900.0
+            peak_ops = props.multi_processor_count * 128 * mhz * 1e6  # thread instructions / s
+            res["issue_peak_thread_ops_per_s"] = peak_ops
+            res["roofline"] = {"bound": "alu", "achieved_canonical_entries_per_s": canon / per,
+                               "ops_per_entry_counted": PHILOX_OPS_PER_ENTRY,
+                               "achieved": canon / per * PHILOX_OPS_PER_ENTRY / 1e12,
+                               "peak": peak_ops / 1e12, "unit": "Tops/s",
+                               "frac": canon / per * PHILOX_OPS_PER_ENTRY / peak_ops}
+        if name == "procedural":
+            nt = plan.cheb_terms(1.0)
+            psi = x.clone()
+            plan.cheb_propagate(psi, 1, 1.0, 0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(args.steps):
+                plan.cheb_propagate(psi, 1, 1.0, 0)
+            e1.record()
+            torch.cuda.synchronize()
+            res["cheb_steps_per_s"] = args.steps / (e0.elapsed_time(e1) / 1e3)
+            res["terms_per_step"] = nt
+        out[name] = res
+        plan.close()
+    print(json.dumps(out))
+    return 0
+
+
+# Operations of the definition per canonical entry of the FP32 Philox form
+# (counted from the generator's steps): half a Philox4x32-10 call (10 rounds
+# of 2 high and 2 low 32-bit products and 2 three-way XORs = 60 per call),
+# two uniforms (6 each), the log polynomial with its division (~24), sqrt
+# (~8), the sin/cos polynomials with the quadrant logic (~24), the scale (3)
+# and the 8 FMAs applying the entry as H and H^dagger.
+PHILOX_OPS_PER_ENTRY = 30 + 12 + 24 + 8 + 24 + 3 + 8
+
+
+def run_batch(args):
+    """256 independent Philox problems (D log-uniform in [1024, 32768] rounded
+    to 128, 1..16 vectors, seeds 0..255), plans chosen per problem by the
+    measured autotuner with a shared 200 GB cache budget, FP32 form,
+    Chebyshev steps of dt = 1: one persistent launch per term under a CUDA
+    graph, against the same problems propagated one after another through
+    their own plans."""
+    import torch
+    import paper_2606_31598_gb300 as mf
+    import workloads as W
+    probs = W.batch_problems(args.batch_n)
+    Ds = [p[0] for p in probs]
+    nv = [p[1] for p in probs]
+    seeds = [p[2] for p in probs]
+    stream = torch.cuda.current_stream().cuda_stream
+    t0 = time.perf_counter()
+    b = mf.Batch(Ds, nv, seeds, mf.MF_GEN_PHILOX_GUE, cache_budget_bytes=int(args.batch_budget_gb * 1e9),
+                 precision=mf.MF_PREC_FP32, planner_mode=mf.MF_PLANNER_AUTOTUNE, autotune_k=4, autotune_repeats=2,
+                 stream=stream)
+    t_create = time.perf_counter() - t0
+    n_items, grid = b.info()
+    parts = [W.random_state(D, k, seed=100 + i).reshape(D, k) for i, (D, k) in enumerate(zip(Ds, nv))]
+    packed = torch.from_numpy(np.concatenate([q.ravel() for q in parts])).cuda()
+    nt = b.propagate(packed, 1.0, args.steps)  # capture the graph once, warm
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    b.propagate(packed, 1.0, args.steps)
+    e1.record()
+    torch.cuda.synchronize()
+    t_batch = e0.elapsed_time(e1) / 1e3
+    stores = {}
+    entries = 0.0
+    for i, (D, k) in enumerate(zip(Ds, nv)):
+        d = mf.mf_plan_describe(b.plan(i))
+        stores[d["storage"]] = stores.get(d["storage"], 0) + 1
+        entries += float(D) * D * k
+    # the same problems one by one through their own plans (same term count;
+    # the plans run on the batch's stream, so time with device syncs)
+    seq = [torch.from_numpy(q.copy()).cuda() for q in parts]
+    for _ in range(args.steps):
+        for i, k in enumerate(nv):
+            mf.mf_cheb_propagate(b.plan(i), seq[i], k, 1.0, nt)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    for _ in range(args.steps):
+        for i, k in enumerate(nv):
+            mf.mf_cheb_propagate(b.plan(i), seq[i], k, 1.0, nt)
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t1
+    applies = args.steps * (nt - 1)
+    out = {"workload": "%d batched Philox problems, D in [1024, 32768], 1-16 vectors, FP32" % len(Ds),
+           "sum_D2_nvec": entries, "terms_per_step": nt, "create_s": t_create, "work_items": n_items,
+           "persistent_grid": grid, "storage_chosen": stores,
+           "batched": {"steps_per_s": args.steps / t_batch, "entries_per_s": entries * applies / t_batch},
+           "sequential": {"steps_per_s": args.steps / t_seq, "entries_per_s": entries * applies / t_seq},
+           "speedup_batched_vs_sequential": t_seq / t_batch,
+           "max_diff_batched_vs_sequential": float(max((packed[int(b.offsets[i]):int(b.offsets[i + 1])]
+                                                        - seq[i].reshape(-1)).abs().max() for i in range(len(Ds))))}
+    print(json.dumps(out))
+    b.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mf", choices=["mf", "reference"])
-    ap.add_argument("--workload", default="dvr", choices=["dvr", "multivector"],
+    ap.add_argument("--batch-n", type=int, default=256, help="batch: number of problems")
+    ap.add_argument("--philox-dim", type=int, default=131072, help="philox: D")
+    ap.add_argument("--batch-budget-gb", type=float, default=200.0, help="batch: shared cache budget")
+    ap.add_argument("--workload", default="dvr", choices=["dvr", "multivector", "batch", "philox"],
                     help="dvr: the benchmark line; multivector: the 64-vector tensor-core workload report")
     ap.add_argument("--fp64", action="store_true", help="multivector: also time the FP64 procedural form")
     ap.add_argument("--mv-dim", type=int, default=262144, help="multivector: D (smaller D keeps the cached fraction)")
@@ -440,6 +580,10 @@ def main():
         return run_reference(args)
     if args.workload == "multivector":
         return run_multivector(args)
+    if args.workload == "batch":
+        return run_batch(args)
+    if args.workload == "philox":
+        return run_philox(args)
     return run_mf(args)
 
 

@@ -133,3 +133,50 @@ def test_mlp_oracle_adam_fits_a_smooth_map():
     mu, sd = MO.zscore(X)
     _, curve = MO.train_adam(p0, mu, sd, X, Y, None, F, H, O, 600, 1e-2)
     assert curve[-1] < 0.02 * curve[0]
+
+
+# ------------------------------------------------------- sweep machinery ----
+def test_sweep_candidates_follow_partial_cache_equation(mf):
+    from paper_2606_31598_gb300 import planner_sweep as PS
+    D, nv, budget = 131072, 16, 30e9   # canonical cache about 69 GB in the FP32 form
+    cs = PS.candidates(mf, 0, mf.MF_PREC_FP32, D, nv, budget, [256, 2048, 4096])
+    for c in cs:
+        b = c["block"]
+        nblk = -(-D // b)
+        npair = nblk * (nblk + 1) // 2
+        if c["storage"] == "partial":
+            assert c["pairs_cached"] == min(npair, math.floor(budget / (8 * b * b)))
+        if c["storage"] == "procedural":
+            assert c["pairs_cached"] == 0
+    assert {c["storage"] for c in cs} == {"procedural", "partial"}
+    # at D = 32768 the whole canonical cache (about 4.6 GB) fits the budget
+    cs2 = PS.candidates(mf, 0, mf.MF_PREC_FP32, 32768, nv, budget, [2048])
+    assert {c["storage"] for c in cs2} == {"procedural", "full"}
+
+
+def test_regret_definition():
+    from paper_2606_31598_gb300 import planner_sweep as PS
+
+    class Fake:  # predicts the measured log-time exactly
+        def __init__(self, recs):
+            self.t = {tuple(r["features"]) + (r["storage"],): r["t_mv"] for r in recs}
+
+        def predict(self, X):
+            out = np.full((len(X), 3), 1e9, np.float32)
+            for i, x in enumerate(X):
+                for k, st in enumerate(PS.STRATEGIES):
+                    key = tuple(float(v) for v in x) + (st,)
+                    if key in self.t:
+                        out[i, k] = math.log(self.t[key])
+            return out
+
+    recs = []
+    for p in range(4):
+        for j, (st, t, sm) in enumerate([("procedural", 2.0, 1.0), ("full", 1.0, 3.0), ("partial", 1.5, 2.0)]):
+            recs.append({"problem": "p%d" % p, "storage": st, "t_mv": t * (1 + p), "S_model": sm,
+                         "features": [float(p), float(j)] + [0.0] * 8})
+    assert PS.regret(recs, Fake(recs))["mean"] == 0.0
+    an = PS.regret(recs, None)   # the model picks procedural: regret 1.0 on every problem
+    assert abs(an["mean"] - 1.0) < 1e-12 and an["zero_regret_frac"] == 0.0
+    tr, te = PS.split(recs, 0.25, seed=0)
+    assert {r["problem"] for r in tr}.isdisjoint({r["problem"] for r in te})
