@@ -31,7 +31,9 @@ namespace tc {
 
 constexpr int RT = 128;          // rows per CTA (MMA M)
 constexpr int KC = 32;           // columns per chunk
-constexpr int NTHREADS = 512;
+constexpr int NGEN = 16;                     // generator warps (fill the A planes)
+constexpr int MMA_WARP = NGEN;               // the copy/MMA-issuing warp
+constexpr int NTHREADS = (NGEN + 1) * 32;
 constexpr int A_PLANE = RT * KC * 2;  // bytes of one bf16 plane of the chunk (8 KB)
 constexpr uint32_t kSpinLimit = 1u << 22;
 // The tensor core's FP32 accumulation is not round-to-nearest over long
@@ -187,16 +189,17 @@ __device__ __forceinline__ void put_vpair(unsigned char* A, int r, int k, float2
   }
 }
 
-// Fill the four A planes of chunk [R0, R0+128) x [c0, c0+32).  Warp w covers
+// Fill the four A planes of chunk [R0, R0+128) x [c0, c0+32) (called by the
+// NGEN generator warps only; no block-wide synchronisation).  Warp w covers
 // the 8-row group w (16 groups) and, per K core kc (4 cores of 8 columns),
 // one 8 x 8 core matrix: horizontal pairs with lane -> (row lane/4, columns
 // 2 (lane%4), +1), vertical pairs with lane -> (rows 2 (lane%4), +1, column
 // lane/4); both keep a warp's stores inside one 128-byte core matrix.
 template <int GEN>
-__device__ __forceinline__ void fill_a(unsigned char* A, float* win, int64_t R0, int64_t c0, uint64_t seed,
+__device__ __forceinline__ void fill_a(unsigned char* A, int64_t R0, int64_t c0, uint64_t seed,
                                        float sigma, const dvr_consts& dk, const float2* __restrict__ cache,
                                        const int64_t* __restrict__ slot_of_pair, int64_t b, int64_t nblk) {
-  const int tid = threadIdx.x, lane = tid & 31, g = tid >> 5;
+  const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
   const int hr = 8 * g + (lane >> 2), hk = 2 * (lane & 3);   // horizontal pair origin within a K core
   const int vr = 8 * g + 2 * (lane & 3), vk = lane >> 2;     // vertical pair origin within a K core
   int64_t slot = -1;
@@ -232,13 +235,11 @@ __device__ __forceinline__ void fill_a(unsigned char* A, float* win, int64_t R0,
     return;
   }
   if (GEN == MF_GEN_SINC_DVR_HO) {
-    const long long kmin = (long long)(R0 - c0) - (KC - 1);
-    for (int j = tid; j < RT + KC - 1; j += NTHREADS) win[j] = dvr_T_f32(dk, kmin + j);
-    __syncthreads();
+    const long long d0 = (long long)(R0 - c0) + hr;
 #pragma unroll
     for (int kc = 0; kc < 4; ++kc) {
       const int k = 8 * kc + hk;
-      put_hpair(A, hr, k, make_float2(win[hr - k + KC - 1], 0.f), make_float2(win[hr - k - 1 + KC - 1], 0.f));
+      put_hpair(A, hr, k, make_float2(dvr_T_f32(dk, d0 - k), 0.f), make_float2(dvr_T_f32(dk, d0 - k - 1), 0.f));
     }
     return;
   }
@@ -273,6 +274,11 @@ __device__ __forceinline__ void fill_a(unsigned char* A, float* win, int64_t R0,
 }
 
 // Y[R0:R0+128, :] over columns [cbeg, cend) into part[slot][row][NV].
+// Warps 0..NGEN-1 generate the A planes of each chunk and arrive on the
+// stage's a_full barrier; warp MMA_WARP streams the X tiles (b_full) and,
+// once both are complete, issues the chunk's MMAs and commits them to the
+// stage's mma barrier, which frees the stage for the chunk two ahead.  The
+// only block-wide barriers are at the SEG-chunk drains.
 template <int GEN, int NV>
 __global__ void __launch_bounds__(NTHREADS, 1)
     tc_rows(int64_t D, int64_t dpad, int64_t split_cols, uint64_t seed, float sigma, dvr_consts dk,
@@ -282,20 +288,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   constexpr int B_TILE = N * KC * 2;    // bytes of one bf16 B tile
   constexpr int B_CHUNK = 4 * B_TILE;   // B1 hi, B1 lo, B2 hi, B2 lo
   constexpr int STAGE = 4 * A_PLANE + B_CHUNK;
-  constexpr int QC = N / 4;  // TMEM columns per thread in the drains
+  constexpr int QC = N / 4;             // TMEM columns per thread in the drains
   constexpr uint32_t TMEM_COLS = N < 32 ? 32 : N;
   constexpr uint32_t IDESC = idesc_bf16(N);
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ uint64_t full_bar[2], mma_bar[2];
+  __shared__ uint64_t a_full[2], b_full[2], mma_bar[2];
   __shared__ uint32_t tmem_base;
-  __shared__ int abort_flag;
-  __shared__ float win[RT + KC];
+  __shared__ volatile int abort_flag;
 
-  const int tid = threadIdx.x, warp = tid >> 5;
-  // drain mapping: warp w reads TMEM lanes 32 (w % 4) .. +31 (rows) and
-  // columns (w / 4) * QC .. +QC of D = [Re Y | Im Y]
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // drain mapping (generator warps): warp w reads TMEM lanes 32 (w % 4) ..
+  // +31 (rows) and columns (w / 4) * QC .. +QC of D = [Re Y | Im Y]
   const int lane_grp = warp & 3, quarter = warp >> 2;
-  const int drow = lane_grp * 32 + (tid & 31);
+  const int drow = lane_grp * 32 + lane;
   float* accs = reinterpret_cast<float*>(smem + 2 * STAGE);  // [N][RT], column-major
   for (int e = tid; e < N * RT; e += NTHREADS) accs[e] = 0.f;
   const int64_t R0 = (int64_t)blockIdx.x * RT;
@@ -304,14 +309,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int nchunk = (int)((cend - cbeg + KC - 1) / KC);
 
   if (tid == 0) {
-    mbar_init(&full_bar[0], 1);
-    mbar_init(&full_bar[1], 1);
-    mbar_init(&mma_bar[0], 1);
-    mbar_init(&mma_bar[1], 1);
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&a_full[s], NGEN);
+      mbar_init(&b_full[s], 1);
+      mbar_init(&mma_bar[s], 1);
+    }
     abort_flag = 0;
     fence_async_smem();
   }
-  if (warp == 0) {
+  if (warp == MMA_WARP) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
                  "r"(TMEM_COLS)
                  : "memory");
@@ -322,103 +328,108 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   tc_fence_after();
   const uint32_t tmem = tmem_base;
 
-  int issued = 0;  // chunks whose MMAs were committed (thread 0's view)
-  for (int kc = 0; kc < nchunk; ++kc) {
-    const int s = kc & 1;
-    unsigned char* A = smem + s * STAGE;
-    unsigned char* B = A + 4 * A_PLANE;
-    const int64_t c0 = cbeg + (int64_t)kc * KC;
-    // the stage's previous MMAs (chunk kc - 2) must be done before overwriting
-    if (kc >= 2 && tid == 0) {
-      if (!mbar_wait(&mma_bar[s], (uint32_t)(((kc - 2) >> 1) & 1))) {
-        atomicCAS(err, 0, 100 + s);
-        abort_flag = 1;
+  bool done_all = false;
+  for (int k0 = 0; k0 < nchunk; k0 += SEG) {
+    const int k1 = k0 + SEG < nchunk ? k0 + SEG : nchunk;
+    if (warp == MMA_WARP) {
+      if (lane == 0) {
+        int last = -1;
+        for (int kc = k0; kc < k1 && !abort_flag; ++kc) {
+          const int s = kc & 1;
+          unsigned char* A = smem + s * STAGE;
+          unsigned char* B = A + 4 * A_PLANE;
+          // the stage's previous MMAs (chunk kc - 2) must be done before its X tiles are replaced
+          if (kc >= 2 && !mbar_wait(&mma_bar[s], (uint32_t)(((kc - 2) >> 1) & 1))) {
+            atomicCAS(err, 0, 100 + s);
+            abort_flag = 1;
+            break;
+          }
+          mbar_expect_tx(&b_full[s], (uint32_t)B_CHUNK);
+          bulk_g2s(B, gB + ((cbeg + (int64_t)kc * KC) / KC) * (int64_t)B_CHUNK, (uint32_t)B_CHUNK, &b_full[s]);
+          const bool a_ok = mbar_wait(&a_full[s], (uint32_t)((kc >> 1) & 1));
+          const bool b_ok = mbar_wait(&b_full[s], (uint32_t)((kc >> 1) & 1));
+          if (!a_ok || !b_ok) {
+            atomicCAS(err, 0, a_ok ? 111 : 110);
+            abort_flag = 1;
+            if (!b_ok) mbar_wait(&b_full[s], (uint32_t)((kc >> 1) & 1));  // bounded wait for the copy in flight
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a0 = smem_u32(A), b0 = smem_u32(B);
+#pragma unroll
+          for (int ks = 0; ks < KC / 16; ++ks) {
+            const uint32_t ko = (uint32_t)ks * 256;  // two 8-element K cores of 128 B
+            const uint64_t are_h = smem_desc(a0 + 0 * A_PLANE + ko), are_l = smem_desc(a0 + 1 * A_PLANE + ko);
+            const uint64_t aim_h = smem_desc(a0 + 2 * A_PLANE + ko), aim_l = smem_desc(a0 + 3 * A_PLANE + ko);
+            const uint64_t b1_h = smem_desc(b0 + 0 * B_TILE + ko), b1_l = smem_desc(b0 + 1 * B_TILE + ko);
+            const uint64_t b2_h = smem_desc(b0 + 2 * B_TILE + ko), b2_l = smem_desc(b0 + 3 * B_TILE + ko);
+            const uint32_t acc0 = (kc != k0 || ks > 0) ? 1u : 0u;
+            mma_bf16(tmem, are_h, b1_h, IDESC, acc0);
+            mma_bf16(tmem, are_h, b1_l, IDESC, 1u);
+            mma_bf16(tmem, are_l, b1_h, IDESC, 1u);
+            mma_bf16(tmem, aim_h, b2_h, IDESC, 1u);
+            mma_bf16(tmem, aim_h, b2_l, IDESC, 1u);
+            mma_bf16(tmem, aim_l, b2_h, IDESC, 1u);
+          }
+          mma_commit(&mma_bar[s]);
+          last = kc;
+        }
+        // the segment's MMAs complete in issue order: wait for the last one
+        if (last >= 0 && !mbar_wait(&mma_bar[last & 1], (uint32_t)((last >> 1) & 1))) {
+          atomicCAS(err, 0, 120);
+          abort_flag = 1;
+        }
+        if (last != k1 - 1) abort_flag = 1;
+      }
+      __syncwarp();
+    } else {
+      for (int kc = k0; kc < k1; ++kc) {
+        const int s = kc & 1;
+        if (kc >= 2) {
+          bool ok = true;
+          if (lane == 0) ok = mbar_wait(&mma_bar[s], (uint32_t)(((kc - 2) >> 1) & 1));
+          ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+          if (!ok) {
+            if (lane == 0) {
+              atomicCAS(err, 0, 102 + s);
+              abort_flag = 1;
+            }
+            break;
+          }
+        }
+        if (abort_flag) break;
+        fill_a<GEN>(smem + s * STAGE, R0, cbeg + (int64_t)kc * KC, seed, sigma, dk, cache, slot_of_pair, b, nblk);
+        fence_async_smem();
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&a_full[s])) : "memory");
       }
     }
     __syncthreads();
     if (abort_flag) break;
-    if (tid == 0) {
-      mbar_expect_tx(&full_bar[s], (uint32_t)B_CHUNK);
-      bulk_g2s(B, gB + (c0 / KC) * (int64_t)B_CHUNK, (uint32_t)B_CHUNK, &full_bar[s]);
-    }
-    fill_a<GEN>(A, win, R0, c0, seed, sigma, dk, cache, slot_of_pair, b, nblk);
-    fence_async_smem();
-    __syncthreads();
-    if (tid == 0) {
-      if (!mbar_wait(&full_bar[s], (uint32_t)((kc >> 1) & 1))) {
-        atomicCAS(err, 0, 110 + s);
-        abort_flag = 1;
-        mbar_wait(&full_bar[s], (uint32_t)((kc >> 1) & 1));  // one more bounded wait for the copy in flight
-      } else {
-        tc_fence_after();
-        const uint32_t a0 = smem_u32(A), b0 = smem_u32(B);
-#pragma unroll
-        for (int ks = 0; ks < KC / 16; ++ks) {
-          const uint32_t ko = (uint32_t)ks * 256;  // two 8-element K cores of 128 B
-          const uint64_t are_h = smem_desc(a0 + 0 * A_PLANE + ko), are_l = smem_desc(a0 + 1 * A_PLANE + ko);
-          const uint64_t aim_h = smem_desc(a0 + 2 * A_PLANE + ko), aim_l = smem_desc(a0 + 3 * A_PLANE + ko);
-          const uint64_t b1_h = smem_desc(b0 + 0 * B_TILE + ko), b1_l = smem_desc(b0 + 1 * B_TILE + ko);
-          const uint64_t b2_h = smem_desc(b0 + 2 * B_TILE + ko), b2_l = smem_desc(b0 + 3 * B_TILE + ko);
-          const uint32_t acc0 = ((kc % SEG) != 0 || ks > 0) ? 1u : 0u;
-          mma_bf16(tmem, are_h, b1_h, IDESC, acc0);
-          mma_bf16(tmem, are_h, b1_l, IDESC, 1u);
-          mma_bf16(tmem, are_l, b1_h, IDESC, 1u);
-          mma_bf16(tmem, aim_h, b2_h, IDESC, 1u);
-          mma_bf16(tmem, aim_h, b2_l, IDESC, 1u);
-          mma_bf16(tmem, aim_l, b2_h, IDESC, 1u);
-        }
-        mma_commit(&mma_bar[s]);
-        issued = kc + 1;
-      }
-    }
-    // end of a segment (not the last chunk): drain TMEM into the shared accumulator
-    if ((kc + 1) % SEG == 0 && kc + 1 < nchunk) {
-      if (tid == 0 && !abort_flag) {
-        if (!mbar_wait(&mma_bar[s], (uint32_t)((kc >> 1) & 1))) {
-          atomicCAS(err, 0, 130);
-          abort_flag = 1;
-        }
-      }
-      __syncthreads();
-      if (abort_flag) break;
-      tc_fence_after();
+    tc_fence_after();
+    if (warp < NGEN) {
       float v[QC];
       tmem_load<QC>(tmem + ((uint32_t)(lane_grp * 32) << 16) + (uint32_t)(quarter * QC), v);
 #pragma unroll
       for (int i = 0; i < QC; ++i) accs[(quarter * QC + i) * RT + drow] += v[i];
-      tc_fence_before();
-      __syncthreads();
     }
+    tc_fence_before();
+    __syncthreads();
+    done_all = k1 == nchunk;
   }
-  // wait for the last committed chunk (MMAs complete in issue order)
-  __shared__ int s_issued;
-  if (tid == 0) {
-    s_issued = issued;
-    if (issued > 0) {
-      const int last = issued - 1;
-      if (!mbar_wait(&mma_bar[last & 1], (uint32_t)((last >> 1) & 1))) {
-        atomicCAS(err, 0, 120);
-        abort_flag = 1;
-      }
-    }
-  }
-  __syncthreads();
-  tc_fence_after();
-  if (!abort_flag && s_issued == nchunk && nchunk > 0) {
-    // last segment, then the sums to the partial slot
-    float v[QC];
-    tmem_load<QC>(tmem + ((uint32_t)(lane_grp * 32) << 16) + (uint32_t)(quarter * QC), v);
+  if (!abort_flag && done_all && warp < NGEN) {
     float* out = reinterpret_cast<float*>(part + ((int64_t)blockIdx.y * dpad + R0 + drow) * NV);
 #pragma unroll
     for (int i = 0; i < QC; ++i) {
       const int col = quarter * QC + i;
       const int vec = col < NV ? col : col - NV;
-      out[2 * vec + (col < NV ? 0 : 1)] = accs[col * RT + drow] + v[i];
+      out[2 * vec + (col < NV ? 0 : 1)] = accs[col * RT + drow];
     }
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  if (warp == MMA_WARP)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
 }
 
 // Operand tiles of X for every 32-row chunk: B1 = [Re X | Im X],
