@@ -104,7 +104,7 @@ def traffic_from_profile():
     """DRAM bytes per launch of the dominant kernel from the committed ncu
     summary, valid only while the kernel source is unchanged."""
     path = os.path.join(ROOT, "profiles", "dvr_window_f32_D131072.md")
-    src = os.path.join(ROOT, "paper_2606_31598_gb300", "csrc", "k_apply.cu")
+    src = os.path.join(ROOT, "paper_2606_31598_gb300", "csrc", "k_dvr.cu")
     try:
         txt = open(path).read()
         want = re.search(r"source_sha256:\s*([0-9a-f]{64})", txt).group(1)

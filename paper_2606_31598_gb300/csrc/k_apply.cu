@@ -1,25 +1,19 @@
-// k_apply.cu -- fused generate-and-apply kernels (SIMT).
+// k_apply.cu -- Hermitian canonical-tile generate-and-apply kernel (SIMT,
+// one vector).
 //
-// (1) Hermitian canonical-tile kernel (Sec. III.A "partial caching" and
-//     Eq. blockmatvec): each CTA owns one canonical kTile x kTile tile
-//     (ti <= tj).  Every canonical entry h_rc (r <= c) is generated in
-//     registers from the Philox ensemble -- or read from the HBM block cache
-//     when its block pair is cached -- exactly once, and applied twice:
-//     y_r += h_rc x_c (block H^[n,m]) and y_c += conj(h_rc) x_r (block
-//     H^[m,n] = (H^[n,m])^dagger).  Row and column sums of the tile go to
-//     partial-sum slots that a fixed-order FP64 reduction combines.
-//
-// (2) DVR Toeplitz-window kernel (Sec. III.A "analytic generation"): the
-//     sinc-DVR kinetic block H^[n,m]_{ab} = T(r - c) depends on r - c only, so
-//     a CTA covering rows [R0, R0+RB) and columns [C0, C0+KC) generates the
-//     RB + KC - 1 distinct entries of its tile once into shared memory and
-//     contracts the whole RB x KC tile from that window: the dense O(RB*KC)
-//     product runs on the FMA pipe with register-blocked 16 x 16 sub-tiles.
+// Sec. III.A ("partial caching") and Eq. blockmatvec: each CTA owns one
+// canonical kTile x kTile tile (ti <= tj).  Every canonical entry h_rc
+// (r <= c) is generated in registers from the Philox ensemble -- or read from
+// the HBM block cache when its block pair is cached -- exactly once, and
+// applied twice: y_r += h_rc x_c (block H^[n,m]) and y_c += conj(h_rc) x_r
+// (block H^[m,n] = (H^[n,m])^dagger).  Row and column sums of the tile go to
+// partial-sum slots that a fixed-order FP64 reduction combines.
 #include <cuda_runtime.h>
 
 #include "mf_internal.h"
 
 namespace mf {
+
 
 template <typename T> __device__ __forceinline__ typename cplx<T>::t czero();
 template <> __device__ __forceinline__ float2 czero<float>() { return make_float2(0.f, 0.f); }
@@ -83,28 +77,43 @@ __global__ void __launch_bounds__(256) herm_tile_nv1(const WorkItem* __restrict_
   const bool active = !(diag && ty > tx);
 
   if (it.cache_off >= 0) {
-    // cached block pair: stream the canonical entries from HBM
+    // cached block pair: stream the canonical entries from HBM, 16-byte
+    // loads, two rows of the thread's 8 x 8 sub-block in flight
+    constexpr int PER16 = 16 / (int)sizeof(C);  // complex entries per 16-byte load
     const C* base = cache + it.cache_off + (int64_t)(ty * 8) * bstride + tx * 8;
 #pragma unroll 1
-    for (int a = 0; a < 8; ++a) {
-      C yra = czero<T>();
+    for (int a2 = 0; a2 < 8; a2 += 2) {
+      C h[2][8];
       if (active) {
-        const C xa = xs_r[ty * 8 + a];
-        C h[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) h[q] = base[(int64_t)a * bstride + q];
+        for (int u = 0; u < 2; ++u)
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int dr = (ty * 8 + a) - (tx * 8 + q);
-          if (!diag || dr < 0) {
-            cmac(yra, h[q], xcv[q]);
-            cmacc(yc[q], h[q], xa);
-          } else if (dr == 0) {
-            cmac(yra, h[q], xcv[q]);
+          for (int q = 0; q < 8; q += PER16) {
+            const float4 v = *reinterpret_cast<const float4*>(base + (int64_t)(a2 + u) * bstride + q);
+            const C* e = reinterpret_cast<const C*>(&v);
+#pragma unroll
+            for (int i = 0; i < PER16; ++i) h[u][q + i] = e[i];
+          }
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int a = a2 + u;
+        C yra = czero<T>();
+        if (active) {
+          const C xa = xs_r[ty * 8 + a];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const int dr = (ty * 8 + a) - (tx * 8 + q);
+            if (!diag || dr < 0) {
+              cmac(yra, h[u][q], xcv[q]);
+              cmacc(yc[q], h[u][q], xa);
+            } else if (dr == 0) {
+              cmac(yra, h[u][q], xcv[q]);
+            }
           }
         }
+        red[tx][ty * 8 + a] = yra;
       }
-      red[tx][ty * 8 + a] = yra;
     }
   } else {
 #pragma unroll 1
@@ -176,121 +185,6 @@ __global__ void __launch_bounds__(256) herm_tile_nv1(const WorkItem* __restrict_
       part[(int64_t)it.ti * dpad + ct0 + tid] = cs;  // rows of tile tj, slot ti
     }
   }
-}
-
-// ---------------------------------------------------------------------------
-// (2) DVR Toeplitz-window kernel.  8 warps share the CTA's RB = 32*P rows and
-// split its KC columns; lane L owns rows R0 + P*L + [0,P).  For a block of U
-// columns the P x U sub-tile needs the P+U-1 window entries T(r - c), loaded
-// from shared memory once and reused from registers.  The window table is
-// stored with one pad slot per P entries so the lane-strided loads are free of
-// bank conflicts.
-// ---------------------------------------------------------------------------
-template <typename T, int P>
-__global__ void __launch_bounds__(256, 2) dvr_window(int64_t D, int64_t dpad, int kc, dvr_consts dk,
-                                                     const typename cplx<T>::t* __restrict__ xc,
-                                                     typename cplx<T>::t* __restrict__ part) {
-  using C = typename cplx<T>::t;
-  constexpr int U = P;
-  constexpr int RB = 32 * P;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int ntb = RB + kc - 1;
-  const int ntb_pad = ((ntb + ntb / P + 1) + 3) & ~3;
-  T* tb = reinterpret_cast<T*>(smem_raw);
-  C* xs = reinterpret_cast<C*>(tb + ntb_pad);
-
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const int64_t R0 = (int64_t)blockIdx.x * RB;
-  const int64_t C0 = (int64_t)blockIdx.y * kc;
-  const long long kmin = (long long)(R0 - C0) - kc + 1;
-  for (int j = tid; j < ntb; j += 256) tb[j + j / P] = dvr_T(dk, kmin + j, T());
-  for (int c = tid; c < kc; c += 256) {
-    const int64_t g = C0 + c;
-    xs[c] = g < D ? xc[g] : czero<T>();
-  }
-  __syncthreads();
-
-  T acc_r[P], acc_i[P];
-#pragma unroll
-  for (int a = 0; a < P; ++a) {
-    acc_r[a] = T(0);
-    acc_i[a] = T(0);
-  }
-  const int kw = kc / 8;
-  const int cbeg = w * kw, cend = cbeg + kw;
-#pragma unroll 1
-  for (int cc0 = cbeg; cc0 < cend; cc0 += U) {
-    // window start jb is a multiple of P, so padded offsets are compile-time
-    const int jb = P * lane - cc0 + kc - 1 - (U - 1);
-    const T* wp = tb + jb + jb / P;
-    T win[P + U - 1];
-#pragma unroll
-    for (int m = 0; m < P + U - 1; ++m) win[m] = wp[m + m / P];
-    C xv[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) xv[u] = xs[cc0 + u];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-#pragma unroll
-      for (int a = 0; a < P; ++a) {
-        const T t = win[a - u + U - 1];
-        acc_r[a] = fma(t, xv[u].x, acc_r[a]);
-        acc_i[a] = fma(t, xv[u].y, acc_i[a]);
-      }
-    }
-  }
-  __syncthreads();
-  // cross-warp sum in fixed warp order (reuses the x region)
-  C* red = xs;  // [8][RB]
-#pragma unroll
-  for (int a = 0; a < P; ++a) {
-    C v;
-    v.x = acc_r[a];
-    v.y = acc_i[a];
-    red[w * RB + P * lane + a] = v;
-  }
-  __syncthreads();
-  for (int r = tid; r < RB; r += 256) {
-    C s = red[r];
-#pragma unroll
-    for (int g = 1; g < 8; ++g) {
-      s.x += red[g * RB + r].x;
-      s.y += red[g * RB + r].y;
-    }
-    part[(int64_t)blockIdx.y * dpad + R0 + r] = s;
-  }
-}
-
-template <typename T, int P>
-static size_t dvr_smem_bytes(int kc) {
-  using C = typename cplx<T>::t;
-  const int RB = 32 * P;
-  const int ntb = RB + kc - 1;
-  const int ntb_pad = ((ntb + ntb / P + 1) + 3) & ~3;
-  const size_t xs = (size_t)kc * sizeof(C), red = (size_t)8 * RB * sizeof(C);
-  return (size_t)ntb_pad * sizeof(T) + (xs > red ? xs : red);
-}
-
-cudaError_t launch_dvr_apply(const Plan& p, const void* xc, void* part, int64_t nvec) {
-  if (nvec != 1) return cudaErrorNotSupported;
-  const int kc = p.dvr_cols;
-  const int64_t nslot = (p.D + kc - 1) / kc;
-  if (p.prec == MF_PREC_FP64) {
-    constexpr int P = 8;
-    const size_t sm = dvr_smem_bytes<double, P>(kc);
-    auto k = dvr_window<double, P>;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    dim3 grid((unsigned)((p.D + 32 * P - 1) / (32 * P)), (unsigned)nslot);
-    k<<<grid, 256, sm, p.stream>>>(p.D, p.dpad, kc, p.dvr, (const double2*)xc, (double2*)part);
-  } else {
-    constexpr int P = 16;
-    const size_t sm = dvr_smem_bytes<float, P>(kc);
-    auto k = dvr_window<float, P>;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    dim3 grid((unsigned)((p.D + 32 * P - 1) / (32 * P)), (unsigned)nslot);
-    k<<<grid, 256, sm, p.stream>>>(p.D, p.dpad, kc, p.dvr, (const float2*)xc, (float2*)part);
-  }
-  return cudaGetLastError();
 }
 
 cudaError_t launch_gue_apply(const Plan& p, const void* xc, void* part, int64_t nvec) {

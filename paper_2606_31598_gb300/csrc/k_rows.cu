@@ -19,7 +19,7 @@ namespace mf {
 
 // Split-K launcher: CTA (row tile, column range) -> part[slot][row][v].
 template <typename T, int GEN, int NV, int TR, int TV, int NT>
-__global__ void __launch_bounds__(NT) rows_simt(int64_t D, int64_t dpad, int64_t ksplit_cols, uint64_t seed,
+__global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) rows_simt(int64_t D, int64_t dpad, int64_t ksplit_cols, uint64_t seed,
                                                 T sigma, dvr_consts dk, const typename cplx<T>::t* __restrict__ xc,
                                                 typename cplx<T>::t* __restrict__ part,
                                                 const typename cplx<T>::t* __restrict__ cache,
@@ -56,8 +56,8 @@ static cudaError_t launch_rows_g(const Plan& p, const void* xc, void* part, int6
     case 16: return launch_rows_t<T, GEN, 16, 2, 4, 256>(p, xc, part);
     case 32: return launch_rows_t<T, GEN, 32, 4, 4, 256>(p, xc, part);
     case 64:
-      if (sizeof(T) == 4) return launch_rows_t<T, GEN, 64, 4, 8, 256>(p, xc, part);
-      return launch_rows_t<T, GEN, 64, 2, 8, 512>(p, xc, part);
+      if constexpr (sizeof(T) == 4) return launch_rows_t<T, GEN, 64, 4, 8, 256>(p, xc, part);
+      else return launch_rows_t<T, GEN, 64, 2, 8, 512>(p, xc, part);
   }
   return cudaErrorNotSupported;
 }

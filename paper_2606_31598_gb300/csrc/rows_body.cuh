@@ -48,17 +48,40 @@ __device__ __forceinline__ void fill_chunk(typename cplx<T>::t* hs, T* win, int6
     }
   }
   if (slot >= 0) {
-    const int64_t bb = b * b;
-    for (int e = tid; e < RT * KCH; e += NT) {
-      const int r = e / KCH, c = e % KCH;
-      C h;
+    // every load of the thread first, then the shared-memory stores; the
+    // transposed orientation walks the cached rows (r fastest) so a warp
+    // reads contiguous memory
+    constexpr int PER = RT * KCH / NT;
+    constexpr int HALF = PER > 8 ? PER / 2 : PER;
+    const C* blk = cache + slot * b * b;
+#pragma unroll
+    for (int i0 = 0; i0 < PER; i0 += HALF) {
+      C h[HALF];
       if (!transposed) {
-        h = cache[slot * bb + (R0 + r - n * b) * b + (c0 + c - m * b)];
+#pragma unroll
+        for (int i = 0; i < HALF; ++i) {
+          const int e = tid + (i0 + i) * NT, r = e / KCH, c = e % KCH;
+          h[i] = blk[(R0 + r - n * b) * b + (c0 + c - m * b)];
+        }
+#pragma unroll
+        for (int i = 0; i < HALF; ++i) {
+          const int e = tid + (i0 + i) * NT;
+          hs[(e / KCH) * LD + e % KCH] = h[i];
+        }
       } else {
-        h = cache[slot * bb + (c0 + c - m * b) * b + (R0 + r - n * b)];
-        h.y = -h.y;
+#pragma unroll
+        for (int i = 0; i < HALF; ++i) {
+          const int e = tid + (i0 + i) * NT, r = e % RT, c = e / RT;
+          h[i] = blk[(c0 + c - m * b) * b + (R0 + r - n * b)];
+        }
+#pragma unroll
+        for (int i = 0; i < HALF; ++i) {
+          const int e = tid + (i0 + i) * NT;
+          C v = h[i];
+          v.y = -v.y;
+          hs[(e % RT) * LD + e / RT] = v;
+        }
       }
-      hs[r * LD + c] = h;
     }
     return;
   }
