@@ -385,6 +385,83 @@ void or_bessel_j(double x, int32_t K, double* J) {
   for (int32_t k = 0; k <= K; ++k) J[k] /= norm;
 }
 
+/* ------------------------------------------------------------------------- */
+/* Scaled modified Bessel functions exp(-x) I_k(x), k = 0..K, by Miller's     */
+/* backward recurrence I_{k-1} = (2k/x) I_k + I_{k+1} (all terms positive),   */
+/* normalised with I_0 + 2 sum_{k>=1} I_k = exp(x), i.e. the scaled values    */
+/* sum to one.  These are the Chebyshev coefficients of exp(-z x) on [-1, 1]:  */
+/* exp(-z x) = I_0(z) + 2 sum (-1)^k I_k(z) T_k(x).                            */
+/* ------------------------------------------------------------------------- */
+void or_bessel_i_scaled(double x, int32_t K, double* I) {
+  for (int32_t k = 0; k <= K; ++k) I[k] = 0.0;
+  if (x == 0.0) {
+    I[0] = 1.0;
+    return;
+  }
+  int64_t top = (int64_t)K > (int64_t)ceil(x) ? (int64_t)K : (int64_t)ceil(x);
+  int64_t N = top + 30 + (int64_t)(20.0 * cbrt(x + 1.0)) + (int64_t)(2.0 * sqrt(x));
+  double ip1 = 0.0, i = 1.0, norm = 2.0;  /* I_N counted twice */
+  if (N <= K) I[N] = i;
+  for (int64_t k = N; k >= 1; --k) {
+    double im1 = (2.0 * (double)k / x) * i + ip1;
+    ip1 = i;
+    i = im1;
+    int64_t idx = k - 1;
+    if (idx <= K) I[idx] = i;
+    norm += (idx == 0) ? i : 2.0 * i;
+    if (i > 1e250) {
+      const double s = 1e-250;
+      i *= s; ip1 *= s; norm *= s;
+      for (int64_t q = idx; q <= K; ++q) I[q] *= s;
+    }
+  }
+  for (int32_t k = 0; k <= K; ++k) I[k] /= norm;
+}
+
+/* Imaginary-time Chebyshev filter (the thermal-pure-state filter of the     */
+/* paper's introduction and Sec. VII): exp(-tau H) = exp(-tau c) sum a_k      */
+/* T_k(Ht), a_0 = I_0(z), a_k = 2 (-1)^k I_k(z), z = tau R; with the scaled   */
+/* I_k the prefactor becomes exp(-tau (c - R)) = exp(-tau Emin), removed.     */
+void or_cheb_imag_step(const or_op* op, int64_t b, int64_t nvec, double* psi, double tau, double c, double R,
+                       int32_t nterms, int normalize, int nthreads) {
+  const int64_t n = op->D * nvec;
+  double* I = (double*)malloc(sizeof(double) * (size_t)(nterms + 1));
+  or_bessel_i_scaled(tau * R, nterms, I);
+  double* qm = (double*)malloc(sizeof(double) * 2 * (size_t)n);
+  double* q = (double*)malloc(sizeof(double) * 2 * (size_t)n);
+  double* y = (double*)malloc(sizeof(double) * 2 * (size_t)n);
+  double* acc = (double*)malloc(sizeof(double) * 2 * (size_t)n);
+  memcpy(q, psi, sizeof(double) * 2 * (size_t)n);
+  for (int64_t e = 0; e < 2 * n; ++e) acc[e] = I[0] * q[e];
+  for (int32_t k = 1; k < nterms; ++k) {
+    or_apply(op, b, nvec, q, y, nthreads);
+    for (int64_t e = 0; e < 2 * n; ++e) {
+      double t = (y[e] - c * q[e]) / R;
+      double qn = (k == 1) ? t : 2.0 * t - qm[e];
+      qm[e] = q[e];
+      q[e] = qn;
+    }
+    double ak = 2.0 * I[k] * ((k & 1) ? -1.0 : 1.0);
+    for (int64_t e = 0; e < 2 * n; ++e) acc[e] += ak * q[e];
+  }
+  if (normalize) {
+    for (int64_t v = 0; v < nvec; ++v) {
+      double s = 0.0;
+      for (int64_t r = 0; r < op->D; ++r) {
+        double a = acc[2 * (r * nvec + v)], bb = acc[2 * (r * nvec + v) + 1];
+        s += a * a + bb * bb;
+      }
+      s = sqrt(s);
+      for (int64_t r = 0; r < op->D; ++r) {
+        acc[2 * (r * nvec + v)] /= s;
+        acc[2 * (r * nvec + v) + 1] /= s;
+      }
+    }
+  }
+  memcpy(psi, acc, sizeof(double) * 2 * (size_t)n);
+  free(I); free(qm); free(q); free(y); free(acc);
+}
+
 /* Terms k = 0..n-1 such that |a_k| < tol for every k >= n, a_0 = J_0,        */
 /* a_k = 2 J_k (the coefficient-tolerance reading of Sec. VII's --cheb-tol).   */
 int32_t or_cheb_terms(double z, double tol) {

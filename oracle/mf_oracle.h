@@ -62,6 +62,12 @@ void or_apply_rows(const or_op* op, int64_t nvec, const double* x, int64_t nrows
 
 /* Bessel J_0..J_K(x) by Miller's backward recurrence. */
 void or_bessel_j(double x, int32_t K, double* J);
+/* Scaled modified Bessel functions exp(-x) I_k(x), k = 0..K (Miller). */
+void or_bessel_i_scaled(double x, int32_t K, double* I);
+/* Imaginary-time filter psi <- exp(-tau (H - Emin)) psi, Emin = c - R, with
+ * nterms terms; columns renormalised to unit norm when normalize != 0. */
+void or_cheb_imag_step(const or_op* op, int64_t b, int64_t nvec, double* psi, double tau, double c, double R,
+                       int32_t nterms, int normalize, int nthreads);
 /* Number of Chebyshev terms for argument z = R*dt at tolerance tol. */
 int32_t or_cheb_terms(double z, double tol);
 /* One Chebyshev step psi <- exp(-i dt H) psi with nterms terms (k = 0..nterms-1),

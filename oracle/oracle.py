@@ -56,6 +56,8 @@ def lib():
         L.or_bessel_j.argtypes = [d, i32, vp]
         L.or_cheb_terms.argtypes = [d, d]; L.or_cheb_terms.restype = i32
         L.or_cheb_step.argtypes = [P(OrOp), i64, i64, vp, d, d, d, i32, ctypes.c_int]
+        L.or_bessel_i_scaled.argtypes = [d, i32, vp]
+        L.or_cheb_imag_step.argtypes = [P(OrOp), i64, i64, vp, d, d, d, i32, ctypes.c_int, ctypes.c_int]
         _lib = L
     return _lib
 
@@ -163,6 +165,32 @@ def bessel_j(x, K):
     J = np.zeros(K + 1, dtype=np.float64)
     lib().or_bessel_j(float(x), int(K), J.ctypes.data)
     return J
+
+
+def bessel_i_scaled(x, K):
+    I = np.zeros(K + 1, dtype=np.float64)
+    lib().or_bessel_i_scaled(float(x), int(K), I.ctypes.data)
+    return I
+
+
+def cheb_imag_terms(z, tol):
+    """Smallest n with |a_k| < tol for every k >= n, a_0 = e^-z I_0(z),
+    a_k = 2 e^-z I_k(z) (the coefficients decrease monotonically in k)."""
+    K = int(np.ceil(z)) + 60 + int(30.0 * np.cbrt(z + 1.0))
+    I = bessel_i_scaled(z, K)
+    a = np.concatenate([[I[0]], 2.0 * I[1:]])
+    big = np.nonzero(a >= tol)[0]
+    return int(big[-1]) + 1 if big.size else 1
+
+
+def cheb_imag_step(op, psi, tau, c, R, nterms, normalize=True, block=0, nthreads=0):
+    """psi <- exp(-tau (H - Emin)) psi (Emin = c - R), optionally renormalised."""
+    psi = np.asarray(psi, dtype=np.complex128)
+    shape = psi.shape
+    P = np.ascontiguousarray(psi.reshape(op.D, -1)).copy()
+    lib().or_cheb_imag_step(ctypes.byref(op), int(block), int(P.shape[1]), P.ctypes.data, float(tau), float(c),
+                            float(R), int(nterms), int(bool(normalize)), int(nthreads))
+    return P.reshape(shape)
 
 
 def cheb_terms(z, tol):

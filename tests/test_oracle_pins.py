@@ -292,3 +292,76 @@ def test_dvr_coherent_state_half_period():
     for _ in range(nsteps):
         psi = O.cheb_step_dense(H, psi, dt, c, R, nterms)
     assert np.max(np.abs(psi + psi0)) < 1e-9
+
+
+# ------------------------------------------------ imaginary-time filter ----
+@pytest.mark.parametrize("x", [0.0, 0.4, 3.0, 57.0, 900.0])
+def test_scaled_modified_bessel_against_scipy(x):
+    from scipy import special
+    K = int(x) + 80
+    I = O.bessel_i_scaled(x, K)
+    ref = special.ive(np.arange(K + 1), x)
+    assert np.max(np.abs(I - ref)) < 1e-15
+    big = ref > 1e-200
+    assert np.max(np.abs(I[big] - ref[big]) / ref[big]) < 1e-11
+
+
+def test_scaled_modified_bessel_chebyshev_identities():
+    """exp(-z x) = I_0 + 2 sum (-1)^k I_k T_k(x): at x = 1 (T_k = 1) the scaled
+    series gives e^{-2z}, at x = -1 it gives 1, at x = 0 it gives e^{-z}."""
+    for z in (0.7, 12.0, 140.0):
+        I = O.bessel_i_scaled(z, int(z) + 120)
+        sgn = (-1.0) ** np.arange(1, I.size)
+        assert abs(I[0] + 2 * I[1:].sum() - 1.0) < 1e-13
+        assert abs(I[0] + 2 * (sgn * I[1:]).sum() - np.exp(-2 * z)) < 1e-13
+        t0 = np.cos(np.arange(1, I.size) * np.pi / 2)  # T_k(0)
+        assert abs(I[0] + 2 * (sgn * I[1:] * t0).sum() - np.exp(-z)) < 1e-13
+
+
+def test_cheb_imag_terms_rule():
+    # the largest dropped coefficient is below tol and the last kept is not
+    for z, tol in ((5.0, 1e-7), (160.0, 1e-10)):
+        n = O.cheb_imag_terms(z, tol)
+        I = O.bessel_i_scaled(z, n + 50)
+        assert 2 * I[n] < tol <= 2 * I[n - 1]
+
+
+@pytest.mark.parametrize("normalize", [False, True])
+def test_cheb_imag_step_matches_eigendecomposition(normalize):
+    """exp(-tau (H - Emin)) on a D = 160 Philox operator, two columns."""
+    D = 160
+    op = O.make_op(O.GEN_PHILOX_GUE, D, seed=3)
+    H = O.dense(op)
+    c, R, E = _bounds(H)
+    rng = np.random.default_rng(9)
+    psi = rng.standard_normal((D, 2)) + 1j * rng.standard_normal((D, 2))
+    tau = 0.8
+    nt = O.cheb_imag_terms(R * tau, 1e-15)
+    out = O.cheb_imag_step(op, psi, tau, c, R, nt, normalize=normalize)
+    w, V = np.linalg.eigh(H)
+    exact = V @ (np.exp(-tau * (w - (c - R)))[:, None] * (V.conj().T @ psi))
+    if normalize:
+        exact /= np.linalg.norm(exact, axis=0)
+    assert np.max(np.abs(out - exact)) < 1e-12 * np.max(np.abs(exact))
+
+
+def test_dvr_imaginary_time_coherent_state_closed_form():
+    """Harmonic oscillator: exp(-tau H) maps the coherent state centred at x0
+    to e^{-tau/2} exp(-x0^2 (1 - e^{-2 tau}) / 4) times the coherent state
+    centred at x0 e^{-tau} (both unit norm), so the filtered, normalised
+    state is a Gaussian at x0 e^{-tau} and the unnormalised norm is fixed."""
+    D = 256
+    op = O.make_op(O.GEN_SINC_DVR_HO, D)
+    dx = 2 * op.L / (D - 1)
+    x = -op.L + dx * np.arange(D)
+    x0, tau = 2.0, 0.6
+    g = lambda m: np.exp(-0.5 * (x - m) ** 2) / np.linalg.norm(np.exp(-0.5 * (x - m) ** 2))
+    psi0 = g(x0).astype(np.complex128)
+    Emin, Emax = 0.0, np.pi ** 2 / (2 * dx * dx) + 0.5 * op.L ** 2
+    c, R = 0.5 * (Emax + Emin), 0.5 * (Emax - Emin)
+    nt = O.cheb_imag_terms(R * tau, 1e-15)
+    raw = O.cheb_imag_step(op, psi0, tau, c, R, nt, normalize=False)
+    want_norm = np.exp(-tau / 2) * np.exp(-x0 ** 2 * (1 - np.exp(-2 * tau)) / 4)
+    assert abs(np.linalg.norm(raw) - want_norm) < 1e-9
+    out = O.cheb_imag_step(op, psi0, tau, c, R, nt, normalize=True)
+    assert np.max(np.abs(out - g(x0 * np.exp(-tau)))) < 1e-9
