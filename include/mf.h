@@ -212,6 +212,25 @@ mf_status mf_cheb_propagate(mf_plan_t p, void* psi, int64_t nvec, double dt, int
 mf_status mf_cheb_terms(mf_plan_t p, double dt, int32_t* nterms);
 
 /*
+ * mf_cheb_filter -- imaginary-time Chebyshev filter, the thermal-pure-state
+ * preparation named in Sec. I and used in Sec. VII (a random vector filtered
+ * by exp(-beta H / 2), then normalised):
+ *   psi <- exp(-tau (H - E_min)) psi,  E_min = c - R (the padded lower bound),
+ * by the recurrence of mf_cheb_propagate with real coefficients
+ * a_0 = e^{-z} I_0(z), a_k = 2 (-1)^k e^{-z} I_k(z), z = R tau (modified Bessel
+ * functions, FP64 on the GPU).  The shift by E_min keeps every factor <= 1.
+ *   psi       : device complex128 [D][nvec] (nvec 1..64), updated in place.
+ *   tau       : imaginary time >= 0 (beta / 2 for a canonical TPQ state).
+ *   order     : terms k = 0..order-1; 0 = smallest count meeting opt.cheb_tol.
+ *   normalize : nonzero = divide each column by its 2-norm afterwards
+ *               (deterministic FP64 reduction; a zero column stays zero).
+ * Errors: MF_ERR_INVALID, MF_ERR_CUDA.  Asynchronous.
+ */
+mf_status mf_cheb_filter(mf_plan_t p, void* psi, int64_t nvec, double tau, int32_t order, int32_t normalize);
+/* Number of terms mf_cheb_filter would use for tau (synchronises). */
+mf_status mf_cheb_filter_terms(mf_plan_t p, double tau, int32_t* nterms);
+
+/*
  * mf_spectral_bounds -- E_min, E_max used by the Chebyshev scaling (Sec. VII):
  * Lanczos with opt.lanczos_m steps on the GPU (Ritz extremes padded by
  * opt.bounds_pad of the half-width) for PHILOX_GUE; [min V, pi^2/(2 dx^2) +

@@ -110,6 +110,8 @@ def lib():
         L.mf_apply.argtypes = [vp, vp, vp, i64]
         L.mf_cheb_propagate.argtypes = [vp, vp, i64, d, i32]
         L.mf_cheb_terms.argtypes = [vp, d, P(i32)]
+        L.mf_cheb_filter.argtypes = [vp, vp, i64, d, i32, i32]
+        L.mf_cheb_filter_terms.argtypes = [vp, d, P(i32)]
         L.mf_spectral_bounds.argtypes = [vp, P(d), P(d)]
         L.mf_plan_set_bounds.argtypes = [vp, d, d]
         L.mf_sync.argtypes = [vp]
@@ -144,7 +146,7 @@ def lib():
             getattr(L, name).restype = ctypes.c_int
         L.mf_plan_profile_read.argtypes = [vp, P(d), P(i64)]
         for name in ("mf_plan_create", "mf_plan_destroy", "mf_apply", "mf_cheb_propagate", "mf_cheb_terms",
-                     "mf_spectral_bounds", "mf_plan_set_bounds", "mf_sync", "mf_plan_describe",
+                     "mf_cheb_filter", "mf_cheb_filter_terms", "mf_spectral_bounds", "mf_plan_set_bounds", "mf_sync", "mf_plan_describe",
                      "mf_debug_entries", "mf_plan_profile", "mf_plan_profile_read", "mf_apply_dvr_noalloc"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
@@ -209,6 +211,17 @@ def mf_cheb_propagate(plan, psi, nvec, dt, order=0):
 def mf_cheb_terms(plan, dt):
     n = ctypes.c_int32()
     _check(lib().mf_cheb_terms(plan, float(dt), ctypes.byref(n)), "mf_cheb_terms")
+    return n.value
+
+
+def mf_cheb_filter(plan, psi, nvec, tau, order=0, normalize=True):
+    return _check(lib().mf_cheb_filter(plan, _ptr(psi), int(nvec), float(tau), int(order), int(bool(normalize))),
+                  "mf_cheb_filter")
+
+
+def mf_cheb_filter_terms(plan, tau):
+    n = ctypes.c_int32()
+    _check(lib().mf_cheb_filter_terms(plan, float(tau), ctypes.byref(n)), "mf_cheb_filter_terms")
     return n.value
 
 
@@ -423,6 +436,12 @@ class Plan:
 
     def cheb_terms(self, dt):
         return mf_cheb_terms(self.handle, dt)
+
+    def cheb_filter(self, psi, nvec, tau, order=0, normalize=True):
+        return mf_cheb_filter(self.handle, psi, nvec, tau, order, normalize)
+
+    def cheb_filter_terms(self, tau):
+        return mf_cheb_filter_terms(self.handle, tau)
 
     def bounds(self):
         return mf_spectral_bounds(self.handle)

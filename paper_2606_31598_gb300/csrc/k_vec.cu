@@ -126,8 +126,9 @@ template <typename C>
 __global__ void k_cheb_update(const C* __restrict__ part, VecShape sh, int64_t n, int dvr, dvr_consts dk,
                               const double2* __restrict__ qcur, double2* __restrict__ qprev,
                               double2* __restrict__ acc, C* __restrict__ xc, const double* __restrict__ J,
-                              int32_t j, double c, double R) {
-  const double aj = 2.0 * J[j];
+                              int32_t j, double c, double R, int imag_time) {
+  // real time: a_j = 2 (-i)^j J_j; imaginary time: a_j = 2 (-1)^j e^{-z} I_j
+  const double aj = (imag_time && (j & 1)) ? -2.0 * J[j] : 2.0 * J[j];
   const int64_t stride = sh.dpad * sh.nb;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t row = e / sh.nv, v = e % sh.nv;
@@ -146,9 +147,9 @@ __global__ void k_cheb_update(const C* __restrict__ part, VecShape sh, int64_t n
       ti = 2.0 * ti - qp.y;
     }
     qprev[e] = make_double2(tr, ti);
-    // (-i)^j rotation, then scale by 2 J_j
+    // (-i)^j rotation (real time only), then scale by a_j
     double rr, ri;
-    switch (j & 3) {
+    switch (imag_time ? 0 : (j & 3)) {
       case 0: rr = tr; ri = ti; break;
       case 1: rr = ti; ri = -tr; break;
       case 2: rr = -tr; ri = -ti; break;
@@ -166,15 +167,15 @@ __global__ void k_cheb_update(const C* __restrict__ part, VecShape sh, int64_t n
 }
 
 cudaError_t launch_cheb_update(const Plan& p, const void* part, const double2* qcur, double2* qprev, double2* acc,
-                               void* xc, VecShape s, int32_t k_next, double c, double R) {
+                               void* xc, VecShape s, int32_t k_next, double c, double R, int imag_time) {
   const int64_t n = p.D * s.nv;
   const int dvr = p.gen == MF_GEN_SINC_DVR_HO;
   if (p.prec == MF_PREC_FP64)
     k_cheb_update<double2><<<grid_for(n), 256, 0, p.stream>>>((const double2*)part, s, n, dvr, p.dvr, qcur, qprev,
-                                                              acc, (double2*)xc, p.d_J, k_next, c, R);
+                                                              acc, (double2*)xc, p.d_J, k_next, c, R, imag_time);
   else
     k_cheb_update<float2><<<grid_for(n), 256, 0, p.stream>>>((const float2*)part, s, n, dvr, p.dvr, qcur, qprev,
-                                                             acc, (float2*)xc, p.d_J, k_next, c, R);
+                                                             acc, (float2*)xc, p.d_J, k_next, c, R, imag_time);
   return cudaGetLastError();
 }
 
@@ -231,6 +232,99 @@ __global__ void k_bessel(double z, int32_t K, double* __restrict__ J) {
 
 cudaError_t launch_bessel(const Plan& p, double z, int32_t K, double* J) {
   k_bessel<<<1, 32, 0, p.stream>>>(z, K, J);
+  return cudaGetLastError();
+}
+
+// Scaled modified Bessel functions e^{-z} I_k(z), k = 0..K: Miller's backward
+// recurrence I_{k-1} = (2k/z) I_k + I_{k+1} (every term positive, so no
+// cancellation), normalised with I_0 + 2 sum_{k>=1} I_k = e^z.  These give the
+// Chebyshev series of exp(-z x) on [-1, 1] with the factor e^{z} taken out.
+__global__ void k_bessel_i(double z, int32_t K, double* __restrict__ I) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int k = 0; k <= K; ++k) I[k] = 0.0;
+  if (z == 0.0) {
+    I[0] = 1.0;
+    return;
+  }
+  const long long zc = (long long)ceil(z);
+  const long long start = (K > zc ? K : zc) + 30 + (long long)(20.0 * cbrt(z + 1.0)) + (long long)(2.0 * sqrt(z));
+  double hi = 0.0, cur = 1.0, sum = 2.0;  // I_start counts twice
+  if (start <= K) I[start] = cur;
+  for (long long k = start; k >= 1; --k) {
+    const double nxt = (2.0 * (double)k / z) * cur + hi;
+    hi = cur;
+    cur = nxt;
+    const long long idx = k - 1;
+    if (idx <= K) I[idx] = cur;
+    sum += (idx == 0) ? cur : 2.0 * cur;
+    if (cur > 1e250) {
+      cur *= 1e-250;
+      hi *= 1e-250;
+      sum *= 1e-250;
+      for (long long q = idx; q <= K; ++q) I[q] *= 1e-250;
+    }
+  }
+  const double inv = 1.0 / sum;
+  for (int k = 0; k <= K; ++k) I[k] *= inv;
+}
+
+cudaError_t launch_bessel_i(const Plan& p, double z, int32_t K, double* I) {
+  k_bessel_i<<<1, 32, 0, p.stream>>>(z, K, I);
+  return cudaGetLastError();
+}
+
+// Column norms of a [D][nv] complex128 block, deterministic: CTA (s, v) sums
+// |a_{r,v}|^2 over rows r = s*256 + t (+ kColSplit*256 strides), then one
+// thread per column adds the kColSplit partials in order and stores 1/norm
+// (0 for a zero column, which is then left as zeros).
+constexpr int kColSplit = 64;
+
+__global__ void k_colnorm_partial(const double2* __restrict__ a, int64_t nrow, int64_t nv,
+                                  double* __restrict__ partial) {
+  __shared__ double sh[256];
+  const int64_t v = blockIdx.y;
+  double s = 0.0;
+  for (int64_t r = (int64_t)blockIdx.x * 256 + threadIdx.x; r < nrow; r += (int64_t)kColSplit * 256) {
+    const double2 u = a[r * nv + v];
+    s += u.x * u.x + u.y * u.y;
+  }
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[v * kColSplit + blockIdx.x] = sh[0];
+}
+
+__global__ void k_colnorm_final(const double* __restrict__ partial, int64_t nv, double* __restrict__ inv) {
+  const int64_t v = threadIdx.x;
+  if (v >= nv) return;
+  double s = 0.0;
+  for (int q = 0; q < kColSplit; ++q) s += partial[v * kColSplit + q];
+  inv[v] = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
+}
+
+// psi[r][v] = acc[r][v] * inv[v] (inv == nullptr: plain copy)
+__global__ void k_scale_columns(const double2* __restrict__ acc, double2* __restrict__ psi, int64_t n, int64_t nv,
+                                const double* __restrict__ inv) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const double s = inv ? inv[e % nv] : 1.0;
+    const double2 a = acc[e];
+    psi[e] = make_double2(s * a.x, s * a.y);
+  }
+}
+
+cudaError_t launch_filter_final(const Plan& p, const double2* acc, double2* psi, int64_t nv, int normalize) {
+  const int64_t n = p.D * nv;
+  double* inv = nullptr;
+  if (normalize) {
+    double* partial = p.d_red;
+    inv = p.d_red + kColSplit * 64;
+    k_colnorm_partial<<<dim3(kColSplit, (unsigned)nv), 256, 0, p.stream>>>(acc, p.D, nv, partial);
+    k_colnorm_final<<<1, 64, 0, p.stream>>>(partial, nv, inv);
+  }
+  k_scale_columns<<<grid_for(n), 256, 0, p.stream>>>(acc, psi, n, nv, inv);
   return cudaGetLastError();
 }
 

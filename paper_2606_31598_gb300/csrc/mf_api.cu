@@ -245,15 +245,21 @@ mf_status compute_bounds(Plan& p) {
 // Bessel coefficients J_k(z), k = 0..K on the device, cached per argument.
 // With order == 0 the term count is the smallest n with |a_k| < tol for all
 // k >= n (a_0 = J_0, a_k = 2 J_k), read back once per argument.
-mf_status coefficients(Plan& p, double z, int32_t order, int32_t* nterms) {
+// kind 1 computes e^{-z} I_k(z) instead (imaginary-time filter), whose terms
+// fall off past k ~ sqrt(z) rather than k ~ z: the same K bound covers them.
+mf_status coefficients(Plan& p, double z, int32_t order, int32_t* nterms, int32_t kind = 0) {
   const int32_t Kmax = (int32_t)std::ceil(z) + 60 + (int32_t)(30.0 * std::cbrt(z + 1.0));
   const int32_t K = std::max(Kmax, order);
-  if (p.J_arg != z || p.J_K < K) {
+  if (p.J_arg != z || p.J_K < K || p.J_kind != kind) {
     mf_status st = ensure_J(p, K);
     if (st != MF_OK) return st;
-    MF_CUDA(launch_bessel(p, z, K, p.d_J));
+    if (kind)
+      MF_CUDA(launch_bessel_i(p, z, K, p.d_J));
+    else
+      MF_CUDA(launch_bessel(p, z, K, p.d_J));
     p.J_arg = z;
     p.J_K = K;
+    p.J_kind = kind;
     p.J_terms = 0;
   }
   if (order > 0) {
@@ -388,7 +394,7 @@ mf_status create_fixed(mf_plan_t* out, int64_t D, int32_t generator, uint64_t se
 
   if (cudaMalloc((void**)&p.d_err, sizeof(int)) != cudaSuccess) return fail(MF_ERR_OOM);
   if (cudaMemsetAsync(p.d_err, 0, sizeof(int), p.stream) != cudaSuccess) return fail(MF_ERR_CUDA);
-  if (cudaMalloc((void**)&p.d_red, 512 * sizeof(double)) != cudaSuccess) return fail(MF_ERR_OOM);
+  if (cudaMalloc((void**)&p.d_red, kRedDoubles * sizeof(double)) != cudaSuccess) return fail(MF_ERR_OOM);
 
   // cache: the first P_cache canonical pairs in row order
   p.pair_slot.assign((size_t)(p.nblk * p.nblk), -1);
@@ -468,8 +474,8 @@ const char* store_name(int s) {
 namespace mf {
 mf_status plan_workspace(Plan& p, int64_t nvec) { return ensure_workspace(p, nvec); }
 mf_status plan_bounds(Plan& p) { return compute_bounds(p); }
-mf_status plan_coefficients(Plan& p, double z, int32_t order, int32_t* nterms) {
-  return coefficients(p, z, order, nterms);
+mf_status plan_coefficients(Plan& p, double z, int32_t order, int32_t* nterms, int32_t kind) {
+  return coefficients(p, z, order, nterms, kind);
 }
 }  // namespace mf
 
@@ -824,10 +830,50 @@ mf_status mf_cheb_propagate(mf_plan_t h, void* psi, int64_t nvec, double dt, int
   MF_CUDA(launch_cheb_init(p, (const double2*)psi, q_cur, acc, p.d_xc, sh));
   for (int32_t j = 1; j < nt; ++j) {
     if ((st = apply_kernel(p, nvec)) != MF_OK) return st;
-    MF_CUDA(launch_cheb_update(p, p.d_part, q_cur, q_prev, acc, p.d_xc, sh, j, c, R));
+    MF_CUDA(launch_cheb_update(p, p.d_part, q_cur, q_prev, acc, p.d_xc, sh, j, c, R, 0));
     std::swap(q_cur, q_prev);
   }
   MF_CUDA(launch_cheb_final(p, acc, (double2*)psi, p.D * nvec, c, dt));
+  return MF_OK;
+}
+
+mf_status mf_cheb_filter_terms(mf_plan_t h, double tau, int32_t* nterms) {
+  if (!h || !nterms || !(tau >= 0) || !std::isfinite(tau)) return MF_ERR_INVALID;
+  Plan& p = h->p;
+  DeviceGuard guard(p.device);
+  mf_status st = compute_bounds(p);
+  if (st != MF_OK) return st;
+  const double R = 0.5 * (p.emax - p.emin);
+  return coefficients(p, R * tau, 0, nterms, 1);
+}
+
+// Same recurrence as mf_cheb_propagate with the real coefficients of
+// exp(-z x) = I_0(z) + 2 sum (-1)^k I_k(z) T_k(x), z = R tau, scaled by e^{-z}:
+// the result is exp(-tau (H - E_min)) psi with E_min = c - R, so no factor
+// e^{-tau E} can overflow or underflow.
+mf_status mf_cheb_filter(mf_plan_t h, void* psi, int64_t nvec, double tau, int32_t order, int32_t normalize) {
+  if (!h || !psi || nvec < 1 || nvec > 64 || !(tau >= 0) || !std::isfinite(tau) || order < 0) return MF_ERR_INVALID;
+  Plan& p = h->p;
+  DeviceGuard guard(p.device);
+  mf_status st = compute_bounds(p);
+  if (st != MF_OK) return st;
+  const double c = 0.5 * (p.emax + p.emin), R = 0.5 * (p.emax - p.emin);
+  int32_t nt = 0;
+  st = coefficients(p, R * tau, order, &nt, 1);
+  if (st != MF_OK) return st;
+  st = ensure_workspace(p, nvec);
+  if (st != MF_OK) return st;
+  const VecShape sh = shape_for(p, nvec);
+  double2* q_prev = p.d_q[0];
+  double2* q_cur = p.d_q[1];
+  double2* acc = p.d_q[2];
+  MF_CUDA(launch_cheb_init(p, (const double2*)psi, q_cur, acc, p.d_xc, sh));
+  for (int32_t j = 1; j < nt; ++j) {
+    if ((st = apply_kernel(p, nvec)) != MF_OK) return st;
+    MF_CUDA(launch_cheb_update(p, p.d_part, q_cur, q_prev, acc, p.d_xc, sh, j, c, R, 1));
+    std::swap(q_cur, q_prev);
+  }
+  MF_CUDA(launch_filter_final(p, acc, (double2*)psi, nvec, normalize != 0));
   return MF_OK;
 }
 

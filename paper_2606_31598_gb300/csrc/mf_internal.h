@@ -63,7 +63,7 @@ struct Plan {
   void* d_xc = nullptr;           // compute-precision copy of the input
   void* d_tcb = nullptr;          // BF16X2: split operand tiles of X
   double2* d_q[3] = {nullptr, nullptr, nullptr};  // Chebyshev q_prev, q_cur, acc
-  double* d_J = nullptr;          // Bessel J_k(R dt)
+  double* d_J = nullptr;          // Bessel J_k(R dt), or scaled I_k(R tau) for the filter
   int32_t J_cap = 0;
   double* d_red = nullptr;        // small reduction scratch (dots/norms)
   int* d_err = nullptr;           // device error word
@@ -72,6 +72,7 @@ struct Plan {
   double emin = 0.0, emax = 0.0;
   // Chebyshev coefficient cache
   double J_arg = -1.0;
+  int32_t J_kind = 0;             // 0: J_k (real time), 1: e^{-z} I_k (imaginary time)
   int32_t J_K = 0;
   int32_t J_terms = 0;
   // per-launch timing of the apply kernel (CUDA events on the plan's stream)
@@ -92,7 +93,7 @@ struct Plan {
 // Plan services shared with the batched path (mf_api.cu).
 mf_status plan_workspace(Plan& p, int64_t nvec);
 mf_status plan_bounds(Plan& p);
-mf_status plan_coefficients(Plan& p, double z, int32_t order, int32_t* nterms);
+mf_status plan_coefficients(Plan& p, double z, int32_t order, int32_t* nterms, int32_t kind = 0);
 
 // ---- launchers (return cudaError_t of the launch) ----
 // Hermitian canonical-tile apply, nvec == 1 register kernel.
@@ -123,9 +124,15 @@ cudaError_t launch_reduce(const Plan& p, const void* part, const double2* x, dou
 // Chebyshev pieces.
 cudaError_t launch_cheb_init(const Plan& p, const double2* psi, double2* q, double2* acc, void* xc, VecShape s);
 cudaError_t launch_cheb_update(const Plan& p, const void* part, const double2* qcur, double2* qprev,
-                               double2* acc, void* xc, VecShape s, int32_t k_next, double c, double R);
+                               double2* acc, void* xc, VecShape s, int32_t k_next, double c, double R,
+                               int imag_time);
 cudaError_t launch_cheb_final(const Plan& p, const double2* acc, double2* psi, int64_t n, double c, double dt);
 cudaError_t launch_bessel(const Plan& p, double z, int32_t K, double* J);
+// Imaginary-time filter pieces: scaled I_k(z) and the final copy with optional
+// per-column renormalisation (reduction scratch in d_red: 64*64 + 64 doubles).
+cudaError_t launch_bessel_i(const Plan& p, double z, int32_t K, double* I);
+cudaError_t launch_filter_final(const Plan& p, const double2* acc, double2* psi, int64_t nv, int normalize);
+constexpr int64_t kRedDoubles = 64 * 64 + 64 + 512;
 // Lanczos helpers: out[0] = Re<a,b>, FP64 reduction into d_red slot.
 cudaError_t launch_dot(const Plan& p, const double2* a, const double2* b, int64_t n, double* out);
 cudaError_t launch_axpby_lanczos(const Plan& p, double2* w, const double2* v, const double2* vprev,
