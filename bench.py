@@ -103,7 +103,7 @@ class ClockSampler:
 def traffic_from_profile():
     """DRAM bytes per launch of the dominant kernel from the committed ncu
     summary, valid only while the kernel source is unchanged."""
-    path = os.path.join(ROOT, "profiles", "dvr_window_f32_D131072.md")
+    path = os.path.join(ROOT, "profiles", "dvr_rows_f32_D131072.md")
     src = os.path.join(ROOT, "paper_2606_31598_gb300", "csrc", "k_dvr.cu")
     try:
         txt = open(path).read()
@@ -325,7 +325,7 @@ def run_mf(args):
             "error": err,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": (achieved / peak) if peak else None, "traffic": traffic,
-                         "kernel": "dvr_window<float,16>", "flop_per_launch": 4.0 * D * D,
+                         "kernel": "dvr_rows_f32", "flop_per_launch": 4.0 * D * D,
                          "peak_basis": "%d SMs x 128 FP32 lanes x 2 FLOP x median sampled SM clock" % nsm,
                          "kernel_ms": per_launch_s * 1e3, "kernel_launches_timed": kern_n},
             "e2e": {"value": e2e_value, "unit": "entries/s", "h2d_bytes_per_step": D * 16, "d2h_bytes_per_step": D * 16},

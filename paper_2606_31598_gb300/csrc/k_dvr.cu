@@ -9,6 +9,8 @@
 // pipe with register-blocked 16 x 16 sub-tiles.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "mf_internal.h"
 
 namespace mf {
@@ -101,6 +103,142 @@ __global__ void __launch_bounds__(256, 2) dvr_window(int64_t D, int64_t dpad, in
   }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 form: persistent row-split kernel.
+//
+// Row tiles of kDvrRB = 4096 rows; warp w of a CTA owns rows 512 w + [0, 512)
+// of the tile, lane L the 16 rows 16 L + [0, 16), so every row's sum stays in
+// one thread's registers: no cross-warp reduction.  The work (row tile,
+// 16-column block) pairs are numbered row tile by row tile and split into
+// gridDim.x contiguous, equal ranges, so the load is balanced to one block.
+// A CTA stages each 2048-column chunk it touches (x chunk and the RB + KC - 1
+// window entries T(r - c), generated once per chunk) in shared memory and
+// keeps its accumulators in registers across the chunks of a row tile.
+//
+// Per 16 x 16 block a lane reads its 31 window entries (32 with one spare)
+// with eight 16-byte loads (the table is padded by 4 floats per 16 entries,
+// so the lanes' 80-byte strided loads are free of bank conflicts) and the 16
+// x entries with eight 16-byte broadcast loads, then issues 256 packed FMAs
+// (__ffma2_rn: per lane and component the rounding of __fmaf_rn) updating
+// the real and imaginary parts of a row together.
+//
+// Each CTA writes one partial per row tile it touched into slot
+// (its index - index of the first CTA of that row tile); the CTA holding the
+// row tile's last block also zero-fills the slots above its own, so every
+// slot row the reduction reads is written.
+// ---------------------------------------------------------------------------
+constexpr int kDvrP = 16, kDvrU = 16, kDvrWarps = 8;
+constexpr int kDvrRB = kDvrWarps * 32 * kDvrP;  // 4096 rows per row tile
+constexpr int kDvrKC = 2048;                    // staged columns per chunk
+constexpr int kDvrNTB = kDvrRB + kDvrKC - 1;    // window entries per chunk
+constexpr int kDvrTbFloats = ((kDvrNTB + 1 + 15) / 16) * 20;
+constexpr size_t kDvrSmem = (size_t)kDvrTbFloats * sizeof(float) + (size_t)kDvrKC * sizeof(float2);
+
+__host__ __device__ __forceinline__ int64_t split_lo(int64_t b, int64_t n, int64_t g) { return b * n / g; }
+// CTA whose range [split_lo(b), split_lo(b + 1)) holds item i
+__host__ __device__ __forceinline__ int64_t split_owner(int64_t i, int64_t n, int64_t g) {
+  int64_t b = i * g / n;
+  while (split_lo(b + 1, n, g) <= i) ++b;
+  while (split_lo(b, n, g) > i) --b;
+  return b;
+}
+__device__ __forceinline__ int dvr_wpad(int j) { return j + (j >> 4) * 4; }
+
+__global__ void __launch_bounds__(256, 2) dvr_rows_f32(int64_t D, int64_t dpad, int64_t nslot, int64_t nbc,
+                                                       int64_t nblocks, dvr_consts dk, const float2* __restrict__ xc,
+                                                       float2* __restrict__ part) {
+  constexpr int P = kDvrP, U = kDvrU, KC = kDvrKC, BPC = KC / U;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* tb = reinterpret_cast<float*>(smem_raw);
+  float2* xs = reinterpret_cast<float2*>(tb + kDvrTbFloats);
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int64_t G = gridDim.x, b = blockIdx.x;
+  const int64_t lo = split_lo(b, nblocks, G), hi = split_lo(b + 1, nblocks, G);
+  const int jb0 = 512 * w + P * lane + KC - U;  // window start of the chunk's first block
+  float2 acc[P];
+  for (int64_t cur = lo; cur < hi;) {
+    const int64_t rt = cur / nbc, cb = cur - rt * nbc;
+    const int64_t chunk = cb / BPC;
+    const int64_t seg_end = min(hi, rt * nbc + min((chunk + 1) * BPC, nbc));
+    if (cur == lo || cb == 0) {
+#pragma unroll
+      for (int a = 0; a < P; ++a) acc[a] = make_float2(0.f, 0.f);
+    }
+    const int64_t R0 = rt * kDvrRB, C0 = chunk * KC;
+    __syncthreads();  // the previous segment is done with the staged chunk
+    for (int c = tid; c < KC; c += 256) {
+      const int64_t g = C0 + c;
+      xs[c] = g < D ? xc[g] : make_float2(0.f, 0.f);
+    }
+    const long long kmin = (long long)(R0 - C0) - KC + 1;
+    for (int j = tid; j <= kDvrNTB; j += 256) tb[dvr_wpad(j)] = j < kDvrNTB ? dvr_T_f32(dk, kmin + j) : 0.f;
+    __syncthreads();
+    const int cc_beg = (int)(cb - chunk * BPC) * U, cc_end = cc_beg + (int)(seg_end - cur) * U;
+#pragma unroll 1
+    for (int cc = cc_beg; cc < cc_end; cc += U) {
+      const int jb = jb0 - cc;  // a multiple of 16
+      float win[32];
+#pragma unroll
+      for (int g = 0; g < 2; ++g) {
+        const float4* q = reinterpret_cast<const float4*>(tb + dvr_wpad(jb + 16 * g));
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const float4 v = q[i];
+          win[16 * g + 4 * i] = v.x;
+          win[16 * g + 4 * i + 1] = v.y;
+          win[16 * g + 4 * i + 2] = v.z;
+          win[16 * g + 4 * i + 3] = v.w;
+        }
+      }
+      float2 xv[U];
+      const float4* xq = reinterpret_cast<const float4*>(xs + cc);
+#pragma unroll
+      for (int i = 0; i < U / 2; ++i) {
+        const float4 v = xq[i];
+        xv[2 * i] = make_float2(v.x, v.y);
+        xv[2 * i + 1] = make_float2(v.z, v.w);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int a = 0; a < P; ++a) {
+          const float t = win[a - u + U - 1];
+          acc[a] = __ffma2_rn(make_float2(t, t), xv[u], acc[a]);
+        }
+    }
+    cur = seg_end;
+    const int64_t rt_end = (rt + 1) * nbc;
+    if (cur == hi || cur == rt_end) {
+      const int64_t slot = b - split_owner(rt * nbc, nblocks, G);
+      const int64_t row = R0 + 512 * w + P * lane;
+#pragma unroll
+      for (int a = 0; a < P; ++a) part[slot * dpad + row + a] = acc[a];
+      if (cur == rt_end)
+        for (int64_t s = slot + 1; s < nslot; ++s)
+#pragma unroll
+          for (int a = 0; a < P; ++a) part[s * dpad + row + a] = make_float2(0.f, 0.f);
+    }
+  }
+}
+
+DvrRowsShape dvr_rows_shape(int64_t D, int num_sms) {
+  DvrRowsShape s{};
+  s.rows = kDvrRB;
+  s.cols = kDvrKC;
+  s.rtiles = (D + kDvrRB - 1) / kDvrRB;
+  s.nbc = (D + kDvrU - 1) / kDvrU;
+  s.nblocks = s.rtiles * s.nbc;
+  s.grid = std::min<int64_t>(2 * (int64_t)num_sms, s.nblocks);
+  s.dpad = s.rtiles * kDvrRB;
+  s.nslot = 1;
+  for (int64_t rt = 0; rt < s.rtiles; ++rt) {
+    const int64_t f = split_owner(rt * s.nbc, s.nblocks, s.grid);
+    const int64_t l = split_owner(rt * s.nbc + s.nbc - 1, s.nblocks, s.grid);
+    s.nslot = std::max(s.nslot, l - f + 1);
+  }
+  return s;
+}
+
 template <typename T, int P>
 static size_t dvr_smem_bytes(int kc) {
   using C = typename cplx<T>::t;
@@ -113,22 +251,20 @@ static size_t dvr_smem_bytes(int kc) {
 
 cudaError_t launch_dvr_apply(const Plan& p, const void* xc, void* part, int64_t nvec) {
   if (nvec != 1) return cudaErrorNotSupported;
-  const int kc = p.dvr_cols;
-  const int64_t nslot = (p.D + kc - 1) / kc;
   if (p.prec == MF_PREC_FP64) {
     constexpr int P = 8;
+    const int kc = p.dvr_cols;
+    const int64_t nslot = (p.D + kc - 1) / kc;
     const size_t sm = dvr_smem_bytes<double, P>(kc);
     auto k = dvr_window<double, P>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     dim3 grid((unsigned)((p.D + 32 * P - 1) / (32 * P)), (unsigned)nslot);
     k<<<grid, 256, sm, p.stream>>>(p.D, p.dpad, kc, p.dvr, (const double2*)xc, (double2*)part);
   } else {
-    constexpr int P = 16;
-    const size_t sm = dvr_smem_bytes<float, P>(kc);
-    auto k = dvr_window<float, P>;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    dim3 grid((unsigned)((p.D + 32 * P - 1) / (32 * P)), (unsigned)nslot);
-    k<<<grid, 256, sm, p.stream>>>(p.D, p.dpad, kc, p.dvr, (const float2*)xc, (float2*)part);
+    const DvrRowsShape s = dvr_rows_shape(p.D, p.num_sms);
+    cudaFuncSetAttribute(dvr_rows_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDvrSmem);
+    dvr_rows_f32<<<(unsigned)s.grid, 256, kDvrSmem, p.stream>>>(p.D, s.dpad, s.nslot, s.nbc, s.nblocks, p.dvr,
+                                                                (const float2*)xc, (float2*)part);
   }
   return cudaGetLastError();
 }

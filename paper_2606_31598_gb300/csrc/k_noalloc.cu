@@ -70,13 +70,11 @@ extern "C" mf_status mf_apply_dvr_noalloc(int64_t D, double dvr_L, const void* x
   p.dvr.t0_32 = (float)p.dvr.t0_64;
   p.dvr.c32 = (float)(1.0 / p.dvr.dx2);
   p.use_dvr_window = true;
-  p.dvr_rows = 512;
-  const int64_t rtiles = (D + p.dvr_rows - 1) / p.dvr_rows;
-  int kc = 4096;
-  while (kc > 128 && rtiles * ((D + kc - 1) / kc) < 8 * (int64_t)p.num_sms) kc /= 2;
-  p.dvr_cols = kc;
-  p.nslot = (D + kc - 1) / kc;
-  p.dpad = rtiles * p.dvr_rows;
+  const DvrRowsShape s = dvr_rows_shape(D, p.num_sms);
+  p.dvr_rows = (int)s.rows;
+  p.dvr_cols = (int)s.cols;
+  p.nslot = s.nslot;
+  p.dpad = s.dpad;
 
   const size_t xc_bytes = ((size_t)p.dpad * sizeof(float2) + 255) & ~(size_t)255;
   const size_t part_bytes = (size_t)p.nslot * (size_t)p.dpad * sizeof(float2);

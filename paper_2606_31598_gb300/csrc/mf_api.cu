@@ -350,8 +350,14 @@ mf_status create_fixed(mf_plan_t* out, int64_t D, int32_t generator, uint64_t se
   // memory feasibility (Eq. planner_memory_constraint): M_op + M_work <= alpha M_free
   const int64_t nv = std::max(1, o.nvec_hint);
   p.use_dvr_window = generator == MF_GEN_SINC_DVR_HO && pc == 0 && p.prec != MF_PREC_BF16X2;
-  if (p.use_dvr_window) {
-    const int P = p.prec == MF_PREC_FP64 ? 8 : 16;
+  if (p.use_dvr_window && p.prec == MF_PREC_FP32) {
+    const DvrRowsShape s = dvr_rows_shape(D, p.num_sms);
+    p.dvr_rows = (int)s.rows;
+    p.dvr_cols = (int)s.cols;
+    p.nslot = s.nslot;
+    p.dpad = s.dpad;
+  } else if (p.use_dvr_window) {
+    const int P = 8;
     p.dvr_rows = 32 * P;
     const int64_t rtiles = (D + p.dvr_rows - 1) / p.dvr_rows;
     int kc = 4096;

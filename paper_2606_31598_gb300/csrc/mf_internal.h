@@ -98,8 +98,16 @@ mf_status plan_coefficients(Plan& p, double z, int32_t order, int32_t* nterms, i
 // ---- launchers (return cudaError_t of the launch) ----
 // Hermitian canonical-tile apply, nvec == 1 register kernel.
 cudaError_t launch_gue_apply(const Plan& p, const void* xc, void* part, int64_t nvec);
-// DVR Toeplitz-window apply (rows x column chunk per CTA).
+// DVR Toeplitz-window apply (FP64 form: rows x column chunk per CTA; FP32
+// form: persistent row-split kernel with the shape below).
 cudaError_t launch_dvr_apply(const Plan& p, const void* xc, void* part, int64_t nvec);
+// Launch shape of the FP32 persistent DVR kernel: row tile and staged chunk
+// sizes, 16-column blocks per row tile, work items, grid, partial slots and
+// padded rows per slot.
+struct DvrRowsShape {
+  int64_t rows, cols, rtiles, nbc, nblocks, grid, nslot, dpad;
+};
+DvrRowsShape dvr_rows_shape(int64_t D, int num_sms);
 // Fill the cache blocks listed in d_pairs (block pair (n, m) per cache slot).
 cudaError_t launch_cache_fill_pairs(const Plan& p, const int2* d_pairs, int64_t npairs);
 // Multi-vector row-owner apply (nvec bucket 2..64).
