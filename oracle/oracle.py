@@ -273,3 +273,40 @@ def apply_bf16x2(op, x, H32=None):
         V = np.array([potential(op, i) for i in range(op.D)])
         Y = Y + V[:, None] * X
     return Y.reshape(x.shape)
+
+
+# ------------------------------------------------------- system-bath form ---
+# H = H_S (x) I_B + I_S (x) H_B + g sum_a A_a (x) B_a (Sec. VII), with the bath
+# operators H_B = B_0 and B_1..B_n Philox ensembles of their own seeds and the
+# small system matrices given.  Two independent statements of the operator:
+# the dense Kronecker form in system-major order (index s*d_B + beta), and the
+# matrix-free form on the bath-major layout X[beta][s] = psi[s*d_B + beta]:
+#   Phi = H_B X + X H_S^T + g sum_a B_a X A_a^T.
+
+def sysbath_dense(d_S, d_B, seeds, H_S, A, g, form=FORM_FP64):
+    """Dense D x D composite operator, D = d_S d_B, system-major order."""
+    H_S = np.asarray(H_S, dtype=np.complex128).reshape(d_S, d_S)
+    A = np.asarray(A, dtype=np.complex128).reshape(-1, d_S, d_S)
+    HB = dense(make_op(GEN_PHILOX_GUE, d_B, seed=seeds[0], form=form))
+    H = np.kron(H_S, np.eye(d_B)) + np.kron(np.eye(d_S), HB)
+    for a in range(A.shape[0]):
+        Ba = dense(make_op(GEN_PHILOX_GUE, d_B, seed=seeds[1 + a], form=form))
+        H = H + g * np.kron(A[a], Ba)
+    return H
+
+
+def sysbath_apply(d_S, d_B, seeds, H_S, A, g, X, form=FORM_FP64):
+    """Phi = H_B X + X H_S^T + g sum_a B_a X A_a^T for X [d_B][d_S] (bath-major)."""
+    H_S = np.asarray(H_S, dtype=np.complex128).reshape(d_S, d_S)
+    A = np.asarray(A, dtype=np.complex128).reshape(-1, d_S, d_S)
+    X = np.asarray(X, dtype=np.complex128).reshape(d_B, d_S)
+    Phi = apply(make_op(GEN_PHILOX_GUE, d_B, seed=seeds[0], form=form), X).reshape(d_B, d_S) + X @ H_S.T
+    for a in range(A.shape[0]):
+        BX = apply(make_op(GEN_PHILOX_GUE, d_B, seed=seeds[1 + a], form=form), X).reshape(d_B, d_S)
+        Phi = Phi + g * (BX @ A[a].T)
+    return Phi
+
+
+def bath_major(psi, d_S, d_B):
+    """System-major psi[s*d_B + beta] -> bath-major X[beta][s]."""
+    return np.ascontiguousarray(np.asarray(psi).reshape(d_S, d_B).T)

@@ -365,3 +365,41 @@ def test_dvr_imaginary_time_coherent_state_closed_form():
     assert abs(np.linalg.norm(raw) - want_norm) < 1e-9
     out = O.cheb_imag_step(op, psi0, tau, c, R, nt, normalize=True)
     assert np.max(np.abs(out - g(x0 * np.exp(-tau)))) < 1e-9
+
+
+# ------------------------------------------------------- system-bath form ---
+def _herm(rng, n):
+    M = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    return 0.5 * (M + M.conj().T)
+
+
+@pytest.mark.parametrize("d_S,d_B,n_int", [(1, 37, 1), (3, 40, 2), (4, 64, 1)])
+def test_sysbath_matrix_free_equals_kronecker_form(d_S, d_B, n_int):
+    """The bath-major matrix-free statement and the system-major Kronecker
+    statement of Sec. VII's operator give the same product."""
+    rng = np.random.default_rng(d_S * 100 + d_B)
+    H_S = _herm(rng, d_S)
+    A = np.stack([_herm(rng, d_S) for _ in range(n_int)])
+    seeds = [11 + 7 * k for k in range(n_int + 1)]
+    g = 0.37
+    H = O.sysbath_dense(d_S, d_B, seeds, H_S, A, g)
+    assert np.max(np.abs(H - H.conj().T)) < 1e-14   # Hermitian composite
+    psi = rng.standard_normal(d_S * d_B) + 1j * rng.standard_normal(d_S * d_B)
+    want = O.bath_major(H @ psi, d_S, d_B)
+    got = O.sysbath_apply(d_S, d_B, seeds, H_S, A, g, O.bath_major(psi, d_S, d_B))
+    assert np.max(np.abs(got - want)) < 1e-12 * np.max(np.abs(want))
+
+
+def test_sysbath_special_cases():
+    """No system term and no coupling: each system column sees H_B alone;
+    d_S = 1: H = h + H_B + g a B_1 (scalars h, a)."""
+    rng = np.random.default_rng(3)
+    d_B = 50
+    X = rng.standard_normal((d_B, 3)) + 1j * rng.standard_normal((d_B, 3))
+    got = O.sysbath_apply(3, d_B, [5], np.zeros((3, 3)), np.zeros((0, 3, 3)), 0.0, X)
+    HB = O.dense(O.make_op(O.GEN_PHILOX_GUE, d_B, seed=5))
+    assert np.max(np.abs(got - HB @ X)) < 1e-13
+    h, a, g = 0.7, -1.3, 0.25
+    H = O.sysbath_dense(1, d_B, [5, 6], [[h]], [[[a]]], g)
+    B1 = O.dense(O.make_op(O.GEN_PHILOX_GUE, d_B, seed=6))
+    assert np.max(np.abs(H - (h * np.eye(d_B) + HB + g * a * B1))) < 1e-15
