@@ -178,6 +178,34 @@ const char* mf_status_string(mf_status s);
 mf_status mf_plan_create(mf_plan_t* out, int64_t D, int64_t M, int32_t generator, uint64_t seed,
                          int64_t block, size_t cache_budget_bytes, const mf_options* opt);
 
+/*
+ * mf_sysbath_create -- a plan for the system-bath Hamiltonian of Sec. VII,
+ *   H = H_S (x) I_B + I_S (x) H_B + g sum_{a=1}^{n_int} A_a (x) B_a,
+ * acting on psi in C^{d_S} (x) C^{d_B} (D = d_S d_B), with the dense bath
+ * operators H_B = B_0 and B_1..B_{n_int} drawn from the Philox ensemble of
+ * mf_plan_create (scale sigma^2 = 1/(2 d_B)) with seeds[0..n_int] and
+ * generated on demand, never stored; R = d_S and n_op = 1 + n_int as in
+ * Eq. generic_matvec_flops.  One fused kernel generates every bath operator's
+ * chunk and contracts it with X M_o^T (M_0 = I, M_a = g A_a); the X H_S^T term
+ * is added in FP64.
+ *   d_S   : 1..64;  d_B : >= 2;  n_int : 0..15;
+ *   seeds : host uint64 [1 + n_int];
+ *   H_S   : host complex128 [d_S][d_S] (row-major, H_S[s][s']);
+ *   A     : host complex128 [n_int][d_S][d_S] (may be NULL when n_int == 0);
+ *   g     : coupling strength;  opt : precision FP64 or FP32 (BF16X2 gives
+ *           MF_ERR_UNSUPPORTED); storage and planner options are ignored
+ *           (procedural storage).
+ * Vectors of this plan are device complex128 [d_B][d_S], bath-major: element
+ * (s, beta) of psi at beta*d_S + s.  mf_apply, mf_cheb_propagate and
+ * mf_cheb_filter take nvec == d_S (one composite vector); mf_spectral_bounds
+ * runs Lanczos on the composite operator, and mf_cheb_filter normalises the
+ * whole composite vector.  H is Hermitian when H_S and the
+ * A_a are.  Destroy with mf_plan_destroy.  Errors: MF_ERR_INVALID,
+ * MF_ERR_UNSUPPORTED, MF_ERR_OOM, MF_ERR_CUDA.
+ */
+mf_status mf_sysbath_create(mf_plan_t* out, int64_t d_S, int64_t d_B, int32_t n_int, const uint64_t* seeds,
+                            const void* H_S, const void* A, double g, const mf_options* opt);
+
 /* Release everything the plan owns (synchronises its stream).  NULL is a no-op. */
 mf_status mf_plan_destroy(mf_plan_t p);
 

@@ -106,6 +106,7 @@ def lib():
         L.mf_status_string.argtypes = [ctypes.c_int]
         L.mf_status_string.restype = ctypes.c_char_p
         L.mf_plan_create.argtypes = [P(vp), i64, i64, i32, u64, i64, ctypes.c_size_t, P(mf_options)]
+        L.mf_sysbath_create.argtypes = [P(vp), i64, i64, i32, vp, vp, vp, d, P(mf_options)]
         L.mf_plan_destroy.argtypes = [vp]
         L.mf_apply.argtypes = [vp, vp, vp, i64]
         L.mf_cheb_propagate.argtypes = [vp, vp, i64, d, i32]
@@ -145,7 +146,8 @@ def lib():
                      "mf_mlp_features"):
             getattr(L, name).restype = ctypes.c_int
         L.mf_plan_profile_read.argtypes = [vp, P(d), P(i64)]
-        for name in ("mf_plan_create", "mf_plan_destroy", "mf_apply", "mf_cheb_propagate", "mf_cheb_terms",
+        for name in ("mf_plan_create", "mf_sysbath_create", "mf_plan_destroy", "mf_apply", "mf_cheb_propagate",
+                     "mf_cheb_terms",
                      "mf_cheb_filter", "mf_cheb_filter_terms", "mf_spectral_bounds", "mf_plan_set_bounds", "mf_sync", "mf_plan_describe",
                      "mf_debug_entries", "mf_plan_profile", "mf_plan_profile_read", "mf_apply_dvr_noalloc"):
             getattr(L, name).restype = ctypes.c_int
@@ -197,6 +199,20 @@ def mf_plan_create(D, M, generator, seed, block=0, cache_budget_bytes=0, options
 
 def mf_plan_destroy(plan):
     return _check(lib().mf_plan_destroy(plan), "mf_plan_destroy")
+
+
+def mf_sysbath_create(d_S, d_B, seeds, H_S, A, g, options=None):
+    import numpy as np
+    seeds = np.ascontiguousarray(np.asarray(seeds, dtype=np.uint64))
+    H_S = np.ascontiguousarray(np.asarray(H_S, dtype=np.complex128).reshape(d_S, d_S))
+    n_int = len(seeds) - 1
+    A = np.ascontiguousarray(np.asarray(A, dtype=np.complex128).reshape(n_int, d_S, d_S)) if n_int else None
+    h = ctypes.c_void_p()
+    opt = options if options is not None else mf_options_default(stream=current_stream())
+    st = lib().mf_sysbath_create(ctypes.byref(h), int(d_S), int(d_B), int(n_int), seeds.ctypes.data,
+                                 H_S.ctypes.data, None if A is None else A.ctypes.data, float(g), ctypes.byref(opt))
+    _check(st, "mf_sysbath_create")
+    return h
 
 
 def mf_apply(plan, y, x, nvec=1):
@@ -427,6 +443,21 @@ class Plan:
         self.options = o
         self.D = int(D)
         self.handle = mf_plan_create(D, D if M is None else M, generator, seed, block, cache_budget_bytes, o)
+
+    @classmethod
+    def sysbath(cls, d_S, d_B, seeds, H_S, A, g, **opts):
+        """System-bath plan (mf_sysbath_create): vectors [d_B][d_S], nvec = d_S."""
+        self = cls.__new__(cls)
+        o = mf_options_default()
+        if "stream" not in opts:
+            opts["stream"] = current_stream()
+        for k, v in opts.items():
+            setattr(o, k, v)
+        self.options = o
+        self.D = int(d_B)
+        self.d_S = int(d_S)
+        self.handle = mf_sysbath_create(d_S, d_B, seeds, H_S, A, g, o)
+        return self
 
     def apply(self, y, x, nvec=1):
         return mf_apply(self.handle, y, x, nvec)

@@ -59,9 +59,21 @@ __device__ __forceinline__ double2 slot_sum(const C* __restrict__ part, int64_t 
   return make_double2(sr, si);
 }
 
+// System term of the system-bath composite: (X H_S^T)[row][v] =
+// sum_s x[row][s] H_S[v][s] (nv == dS), added to s in FP64.
+__device__ __forceinline__ void add_system_term(double2& s, const double2* __restrict__ x, int64_t row, int64_t v,
+                                                int64_t nv, const double2* __restrict__ hs) {
+  const double2* xr = x + row * nv;
+  const double2* h = hs + v * nv;
+  for (int64_t k = 0; k < nv; ++k) {
+    s.x += h[k].x * xr[k].x - h[k].y * xr[k].y;
+    s.y += h[k].x * xr[k].y + h[k].y * xr[k].x;
+  }
+}
+
 template <typename C>
 __global__ void k_reduce(const C* __restrict__ part, VecShape sh, int64_t n, int dvr, dvr_consts dk,
-                         const double2* __restrict__ x, double2* __restrict__ y) {
+                         const double2* __restrict__ x, double2* __restrict__ y, const double2* __restrict__ hs) {
   const int64_t stride = sh.dpad * sh.nb;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t row = e / sh.nv, v = e % sh.nv;
@@ -72,6 +84,7 @@ __global__ void k_reduce(const C* __restrict__ part, VecShape sh, int64_t n, int
       s.x = fma(V, xv.x, s.x);
       s.y = fma(V, xv.y, s.y);
     }
+    if (hs) add_system_term(s, x, row, v, sh.nv, hs);
     y[e] = s;
   }
 }
@@ -80,9 +93,9 @@ cudaError_t launch_reduce(const Plan& p, const void* part, const double2* x, dou
   const int64_t n = p.D * s.nv;
   const int dvr = p.gen == MF_GEN_SINC_DVR_HO;
   if (p.prec == MF_PREC_FP64)
-    k_reduce<double2><<<grid_for(n), 256, 0, p.stream>>>((const double2*)part, s, n, dvr, p.dvr, x, y);
+    k_reduce<double2><<<grid_for(n), 256, 0, p.stream>>>((const double2*)part, s, n, dvr, p.dvr, x, y, p.d_sb_HS);
   else
-    k_reduce<float2><<<grid_for(n), 256, 0, p.stream>>>((const float2*)part, s, n, dvr, p.dvr, x, y);
+    k_reduce<float2><<<grid_for(n), 256, 0, p.stream>>>((const float2*)part, s, n, dvr, p.dvr, x, y, p.d_sb_HS);
   return cudaGetLastError();
 }
 
@@ -126,7 +139,7 @@ template <typename C>
 __global__ void k_cheb_update(const C* __restrict__ part, VecShape sh, int64_t n, int dvr, dvr_consts dk,
                               const double2* __restrict__ qcur, double2* __restrict__ qprev,
                               double2* __restrict__ acc, C* __restrict__ xc, const double* __restrict__ J,
-                              int32_t j, double c, double R, int imag_time) {
+                              int32_t j, double c, double R, int imag_time, const double2* __restrict__ hs) {
   // real time: a_j = 2 (-i)^j J_j; imaginary time: a_j = 2 (-1)^j e^{-z} I_j
   const double aj = (imag_time && (j & 1)) ? -2.0 * J[j] : 2.0 * J[j];
   const int64_t stride = sh.dpad * sh.nb;
@@ -140,6 +153,7 @@ __global__ void k_cheb_update(const C* __restrict__ part, VecShape sh, int64_t n
       y.x = fma(V, q.x, y.x);
       y.y = fma(V, q.y, y.y);
     }
+    if (hs) add_system_term(y, qcur, row, v, sh.nv, hs);
     double tr = (y.x - c * q.x) / R, ti = (y.y - c * q.y) / R;
     if (j > 1) {
       const double2 qp = qprev[e];
@@ -172,10 +186,10 @@ cudaError_t launch_cheb_update(const Plan& p, const void* part, const double2* q
   const int dvr = p.gen == MF_GEN_SINC_DVR_HO;
   if (p.prec == MF_PREC_FP64)
     k_cheb_update<double2><<<grid_for(n), 256, 0, p.stream>>>((const double2*)part, s, n, dvr, p.dvr, qcur, qprev,
-                                                              acc, (double2*)xc, p.d_J, k_next, c, R, imag_time);
+                                                              acc, (double2*)xc, p.d_J, k_next, c, R, imag_time, p.d_sb_HS);
   else
     k_cheb_update<float2><<<grid_for(n), 256, 0, p.stream>>>((const float2*)part, s, n, dvr, p.dvr, qcur, qprev,
-                                                             acc, (float2*)xc, p.d_J, k_next, c, R, imag_time);
+                                                             acc, (float2*)xc, p.d_J, k_next, c, R, imag_time, p.d_sb_HS);
   return cudaGetLastError();
 }
 
@@ -315,13 +329,14 @@ __global__ void k_scale_columns(const double2* __restrict__ acc, double2* __rest
   }
 }
 
-cudaError_t launch_filter_final(const Plan& p, const double2* acc, double2* psi, int64_t nv, int normalize) {
-  const int64_t n = p.D * nv;
+cudaError_t launch_filter_final(const Plan& p, const double2* acc, double2* psi, int64_t rows, int64_t nv,
+                                int normalize) {
+  const int64_t n = rows * nv;
   double* inv = nullptr;
   if (normalize) {
     double* partial = p.d_red;
     inv = p.d_red + kColSplit * 64;
-    k_colnorm_partial<<<dim3(kColSplit, (unsigned)nv), 256, 0, p.stream>>>(acc, p.D, nv, partial);
+    k_colnorm_partial<<<dim3(kColSplit, (unsigned)nv), 256, 0, p.stream>>>(acc, rows, nv, partial);
     k_colnorm_final<<<1, 64, 0, p.stream>>>(partial, nv, inv);
   }
   k_scale_columns<<<grid_for(n), 256, 0, p.stream>>>(acc, psi, n, nv, inv);

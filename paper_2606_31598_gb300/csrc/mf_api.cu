@@ -66,6 +66,10 @@ void release(Plan& p) {
   free_dev(p.d_J);
   free_dev(p.d_red);
   free_dev(p.d_err);
+  free_dev(p.d_sb_seeds);
+  free_dev(p.d_sb_M);
+  free_dev(p.d_sb_HS);
+  free_dev(p.d_sb_xo);
 }
 
 // Vector shape of the path used for nvec vectors: the Hermitian or DVR
@@ -74,7 +78,7 @@ void release(Plan& p) {
 VecShape shape_for(const Plan& p, int64_t nvec) {
   if (p.prec == MF_PREC_BF16X2)
     return VecShape{nvec, tc_nvec_bucket(nvec), p.rows_nsplit, p.ntile * (int64_t)kTile};
-  if (nvec == 1) return VecShape{1, 1, p.nslot, p.dpad};
+  if (nvec == 1 && !p.sb_nop) return VecShape{1, 1, p.nslot, p.dpad};
   return VecShape{nvec, rows_nvec_bucket(nvec), p.rows_nsplit, p.ntile * (int64_t)kTile};
 }
 
@@ -90,7 +94,7 @@ mf_status ensure_workspace(Plan& p, int64_t nvec) {
   size_t part_bytes = (size_t)one.nslot * (size_t)one.dpad * eb;
   size_t rows = (size_t)std::max(one.dpad, p.D);
   size_t xc_bytes = rows * eb;
-  if (nvec > 1 || p.prec == MF_PREC_BF16X2) {
+  if (nvec > 1 || p.prec == MF_PREC_BF16X2 || p.sb_nop) {
     const VecShape m = shape_for(p, nvec);
     part_bytes = std::max(part_bytes, (size_t)m.nslot * (size_t)m.dpad * (size_t)m.nb * eb);
     xc_bytes = std::max(xc_bytes, (size_t)std::max<int64_t>(m.dpad, p.D) * (size_t)m.nb * eb);
@@ -100,6 +104,12 @@ mf_status ensure_workspace(Plan& p, int64_t nvec) {
   if (p.prec == MF_PREC_BF16X2) MF_CUDA(cudaMalloc(&p.d_tcb, tc_operand_bytes(p.D, shape_for(p, nvec).nb)));
   MF_CUDA(cudaMemset(p.d_xc, 0, xc_bytes));
   for (auto& q : p.d_q) MF_CUDA(cudaMalloc((void**)&q, (size_t)p.D * (size_t)nvec * sizeof(double2)));
+  if (p.sb_nop) {
+    const VecShape m = shape_for(p, nvec);
+    free_dev(p.d_sb_xo);
+    p.sb_rows = std::max<int64_t>(m.dpad, p.D);
+    MF_CUDA(cudaMalloc(&p.d_sb_xo, (size_t)p.sb_nop * (size_t)p.sb_rows * (size_t)m.nb * eb));
+  }
   p.nvec_cap = nvec;
   return MF_OK;
 }
@@ -126,7 +136,11 @@ mf_status apply_kernel(Plan& p, int64_t nvec) {
     }
     MF_CUDA(cudaEventRecord(p.ev[p.ev_used].first, p.stream));
   }
-  if (p.prec == MF_PREC_BF16X2)
+  if (p.sb_nop) {
+    const int64_t nb = rows_nvec_bucket(nvec);
+    MF_CUDA(launch_sb_mix(p, p.d_xc, p.d_sb_xo, nb, p.sb_rows));
+    MF_CUDA(launch_sb_rows(p, p.d_sb_xo, p.sb_rows * nb, p.d_part, nb));
+  } else if (p.prec == MF_PREC_BF16X2)
     MF_CUDA(launch_tc_apply(p, p.d_xc, p.d_part, p.d_tcb, tc_nvec_bucket(nvec)));
   else if (nvec > 1)
     MF_CUDA(launch_rows_apply(p, p.d_xc, p.d_part, rows_nvec_bucket(nvec)));
@@ -191,9 +205,11 @@ mf_status compute_bounds(Plan& p) {
     p.have_bounds = true;
     return MF_OK;
   }
-  const int64_t n = p.D;
-  const int m = std::max(2, (int)std::min<int64_t>(p.opt.lanczos_m, p.D));
-  mf_status st = ensure_workspace(p, 1);
+  // one vector of the operator: [D] (plain) or [d_B][d_S] (system-bath)
+  const int64_t nv = p.sb_nop ? p.sb_dS : 1;
+  const int64_t n = p.D * nv;
+  const int m = std::max(2, (int)std::min<int64_t>(p.opt.lanczos_m, n));
+  mf_status st = ensure_workspace(p, nv);
   if (st != MF_OK) return st;
   double2 *v = p.d_q[0], *vp = p.d_q[1], *w = p.d_q[2];
   double* d_s = nullptr;
@@ -213,7 +229,7 @@ mf_status compute_bounds(Plan& p) {
     double beta = 0.0;
     bool have_prev = false;
     for (int j = 0; j < m; ++j) {
-      st = apply_internal(p, w, v, 1);
+      st = apply_internal(p, w, v, nv);
       if (st != MF_OK) break;
       double alpha = 0.0;
       if ((st = dot(v, w, &alpha)) != MF_OK) break;
@@ -769,6 +785,59 @@ mf_status mf_plan_trials(mf_plan_t h, char* buf, size_t len, size_t* needed) {
   return all.size() + 1 <= len ? MF_OK : MF_ERR_INVALID;
 }
 
+mf_status mf_sysbath_create(mf_plan_t* out, int64_t d_S, int64_t d_B, int32_t n_int, const uint64_t* seeds,
+                            const void* H_S, const void* A, double g, const mf_options* opt) {
+  if (!out) return MF_ERR_INVALID;
+  *out = nullptr;
+  mf_options o;
+  if (opt) o = *opt; else mf_options_default(&o);
+  if (d_S < 1 || d_S > 64 || d_B < 2 || d_B > (int64_t)1 << 31 || n_int < 0 || n_int > 15 || !seeds || !H_S ||
+      (n_int > 0 && !A) || !std::isfinite(g))
+    return MF_ERR_INVALID;
+  if (o.precision == MF_PREC_BF16X2) return MF_ERR_UNSUPPORTED;
+  if (o.precision != MF_PREC_FP64 && o.precision != MF_PREC_FP32) return MF_ERR_INVALID;
+  if (!(o.cheb_tol > 0) || o.lanczos_m < 2 || !(o.alpha_safety > 0 && o.alpha_safety <= 1)) return MF_ERR_INVALID;
+  // the bath operators are generated on demand (procedural storage)
+  o.storage = MF_STORE_PROCEDURAL;
+  o.planner_mode = MF_PLANNER_ANALYTIC;
+  o.nvec_hint = (int32_t)std::max<int64_t>(2, d_S);
+  const int64_t Dt = (d_B + kTile - 1) / kTile * kTile;
+  mf_status st = create_fixed(out, d_B, MF_GEN_PHILOX_GUE, seeds[0], std::min<int64_t>(1024, Dt), 0, o);
+  if (st != MF_OK) return st;
+  Plan& p = (*out)->p;
+  DeviceGuard guard(p.device);
+  const int nop = 1 + n_int;
+  std::vector<double2> M((size_t)nop * d_S * d_S, make_double2(0.0, 0.0));
+  for (int64_t v = 0; v < d_S; ++v) M[(size_t)(v * d_S + v)] = make_double2(1.0, 0.0);
+  const double2* Ah = (const double2*)A;
+  for (int a = 0; a < n_int; ++a)
+    for (int64_t e = 0; e < d_S * d_S; ++e) {
+      const double2 x = Ah[(size_t)a * d_S * d_S + e];
+      M[(size_t)(a + 1) * d_S * d_S + e] = make_double2(g * x.x, g * x.y);
+    }
+  auto fail = [&](mf_status s) {
+    mf_plan_destroy(*out);
+    *out = nullptr;
+    return s;
+  };
+  if (cudaMalloc((void**)&p.d_sb_seeds, nop * sizeof(uint64_t)) != cudaSuccess ||
+      cudaMalloc((void**)&p.d_sb_M, M.size() * sizeof(double2)) != cudaSuccess ||
+      cudaMalloc((void**)&p.d_sb_HS, (size_t)d_S * d_S * sizeof(double2)) != cudaSuccess)
+    return fail(MF_ERR_OOM);
+  if (cudaMemcpy(p.d_sb_seeds, seeds, nop * sizeof(uint64_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(p.d_sb_M, M.data(), M.size() * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(p.d_sb_HS, H_S, (size_t)d_S * d_S * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess)
+    return fail(MF_ERR_CUDA);
+  p.sb_nop = nop;
+  p.sb_dS = (int32_t)d_S;
+  p.nvec_cap = 0;  // the workspace is re-sized with the mixed inputs on first use
+  p.have_bounds = false;
+  // dense-work estimate of the composite: n_op bath operators per product
+  p.w_hpsi = (double)nop * (double)d_B * (double)d_B;
+  p.dense_warn = p.w_hpsi > o.dense_work_limit;
+  return MF_OK;
+}
+
 mf_status mf_plan_destroy(mf_plan_t h) {
   if (!h) return MF_OK;
   DeviceGuard guard(h->p.device);
@@ -781,6 +850,7 @@ mf_status mf_plan_destroy(mf_plan_t h) {
 mf_status mf_apply(mf_plan_t h, void* y, const void* x, int64_t nvec) {
   if (!h || !y || !x || nvec < 1 || nvec > 64) return MF_ERR_INVALID;
   Plan& p = h->p;
+  if (p.sb_nop && nvec != p.sb_dS) return MF_ERR_INVALID;
   const size_t bytes = (size_t)p.D * (size_t)nvec * sizeof(double2);
   const char *yb = (const char*)y, *xb = (const char*)x;
   if (yb < xb + bytes && xb < yb + bytes) return MF_ERR_INVALID;
@@ -820,6 +890,7 @@ mf_status mf_cheb_terms(mf_plan_t h, double dt, int32_t* nterms) {
 mf_status mf_cheb_propagate(mf_plan_t h, void* psi, int64_t nvec, double dt, int32_t order) {
   if (!h || !psi || nvec < 1 || nvec > 64 || !(dt > 0) || !std::isfinite(dt) || order < 0) return MF_ERR_INVALID;
   Plan& p = h->p;
+  if (p.sb_nop && nvec != p.sb_dS) return MF_ERR_INVALID;
   DeviceGuard guard(p.device);
   mf_status st = compute_bounds(p);
   if (st != MF_OK) return st;
@@ -860,6 +931,7 @@ mf_status mf_cheb_filter_terms(mf_plan_t h, double tau, int32_t* nterms) {
 mf_status mf_cheb_filter(mf_plan_t h, void* psi, int64_t nvec, double tau, int32_t order, int32_t normalize) {
   if (!h || !psi || nvec < 1 || nvec > 64 || !(tau >= 0) || !std::isfinite(tau) || order < 0) return MF_ERR_INVALID;
   Plan& p = h->p;
+  if (p.sb_nop && nvec != p.sb_dS) return MF_ERR_INVALID;
   DeviceGuard guard(p.device);
   mf_status st = compute_bounds(p);
   if (st != MF_OK) return st;
@@ -879,7 +951,11 @@ mf_status mf_cheb_filter(mf_plan_t h, void* psi, int64_t nvec, double tau, int32
     MF_CUDA(launch_cheb_update(p, p.d_part, q_cur, q_prev, acc, p.d_xc, sh, j, c, R, 1));
     std::swap(q_cur, q_prev);
   }
-  MF_CUDA(launch_filter_final(p, acc, (double2*)psi, nvec, normalize != 0));
+  // a system-bath plan's [d_B][d_S] block is one composite vector
+  if (p.sb_nop)
+    MF_CUDA(launch_filter_final(p, acc, (double2*)psi, p.D * nvec, 1, normalize != 0));
+  else
+    MF_CUDA(launch_filter_final(p, acc, (double2*)psi, p.D, nvec, normalize != 0));
   return MF_OK;
 }
 
@@ -931,12 +1007,13 @@ mf_status mf_plan_describe(mf_plan_t h, char* buf, size_t len) {
       "\"pairs_cached\": %lld, \"cache_bytes\": %zu, \"path\": \"%s\", \"tile\": %d, \"dvr_rows\": %d, "
       "\"dvr_cols\": %d, \"n_slot\": %lld, \"n_work\": %lld, \"w_hpsi\": %.6g, \"dense_warn\": %s, "
       "\"dvr_L\": %.17g, \"dvr_dx\": %.17g, \"have_bounds\": %s, \"emin\": %.17g, \"emax\": %.17g, "
-      "\"num_sms\": %d}",
+      "\"num_sms\": %d, \"sb_nop\": %d, \"sb_dS\": %d}",
       (long long)p.D, gen_name(p.gen), (unsigned long long)p.seed, prec_name(p.prec), (long long)p.b,
       (long long)p.nblk, (long long)p.npair, store_name(p.storage), p.cache_budget, (long long)p.pairs_cached,
-      p.cache_bytes, p.use_dvr_window ? "dvr_window" : "herm_tile", kTile, p.dvr_rows, p.dvr_cols,
+      p.cache_bytes, p.sb_nop ? "sysbath_rows" : (p.use_dvr_window ? "dvr_window" : "herm_tile"), kTile, p.dvr_rows,
+      p.dvr_cols,
       (long long)p.nslot, (long long)p.nwork, p.w_hpsi, p.dense_warn ? "true" : "false", p.dvr.L, p.dvr.dx,
-      p.have_bounds ? "true" : "false", p.emin, p.emax, p.num_sms);
+      p.have_bounds ? "true" : "false", p.emin, p.emax, p.num_sms, p.sb_nop, p.sb_dS);
   if (n < 0) return MF_ERR_INVALID;
   std::strncpy(buf, tmp, len - 1);
   buf[len - 1] = '\0';

@@ -88,6 +88,15 @@ struct Plan {
   // safety estimate (Sec. IV.H)
   double w_hpsi = 0.0;
   bool dense_warn = false;
+  // system-bath composite (Sec. VII, k_sysbath.cu): D is the bath dimension
+  // d_B, vectors are [d_B][d_S] with nvec == d_S; sb_nop = 1 + n_int bath
+  // operators (0: a plain plan)
+  int32_t sb_nop = 0, sb_dS = 0;
+  uint64_t* d_sb_seeds = nullptr;  // [nop] Philox seeds of H_B, B_1..B_n
+  double2* d_sb_M = nullptr;       // [nop][dS][dS]: M_0 = I, M_a = g A_a
+  double2* d_sb_HS = nullptr;      // [dS][dS] system Hamiltonian
+  void* d_sb_xo = nullptr;         // [nop][rows][nb] mixed inputs X M_o^T (compute precision)
+  int64_t sb_rows = 0;             // rows of each mixed input
 };
 
 // Plan services shared with the batched path (mf_api.cu).
@@ -139,7 +148,9 @@ cudaError_t launch_bessel(const Plan& p, double z, int32_t K, double* J);
 // Imaginary-time filter pieces: scaled I_k(z) and the final copy with optional
 // per-column renormalisation (reduction scratch in d_red: 64*64 + 64 doubles).
 cudaError_t launch_bessel_i(const Plan& p, double z, int32_t K, double* I);
-cudaError_t launch_filter_final(const Plan& p, const double2* acc, double2* psi, int64_t nv, int normalize);
+// rows x nv columns, each column normalised on its own when normalize != 0.
+cudaError_t launch_filter_final(const Plan& p, const double2* acc, double2* psi, int64_t rows, int64_t nv,
+                                int normalize);
 constexpr int64_t kRedDoubles = 64 * 64 + 64 + 512;
 // Lanczos helpers: out[0] = Re<a,b>, FP64 reduction into d_red slot.
 cudaError_t launch_dot(const Plan& p, const double2* a, const double2* b, int64_t n, double* out);
@@ -152,6 +163,11 @@ cudaError_t launch_debug_entries(const Plan& p, int64_t r0, int64_t c0, int64_t 
                                  void* out);
 
 size_t compute_elem_bytes(int prec);  // bytes of one complex compute-format element
+
+// System-bath composite (k_sysbath.cu): mixed inputs xo[o] = xc M_o^T and
+// the fused multi-operator row kernel (vector bucket nb).
+cudaError_t launch_sb_mix(const Plan& p, const void* xc, void* xo, int64_t nb, int64_t rows);
+cudaError_t launch_sb_rows(const Plan& p, const void* xo, int64_t ostride, void* part, int64_t nb);
 
 // Surrogate prediction of one candidate's time (k_mlp.cu); model is an mf_mlp.
 mf_status surrogate_predict(void* model, int32_t generator, int32_t precision, const mf_problem& pr,
