@@ -562,6 +562,66 @@ def run_batch(args):
     return 0
 
 
+def run_sysbath(args):
+    """The system-bath shape of Sec. VII: d_S = 4 (two system qubits),
+    d_B = 65536 (16 bath qubits), D = 262144, one interaction term (n_op = 2
+    dense bath operators H_B, B_1, Philox-generated on demand, never stored),
+    random Hermitian H_S and A_1 (numpy seed 0), g = 1, FP32 form.  Reports
+    the time per H psi, entries applied/s (n_op d_B^2 d_S per product), real
+    FLOP/s by Eq. generic_matvec_flops (8 n_op d_B^2 d_S), an imaginary-time
+    filter of 80 terms (the paper's TPQ order) and the FP32 form's error
+    against the FP64 form on one product."""
+    import torch
+    import paper_2606_31598_gb300 as mf
+    d_S, d_B, n_int, g = args.sb_ds, args.sb_db, 1, 1.0
+    rng = np.random.default_rng(0)
+
+    def herm(n):
+        m = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+        return 0.5 * (m + m.conj().T)
+
+    H_S = herm(d_S)
+    A = np.stack([herm(d_S) for _ in range(n_int)])
+    seeds = [1 + k for k in range(n_int + 1)]
+    nop = n_int + 1
+    stream = torch.cuda.current_stream().cuda_stream
+    X = torch.from_numpy(np.ascontiguousarray(
+        (rng.standard_normal((d_B, d_S)) + 1j * rng.standard_normal((d_B, d_S))) / np.sqrt(2.0 * d_B * d_S))).cuda()
+    Y = torch.empty_like(X)
+    p32 = mf.Plan.sysbath(d_S, d_B, seeds, H_S, A, g, precision=mf.MF_PREC_FP32, stream=stream)
+    clock = ClockSampler(0)
+    clock.start()
+    t_apply = time_applies(p32, X, Y, d_S, args.steps)
+    Y32 = Y.clone()
+    emin, emax = p32.bounds()
+    psi = X.clone()
+    p32.cheb_filter(psi, d_S, 0.1, 80, True)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    p32.cheb_filter(psi, d_S, 0.1, 80, True)
+    e1.record()
+    torch.cuda.synchronize()
+    t_filter = e0.elapsed_time(e1) / 1e3
+    clk = clock.stop()
+    p32.close()
+    entries = float(nop) * d_B * d_B * d_S
+    out = {"workload": "system-bath d_S=%d d_B=%d n_int=%d (D=%d), Philox bath operators, FP32 form"
+                       % (d_S, d_B, n_int, d_S * d_B),
+           "apply_s": t_apply, "entries_per_s": entries / t_apply, "real_flops_per_s": 8.0 * entries / t_apply,
+           "tpq_filter_80_terms_s": t_filter, "bounds": [emin, emax], "clocks": clk,
+           "paper_context": "0.104089 s per H psi on 8 L40S GPUs with a full cache (Sec. VII)"}
+    if args.fp64:
+        p64 = mf.Plan.sysbath(d_S, d_B, seeds, H_S, A, g, precision=mf.MF_PREC_FP64, stream=stream)
+        t64 = time_applies(p64, X, Y, d_S, 1)
+        p64.close()
+        out["fp64"] = {"apply_s": t64, "entries_per_s": entries / t64}
+        out["fp32_vs_fp64_form"] = float((Y32 - Y).abs().max() / Y.abs().max())
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -571,7 +631,9 @@ def main():
     ap.add_argument("--batch-n", type=int, default=256, help="batch: number of problems")
     ap.add_argument("--philox-dim", type=int, default=131072, help="philox: D")
     ap.add_argument("--batch-budget-gb", type=float, default=200.0, help="batch: shared cache budget")
-    ap.add_argument("--workload", default="dvr", choices=["dvr", "multivector", "batch", "philox"],
+    ap.add_argument("--sb-ds", type=int, default=4, help="sysbath: system dimension d_S")
+    ap.add_argument("--sb-db", type=int, default=65536, help="sysbath: bath dimension d_B")
+    ap.add_argument("--workload", default="dvr", choices=["dvr", "multivector", "batch", "philox", "sysbath"],
                     help="dvr: the benchmark line; multivector: the 64-vector tensor-core workload report")
     ap.add_argument("--fp64", action="store_true", help="multivector: also time the FP64 procedural form")
     ap.add_argument("--mv-dim", type=int, default=262144, help="multivector: D (smaller D keeps the cached fraction)")
@@ -584,6 +646,8 @@ def main():
         return run_batch(args)
     if args.workload == "philox":
         return run_philox(args)
+    if args.workload == "sysbath":
+        return run_sysbath(args)
     return run_mf(args)
 
 
