@@ -34,13 +34,68 @@ template <typename C> __device__ __forceinline__ void cmacc(C& acc, const C& h, 
   acc.y = fma(-h.y, x.x, acc.y);
 }
 
+// Procedural part of the Hermitian tile: thread rows r0 + [0, 8), columns
+// c0 + [0, 8); DIAG selects the diagonal tile (entries below the diagonal
+// skipped, the diagonal applied once), the off-diagonal tiles need no test.
+template <typename T, int GEN, bool DIAG>
+__device__ __forceinline__ void proc_tile(typename cplx<T>::t (&yc)[8], const typename cplx<T>::t (&xcv)[8],
+                                          const typename cplx<T>::t* xs_r, typename cplx<T>::t (*red)[kTile + 1],
+                                          int64_t r0, int64_t c0, int ty, int tx, bool active, uint64_t seed,
+                                          T sigma, const dvr_consts& dk) {
+  using C = typename cplx<T>::t;
+#pragma unroll 1
+  for (int a = 0; a < 8; ++a) {
+    C yra = czero<T>();
+    const int64_t r = r0 + a;
+    if (active) {
+      const C xa = xs_r[ty * 8 + a];
+#pragma unroll
+      for (int pb = 0; pb < 4; ++pb) {
+        const int64_t c = c0 + 2 * pb;
+        if (DIAG && r > c + 1) continue;  // both entries below the diagonal
+        C h0, h1;
+        if (GEN == MF_GEN_PHILOX_GUE) {
+          gue_pair<T>(seed, sigma, (uint32_t)r, (uint32_t)(c >> 1), h0, h1);
+        } else {
+          h0.x = dvr_T(dk, (long long)(r - c), T());
+          h1.x = dvr_T(dk, (long long)(r - c - 1), T());
+          h0.y = T(0);
+          h1.y = T(0);
+        }
+        if (!DIAG) {
+          cmac(yra, h0, xcv[2 * pb]);
+          cmacc(yc[2 * pb], h0, xa);
+          cmac(yra, h1, xcv[2 * pb + 1]);
+          cmacc(yc[2 * pb + 1], h1, xa);
+          continue;
+        }
+        // entry (r, c)
+        if (r < c) {
+          cmac(yra, h0, xcv[2 * pb]);
+          cmacc(yc[2 * pb], h0, xa);
+        } else if (r == c) {
+          cmac(yra, h0, xcv[2 * pb]);
+        }
+        // entry (r, c+1)
+        if (r < c + 1) {
+          cmac(yra, h1, xcv[2 * pb + 1]);
+          cmacc(yc[2 * pb + 1], h1, xa);
+        } else if (r == c + 1) {
+          cmac(yra, h1, xcv[2 * pb + 1]);
+        }
+      }
+    }
+    red[tx][ty * 8 + a] = yra;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // (1) Hermitian canonical-tile kernel, one vector.
 // Thread (ty, tx) of the 16 x 16 grid owns rows ti*128 + ty*8 + [0,8) and
 // columns tj*128 + tx*8 + [0,8): 32 Philox calls, 64 canonical entries.
 // ---------------------------------------------------------------------------
 template <typename T, int GEN>
-__global__ void __launch_bounds__(256) herm_tile_nv1(const WorkItem* __restrict__ work, int64_t D,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) herm_tile_nv1(const WorkItem* __restrict__ work, int64_t D,
                                                      int64_t dpad, uint64_t seed, T sigma, dvr_consts dk,
                                                      const typename cplx<T>::t* __restrict__ xc,
                                                      typename cplx<T>::t* __restrict__ part,
@@ -115,44 +170,10 @@ __global__ void __launch_bounds__(256) herm_tile_nv1(const WorkItem* __restrict_
         red[tx][ty * 8 + a] = yra;
       }
     }
+  } else if (diag) {
+    proc_tile<T, GEN, true>(yc, xcv, xs_r, red, r0, c0, ty, tx, active, seed, sigma, dk);
   } else {
-#pragma unroll 1
-    for (int a = 0; a < 8; ++a) {
-      C yra = czero<T>();
-      const int64_t r = r0 + a;
-      if (active) {
-        const C xa = xs_r[ty * 8 + a];
-#pragma unroll
-        for (int pb = 0; pb < 4; ++pb) {
-          const int64_t c = c0 + 2 * pb;
-          if (diag && r > c + 1) continue;  // both entries below the diagonal
-          C h0, h1;
-          if (GEN == MF_GEN_PHILOX_GUE) {
-            gue_pair<T>(seed, sigma, (uint32_t)r, (uint32_t)(c >> 1), h0, h1);
-          } else {
-            h0.x = dvr_T(dk, (long long)(r - c), T());
-            h1.x = dvr_T(dk, (long long)(r - c - 1), T());
-            h0.y = T(0);
-            h1.y = T(0);
-          }
-          // entry (r, c)
-          if (r < c) {
-            cmac(yra, h0, xcv[2 * pb]);
-            cmacc(yc[2 * pb], h0, xa);
-          } else if (r == c) {
-            cmac(yra, h0, xcv[2 * pb]);
-          }
-          // entry (r, c+1)
-          if (r < c + 1) {
-            cmac(yra, h1, xcv[2 * pb + 1]);
-            cmacc(yc[2 * pb + 1], h1, xa);
-          } else if (r == c + 1) {
-            cmac(yra, h1, xcv[2 * pb + 1]);
-          }
-        }
-      }
-      red[tx][ty * 8 + a] = yra;
-    }
+    proc_tile<T, GEN, false>(yc, xcv, xs_r, red, r0, c0, ty, tx, active, seed, sigma, dk);
   }
 
   // row sums over the 16 column groups, then column sums over the 16 row groups
