@@ -310,3 +310,35 @@ def sysbath_apply(d_S, d_B, seeds, H_S, A, g, X, form=FORM_FP64):
 def bath_major(psi, d_S, d_B):
     """System-major psi[s*d_B + beta] -> bath-major X[beta][s]."""
     return np.ascontiguousarray(np.asarray(psi).reshape(d_S, d_B).T)
+
+
+# ------------------------------------------------ externally stored blocks ---
+# H^[n,m] = D[key(n,m)] (Sec. II): a Hermitian operator given by its canonical
+# blocks n <= m, stored in row order of the pairs, each b x b (rows/columns
+# past D are padding).  Off-diagonal blocks below the diagonal are the
+# conjugate transposes; inside a diagonal block only the upper triangle
+# (diagonal included) is read and the lower triangle is its conjugate.
+
+def external_pairs(D, b):
+    """The canonical pairs (n, m), n <= m, in storage order."""
+    nblk = -(-D // b)
+    return [(n, m) for n in range(nblk) for m in range(n, nblk)]
+
+
+def external_dense(D, b, blocks):
+    """Dense D x D operator assembled from the stored canonical blocks."""
+    blocks = np.asarray(blocks, dtype=np.complex128)
+    pairs = external_pairs(D, b)
+    blocks = blocks.reshape(len(pairs), b, b)
+    nblk = -(-D // b)
+    P = nblk * b
+    H = np.zeros((P, P), dtype=np.complex128)
+    for k, (n, m) in enumerate(pairs):
+        B = blocks[k]
+        if n == m:
+            U = np.triu(B)
+            H[n * b:(n + 1) * b, n * b:(n + 1) * b] = U + np.triu(U, 1).conj().T
+        else:
+            H[n * b:(n + 1) * b, m * b:(m + 1) * b] = B
+            H[m * b:(m + 1) * b, n * b:(n + 1) * b] = B.conj().T
+    return H[:D, :D]

@@ -403,3 +403,39 @@ def test_sysbath_special_cases():
     H = O.sysbath_dense(1, d_B, [5, 6], [[h]], [[[a]]], g)
     B1 = O.dense(O.make_op(O.GEN_PHILOX_GUE, d_B, seed=6))
     assert np.max(np.abs(H - (h * np.eye(d_B) + HB + g * a * B1))) < 1e-15
+
+
+# ------------------------------------------------ externally stored blocks ---
+def _cut_canonical(H, b):
+    """Canonical blocks of a Hermitian H (padded to whole blocks); the lower
+    triangles of the diagonal blocks are filled with junk the assembly must
+    ignore."""
+    D = H.shape[0]
+    nblk = -(-D // b)
+    P = np.zeros((nblk * b, nblk * b), dtype=np.complex128)
+    P[:D, :D] = H
+    out = []
+    rng = np.random.default_rng(99)
+    for n, m in O.external_pairs(D, b):
+        B = P[n * b:(n + 1) * b, m * b:(m + 1) * b].copy()
+        if n == m:
+            junk = rng.standard_normal((b, b)) + 1j * rng.standard_normal((b, b))
+            B = np.triu(B) + np.tril(junk, -1)
+        out.append(B)
+    return np.stack(out)
+
+
+@pytest.mark.parametrize("D,b", [(300, 128), (256, 128), (130, 128)])
+def test_external_assembly_recovers_a_hermitian_matrix(D, b):
+    rng = np.random.default_rng(D)
+    M = rng.standard_normal((D, D)) + 1j * rng.standard_normal((D, D))
+    H = 0.5 * (M + M.conj().T)
+    blocks = _cut_canonical(H, b)
+    nblk = -(-D // b)
+    assert blocks.shape[0] == nblk * (nblk + 1) // 2
+    assert np.array_equal(O.external_dense(D, b, blocks), H)
+    # the stored Philox ensemble read back as blocks is the same operator
+    op = O.make_op(O.GEN_PHILOX_GUE, D, seed=4)
+    G = O.dense(op)
+    x = rng.standard_normal(D) + 1j * rng.standard_normal(D)
+    assert np.max(np.abs(O.external_dense(D, b, _cut_canonical(G, b)) @ x - O.apply(op, x))) < 1e-13
