@@ -55,7 +55,7 @@ typedef enum {
  * partition invariant, Sec. II).  SINC_DVR_HO is "analytic generation": the
  * Colbert-Miller sinc-DVR kinetic energy on x_i = -L + i*2L/(D-1) plus
  * V = x^2/2 (hbar = m = omega = 1). */
-typedef enum { MF_GEN_PHILOX_GUE = 0, MF_GEN_SINC_DVR_HO = 1 } mf_generator;
+typedef enum { MF_GEN_PHILOX_GUE = 0, MF_GEN_SINC_DVR_HO = 1, MF_GEN_EXTERNAL = 2 } mf_generator;
 
 /* Entry precision forms.  FP64: entries, products and sums in double.
  * FP32: entries generated in single precision by the FP32 steps of the
@@ -177,6 +177,35 @@ const char* mf_status_string(mf_status s);
  */
 mf_status mf_plan_create(mf_plan_t* out, int64_t D, int64_t M, int32_t generator, uint64_t seed,
                          int64_t block, size_t cache_budget_bytes, const mf_options* opt);
+
+/*
+ * mf_external_create -- a plan for a Hermitian operator given by externally
+ * stored blocks, H^[n,m] = D[key(n,m)] (Sec. II), held in host memory.
+ *   blocks : host array of the N_pair = N_blk (N_blk + 1) / 2 canonical blocks
+ *            (n <= m, N_blk = ceil(D / block)) in row order of the pairs
+ *            ((0,0), (0,1), ..., (0,N_blk-1), (1,1), ...), each block x block
+ *            row-major, complex64 for the FP32 and BF16X2 forms, complex128
+ *            for FP64; 16-byte aligned.  Rows and columns past D are padding
+ *            (read and multiplied by zero; must be finite).  Blocks below the
+ *            diagonal are the conjugate transposes of the stored ones; the
+ *            diagonal blocks must themselves be Hermitian (the one-vector
+ *            kernel reads their upper triangle, the multi-vector kernels all
+ *            of them).  Owned by the caller: it must stay alive and unchanged
+ *            until mf_plan_destroy.
+ *   block  : b, a multiple of 128, at most D rounded up to 128.
+ *   cache_budget_bytes : HBM for the block cache; the first
+ *            P_cache = min(N_pair, floor(budget / (B_c b^2))) stored pairs
+ *            (Eq. partial_cache_pairs) are copied into HBM once, the others
+ *            are read from the host array over the host link by the kernels
+ *            on every product (the array is registered with
+ *            cudaHostRegister for the plan's lifetime).  opt->storage ==
+ *            MF_STORE_FULL requires every pair in HBM (MF_ERR_OOM otherwise).
+ * All plan calls apply (mf_apply, propagator, filter, bounds, profiling);
+ * mf_debug_entries returns MF_ERR_UNSUPPORTED.  Errors: MF_ERR_INVALID,
+ * MF_ERR_OOM, MF_ERR_CUDA.
+ */
+mf_status mf_external_create(mf_plan_t* out, int64_t D, int64_t block, const void* blocks,
+                             size_t cache_budget_bytes, const mf_options* opt);
 
 /*
  * mf_sysbath_create -- a plan for the system-bath Hamiltonian of Sec. VII,

@@ -107,6 +107,7 @@ def lib():
         L.mf_status_string.restype = ctypes.c_char_p
         L.mf_plan_create.argtypes = [P(vp), i64, i64, i32, u64, i64, ctypes.c_size_t, P(mf_options)]
         L.mf_sysbath_create.argtypes = [P(vp), i64, i64, i32, vp, vp, vp, d, P(mf_options)]
+        L.mf_external_create.argtypes = [P(vp), i64, i64, vp, ctypes.c_size_t, P(mf_options)]
         L.mf_plan_destroy.argtypes = [vp]
         L.mf_apply.argtypes = [vp, vp, vp, i64]
         L.mf_cheb_propagate.argtypes = [vp, vp, i64, d, i32]
@@ -146,7 +147,8 @@ def lib():
                      "mf_mlp_features"):
             getattr(L, name).restype = ctypes.c_int
         L.mf_plan_profile_read.argtypes = [vp, P(d), P(i64)]
-        for name in ("mf_plan_create", "mf_sysbath_create", "mf_plan_destroy", "mf_apply", "mf_cheb_propagate",
+        for name in ("mf_plan_create", "mf_sysbath_create", "mf_external_create", "mf_plan_destroy", "mf_apply",
+                     "mf_cheb_propagate",
                      "mf_cheb_terms",
                      "mf_cheb_filter", "mf_cheb_filter_terms", "mf_spectral_bounds", "mf_plan_set_bounds", "mf_sync", "mf_plan_describe",
                      "mf_debug_entries", "mf_plan_profile", "mf_plan_profile_read", "mf_apply_dvr_noalloc"):
@@ -212,6 +214,17 @@ def mf_sysbath_create(d_S, d_B, seeds, H_S, A, g, options=None):
     st = lib().mf_sysbath_create(ctypes.byref(h), int(d_S), int(d_B), int(n_int), seeds.ctypes.data,
                                  H_S.ctypes.data, None if A is None else A.ctypes.data, float(g), ctypes.byref(opt))
     _check(st, "mf_sysbath_create")
+    return h
+
+
+def mf_external_create(D, block, blocks, cache_budget_bytes=0, options=None):
+    """blocks: a numpy array of the canonical blocks (kept referenced by the
+    returned Plan; it must not change while the plan exists)."""
+    h = ctypes.c_void_p()
+    opt = options if options is not None else mf_options_default(stream=current_stream())
+    st = lib().mf_external_create(ctypes.byref(h), int(D), int(block), ctypes.c_void_p(blocks.ctypes.data),
+                                  int(cache_budget_bytes), ctypes.byref(opt))
+    _check(st, "mf_external_create")
     return h
 
 
@@ -443,6 +456,27 @@ class Plan:
         self.options = o
         self.D = int(D)
         self.handle = mf_plan_create(D, D if M is None else M, generator, seed, block, cache_budget_bytes, o)
+
+    @classmethod
+    def external(cls, D, block, blocks, cache_budget_bytes=0, **opts):
+        """Externally stored canonical blocks (mf_external_create); blocks is a
+        C-contiguous numpy array (complex64 for FP32/BF16X2, complex128 for
+        FP64) that the plan keeps referenced."""
+        import numpy as np
+        self = cls.__new__(cls)
+        o = mf_options_default()
+        if "stream" not in opts:
+            opts["stream"] = current_stream()
+        for k, v in opts.items():
+            setattr(o, k, v)
+        want = np.complex128 if o.precision == MF_PREC_FP64 else np.complex64
+        if blocks.dtype != want or not blocks.flags["C_CONTIGUOUS"]:
+            raise MFError(MF_ERR_INVALID, "mf_external_create: blocks must be C-contiguous %s" % np.dtype(want).name)
+        self.options = o
+        self.D = int(D)
+        self._blocks = blocks
+        self.handle = mf_external_create(D, block, blocks, cache_budget_bytes, o)
+        return self
 
     @classmethod
     def sysbath(cls, d_S, d_B, seeds, H_S, A, g, **opts):

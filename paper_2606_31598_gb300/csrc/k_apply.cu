@@ -100,7 +100,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) herm_tile_nv1(con
                                                      const typename cplx<T>::t* __restrict__ xc,
                                                      typename cplx<T>::t* __restrict__ part,
                                                      const typename cplx<T>::t* __restrict__ cache,
-                                                     int64_t bstride) {
+                                                     int64_t bstride,
+                                                     const typename cplx<T>::t* __restrict__ hcache) {
   using C = typename cplx<T>::t;
   __shared__ C xs_r[kTile], xs_c[kTile];
   __shared__ C red[16][kTile + 1];
@@ -131,11 +132,13 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) herm_tile_nv1(con
   const int64_t r0 = rt0 + ty * 8, c0 = ct0 + tx * 8;
   const bool active = !(diag && ty > tx);
 
-  if (it.cache_off >= 0) {
-    // cached block pair: stream the canonical entries from HBM, 16-byte
-    // loads, two rows of the thread's 8 x 8 sub-block in flight
+  if (it.cache_off != -1) {
+    // stored block pair: stream the canonical entries from the HBM cache
+    // (offset >= 0) or from the external host array (offset -2 - e),
+    // 16-byte loads, two rows of the thread's 8 x 8 sub-block in flight
     constexpr int PER16 = 16 / (int)sizeof(C);  // complex entries per 16-byte load
-    const C* base = cache + it.cache_off + (int64_t)(ty * 8) * bstride + tx * 8;
+    const C* src = it.cache_off >= 0 ? cache + it.cache_off : hcache + (-2 - it.cache_off);
+    const C* base = src + (int64_t)(ty * 8) * bstride + tx * 8;
 #pragma unroll 1
     for (int a2 = 0; a2 < 8; a2 += 2) {
       C h[2][8];
@@ -213,23 +216,23 @@ cudaError_t launch_gue_apply(const Plan& p, const void* xc, void* part, int64_t 
   const int64_t dpad = p.dpad;
   const unsigned grid = (unsigned)p.nwork;
   if (p.prec == MF_PREC_FP64) {
-    if (p.gen == MF_GEN_PHILOX_GUE)
+    if (p.gen != MF_GEN_SINC_DVR_HO)
       herm_tile_nv1<double, MF_GEN_PHILOX_GUE><<<grid, 256, 0, p.stream>>>(
           p.d_work, p.D, dpad, p.seed, p.sigma64, p.dvr, (const double2*)xc, (double2*)part,
-          (const double2*)p.d_cache, p.b);
+          (const double2*)p.d_cache, p.b, (const double2*)p.d_hblocks);
     else
       herm_tile_nv1<double, MF_GEN_SINC_DVR_HO><<<grid, 256, 0, p.stream>>>(
           p.d_work, p.D, dpad, p.seed, p.sigma64, p.dvr, (const double2*)xc, (double2*)part,
-          (const double2*)p.d_cache, p.b);
+          (const double2*)p.d_cache, p.b, (const double2*)p.d_hblocks);
   } else {
-    if (p.gen == MF_GEN_PHILOX_GUE)
+    if (p.gen != MF_GEN_SINC_DVR_HO)
       herm_tile_nv1<float, MF_GEN_PHILOX_GUE><<<grid, 256, 0, p.stream>>>(
           p.d_work, p.D, dpad, p.seed, p.sigma32, p.dvr, (const float2*)xc, (float2*)part,
-          (const float2*)p.d_cache, p.b);
+          (const float2*)p.d_cache, p.b, (const float2*)p.d_hblocks);
     else
       herm_tile_nv1<float, MF_GEN_SINC_DVR_HO><<<grid, 256, 0, p.stream>>>(
           p.d_work, p.D, dpad, p.seed, p.sigma32, p.dvr, (const float2*)xc, (float2*)part,
-          (const float2*)p.d_cache, p.b);
+          (const float2*)p.d_cache, p.b, (const float2*)p.d_hblocks);
   }
   return cudaGetLastError();
 }

@@ -23,13 +23,14 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) rows_simt(int64_t D, in
                                                 T sigma, dvr_consts dk, const typename cplx<T>::t* __restrict__ xc,
                                                 typename cplx<T>::t* __restrict__ part,
                                                 const typename cplx<T>::t* __restrict__ cache,
-                                                const int64_t* __restrict__ slot_of_pair, int64_t b, int64_t nblk) {
+                                                const int64_t* __restrict__ slot_of_pair, int64_t b, int64_t nblk,
+                                                const typename cplx<T>::t* __restrict__ hcache) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int64_t R0 = (int64_t)blockIdx.x * RT;
   const int64_t cbeg = (int64_t)blockIdx.y * ksplit_cols;
   const int64_t cend = cbeg + ksplit_cols < D ? cbeg + ksplit_cols : D;
   row_tile<T, GEN, NV, TR, TV, NT>(smem_raw, R0, cbeg, cend, D, seed, sigma, dk, xc,
-                                   part + ((int64_t)blockIdx.y * dpad + R0) * NV, cache, slot_of_pair, b, nblk);
+                                   part + ((int64_t)blockIdx.y * dpad + R0) * NV, cache, slot_of_pair, b, nblk, hcache);
 }
 
 template <typename T, int GEN, int NV, int TR, int TV, int NT>
@@ -42,7 +43,8 @@ static cudaError_t launch_rows_t(const Plan& p, const void* xc, void* part) {
   dim3 grid((unsigned)p.ntile, (unsigned)p.rows_nsplit);
   const T sigma = sizeof(T) == 4 ? (T)p.sigma32 : (T)p.sigma64;
   k<<<grid, NT, sm, p.stream>>>(p.D, p.ntile * (int64_t)kTile, p.rows_split_cols, p.seed, sigma, p.dvr,
-                                (const C*)xc, (C*)part, (const C*)p.d_cache, p.d_pair_slot, p.b, p.nblk);
+                                (const C*)xc, (C*)part, (const C*)p.d_cache, p.d_pair_slot, p.b, p.nblk,
+                                (const C*)p.d_hblocks);
   return cudaGetLastError();
 }
 
@@ -72,10 +74,10 @@ int64_t rows_nvec_bucket(int64_t nvec) {
 
 cudaError_t launch_rows_apply(const Plan& p, const void* xc, void* part, int64_t nvec_bucket) {
   if (p.prec == MF_PREC_FP64)
-    return p.gen == MF_GEN_PHILOX_GUE ? launch_rows_g<double, MF_GEN_PHILOX_GUE>(p, xc, part, nvec_bucket)
-                                      : launch_rows_g<double, MF_GEN_SINC_DVR_HO>(p, xc, part, nvec_bucket);
-  return p.gen == MF_GEN_PHILOX_GUE ? launch_rows_g<float, MF_GEN_PHILOX_GUE>(p, xc, part, nvec_bucket)
-                                    : launch_rows_g<float, MF_GEN_SINC_DVR_HO>(p, xc, part, nvec_bucket);
+    return p.gen != MF_GEN_SINC_DVR_HO ? launch_rows_g<double, MF_GEN_PHILOX_GUE>(p, xc, part, nvec_bucket)
+                                       : launch_rows_g<double, MF_GEN_SINC_DVR_HO>(p, xc, part, nvec_bucket);
+  return p.gen != MF_GEN_SINC_DVR_HO ? launch_rows_g<float, MF_GEN_PHILOX_GUE>(p, xc, part, nvec_bucket)
+                                     : launch_rows_g<float, MF_GEN_SINC_DVR_HO>(p, xc, part, nvec_bucket);
 }
 
 }  // namespace mf

@@ -198,22 +198,24 @@ __device__ __forceinline__ void put_vpair(unsigned char* A, int r, int k, float2
 template <int GEN>
 __device__ __forceinline__ void fill_a(unsigned char* A, int64_t R0, int64_t c0, uint64_t seed,
                                        float sigma, const dvr_consts& dk, const float2* __restrict__ cache,
-                                       const int64_t* __restrict__ slot_of_pair, int64_t b, int64_t nblk) {
+                                       const int64_t* __restrict__ slot_of_pair, int64_t b, int64_t nblk,
+                                       const float2* __restrict__ hcache) {
   const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
   const int hr = 8 * g + (lane >> 2), hk = 2 * (lane & 3);   // horizontal pair origin within a K core
   const int vr = 8 * g + 2 * (lane & 3), vk = lane >> 2;     // vertical pair origin within a K core
   int64_t slot = -1;
   bool transposed = false;
   const int64_t n = R0 / b, m = c0 / b;
-  if (cache) {
+  if (cache || hcache) {
     if (n <= m) slot = slot_of_pair[n * nblk + m];
     else {
       slot = slot_of_pair[m * nblk + n];
       transposed = true;
     }
   }
-  if (slot >= 0) {
-    const float2* blk = cache + slot * b * b;
+  if (slot >= 0 || slot <= -2) {
+    // HBM cache slot, or (slot <= -2) block -2 - slot of the host array
+    const float2* blk = slot >= 0 ? cache + slot * b * b : hcache + (-2 - slot) * b * b;
     float4 q[4];
     if (!transposed) {
       // H[r][k], H[r][k+1] adjacent in the cached row: one 16-byte load
@@ -283,7 +285,8 @@ template <int GEN, int NV>
 __global__ void __launch_bounds__(NTHREADS, 1)
     tc_rows(int64_t D, int64_t dpad, int64_t split_cols, uint64_t seed, float sigma, dvr_consts dk,
             const unsigned char* __restrict__ gB, float2* __restrict__ part, const float2* __restrict__ cache,
-            const int64_t* __restrict__ slot_of_pair, int64_t b, int64_t nblk, int* __restrict__ err) {
+            const int64_t* __restrict__ slot_of_pair, int64_t b, int64_t nblk, int* __restrict__ err,
+            const float2* __restrict__ hcache) {
   constexpr int N = 2 * NV;             // MMA N: [Re | Im] of NV vectors
   constexpr int B_TILE = N * KC * 2;    // bytes of one bf16 B tile
   constexpr int B_CHUNK = 4 * B_TILE;   // B1 hi, B1 lo, B2 hi, B2 lo
@@ -398,7 +401,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
         }
         if (abort_flag) break;
-        fill_a<GEN>(smem + s * STAGE, R0, cbeg + (int64_t)kc * KC, seed, sigma, dk, cache, slot_of_pair, b, nblk);
+        fill_a<GEN>(smem + s * STAGE, R0, cbeg + (int64_t)kc * KC, seed, sigma, dk, cache, slot_of_pair, b, nblk,
+                    hcache);
         fence_async_smem();
         __syncwarp();
         if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&a_full[s])) : "memory");
@@ -477,7 +481,7 @@ cudaError_t launch_tc_t(const Plan& p, const void* xc, void* part, void* gB, int
   k<<<grid, NTHREADS, smem, p.stream>>>(p.D, p.ntile * (int64_t)kTile, p.rows_split_cols, p.seed, p.sigma32, p.dvr,
                                         (const unsigned char*)gB, (float2*)part,
                                         p.pairs_cached > 0 ? (const float2*)p.d_cache : nullptr, p.d_pair_slot, p.b,
-                                        p.nblk, err);
+                                        p.nblk, err, (const float2*)p.d_hblocks);
   return cudaGetLastError();
 }
 

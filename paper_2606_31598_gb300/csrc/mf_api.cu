@@ -66,6 +66,8 @@ void release(Plan& p) {
   free_dev(p.d_J);
   free_dev(p.d_red);
   free_dev(p.d_err);
+  if (p.h_registered) cudaHostUnregister(const_cast<void*>(p.h_blocks));
+  p.h_registered = false;
   free_dev(p.d_sb_seeds);
   free_dev(p.d_sb_M);
   free_dev(p.d_sb_HS);
@@ -300,8 +302,11 @@ mf_status coefficients(Plan& p, double z, int32_t order, int32_t* nterms, int32_
 // Build a plan for one explicit candidate: block size b (> 0, multiple of the
 // tile) and storage mode (procedural, partial or full; partial takes
 // P_cache from the budget).  Arguments are validated by the caller.
+// For MF_GEN_EXTERNAL, ext is the caller's host array of canonical blocks:
+// the first P_cache pairs are copied into the HBM cache, the rest are read
+// from the (registered) host array by the kernels.
 mf_status create_fixed(mf_plan_t* out, int64_t D, int32_t generator, uint64_t seed, int64_t block,
-                       size_t cache_budget_bytes, const mf_options& o) {
+                       size_t cache_budget_bytes, const mf_options& o, const void* ext = nullptr) {
   *out = nullptr;
 
   mf_plan* h = new (std::nothrow) mf_plan();
@@ -352,13 +357,14 @@ mf_status create_fixed(mf_plan_t* out, int64_t D, int32_t generator, uint64_t se
   const double blk_bytes = (double)eb * (double)p.b * (double)p.b;
   int64_t pc = (int64_t)std::min<double>((double)p.npair, std::floor((double)budget / blk_bytes));
   int32_t storage = o.storage;
-  if (storage == MF_STORE_PROCEDURAL) {
+  if (storage == MF_STORE_PROCEDURAL && generator != MF_GEN_EXTERNAL) {
     pc = 0;
   } else if (storage == MF_STORE_FULL) {
     if (pc < p.npair) return fail(MF_ERR_OOM);
   }
-  if (pc == 0) storage = MF_STORE_PROCEDURAL;
-  else if (pc == p.npair) storage = MF_STORE_FULL;
+  if (pc == p.npair) storage = MF_STORE_FULL;
+  else if (generator == MF_GEN_EXTERNAL) storage = MF_STORE_PARTIAL;  // the rest stays in host memory
+  else if (pc == 0) storage = MF_STORE_PROCEDURAL;
   p.storage = storage;
   p.pairs_cached = pc;
   p.cache_budget = budget;
@@ -400,13 +406,15 @@ mf_status create_fixed(mf_plan_t* out, int64_t D, int32_t generator, uint64_t se
   p.m_work = m_work;
   const double m_op = (double)pc * blk_bytes;
   if (m_op + m_work > o.alpha_safety * (double)mfree) {
-    if (o.storage == MF_STORE_FULL || o.storage == MF_STORE_PARTIAL) return fail(MF_ERR_OOM);
+    if (o.storage == MF_STORE_FULL || (o.storage == MF_STORE_PARTIAL && generator != MF_GEN_EXTERNAL))
+      return fail(MF_ERR_OOM);
     // shrink the cache until the plan fits
     const double room = o.alpha_safety * (double)mfree - m_work;
     pc = room > 0 ? (int64_t)std::floor(room / blk_bytes) : 0;
     pc = std::min(pc, p.npair);
     p.pairs_cached = pc;
-    p.storage = pc == 0 ? MF_STORE_PROCEDURAL : (pc == p.npair ? MF_STORE_FULL : MF_STORE_PARTIAL);
+    p.storage = pc == p.npair ? MF_STORE_FULL
+                : (pc == 0 && generator != MF_GEN_EXTERNAL ? MF_STORE_PROCEDURAL : MF_STORE_PARTIAL);
     if (m_work > o.alpha_safety * (double)mfree) return fail(MF_ERR_OOM);
   }
 
@@ -426,10 +434,41 @@ mf_status create_fixed(mf_plan_t* out, int64_t D, int32_t generator, uint64_t se
       p.pair_slot[(size_t)(n * p.nblk + m)] = s;
       pairs.push_back(make_int2((int)n, (int)m));
     }
+  if (generator == MF_GEN_EXTERNAL) {
+    // pairs past P_cache stay in the caller's host array: slot -2 - k for
+    // the k-th stored pair
+    int64_t k = 0;
+    for (int64_t n = 0; n < p.nblk; ++n)
+      for (int64_t m = n; m < p.nblk; ++m, ++k)
+        if (k >= p.pairs_cached) p.pair_slot[(size_t)(n * p.nblk + m)] = -2 - k;
+    if (p.pairs_cached < p.npair) {
+      const size_t bytes = (size_t)p.npair * (size_t)blk_bytes;
+      void* hp = const_cast<void*>(ext);
+      cudaError_t e = cudaHostRegister(hp, bytes, cudaHostRegisterMapped);
+      if (e == cudaSuccess) {
+        p.h_registered = true;
+      } else if (e == cudaErrorHostMemoryAlreadyRegistered) {
+        cudaGetLastError();
+      } else {
+        cudaGetLastError();
+        return fail(MF_ERR_CUDA);
+      }
+      p.h_blocks = ext;
+      void* dp = nullptr;
+      if (cudaHostGetDevicePointer(&dp, hp, 0) != cudaSuccess) return fail(MF_ERR_CUDA);
+      p.d_hblocks = dp;
+    }
+  }
   if (p.pairs_cached > 0) {
     p.cache_bytes = (size_t)p.pairs_cached * (size_t)blk_bytes;
     cudaError_t e = cudaMalloc(&p.d_cache, p.cache_bytes);
     if (e != cudaSuccess) return fail(MF_ERR_OOM);
+  }
+  if (p.pairs_cached > 0 && generator == MF_GEN_EXTERNAL) {
+    // the cached pairs are the first P_cache stored blocks: one copy
+    if (cudaMemcpy(p.d_cache, ext, p.cache_bytes, cudaMemcpyHostToDevice) != cudaSuccess) return fail(MF_ERR_CUDA);
+  } else if (p.pairs_cached > 0) {
+    cudaError_t e;
     int2* d_pairs = nullptr;
     if (cudaMalloc((void**)&d_pairs, pairs.size() * sizeof(int2)) != cudaSuccess) return fail(MF_ERR_OOM);
     cudaMemcpyAsync(d_pairs, pairs.data(), pairs.size() * sizeof(int2), cudaMemcpyHostToDevice, p.stream);
@@ -449,10 +488,13 @@ mf_status create_fixed(mf_plan_t* out, int64_t D, int32_t generator, uint64_t se
         const int64_t n = ti / tpb, m = tj / tpb;
         const int64_t slot = p.pair_slot[(size_t)(n * p.nblk + m)];
         WorkItem it{(int32_t)ti, (int32_t)tj, -1};
+        const int64_t in_blk = (ti * kTile - n * p.b) * p.b + (tj * kTile - m * p.b);
         if (slot >= 0) {
-          it.cache_off = slot * p.b * p.b + (ti * kTile - n * p.b) * p.b + (tj * kTile - m * p.b);
+          it.cache_off = slot * p.b * p.b + in_blk;
           cached.push_back(it);
         } else {
+          // generated, or read from the external host array (block -2 - slot)
+          if (slot <= -2) it.cache_off = -2 - ((-2 - slot) * p.b * p.b + in_blk);
           proc.push_back(it);
         }
       }
@@ -471,7 +513,7 @@ mf_status create_fixed(mf_plan_t* out, int64_t D, int32_t generator, uint64_t se
                         p.stream) != cudaSuccess)
       return fail(MF_ERR_CUDA);
   }
-  if (p.pairs_cached > 0) {
+  if (p.pairs_cached > 0 || generator == MF_GEN_EXTERNAL) {
     const size_t nb = p.pair_slot.size() * sizeof(int64_t);
     if (cudaMalloc((void**)&p.d_pair_slot, nb) != cudaSuccess) return fail(MF_ERR_OOM);
     if (cudaMemcpyAsync(p.d_pair_slot, p.pair_slot.data(), nb, cudaMemcpyHostToDevice, p.stream) != cudaSuccess)
@@ -485,7 +527,9 @@ mf_status create_fixed(mf_plan_t* out, int64_t D, int32_t generator, uint64_t se
 }
 
 
-const char* gen_name(int g) { return g == MF_GEN_PHILOX_GUE ? "philox_gue" : "sinc_dvr_ho"; }
+const char* gen_name(int g) {
+  return g == MF_GEN_PHILOX_GUE ? "philox_gue" : (g == MF_GEN_SINC_DVR_HO ? "sinc_dvr_ho" : "external");
+}
 const char* prec_name(int g) { return g == MF_PREC_FP64 ? "fp64" : (g == MF_PREC_FP32 ? "fp32" : "bf16x2"); }
 const char* store_name(int s) {
   return s == MF_STORE_FULL ? "full" : (s == MF_STORE_PARTIAL ? "partial" : "procedural");
@@ -785,6 +829,27 @@ mf_status mf_plan_trials(mf_plan_t h, char* buf, size_t len, size_t* needed) {
   return all.size() + 1 <= len ? MF_OK : MF_ERR_INVALID;
 }
 
+mf_status mf_external_create(mf_plan_t* out, int64_t D, int64_t block, const void* blocks,
+                             size_t cache_budget_bytes, const mf_options* opt) {
+  if (!out) return MF_ERR_INVALID;
+  *out = nullptr;
+  mf_options o;
+  if (opt) o = *opt; else mf_options_default(&o);
+  if (D < 2 || D > (int64_t)1 << 31 || !blocks || block < kTile || block % kTile != 0) return MF_ERR_INVALID;
+  if ((uintptr_t)blocks % 16 != 0) return MF_ERR_INVALID;  // the kernels read 16-byte words
+  if (o.precision != MF_PREC_FP64 && o.precision != MF_PREC_FP32 && o.precision != MF_PREC_BF16X2)
+    return MF_ERR_INVALID;
+  if (!(o.cheb_tol > 0) || o.lanczos_m < 2 || !(o.alpha_safety > 0 && o.alpha_safety <= 1)) return MF_ERR_INVALID;
+  if (o.nvec_hint < 1 || o.nvec_hint > 64) return MF_ERR_INVALID;
+  // block larger than D rounded to the tile: the stored blocks would be
+  // smaller than b x b
+  if (block > (D + kTile - 1) / kTile * kTile) return MF_ERR_INVALID;
+  // P_cache from the budget (Eq. partial_cache_pairs); STORE_FULL insists
+  if (o.storage != MF_STORE_FULL) o.storage = MF_STORE_PARTIAL;
+  o.planner_mode = MF_PLANNER_ANALYTIC;
+  return create_fixed(out, D, MF_GEN_EXTERNAL, 0, block, cache_budget_bytes, o, blocks);
+}
+
 mf_status mf_sysbath_create(mf_plan_t* out, int64_t d_S, int64_t d_B, int32_t n_int, const uint64_t* seeds,
                             const void* H_S, const void* A, double g, const mf_options* opt) {
   if (!out) return MF_ERR_INVALID;
@@ -1023,6 +1088,7 @@ mf_status mf_plan_describe(mf_plan_t h, char* buf, size_t len) {
 mf_status mf_debug_entries(mf_plan_t h, int64_t r0, int64_t c0, int64_t rows, int64_t cols, void* out_host) {
   if (!h || !out_host || rows < 1 || cols < 1) return MF_ERR_INVALID;
   Plan& p = h->p;
+  if (p.gen == MF_GEN_EXTERNAL) return MF_ERR_UNSUPPORTED;
   if (r0 < 0 || c0 < 0 || r0 + rows > p.D || c0 + cols > p.D) return MF_ERR_INVALID;
   DeviceGuard guard(p.device);
   const size_t bytes = (size_t)rows * (size_t)cols * compute_elem_bytes(p.prec);

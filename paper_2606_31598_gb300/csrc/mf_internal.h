@@ -21,7 +21,9 @@ constexpr int kTile = 128;  // CTA tile edge of the Hermitian (canonical-pair) k
 // block pair is generated procedurally).
 struct WorkItem {
   int32_t ti, tj;
-  int64_t cache_off;  // element offset of the tile's cached block, or -1
+  // element offset of the tile in the HBM cache (>= 0), -1 when generated,
+  // or -2 - (element offset in the external host array)
+  int64_t cache_off;
 };
 
 struct Plan {
@@ -41,6 +43,12 @@ struct Plan {
   int64_t pairs_cached = 0;
   std::vector<int64_t> pair_slot;  // nblk*nblk (n<=m) -> cache slot or -1
   void* d_cache = nullptr;
+  // externally stored blocks (MF_GEN_EXTERNAL): the caller's host array of
+  // canonical blocks, registered and read by the kernels over the host link
+  // for the pairs not copied into d_cache
+  const void* h_blocks = nullptr;
+  const void* d_hblocks = nullptr;  // device-visible address of h_blocks
+  bool h_registered = false;
   // generator constants
   float sigma32 = 0.f;
   double sigma64 = 0.0;

@@ -30,7 +30,8 @@ template <typename T, int GEN, int NT>
 __device__ __forceinline__ void fill_chunk(typename cplx<T>::t* hs, T* win, int64_t R0, int64_t c0, int64_t D,
                                            uint64_t seed, T sigma, const dvr_consts& dk,
                                            const typename cplx<T>::t* __restrict__ cache,
-                                           const int64_t* __restrict__ slot_of_pair, int64_t b, int64_t nblk) {
+                                           const int64_t* __restrict__ slot_of_pair, int64_t b, int64_t nblk,
+                                           const typename cplx<T>::t* __restrict__ hcache = nullptr) {
   using C = typename cplx<T>::t;
   const int tid = threadIdx.x;
   constexpr int LD = KCH + HPAD;
@@ -39,7 +40,7 @@ __device__ __forceinline__ void fill_chunk(typename cplx<T>::t* hs, T* win, int6
   int64_t slot = -1;
   bool transposed = false;
   int64_t n = R0 / b, m = c0 / b;
-  if (cache) {
+  if (cache || hcache) {
     if (n <= m) {
       slot = slot_of_pair[n * nblk + m];
     } else {
@@ -47,13 +48,14 @@ __device__ __forceinline__ void fill_chunk(typename cplx<T>::t* hs, T* win, int6
       transposed = true;
     }
   }
-  if (slot >= 0) {
+  if (slot >= 0 || slot <= -2) {
     // every load of the thread first, then the shared-memory stores; the
     // transposed orientation walks the cached rows (r fastest) so a warp
     // reads contiguous memory
     constexpr int PER = RT * KCH / NT;
     constexpr int HALF = PER > 8 ? PER / 2 : PER;
-    const C* blk = cache + slot * b * b;
+    // HBM cache slot, or (slot <= -2) block -2 - slot of the host array
+    const C* blk = slot >= 0 ? cache + slot * b * b : hcache + (-2 - slot) * b * b;
 #pragma unroll
     for (int i0 = 0; i0 < PER; i0 += HALF) {
       C h[HALF];
@@ -137,7 +139,8 @@ __device__ __forceinline__ void row_tile(unsigned char* smem_raw, int64_t R0, in
                                          const typename cplx<T>::t* __restrict__ xc,
                                          typename cplx<T>::t* __restrict__ out,
                                          const typename cplx<T>::t* __restrict__ cache,
-                                         const int64_t* __restrict__ slot_of_pair, int64_t b, int64_t nblk) {
+                                         const int64_t* __restrict__ slot_of_pair, int64_t b, int64_t nblk,
+                                         const typename cplx<T>::t* __restrict__ hcache = nullptr) {
   using C = typename cplx<T>::t;
   static_assert((RT / TR) * (NV / TV) == NT, "thread blocking must cover the tile");
   constexpr int LD = KCH + HPAD;
@@ -156,7 +159,7 @@ __device__ __forceinline__ void row_tile(unsigned char* smem_raw, int64_t R0, in
     for (int j = 0; j < TV; ++j) acc[i][j] = zc<T>();
 
   for (int64_t c0 = cbeg; c0 < cend; c0 += KCH) {
-    fill_chunk<T, GEN, NT>(hs, win, R0, c0, D, seed, sigma, dk, cache, slot_of_pair, b, nblk);
+    fill_chunk<T, GEN, NT>(hs, win, R0, c0, D, seed, sigma, dk, cache, slot_of_pair, b, nblk, hcache);
     for (int e = tid; e < KCH * NV; e += NT) {
       const int64_t c = c0 + e / NV;
       xs[e] = c < cend ? xc[c * NV + e % NV] : zc<T>();
