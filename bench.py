@@ -622,6 +622,69 @@ def run_sysbath(args):
     return 0
 
 
+def run_external(args):
+    """The storage hierarchy on one operator: the Philox ensemble at D (FP32
+    form) written out as externally stored canonical blocks (b = 2048) in host
+    memory, applied with all pairs read from host memory over the host link,
+    with half of them in the HBM cache, and with all of them in HBM; beside
+    it, the same operator generated procedurally.  Host-link bandwidth =
+    host-resident block bytes / apply time."""
+    import torch
+    import paper_2606_31598_gb300 as mf
+    import workloads as W
+    D, b = args.ext_dim, 2048
+    stream = torch.cuda.current_stream().cuda_stream
+    nblk = -(-D // b)
+    pairs = [(n, m) for n in range(nblk) for m in range(n, nblk)]
+    gen = mf.Plan(D, mf.MF_GEN_PHILOX_GUE, seed=1, block=b, precision=mf.MF_PREC_FP32,
+                  storage=mf.MF_STORE_PROCEDURAL, stream=stream)
+    t0 = time.perf_counter()
+    blocks = np.zeros((len(pairs), b, b), dtype=np.complex64)
+    for k, (n, m) in enumerate(pairs):
+        rows, cols = min(b, D - n * b), min(b, D - m * b)
+        blocks[k, :rows, :cols] = gen.entries(n * b, m * b, rows, cols)
+    t_fill = time.perf_counter() - t0
+    x = torch.from_numpy(W.random_state(D, 1, seed=3)).cuda()
+    y = torch.empty_like(x)
+    out = {"workload": "externally stored blocks: Philox D=%d as %d canonical %dx%d complex64 blocks (%.1f GB) "
+                       "in host memory" % (D, len(pairs), b, b, blocks.nbytes / 1e9),
+           "fill_s": t_fill}
+    t_gen = time_applies(gen, x, y, 1, args.steps)
+    y_gen = y.clone()
+    out["procedural"] = {"apply_s": t_gen}
+    gen.close()
+    blk = 8.0 * b * b
+    for name, npc in [("host_all", 0), ("host_half", len(pairs) // 2), ("hbm_all", len(pairs))]:
+        plan = mf.Plan.external(D, b, blocks, cache_budget_bytes=int(npc * blk), precision=mf.MF_PREC_FP32,
+                                stream=stream)
+        t = time_applies(plan, x, y, 1, args.steps)
+        host_bytes = (len(pairs) - npc) * blk
+        res = {"apply_s": t, "pairs_in_hbm": npc, "host_bytes": host_bytes,
+               "max_rel_diff_vs_procedural": float((y - y_gen).abs().max() / y_gen.abs().max())}
+        if host_bytes > 0:
+            res["host_link_gbs"] = host_bytes / t / 1e9
+        if npc == len(pairs):
+            res["hbm_gbs"] = npc * blk / t / 1e9
+        out[name] = res
+        plan.close()
+    # the host link's copy-engine rate for context: one pinned 2 GB buffer
+    h = torch.empty(1 << 28, dtype=torch.complex64).pin_memory()
+    dbuf = torch.empty(1 << 28, dtype=torch.complex64, device="cuda")
+    dbuf.copy_(h, non_blocking=True)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(3):
+        dbuf.copy_(h, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    out["h2d_copy_engine_gbs"] = 3 * h.numel() * 8 / (e0.elapsed_time(e1) / 1e3) / 1e9
+    del h, dbuf
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -633,7 +696,9 @@ def main():
     ap.add_argument("--batch-budget-gb", type=float, default=200.0, help="batch: shared cache budget")
     ap.add_argument("--sb-ds", type=int, default=4, help="sysbath: system dimension d_S")
     ap.add_argument("--sb-db", type=int, default=65536, help="sysbath: bath dimension d_B")
-    ap.add_argument("--workload", default="dvr", choices=["dvr", "multivector", "batch", "philox", "sysbath"],
+    ap.add_argument("--ext-dim", type=int, default=65536, help="external: D")
+    ap.add_argument("--workload", default="dvr",
+                    choices=["dvr", "multivector", "batch", "philox", "sysbath", "external"],
                     help="dvr: the benchmark line; multivector: the 64-vector tensor-core workload report")
     ap.add_argument("--fp64", action="store_true", help="multivector: also time the FP64 procedural form")
     ap.add_argument("--mv-dim", type=int, default=262144, help="multivector: D (smaller D keeps the cached fraction)")
@@ -648,6 +713,8 @@ def main():
         return run_philox(args)
     if args.workload == "sysbath":
         return run_sysbath(args)
+    if args.workload == "external":
+        return run_external(args)
     return run_mf(args)
 
 
