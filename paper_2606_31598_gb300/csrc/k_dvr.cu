@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(256, 2) dvr_window(int64_t D, int64_t dpad, in
 // ---------------------------------------------------------------------------
 constexpr int kDvrP = 16, kDvrU = 16, kDvrWarps = 8;
 constexpr int kDvrRB = kDvrWarps * 32 * kDvrP;  // 4096 rows per row tile
-constexpr int kDvrKC = 2048;                    // staged columns per chunk
+constexpr int kDvrKC = 4096;                    // staged columns per chunk
 constexpr int kDvrNTB = kDvrRB + kDvrKC - 1;    // window entries per chunk
 constexpr int kDvrTbFloats = ((kDvrNTB + 1 + 15) / 16) * 20;
 constexpr size_t kDvrSmem = (size_t)kDvrTbFloats * sizeof(float) + (size_t)kDvrKC * sizeof(float2);
