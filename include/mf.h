@@ -430,6 +430,19 @@ mf_status mf_debug_entries(mf_plan_t p, int64_t r0, int64_t c0, int64_t rows, in
  */
 mf_status mf_apply_dvr_noalloc(int64_t D, double dvr_L, const void* x, void* y, void* stream);
 
+/*
+ * mf_selfcheck_generator -- compare, on the current device, the Philox
+ * ensemble's FP32 division and square root (hardware reciprocal and
+ * reciprocal-square-root approximations with one Markstein correction) with
+ * IEEE round-to-nearest division and square root on every float of the
+ * ranges the generator uses them on: numerator m - 1 over denominator m + 1
+ * for all m in [0.5, 2), square roots of 0 and of all x in [2^-33, 64).  Nonzero
+ * counts mean the FP32 entries would not match the IEEE definition on this
+ * device.  The paper has no counterpart.  Synchronises; a few milliseconds.
+ * Errors: MF_ERR_INVALID, MF_ERR_OOM, MF_ERR_CUDA.
+ */
+mf_status mf_selfcheck_generator(int64_t* div_mismatches, int64_t* sqrt_mismatches);
+
 #ifdef __cplusplus
 }
 #endif

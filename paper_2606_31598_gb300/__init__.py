@@ -108,6 +108,8 @@ def lib():
         L.mf_plan_create.argtypes = [P(vp), i64, i64, i32, u64, i64, ctypes.c_size_t, P(mf_options)]
         L.mf_sysbath_create.argtypes = [P(vp), i64, i64, i32, vp, vp, vp, d, P(mf_options)]
         L.mf_external_create.argtypes = [P(vp), i64, i64, vp, ctypes.c_size_t, P(mf_options)]
+        L.mf_selfcheck_generator.argtypes = [P(i64), P(i64)]
+        L.mf_selfcheck_generator.restype = ctypes.c_int
         L.mf_plan_destroy.argtypes = [vp]
         L.mf_apply.argtypes = [vp, vp, vp, i64]
         L.mf_cheb_propagate.argtypes = [vp, vp, i64, d, i32]
@@ -226,6 +228,14 @@ def mf_external_create(D, block, blocks, cache_budget_bytes=0, options=None):
                                   int(cache_budget_bytes), ctypes.byref(opt))
     _check(st, "mf_external_create")
     return h
+
+
+def mf_selfcheck_generator():
+    """(division mismatches, square-root mismatches) of the generator's FP32
+    arithmetic against IEEE on the current device (both 0 when exact)."""
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().mf_selfcheck_generator(ctypes.byref(a), ctypes.byref(b)), "mf_selfcheck_generator")
+    return a.value, b.value
 
 
 def mf_apply(plan, y, x, nvec=1):

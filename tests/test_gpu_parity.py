@@ -272,3 +272,9 @@ def test_multivector_cheb_matches_oracle(mf, prec):
     c, R = 0.5 * (emax + emin), 0.5 * (emax - emin)
     ref = O.cheb_step_dense(H, X, 0.7, c, R, 24)
     assert np.max(np.abs(out - ref)) < (1e-11 if prec == 0 else 2e-5)
+
+
+def test_generator_division_and_sqrt_exact_on_this_gpu(mf):
+    """The FP32 generator's Markstein-corrected division and square root equal
+    IEEE round-to-nearest on every float of their input ranges."""
+    assert mf.mf_selfcheck_generator() == (0, 0)
