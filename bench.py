@@ -43,6 +43,30 @@ def env_rank():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
 
 
+# ----------------------------------------------------------- multi-rank ---
+# N ranks run N independent propagations (weak scaling, no data-path
+# collective); the only cross-rank steps are the barriers around the timed
+# region and the max-over-ranks job time.
+def rank_task(rank):
+    """Centre x0 of rank's coherent state (an independent problem per rank)."""
+    return 2.0 + 0.25 * rank
+
+
+def job_seconds(t_local, world, device=None):
+    """The slowest rank's seconds (all ranks get the same value)."""
+    import torch
+    t = torch.tensor([t_local], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, steps, entries_per_step, t_job):
+    """Whole-job entries/s: the units all ranks processed over the job time."""
+    return world * steps * entries_per_step / t_job
+
+
 # ------------------------------------------------------------------ clocks ---
 class ClockSampler:
     """nvidia-smi sampling of SM clock and throttle reasons during a region."""
@@ -206,7 +230,7 @@ def run_mf(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream().cuda_stream
     props = torch.cuda.get_device_properties(dev)
-    x0 = 2.0 + 0.25 * rank  # independent task per rank
+    x0 = rank_task(rank)
 
     plan = mf.Plan(D, mf.MF_GEN_SINC_DVR_HO, precision=mf.MF_PREC_FP32, stream=stream)
     desc = plan.describe()
@@ -246,11 +270,8 @@ def run_mf(args):
     clocks = clock.stop()
     step_ms = [a.elapsed_time(b) for a, b in zip(starts, stops)]
     t_local = sum(step_ms) / 1e3
-    t = torch.tensor([t_local], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    t_job = float(t.item())
-    value = world * args.steps * entries_per_step / t_job
+    t_job = job_seconds(t_local, world, dev)
+    value = job_value(world, args.steps, entries_per_step, t_job)
     psi_timed = psi.cpu().numpy()
 
     # end to end through the public call: pinned host psi in, result out
@@ -268,10 +289,8 @@ def run_mf(args):
         host_in, host_out = host_out, host_in
     e_b.record()
     torch.cuda.synchronize()
-    t_e2e = torch.tensor([e_a.elapsed_time(e_b) / 1e3], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_e2e, op=dist.ReduceOp.MAX)
-    e2e_value = world * args.steps * entries_per_step / float(t_e2e.item())
+    t_e2e = job_seconds(e_a.elapsed_time(e_b) / 1e3, world, dev)
+    e2e_value = job_value(world, args.steps, entries_per_step, t_e2e)
 
     # stated error: one step of the FP32 form vs the FP64 form and vs the
     # closed-form coherent state
