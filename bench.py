@@ -516,6 +516,21 @@ def run_philox(args):
 PHILOX_OPS_PER_ENTRY = 30 + 12 + 24 + 8 + 24 + 3 + 8
 
 
+def batch_roofline(hbm_bytes, gen_entries, flops, t_apply):
+    """Lower bounds of one batched product from its three resources, each at
+    its measured or stated peak: HBM (the measured copy rate), the FP32 FMA
+    pipe (152 x 128 lanes x 2 FLOP x 2070 MHz) and entry generation (the
+    Philox row-owner rate, 1.5e11 entries/s measured in the 64-vector FP32
+    run); achieved fraction = largest bound / measured time."""
+    t_hbm = hbm_bytes / 6781.4e9
+    t_fma = flops / (152 * 128 * 2 * 2.07e9)
+    t_gen = gen_entries / 1.5e11
+    bound = max(t_hbm, t_fma, t_gen)
+    name = {t_hbm: "hbm", t_fma: "fma", t_gen: "generation"}[bound]
+    return {"t_apply_s": t_apply, "t_hbm_s": t_hbm, "t_fma_s": t_fma, "t_gen_s": t_gen, "bound": name,
+            "frac": bound / t_apply, "sum_of_bounds_frac": (t_hbm + t_fma + t_gen) / t_apply}
+
+
 def run_batch(args):
     """256 independent Philox problems (D log-uniform in [1024, 32768] rounded
     to 128, 1..16 vectors, seeds 0..255), plans chosen per problem by the
@@ -550,10 +565,17 @@ def run_batch(args):
     t_batch = e0.elapsed_time(e1) / 1e3
     stores = {}
     entries = 0.0
+    hbm_bytes = 0.0     # cached entries read per product (each stored pair as H and as H^dagger)
+    gen_entries = 0.0   # entries generated per product
+    flops = 0.0         # 8 real FLOP per entry and vector
     for i, (D, k) in enumerate(zip(Ds, nv)):
         d = mf.mf_plan_describe(b.plan(i))
         stores[d["storage"]] = stores.get(d["storage"], 0) + 1
         entries += float(D) * D * k
+        cached = min(float(D) * D, 2.0 * d["pairs_cached"] * d["block"] ** 2)
+        hbm_bytes += 8.0 * cached
+        gen_entries += float(D) * D - cached
+        flops += 8.0 * D * D * k
     # the same problems one by one through their own plans (same term count;
     # the plans run on the batch's stream, so time with device syncs)
     seq = [torch.from_numpy(q.copy()).cuda() for q in parts]
@@ -574,6 +596,7 @@ def run_batch(args):
            "batched": {"steps_per_s": args.steps / t_batch, "entries_per_s": entries * applies / t_batch},
            "sequential": {"steps_per_s": args.steps / t_seq, "entries_per_s": entries * applies / t_seq},
            "speedup_batched_vs_sequential": t_seq / t_batch,
+           "roofline": batch_roofline(hbm_bytes, gen_entries, flops, t_batch / applies),
            "max_diff_batched_vs_sequential": float(max((packed[int(b.offsets[i]):int(b.offsets[i + 1])]
                                                         - seq[i].reshape(-1)).abs().max() for i in range(len(Ds))))}
     print(json.dumps(out))

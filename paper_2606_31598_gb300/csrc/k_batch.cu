@@ -63,19 +63,19 @@ __global__ void __launch_bounds__(256) k_batch_apply(const BatchItem* __restrict
     const C* cache = (const C*)P.cache;
     switch (P.nb) {
       case 2:
-        row_tile<T, GEN, 2, 1, 1, 256>(smem_raw, R0, 0, P.D, P.D, P.seed, sigma, P.dk, xc, (C*)P.part + R0 * 2, cache,
+        row_tile<T, GEN, 2, 1, 1, 256, false>(smem_raw, R0, 0, P.D, P.D, P.seed, sigma, P.dk, xc, (C*)P.part + R0 * 2, cache,
                                        P.slot, P.b, P.nblk);
         break;
       case 4:
-        row_tile<T, GEN, 4, 1, 2, 256>(smem_raw, R0, 0, P.D, P.D, P.seed, sigma, P.dk, xc, (C*)P.part + R0 * 4, cache,
+        row_tile<T, GEN, 4, 1, 2, 256, false>(smem_raw, R0, 0, P.D, P.D, P.seed, sigma, P.dk, xc, (C*)P.part + R0 * 4, cache,
                                        P.slot, P.b, P.nblk);
         break;
       case 8:
-        row_tile<T, GEN, 8, 2, 2, 256>(smem_raw, R0, 0, P.D, P.D, P.seed, sigma, P.dk, xc, (C*)P.part + R0 * 8, cache,
+        row_tile<T, GEN, 8, 2, 2, 256, false>(smem_raw, R0, 0, P.D, P.D, P.seed, sigma, P.dk, xc, (C*)P.part + R0 * 8, cache,
                                        P.slot, P.b, P.nblk);
         break;
       default:
-        row_tile<T, GEN, 16, 2, 4, 256>(smem_raw, R0, 0, P.D, P.D, P.seed, sigma, P.dk, xc, (C*)P.part + R0 * 16,
+        row_tile<T, GEN, 16, 2, 4, 256, false>(smem_raw, R0, 0, P.D, P.D, P.seed, sigma, P.dk, xc, (C*)P.part + R0 * 16,
                                         cache, P.slot, P.b, P.nblk);
         break;
     }

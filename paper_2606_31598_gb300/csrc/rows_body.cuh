@@ -25,6 +25,61 @@ template <typename T> __device__ __forceinline__ typename cplx<T>::t zc() {
 }  // namespace rows
 using namespace rows;
 
+// Stored block pair of chunk (R0, c0): the HBM cache slot (>= 0), the host
+// array block -2 - slot (<= -2) or -1 (generated); transposed when the chunk
+// lies below the diagonal and is read from the canonical pair (m, n).
+__device__ __forceinline__ int64_t chunk_slot(int64_t R0, int64_t c0, const void* cache, const void* hcache,
+                                              const int64_t* __restrict__ slot_of_pair, int64_t b, int64_t nblk,
+                                              bool& transposed) {
+  transposed = false;
+  if (!cache && !hcache) return -1;
+  const int64_t n = R0 / b, m = c0 / b;
+  if (n <= m) return slot_of_pair[n * nblk + m];
+  transposed = true;
+  return slot_of_pair[m * nblk + n];
+}
+
+// Loads of a stored chunk into the thread's registers (element e = tid +
+// i NT of the chunk); the transposed orientation walks the stored rows
+// (r fastest) so a warp reads contiguous memory.
+template <typename T, int NT, int PER>
+__device__ __forceinline__ void chunk_load(typename cplx<T>::t (&h)[PER], int64_t slot, bool transposed,
+                                           int64_t R0, int64_t c0, const typename cplx<T>::t* __restrict__ cache,
+                                           const typename cplx<T>::t* __restrict__ hcache, int64_t b) {
+  const int tid = threadIdx.x;
+  const int64_t n = R0 / b, m = c0 / b;
+  const typename cplx<T>::t* blk = slot >= 0 ? cache + slot * b * b : hcache + (-2 - slot) * b * b;
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    const int e = tid + i * NT;
+    if (!transposed) {
+      const int r = e / KCH, c = e % KCH;
+      h[i] = blk[(R0 + r - n * b) * b + (c0 + c - m * b)];
+    } else {
+      const int r = e % RT, c = e / RT;
+      h[i] = blk[(c0 + c - m * b) * b + (R0 + r - n * b)];
+    }
+  }
+}
+
+template <typename T, int NT, int PER>
+__device__ __forceinline__ void chunk_store(typename cplx<T>::t* hs, const typename cplx<T>::t (&h)[PER],
+                                            bool transposed) {
+  constexpr int LD = KCH + HPAD;
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    const int e = tid + i * NT;
+    if (!transposed) {
+      hs[(e / KCH) * LD + e % KCH] = h[i];
+    } else {
+      typename cplx<T>::t v = h[i];
+      v.y = -v.y;
+      hs[(e % RT) * LD + e / RT] = v;
+    }
+  }
+}
+
 // Generate (or load) H[R0 : R0+RT, c0 : c0+KCH] into hs[RT][KCH+HPAD].
 template <typename T, int GEN, int NT>
 __device__ __forceinline__ void fill_chunk(typename cplx<T>::t* hs, T* win, int64_t R0, int64_t c0, int64_t D,
@@ -133,7 +188,7 @@ __device__ __forceinline__ void fill_chunk(typename cplx<T>::t* hs, T* win, int6
 // Y[R0 : R0+RT, :] over columns [cbeg, cend) -> out[row][v] (row-major,
 // NV vectors per row).  Called by all NT threads of the CTA; smem_raw holds
 // rows_smem_bytes<T, NV>() bytes.
-template <typename T, int GEN, int NV, int TR, int TV, int NT>
+template <typename T, int GEN, int NV, int TR, int TV, int NT, bool PIPE = true>
 __device__ __forceinline__ void row_tile(unsigned char* smem_raw, int64_t R0, int64_t cbeg, int64_t cend, int64_t D,
                                          uint64_t seed, T sigma, const dvr_consts& dk,
                                          const typename cplx<T>::t* __restrict__ xc,
@@ -158,13 +213,35 @@ __device__ __forceinline__ void row_tile(unsigned char* smem_raw, int64_t R0, in
 #pragma unroll
     for (int j = 0; j < TV; ++j) acc[i][j] = zc<T>();
 
+  // FP32 with up to 16 accumulators per thread: the next stored chunk's
+  // loads are issued into registers before this chunk's products, so the
+  // cache (or host) latency overlaps them
+  constexpr bool kPipe = PIPE && sizeof(T) == 4 && TR * TV <= 16;
+  constexpr int PER = RT * KCH / NT;
+  C hreg[kPipe ? PER : 1];
+  bool ptrans = false;
+  int64_t pslot = -1;
+  if (kPipe && cbeg < cend) {
+    pslot = chunk_slot(R0, cbeg, cache, hcache, slot_of_pair, b, nblk, ptrans);
+    if (pslot != -1) chunk_load<T, NT, kPipe ? PER : 1>(hreg, pslot, ptrans, R0, cbeg, cache, hcache, b);
+  }
   for (int64_t c0 = cbeg; c0 < cend; c0 += KCH) {
-    fill_chunk<T, GEN, NT>(hs, win, R0, c0, D, seed, sigma, dk, cache, slot_of_pair, b, nblk, hcache);
+    if (kPipe && pslot != -1)
+      chunk_store<T, NT, kPipe ? PER : 1>(hs, hreg, ptrans);
+    else
+      fill_chunk<T, GEN, NT>(hs, win, R0, c0, D, seed, sigma, dk, cache, slot_of_pair, b, nblk, hcache);
     for (int e = tid; e < KCH * NV; e += NT) {
       const int64_t c = c0 + e / NV;
       xs[e] = c < cend ? xc[c * NV + e % NV] : zc<T>();
     }
     __syncthreads();
+    if (kPipe) {
+      pslot = -1;
+      if (c0 + KCH < cend) {
+        pslot = chunk_slot(R0, c0 + KCH, cache, hcache, slot_of_pair, b, nblk, ptrans);
+        if (pslot != -1) chunk_load<T, NT, kPipe ? PER : 1>(hreg, pslot, ptrans, R0, c0 + KCH, cache, hcache, b);
+      }
+    }
 #pragma unroll 4
     for (int k = 0; k < KCH; ++k) {
       C h[TR], x[TV];
