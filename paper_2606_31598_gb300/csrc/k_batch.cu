@@ -63,20 +63,20 @@ __global__ void __launch_bounds__(256) k_batch_apply(const BatchItem* __restrict
     const C* cache = (const C*)P.cache;
     switch (P.nb) {
       case 2:
-        row_tile<T, GEN, 2, 1, 1, 256, false>(smem_raw, R0, 0, P.D, P.D, P.seed, sigma, P.dk, xc, (C*)P.part + R0 * 2, cache,
-                                       P.slot, P.b, P.nblk);
+        row_tile_async<T, GEN, 2, 1, 1, 256>(smem_raw, R0, 0, P.D, P.seed, sigma, P.dk, xc, (C*)P.part + R0 * 2,
+                                             cache, P.slot, P.b, P.nblk);
         break;
       case 4:
-        row_tile<T, GEN, 4, 1, 2, 256, false>(smem_raw, R0, 0, P.D, P.D, P.seed, sigma, P.dk, xc, (C*)P.part + R0 * 4, cache,
-                                       P.slot, P.b, P.nblk);
+        row_tile_async<T, GEN, 4, 1, 2, 256>(smem_raw, R0, 0, P.D, P.seed, sigma, P.dk, xc, (C*)P.part + R0 * 4,
+                                             cache, P.slot, P.b, P.nblk);
         break;
       case 8:
-        row_tile<T, GEN, 8, 2, 2, 256, false>(smem_raw, R0, 0, P.D, P.D, P.seed, sigma, P.dk, xc, (C*)P.part + R0 * 8, cache,
-                                       P.slot, P.b, P.nblk);
+        row_tile_async<T, GEN, 8, 2, 2, 256>(smem_raw, R0, 0, P.D, P.seed, sigma, P.dk, xc, (C*)P.part + R0 * 8,
+                                             cache, P.slot, P.b, P.nblk);
         break;
       default:
-        row_tile<T, GEN, 16, 2, 4, 256, false>(smem_raw, R0, 0, P.D, P.D, P.seed, sigma, P.dk, xc, (C*)P.part + R0 * 16,
-                                        cache, P.slot, P.b, P.nblk);
+        row_tile_async<T, GEN, 16, 2, 4, 256>(smem_raw, R0, 0, P.D, P.seed, sigma, P.dk, xc, (C*)P.part + R0 * 16,
+                                              cache, P.slot, P.b, P.nblk);
         break;
     }
   }
@@ -305,7 +305,7 @@ mf_status mf_batch_create(mf_batch_t* out, int32_t nprob, const int64_t* D, cons
   std::vector<BatchItem> sorted;
   for (size_t k : idx) sorted.push_back(items[k]);
   b->n_items = (int)sorted.size();
-  b->smem = o.precision == MF_PREC_FP64 ? rows_smem_bytes<double, 16>() : rows_smem_bytes<float, 16>();
+  b->smem = o.precision == MF_PREC_FP64 ? rows_smem_bytes_async<double, 16>() : rows_smem_bytes_async<float, 16>();
   cudaError_t e = cudaMalloc((void**)&b->d_items, sorted.size() * sizeof(BatchItem));
   if (e == cudaSuccess)
     e = cudaMemcpy(b->d_items, sorted.data(), sorted.size() * sizeof(BatchItem), cudaMemcpyHostToDevice);

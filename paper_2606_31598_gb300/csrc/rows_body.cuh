@@ -80,6 +80,58 @@ __device__ __forceinline__ void chunk_store(typename cplx<T>::t* hs, const typen
   }
 }
 
+// Generate H[R0 : R0+RT, c0 : c0+KCH] into hs[RT][KCH+HPAD]: canonical
+// entries from the Philox ensemble (conjugates below the diagonal) or DVR
+// entries from a window table.
+template <typename T, int GEN, int NT>
+__device__ __forceinline__ void fill_chunk_gen(typename cplx<T>::t* hs, T* win, int64_t R0, int64_t c0,
+                                               uint64_t seed, T sigma, const dvr_consts& dk) {
+  using C = typename cplx<T>::t;
+  const int tid = threadIdx.x;
+  constexpr int LD = KCH + HPAD;
+  if (GEN == MF_GEN_SINC_DVR_HO) {
+    // window table: T(k) for k = r - c in (R0 - c0 - KCH, R0 - c0 + RT)
+    const long long kmin = (long long)(R0 - c0) - (KCH - 1);
+    for (int j = tid; j < RT + KCH - 1; j += NT) win[j] = dvr_T(dk, kmin + j, T());
+    __syncthreads();
+    for (int e = tid; e < RT * KCH; e += NT) {
+      const int r = e / KCH, c = e % KCH;
+      C h;
+      h.x = win[r - c + KCH - 1];
+      h.y = T(0);
+      hs[r * LD + c] = h;
+    }
+    return;
+  }
+  if (c0 >= R0 + RT) {
+    // strictly above the diagonal: canonical pairs along rows
+    for (int e = tid; e < RT * (KCH / 2); e += NT) {
+      const int r = e / (KCH / 2), pc = e % (KCH / 2);
+      C h0, h1;
+      gue_pair<T>(seed, sigma, (uint32_t)(R0 + r), (uint32_t)((c0 >> 1) + pc), h0, h1);
+      hs[r * LD + 2 * pc] = h0;
+      hs[r * LD + 2 * pc + 1] = h1;
+    }
+  } else if (c0 + KCH <= R0) {
+    // strictly below: H[r][c] = conj(H[c][r]); canonical row c holds the
+    // pair of columns (rows here) r = 2p, 2p + 1
+    for (int e = tid; e < KCH * (RT / 2); e += NT) {
+      const int c = e / (RT / 2), pr = e % (RT / 2);
+      C h0, h1;
+      gue_pair<T>(seed, sigma, (uint32_t)(c0 + c), (uint32_t)((R0 >> 1) + pr), h0, h1);
+      h0.y = -h0.y;
+      h1.y = -h1.y;
+      hs[(2 * pr) * LD + c] = h0;
+      hs[(2 * pr + 1) * LD + c] = h1;
+    }
+  } else {
+    for (int e = tid; e < RT * KCH; e += NT) {
+      const int r = e / KCH, c = e % KCH;
+      hs[r * LD + c] = gue_entry<T>(seed, sigma, R0 + r, c0 + c);
+    }
+  }
+}
+
 // Generate (or load) H[R0 : R0+RT, c0 : c0+KCH] into hs[RT][KCH+HPAD].
 template <typename T, int GEN, int NT>
 __device__ __forceinline__ void fill_chunk(typename cplx<T>::t* hs, T* win, int64_t R0, int64_t c0, int64_t D,
@@ -142,47 +194,7 @@ __device__ __forceinline__ void fill_chunk(typename cplx<T>::t* hs, T* win, int6
     }
     return;
   }
-  if (GEN == MF_GEN_SINC_DVR_HO) {
-    // window table: T(k) for k = r - c in (R0 - c0 - KCH, R0 - c0 + RT)
-    const long long kmin = (long long)(R0 - c0) - (KCH - 1);
-    for (int j = tid; j < RT + KCH - 1; j += NT) win[j] = dvr_T(dk, kmin + j, T());
-    __syncthreads();
-    for (int e = tid; e < RT * KCH; e += NT) {
-      const int r = e / KCH, c = e % KCH;
-      C h;
-      h.x = win[r - c + KCH - 1];
-      h.y = T(0);
-      hs[r * LD + c] = h;
-    }
-    return;
-  }
-  if (c0 >= R0 + RT) {
-    // strictly above the diagonal: canonical pairs along rows
-    for (int e = tid; e < RT * (KCH / 2); e += NT) {
-      const int r = e / (KCH / 2), pc = e % (KCH / 2);
-      C h0, h1;
-      gue_pair<T>(seed, sigma, (uint32_t)(R0 + r), (uint32_t)((c0 >> 1) + pc), h0, h1);
-      hs[r * LD + 2 * pc] = h0;
-      hs[r * LD + 2 * pc + 1] = h1;
-    }
-  } else if (c0 + KCH <= R0) {
-    // strictly below: H[r][c] = conj(H[c][r]); canonical row c holds the
-    // pair of columns (rows here) r = 2p, 2p + 1
-    for (int e = tid; e < KCH * (RT / 2); e += NT) {
-      const int c = e / (RT / 2), pr = e % (RT / 2);
-      C h0, h1;
-      gue_pair<T>(seed, sigma, (uint32_t)(c0 + c), (uint32_t)((R0 >> 1) + pr), h0, h1);
-      h0.y = -h0.y;
-      h1.y = -h1.y;
-      hs[(2 * pr) * LD + c] = h0;
-      hs[(2 * pr + 1) * LD + c] = h1;
-    }
-  } else {
-    for (int e = tid; e < RT * KCH; e += NT) {
-      const int r = e / KCH, c = e % KCH;
-      hs[r * LD + c] = gue_entry<T>(seed, sigma, R0 + r, c0 + c);
-    }
-  }
+  fill_chunk_gen<T, GEN, NT>(hs, win, R0, c0, seed, sigma, dk);
 }
 
 // Y[R0 : R0+RT, :] over columns [cbeg, cend) -> out[row][v] (row-major,
@@ -265,6 +277,146 @@ __device__ __forceinline__ void row_tile(unsigned char* smem_raw, int64_t R0, in
   for (int i = 0; i < TR; ++i)
 #pragma unroll
     for (int j = 0; j < TV; ++j) out[(r0 + i) * NV + tv + j * (NV / TV)] = acc[i][j];
+}
+
+// ---------------------------------------------------------------------------
+// Asynchronous variant of row_tile for the persistent batched kernel: two
+// chunk buffers; a stored chunk is copied into the free buffer with cp.async
+// (no registers held) while the current chunk is contracted; a generated
+// chunk is generated into it after the contraction.  Chunks read transposed
+// from the canonical pair are stored raw and conjugated as they are used.
+// smem_raw holds rows_smem_bytes_async<T, NV>() bytes.
+// ---------------------------------------------------------------------------
+template <int BYTES>
+__device__ __forceinline__ void cp_async_elem(void* dst, const void* src) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+  if constexpr (BYTES == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+template <typename T, int NT>
+__device__ __forceinline__ void chunk_copy_async(typename cplx<T>::t* hb, int64_t slot, bool transposed, int64_t R0,
+                                                 int64_t c0, const typename cplx<T>::t* __restrict__ cache,
+                                                 const typename cplx<T>::t* __restrict__ hcache, int64_t b) {
+  using C = typename cplx<T>::t;
+  constexpr int LD = KCH + HPAD;
+  const int tid = threadIdx.x;
+  const int64_t n = R0 / b, m = c0 / b;
+  const C* blk = slot >= 0 ? cache + slot * b * b : hcache + (-2 - slot) * b * b;
+  for (int e = tid; e < RT * KCH; e += NT) {
+    int r, c;
+    const C* src;
+    if (!transposed) {
+      r = e / KCH;
+      c = e % KCH;
+      src = blk + (R0 + r - n * b) * b + (c0 + c - m * b);
+    } else {
+      r = e % RT;
+      c = e / RT;
+      src = blk + (c0 + c - m * b) * b + (R0 + r - n * b);
+    }
+    cp_async_elem<(int)sizeof(C)>(hb + r * LD + c, src);
+  }
+  cp_async_commit();
+}
+
+template <typename T, int GEN, int NV, int TR, int TV, int NT>
+__device__ __forceinline__ void row_tile_async(unsigned char* smem_raw, int64_t R0, int64_t cbeg, int64_t cend,
+                                               uint64_t seed, T sigma, const dvr_consts& dk,
+                                               const typename cplx<T>::t* __restrict__ xc,
+                                               typename cplx<T>::t* __restrict__ out,
+                                               const typename cplx<T>::t* __restrict__ cache,
+                                               const int64_t* __restrict__ slot_of_pair, int64_t b, int64_t nblk) {
+  using C = typename cplx<T>::t;
+  static_assert((RT / TR) * (NV / TV) == NT, "thread blocking must cover the tile");
+  constexpr int LD = KCH + HPAD;
+  C* hs0 = reinterpret_cast<C*>(smem_raw);
+  C* hs1 = hs0 + RT * LD;
+  C* xs = hs1 + RT * LD;                         // [KCH][NV]
+  T* win = reinterpret_cast<T*>(xs + KCH * NV);  // [RT + KCH]
+  const int tid = threadIdx.x;
+  const int tv = tid % (NV / TV), tr = tid / (NV / TV);
+  const int r0 = tr * TR;
+  C acc[TR][TV];
+#pragma unroll
+  for (int i = 0; i < TR; ++i)
+#pragma unroll
+    for (int j = 0; j < TV; ++j) acc[i][j] = zc<T>();
+  if (cbeg >= cend) return;
+  // chunk 0 into buffer 0
+  bool conj0 = false, conj1 = false;  // chunk in buffer 0 / 1 read transposed (conjugate on use)
+  {
+    bool t0 = false;
+    const int64_t s0 = chunk_slot(R0, cbeg, cache, nullptr, slot_of_pair, b, nblk, t0);
+    if (s0 != -1) {
+      chunk_copy_async<T, NT>(hs0, s0, t0, R0, cbeg, cache, nullptr, b);
+      conj0 = t0;
+      cp_async_wait_all();
+    } else {
+      fill_chunk_gen<T, GEN, NT>(hs0, win, R0, cbeg, seed, sigma, dk);
+    }
+  }
+  int k = 0;
+  for (int64_t c0 = cbeg; c0 < cend; c0 += KCH, ++k) {
+    C* cur = (k & 1) ? hs1 : hs0;
+    C* nxt = (k & 1) ? hs0 : hs1;
+    const bool cj = (k & 1) ? conj1 : conj0;
+    for (int e = tid; e < KCH * NV; e += NT) {
+      const int64_t c = c0 + e / NV;
+      xs[e] = c < cend ? xc[c * NV + e % NV] : zc<T>();
+    }
+    const int64_t c1 = c0 + KCH;
+    bool t1 = false;
+    int64_t s1 = -1;
+    if (c1 < cend) {
+      s1 = chunk_slot(R0, c1, cache, nullptr, slot_of_pair, b, nblk, t1);
+      if (s1 != -1) chunk_copy_async<T, NT>(nxt, s1, t1, R0, c1, cache, nullptr, b);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < KCH; ++kk) {
+      C h[TR], x[TV];
+#pragma unroll
+      for (int i = 0; i < TR; ++i) {
+        h[i] = cur[(r0 + i) * LD + kk];
+        if (cj) h[i].y = -h[i].y;
+      }
+#pragma unroll
+      for (int j = 0; j < TV; ++j) x[j] = xs[kk * NV + tv + j * (NV / TV)];
+#pragma unroll
+      for (int i = 0; i < TR; ++i)
+#pragma unroll
+        for (int j = 0; j < TV; ++j) {
+          acc[i][j].x = fma(h[i].x, x[j].x, acc[i][j].x);
+          acc[i][j].x = fma(-h[i].y, x[j].y, acc[i][j].x);
+          acc[i][j].y = fma(h[i].x, x[j].y, acc[i][j].y);
+          acc[i][j].y = fma(h[i].y, x[j].x, acc[i][j].y);
+        }
+    }
+    if (c1 < cend && s1 == -1) {
+      __syncthreads();  // the DVR window table and xs are free again
+      fill_chunk_gen<T, GEN, NT>(nxt, win, R0, c1, seed, sigma, dk);
+    }
+    if (k & 1)
+      conj0 = s1 != -1 && t1;
+    else
+      conj1 = s1 != -1 && t1;
+    cp_async_wait_all();
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < TR; ++i)
+#pragma unroll
+    for (int j = 0; j < TV; ++j) out[(r0 + i) * NV + tv + j * (NV / TV)] = acc[i][j];
+}
+
+template <typename T, int NV>
+__host__ __device__ constexpr size_t rows_smem_bytes_async() {
+  return sizeof(typename cplx<T>::t) * (2 * (size_t)RT * (KCH + HPAD) + (size_t)KCH * NV) + sizeof(T) * (RT + KCH);
 }
 
 template <typename T, int NV>
