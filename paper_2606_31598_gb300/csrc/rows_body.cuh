@@ -197,6 +197,23 @@ __device__ __forceinline__ void fill_chunk(typename cplx<T>::t* hs, T* win, int6
   fill_chunk_gen<T, GEN, NT>(hs, win, R0, c0, seed, sigma, dk);
 }
 
+// acc[i][j] += h[i] x[j] (complex) for a TR x TV register tile.  (A packed
+// FP32 form of these four fused operations measured slower here: its operand
+// pairs cost more registers than the issue slots it saves.)
+template <typename T, int TR, int TV>
+__device__ __forceinline__ void tile_cmac(typename cplx<T>::t (&acc)[TR][TV], const typename cplx<T>::t (&h)[TR],
+                                          const typename cplx<T>::t (&x)[TV]) {
+#pragma unroll
+  for (int i = 0; i < TR; ++i)
+#pragma unroll
+    for (int j = 0; j < TV; ++j) {
+      acc[i][j].x = fma(h[i].x, x[j].x, acc[i][j].x);
+      acc[i][j].x = fma(-h[i].y, x[j].y, acc[i][j].x);
+      acc[i][j].y = fma(h[i].x, x[j].y, acc[i][j].y);
+      acc[i][j].y = fma(h[i].y, x[j].x, acc[i][j].y);
+    }
+}
+
 // Y[R0 : R0+RT, :] over columns [cbeg, cend) -> out[row][v] (row-major,
 // NV vectors per row).  Called by all NT threads of the CTA; smem_raw holds
 // rows_smem_bytes<T, NV>() bytes.
@@ -261,15 +278,7 @@ __device__ __forceinline__ void row_tile(unsigned char* smem_raw, int64_t R0, in
       for (int i = 0; i < TR; ++i) h[i] = hs[(r0 + i) * LD + k];
 #pragma unroll
       for (int j = 0; j < TV; ++j) x[j] = xs[k * NV + tv + j * (NV / TV)];
-#pragma unroll
-      for (int i = 0; i < TR; ++i)
-#pragma unroll
-        for (int j = 0; j < TV; ++j) {
-          acc[i][j].x = fma(h[i].x, x[j].x, acc[i][j].x);
-          acc[i][j].x = fma(-h[i].y, x[j].y, acc[i][j].x);
-          acc[i][j].y = fma(h[i].x, x[j].y, acc[i][j].y);
-          acc[i][j].y = fma(h[i].y, x[j].x, acc[i][j].y);
-        }
+      tile_cmac<T, TR, TV>(acc, h, x);
     }
     __syncthreads();
   }
@@ -307,19 +316,23 @@ __device__ __forceinline__ void chunk_copy_async(typename cplx<T>::t* hb, int64_
   const int tid = threadIdx.x;
   const int64_t n = R0 / b, m = c0 / b;
   const C* blk = slot >= 0 ? cache + slot * b * b : hcache + (-2 - slot) * b * b;
-  for (int e = tid; e < RT * KCH; e += NT) {
-    int r, c;
-    const C* src;
-    if (!transposed) {
-      r = e / KCH;
-      c = e % KCH;
-      src = blk + (R0 + r - n * b) * b + (c0 + c - m * b);
-    } else {
-      r = e % RT;
-      c = e / RT;
-      src = blk + (c0 + c - m * b) * b + (R0 + r - n * b);
-    }
-    cp_async_elem<(int)sizeof(C)>(hb + r * LD + c, src);
+  static_assert(NT % KCH == 0 && NT % RT == 0, "element strides must be whole rows");
+  if (!transposed) {
+    // element e = tid + i NT: row e / KCH advances by NT / KCH, column fixed
+    const int r = tid / KCH, c = tid % KCH;
+    const C* src = blk + (R0 + r - n * b) * b + (c0 + c - m * b);
+    C* dst = hb + r * LD + c;
+    const int64_t sstep = (int64_t)(NT / KCH) * b;
+#pragma unroll 4
+    for (int i = 0; i < RT * KCH / NT; ++i) cp_async_elem<(int)sizeof(C)>(dst + i * (NT / KCH) * LD, src + i * sstep);
+  } else {
+    // element e = tid + i NT: row e % RT fixed, column e / RT advances by NT / RT
+    const int r = tid % RT, c = tid / RT;
+    const C* src = blk + (c0 + c - m * b) * b + (R0 + r - n * b);
+    C* dst = hb + r * LD + c;
+    const int64_t sstep = (int64_t)(NT / RT) * b;
+#pragma unroll 4
+    for (int i = 0; i < RT * KCH / NT; ++i) cp_async_elem<(int)sizeof(C)>(dst + i * (NT / RT), src + i * sstep);
   }
   cp_async_commit();
 }
@@ -387,15 +400,7 @@ __device__ __forceinline__ void row_tile_async(unsigned char* smem_raw, int64_t 
       }
 #pragma unroll
       for (int j = 0; j < TV; ++j) x[j] = xs[kk * NV + tv + j * (NV / TV)];
-#pragma unroll
-      for (int i = 0; i < TR; ++i)
-#pragma unroll
-        for (int j = 0; j < TV; ++j) {
-          acc[i][j].x = fma(h[i].x, x[j].x, acc[i][j].x);
-          acc[i][j].x = fma(-h[i].y, x[j].y, acc[i][j].x);
-          acc[i][j].y = fma(h[i].x, x[j].y, acc[i][j].y);
-          acc[i][j].y = fma(h[i].y, x[j].x, acc[i][j].y);
-        }
+      tile_cmac<T, TR, TV>(acc, h, x);
     }
     if (c1 < cend && s1 == -1) {
       __syncthreads();  // the DVR window table and xs are free again
