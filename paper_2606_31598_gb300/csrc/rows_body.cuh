@@ -49,17 +49,15 @@ __device__ __forceinline__ void chunk_load(typename cplx<T>::t (&h)[PER], int64_
   const int tid = threadIdx.x;
   const int64_t n = R0 / b, m = c0 / b;
   const typename cplx<T>::t* blk = slot >= 0 ? cache + slot * b * b : hcache + (-2 - slot) * b * b;
+  static_assert(NT % KCH == 0 && NT % RT == 0, "element strides must be whole rows");
+  // element e = tid + i NT: (row e / KCH, column e % KCH) advances by whole
+  // rows, (row e % RT, column e / RT) by whole columns
+  const typename cplx<T>::t* src =
+      !transposed ? blk + (R0 + tid / KCH - n * b) * b + (c0 + tid % KCH - m * b)
+                  : blk + (c0 + tid / RT - m * b) * b + (R0 + tid % RT - n * b);
+  const int64_t step = (int64_t)(!transposed ? NT / KCH : NT / RT) * b;
 #pragma unroll
-  for (int i = 0; i < PER; ++i) {
-    const int e = tid + i * NT;
-    if (!transposed) {
-      const int r = e / KCH, c = e % KCH;
-      h[i] = blk[(R0 + r - n * b) * b + (c0 + c - m * b)];
-    } else {
-      const int r = e % RT, c = e / RT;
-      h[i] = blk[(c0 + c - m * b) * b + (R0 + r - n * b)];
-    }
-  }
+  for (int i = 0; i < PER; ++i) h[i] = src[i * step];
 }
 
 template <typename T, int NT, int PER>
