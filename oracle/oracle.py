@@ -342,3 +342,18 @@ def external_dense(D, b, blocks):
             H[n * b:(n + 1) * b, m * b:(m + 1) * b] = B
             H[m * b:(m + 1) * b, n * b:(n + 1) * b] = B.conj().T
     return H[:D, :D]
+
+
+def dvr_apply_fft(op, x):
+    """DVR product y = (T + V) x for any D by the FFT: T is the symmetric
+    Toeplitz matrix of T(k), so T x is the first D entries of the circular
+    convolution of the length-2D embedding [T(0..D-1), 0, T(D-1..1)] with
+    [x, 0] (a library FFT as one step), plus V_i x_i."""
+    D = op.D
+    x = np.asarray(x, dtype=np.complex128).reshape(D)
+    t = kinetic_window(op, 0, 0, D, 1)[:, 0]
+    c = np.concatenate([t, [0.0], t[:0:-1]])
+    xp = np.concatenate([x, np.zeros(D, dtype=np.complex128)])
+    y = np.fft.ifft(np.fft.fft(c) * np.fft.fft(xp))[:D]
+    V = np.array([potential(op, i) for i in range(D)])
+    return y + V * x

@@ -122,6 +122,21 @@ def test_dvr_full_size_sampled_rows(mf, prec):
     assert err < (1e-11 if prec == 0 else 2e-3)
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_dvr_full_size_every_row_against_fft(mf, prec):
+    """D = 131072 in the benchmark's launch shape, every output row against
+    the oracle's FFT form of the Toeplitz product (FP64 reference of the
+    FP64 form, or of the FP32 form's entries)."""
+    D = 131072
+    p = _plan(mf, D, mf.MF_GEN_SINC_DVR_HO, prec)
+    rng = np.random.default_rng(11)
+    x = (rng.standard_normal(D) + 1j * rng.standard_normal(D)) / np.sqrt(2.0 * D)
+    y = _apply(p, x)
+    ref = O.dvr_apply_fft(O.make_op(O.GEN_SINC_DVR_HO, D, form=_form(prec)), x)
+    # a random x has no cancellation: the FP32 tile sums hold 2e-5 of max|y|
+    assert _relerr(y, ref) < (1e-11 if prec == 0 else 2e-5)
+
+
 def test_hermitian_identity_on_gpu(mf):
     D = 2048
     p = _plan(mf, D, 0, 0, seed=3)

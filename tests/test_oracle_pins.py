@@ -439,3 +439,14 @@ def test_external_assembly_recovers_a_hermitian_matrix(D, b):
     G = O.dense(op)
     x = rng.standard_normal(D) + 1j * rng.standard_normal(D)
     assert np.max(np.abs(O.external_dense(D, b, _cut_canonical(G, b)) @ x - O.apply(op, x))) < 1e-13
+
+
+@pytest.mark.parametrize("D", [257, 700])
+def test_dvr_fft_product_matches_direct_sum(D):
+    """The FFT (circulant embedding) form of the DVR product equals the
+    oracle's direct blockwise sum; it serves as the full-size reference."""
+    op = O.make_op(O.GEN_SINC_DVR_HO, D)
+    rng = np.random.default_rng(D)
+    x = rng.standard_normal(D) + 1j * rng.standard_normal(D)
+    ref = O.apply(op, x)
+    assert np.max(np.abs(O.dvr_apply_fft(op, x) - ref)) < 1e-11 * np.max(np.abs(ref))
