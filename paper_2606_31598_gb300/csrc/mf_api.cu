@@ -58,6 +58,7 @@ void release(Plan& p) {
   p.ev.clear();
   free_dev(p.d_cache);
   free_dev(p.d_work);
+  free_dev(p.d_herm_items);
   free_dev(p.d_pair_slot);
   free_dev(p.d_part);
   free_dev(p.d_xc);
@@ -77,11 +78,24 @@ void release(Plan& p) {
 // Vector shape of the path used for nvec vectors: the Hermitian or DVR
 // window path for one vector, the row-owner path (padded to a compiled
 // vector count) for several.
+// The Hermitian-reuse multi-vector path (each canonical entry applied as H
+// and H^dagger) is used for the Philox ensemble and stored blocks with up to
+// 16 vectors while its partial slots (one per owner item and per row tile)
+// take at most 4 GB; otherwise the row-owner path.
+bool use_rows_herm(const Plan& p, int64_t nb) {
+  if (!p.d_herm_items || p.gen == MF_GEN_SINC_DVR_HO || p.prec == MF_PREC_BF16X2 || nb > 16) return false;
+  const double bytes = (double)(p.herm_ns + p.ntile) * (double)(p.ntile * kTile) * (double)nb *
+                       (double)compute_elem_bytes(p.prec);
+  return bytes <= 4e9;
+}
+
 VecShape shape_for(const Plan& p, int64_t nvec) {
   if (p.prec == MF_PREC_BF16X2)
     return VecShape{nvec, tc_nvec_bucket(nvec), p.rows_nsplit, p.ntile * (int64_t)kTile};
   if (nvec == 1 && !p.sb_nop) return VecShape{1, 1, p.nslot, p.dpad};
-  return VecShape{nvec, rows_nvec_bucket(nvec), p.rows_nsplit, p.ntile * (int64_t)kTile};
+  const int64_t nb = rows_nvec_bucket(nvec);
+  if (use_rows_herm(p, nb)) return VecShape{nvec, nb, p.herm_ns + p.ntile, p.ntile * (int64_t)kTile};
+  return VecShape{nvec, nb, p.rows_nsplit, p.ntile * (int64_t)kTile};
 }
 
 // Workspace for nvec vectors: partial slots, compute copy, three FP64 vectors.
@@ -138,14 +152,24 @@ mf_status apply_kernel(Plan& p, int64_t nvec) {
     }
     MF_CUDA(cudaEventRecord(p.ev[p.ev_used].first, p.stream));
   }
+  const int64_t nbr = rows_nvec_bucket(nvec);
+  const bool herm = (nvec > 1 || p.sb_nop) && p.prec != MF_PREC_BF16X2 && use_rows_herm(p, nbr);
+  if (herm) {
+    const VecShape sh = shape_for(p, nvec);
+    MF_CUDA(cudaMemsetAsync(p.d_part, 0, (size_t)sh.nslot * sh.dpad * sh.nb * compute_elem_bytes(p.prec), p.stream));
+  }
   if (p.sb_nop) {
-    const int64_t nb = rows_nvec_bucket(nvec);
-    MF_CUDA(launch_sb_mix(p, p.d_xc, p.d_sb_xo, nb, p.sb_rows));
-    MF_CUDA(launch_sb_rows(p, p.d_sb_xo, p.sb_rows * nb, p.d_part, nb));
+    MF_CUDA(launch_sb_mix(p, p.d_xc, p.d_sb_xo, nbr, p.sb_rows));
+    if (herm)
+      MF_CUDA(launch_rows_herm(p, p.d_sb_xo, p.sb_rows * nbr, p.d_part, nbr, p.sb_nop, p.d_sb_seeds));
+    else
+      MF_CUDA(launch_sb_rows(p, p.d_sb_xo, p.sb_rows * nbr, p.d_part, nbr));
   } else if (p.prec == MF_PREC_BF16X2)
     MF_CUDA(launch_tc_apply(p, p.d_xc, p.d_part, p.d_tcb, tc_nvec_bucket(nvec)));
+  else if (nvec > 1 && herm)
+    MF_CUDA(launch_rows_herm(p, p.d_xc, 0, p.d_part, nbr, 1, nullptr));
   else if (nvec > 1)
-    MF_CUDA(launch_rows_apply(p, p.d_xc, p.d_part, rows_nvec_bucket(nvec)));
+    MF_CUDA(launch_rows_apply(p, p.d_xc, p.d_part, nbr));
   else if (p.use_dvr_window)
     MF_CUDA(launch_dvr_apply(p, p.d_xc, p.d_part, 1));
   else
@@ -510,6 +534,14 @@ mf_status create_fixed(mf_plan_t* out, int64_t D, int32_t generator, uint64_t se
     p.nwork = (int64_t)work.size();
     if (cudaMalloc((void**)&p.d_work, work.size() * sizeof(WorkItem)) != cudaSuccess) return fail(MF_ERR_OOM);
     if (cudaMemcpyAsync(p.d_work, work.data(), work.size() * sizeof(WorkItem), cudaMemcpyHostToDevice,
+                        p.stream) != cudaSuccess)
+      return fail(MF_ERR_CUDA);
+  }
+  if (!p.use_dvr_window && generator != MF_GEN_SINC_DVR_HO && p.prec != MF_PREC_BF16X2) {
+    const std::vector<HermItem> hi = rows_herm_items(D, p.num_sms, &p.herm_ns);
+    p.herm_nitems = (int64_t)hi.size();
+    if (cudaMalloc((void**)&p.d_herm_items, hi.size() * sizeof(HermItem)) != cudaSuccess) return fail(MF_ERR_OOM);
+    if (cudaMemcpyAsync(p.d_herm_items, hi.data(), hi.size() * sizeof(HermItem), cudaMemcpyHostToDevice,
                         p.stream) != cudaSuccess)
       return fail(MF_ERR_CUDA);
   }

@@ -26,6 +26,14 @@ struct WorkItem {
   int64_t cache_off;
 };
 
+// One CTA of the Hermitian multi-vector kernel (k_rows_herm.cu): row tile
+// ti, its owner-row partial slot, and the columns [c_beg, c_end) it covers
+// (c_beg >= 128 ti).
+struct HermItem {
+  int32_t ti, slot;
+  int64_t c_beg, c_end;
+};
+
 struct Plan {
   // problem
   int64_t D = 0;
@@ -60,6 +68,9 @@ struct Plan {
   // multi-vector row-owner path: split-K over column ranges
   int64_t rows_nsplit = 1, rows_split_cols = 0;
   int64_t* d_pair_slot = nullptr;  // device copy of pair_slot
+  // multi-vector Hermitian-reuse path: column items, owner slots per tile
+  HermItem* d_herm_items = nullptr;
+  int64_t herm_nitems = 0, herm_ns = 0;
   // DVR launch shape
   int dvr_rows = 512, dvr_cols = 4096;
   // workspace (sized for nvec_cap vectors)
@@ -129,6 +140,12 @@ DvrRowsShape dvr_rows_shape(int64_t D, int num_sms);
 cudaError_t launch_cache_fill_pairs(const Plan& p, const int2* d_pairs, int64_t npairs);
 // Multi-vector row-owner apply (nvec bucket 2..64).
 cudaError_t launch_rows_apply(const Plan& p, const void* xc, void* part, int64_t nvec_bucket);
+// Hermitian-reuse multi-vector apply (k_rows_herm.cu): nop operators (seeds
+// per operator, or the plan's seed when seeds == nullptr) on inputs xc + o
+// xstride; part must be zero-filled ([herm_ns + ntile][ntile 128][nb]).
+std::vector<HermItem> rows_herm_items(int64_t D, int num_sms, int64_t* ns_out);
+cudaError_t launch_rows_herm(const Plan& p, const void* xc, int64_t xstride, void* part, int64_t nb, int nop,
+                             const uint64_t* seeds);
 int64_t rows_nvec_bucket(int64_t nvec);
 // Tensor-core BF16X2 apply (k_tc.cu): vector buckets 8..64, operand tiles of
 // X in gB (tc_operand_bytes bytes).
