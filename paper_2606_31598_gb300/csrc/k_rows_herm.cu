@@ -186,11 +186,11 @@ cudaError_t launch_g(const Plan& p, const void* xc, int64_t xstride, void* part,
 
 // Column items of the Hermitian multi-vector kernel: for each row tile ti the
 // columns [128 ti, D) in pieces of at most w columns (a multiple of 32), w
-// chosen for about 4 items per SM; longest items first.
+// chosen for about 12 items per SM (a short tail); longest items first.
 std::vector<HermItem> rows_herm_items(int64_t D, int num_sms, int64_t* ns_out) {
   const int64_t ntile = (D + kTile - 1) / kTile;
   const double total = 0.5 * (double)ntile * (double)(D + kTile);
-  int64_t w = (int64_t)std::ceil(total / (4.0 * num_sms));
+  int64_t w = (int64_t)std::ceil(total / (12.0 * num_sms));
   w = std::max<int64_t>(256, (w + 31) / 32 * 32);
   std::vector<HermItem> items;
   int64_t ns = 1;
