@@ -99,6 +99,10 @@ typedef struct {
   double dense_work_limit; /* W_Hpsi threshold in entries for MF_WARN_DENSE_WORK (1e13) */
   int32_t device;          /* CUDA device ordinal (0) */
   mf_mlp_t model;          /* trained surrogate for MF_PLANNER_LEARNED/_HYBRID (NULL) */
+  int32_t hermitian_reuse; /* 2..16 vectors: -1 = automatic (default; each canonical
+                              chunk applied as H and H^dagger while its partial slots
+                              fit min(16 GB, 10 % of free memory)), 0 = row-owner
+                              kernel (every entry generated or read for each use) */
 } mf_options;
 
 /* Generic planning instance P_mv of Sec. IV.A (Y = A X with A of size

@@ -63,6 +63,7 @@ class mf_options(ctypes.Structure):
         ("dense_work_limit", ctypes.c_double),
         ("device", ctypes.c_int32),
         ("model", ctypes.c_void_p),
+        ("hermitian_reuse", ctypes.c_int32),
     ]
 
 

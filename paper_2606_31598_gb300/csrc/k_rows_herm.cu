@@ -22,36 +22,42 @@
 namespace mf {
 namespace {
 
-// Transposed product of one staged chunk: y[c][v] = sum_r conj(hs[r][c])
-// xr[r][v] for the chunk's 32 columns, P parts over r combined in shared
-// memory; added into out (rows c0 + c of slot NS + ti).
+// Transposed product of one staged chunk: y[c][v] += sum_r conj(hs[r][c])
+// xr[r][v] for the chunk's 32 columns.  Thread (part p, slot q) owns CT
+// columns x VT vectors over the rows of part p (register tile: each staged
+// value read once per CT or VT products); the P parts are combined later.
+template <typename T, int NV> struct Dag {
+  static constexpr int VT = NV < 4 ? NV : 4;                         // vectors per thread
+  static constexpr int CT = (NV == 16 && sizeof(T) == 4) ? 4 : 2;    // columns per thread
+  static constexpr int TPP = (KCH / CT) * (NV / VT);                 // threads per part
+};
+
 template <typename T, int NV, int NT>
 __device__ __forceinline__ void chunk_dagger(const typename cplx<T>::t* hs, const typename cplx<T>::t* xr,
-                                             typename cplx<T>::t* red, typename cplx<T>::t (&yt)[(32 * NV + NT - 1) / NT]) {
+                                             typename cplx<T>::t (&yt)[Dag<T, NV>::CT][Dag<T, NV>::VT]) {
   using C = typename cplx<T>::t;
   constexpr int LD = KCH + HPAD;
-  constexpr int O = KCH * NV;                  // outputs of the chunk
-  constexpr int P = O >= NT ? 1 : NT / O;      // parts over r per output
-  constexpr int PER = (O + NT - 1) / NT;       // outputs per thread
-  constexpr int RP = RT / P;
-  const int tid = threadIdx.x;
-  const int p = O >= NT ? 0 : tid / O;
+  constexpr int VT = Dag<T, NV>::VT, CT = Dag<T, NV>::CT, TPP = Dag<T, NV>::TPP;
+  constexpr int P = NT / TPP, RP = RT / P;
+  const int tid = threadIdx.x, p = tid / TPP, q = tid % TPP;
+  const int cg = q / (NV / VT), vg = q % (NV / VT);
+  for (int r = p * RP; r < (p + 1) * RP; ++r) {
+    C h[CT], x[VT];
 #pragma unroll
-  for (int k = 0; k < PER; ++k) {
-    const int o = (O >= NT ? tid + k * NT : tid % O);
-    const int c = o / NV, v = o % NV;
-    C s = yt[k];
-    for (int r = p * RP; r < (p + 1) * RP; ++r) {
-      const C h = hs[r * LD + c], x = xr[r * NV + v];
-      // s += conj(h) x
-      s.x = fma(h.x, x.x, s.x);
-      s.x = fma(h.y, x.y, s.x);
-      s.y = fma(h.x, x.y, s.y);
-      s.y = fma(-h.y, x.x, s.y);
-    }
-    yt[k] = s;
+    for (int j = 0; j < CT; ++j) h[j] = hs[r * LD + cg + j * (KCH / CT)];
+#pragma unroll
+    for (int i = 0; i < VT; ++i) x[i] = xr[r * NV + vg + i * (NV / VT)];
+#pragma unroll
+    for (int j = 0; j < CT; ++j)
+#pragma unroll
+      for (int i = 0; i < VT; ++i) {
+        // yt += conj(h) x
+        yt[j][i].x = fma(h[j].x, x[i].x, yt[j][i].x);
+        yt[j][i].x = fma(h[j].y, x[i].y, yt[j][i].x);
+        yt[j][i].y = fma(h[j].x, x[i].y, yt[j][i].y);
+        yt[j][i].y = fma(-h[j].y, x[i].x, yt[j][i].y);
+      }
   }
-  (void)red;
 }
 
 template <typename T, int GEN, int NV, int TR, int TV, int NT>
@@ -65,8 +71,9 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1)
   static_assert((RT / TR) * (NV / TV) == NT, "thread blocking must cover the tile");
   constexpr int LD = KCH + HPAD;
   constexpr int O = KCH * NV;
-  constexpr int P = O >= NT ? 1 : NT / O;
-  constexpr int PER = (O + NT - 1) / NT;
+  constexpr int VT = Dag<T, NV>::VT, CT = Dag<T, NV>::CT, TPP = Dag<T, NV>::TPP;
+  constexpr int P = NT / TPP;
+  static_assert(NT % TPP == 0 && RT % P == 0, "transposed tile must cover the chunk");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* hs = reinterpret_cast<C*>(smem_raw);     // [RT][LD]
   C* xs = hs + RT * LD;                        // [KCH][NV]
@@ -88,9 +95,11 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1)
 
   for (int64_t c0 = it.c_beg; c0 < cend; c0 += KCH) {
     const bool upper = c0 >= R0 + RT;
-    C yt[PER];
+    C yt[CT][VT];
 #pragma unroll
-    for (int k = 0; k < PER; ++k) yt[k] = zc<T>();
+    for (int j = 0; j < CT; ++j)
+#pragma unroll
+      for (int i = 0; i < VT; ++i) yt[j][i] = zc<T>();
     for (int o = 0; o < nop; ++o) {
       const C* x = xc + (int64_t)o * xstride;
       const uint64_t sd = seeds ? seeds[o] : seed;
@@ -114,28 +123,29 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1)
         for (int j = 0; j < TV; ++j) xv[j] = xs[k * NV + tv + j * (NV / TV)];
         tile_cmac<T, TR, TV>(acc, h, xv);
       }
-      if (upper) chunk_dagger<T, NV, NT>(hs, xr, red, yt);
+      if (upper) chunk_dagger<T, NV, NT>(hs, xr, yt);
       __syncthreads();
     }
     if (upper) {
-      // combine the P parts over r, then write the chunk's 32 rows
-      if (P > 1) {
+      // combine the P parts over r in fixed order, then write the chunk's 32 rows
+      {
+        const int q = tid % TPP, pp = tid / TPP;
+        const int cg = q / (NV / VT), vg = q % (NV / VT);
 #pragma unroll
-        for (int k = 0; k < PER; ++k) red[tid] = yt[k];
-        __syncthreads();
-        if (tid < O) {
-          C s = red[tid];
-          for (int q = 1; q < P; ++q) {
-            s.x += red[q * O + tid].x;
-            s.y += red[q * O + tid].y;
-          }
-          part[((ns + it.ti) * dpad + c0) * NV + tid] = s;
-        }
-        __syncthreads();
-      } else {
+        for (int j = 0; j < CT; ++j)
 #pragma unroll
-        for (int k = 0; k < PER; ++k) part[((ns + it.ti) * dpad + c0) * NV + tid + k * NT] = yt[k];
+          for (int i = 0; i < VT; ++i) red[pp * O + (cg + j * (KCH / CT)) * NV + vg + i * (NV / VT)] = yt[j][i];
       }
+      __syncthreads();
+      for (int o = tid; o < O; o += NT) {
+        C sacc = red[o];
+        for (int q2 = 1; q2 < P; ++q2) {
+          sacc.x += red[q2 * O + o].x;
+          sacc.y += red[q2 * O + o].y;
+        }
+        part[((ns + it.ti) * dpad + c0) * NV + o] = sacc;
+      }
+      __syncthreads();
     }
   }
   C* out = part + ((int64_t)it.slot * dpad + R0) * NV;
@@ -149,7 +159,7 @@ template <typename T, int NV>
 constexpr size_t herm_smem_bytes() {
   constexpr int O = KCH * NV;
   constexpr int NT = 256;
-  constexpr int P = O >= NT ? 1 : NT / O;
+  constexpr int P = NT / Dag<T, NV>::TPP;
   return sizeof(typename cplx<T>::t) * ((size_t)RT * (KCH + HPAD) + (size_t)KCH * NV + (size_t)RT * NV + (size_t)P * O) +
          sizeof(T) * (RT + KCH);
 }

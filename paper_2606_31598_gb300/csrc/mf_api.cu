@@ -81,12 +81,14 @@ void release(Plan& p) {
 // The Hermitian-reuse multi-vector path (each canonical entry applied as H
 // and H^dagger) is used for the Philox ensemble and stored blocks with up to
 // 16 vectors while its partial slots (one per owner item and per row tile)
-// take at most 4 GB; otherwise the row-owner path.
+// take at most min(16 GB, 10 % of the memory free at plan creation);
+// otherwise the row-owner path.
 bool use_rows_herm(const Plan& p, int64_t nb) {
   if (!p.d_herm_items || p.gen == MF_GEN_SINC_DVR_HO || p.prec == MF_PREC_BF16X2 || nb > 16) return false;
+  if (p.opt.hermitian_reuse == 0) return false;
   const double bytes = (double)(p.herm_ns + p.ntile) * (double)(p.ntile * kTile) * (double)nb *
                        (double)compute_elem_bytes(p.prec);
-  return bytes <= 4e9;
+  return bytes <= p.herm_limit;
 }
 
 VecShape shape_for(const Plan& p, int64_t nvec) {
@@ -538,6 +540,7 @@ mf_status create_fixed(mf_plan_t* out, int64_t D, int32_t generator, uint64_t se
       return fail(MF_ERR_CUDA);
   }
   if (!p.use_dvr_window && generator != MF_GEN_SINC_DVR_HO && p.prec != MF_PREC_BF16X2) {
+    p.herm_limit = std::min(16e9, 0.1 * (double)mfree);
     const std::vector<HermItem> hi = rows_herm_items(D, p.num_sms, &p.herm_ns);
     p.herm_nitems = (int64_t)hi.size();
     if (cudaMalloc((void**)&p.d_herm_items, hi.size() * sizeof(HermItem)) != cudaSuccess) return fail(MF_ERR_OOM);
@@ -674,6 +677,7 @@ void mf_options_default(mf_options* o) {
   o->dense_work_limit = 1e13;
   o->device = 0;
   o->model = nullptr;
+  o->hermitian_reuse = -1;
 }
 
 const char* mf_status_string(mf_status s) {
@@ -707,6 +711,7 @@ mf_status mf_plan_create(mf_plan_t* out, int64_t D, int64_t M, int32_t generator
   if (!(o.cheb_tol > 0) || o.lanczos_m < 2 || !(o.alpha_safety > 0 && o.alpha_safety <= 1)) return MF_ERR_INVALID;
   if (o.nvec_hint < 1 || o.nvec_hint > 64 || o.autotune_k < 1 || o.autotune_repeats < 1 || o.autotune_warmup < 0)
     return MF_ERR_INVALID;
+  if (o.hermitian_reuse < -1 || o.hermitian_reuse > 1) return MF_ERR_INVALID;
   if ((o.planner_mode == MF_PLANNER_LEARNED || o.planner_mode == MF_PLANNER_HYBRID) && !o.model)
     return MF_ERR_INVALID;
 

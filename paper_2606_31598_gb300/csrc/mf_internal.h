@@ -71,6 +71,7 @@ struct Plan {
   // multi-vector Hermitian-reuse path: column items, owner slots per tile
   HermItem* d_herm_items = nullptr;
   int64_t herm_nitems = 0, herm_ns = 0;
+  double herm_limit = 0.0;  // largest partial-slot buffer (bytes) the path may use
   // DVR launch shape
   int dvr_rows = 512, dvr_cols = 4096;
   // workspace (sized for nvec_cap vectors)

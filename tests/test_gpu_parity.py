@@ -252,6 +252,23 @@ def test_multivector_apply_matches_oracle(mf, gen, prec, nvec):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
+def test_multivector_row_owner_and_hermitian_reuse_agree(mf, prec):
+    """The row-owner kernel (hermitian_reuse = 0) and the Hermitian-reuse
+    kernel give the oracle's product (ragged D, 5 vectors, cached and
+    generated block pairs)."""
+    D, nvec = 1000, 5
+    op = O.make_op(O.GEN_PHILOX_GUE, D, seed=3, form=_form(prec))
+    X = W.random_state(D, nvec, seed=8).reshape(D, nvec)
+    ref = O.apply(op, X)
+    eb = 16 if prec == 0 else 8
+    for reuse in (0, -1):
+        p = _plan(mf, D, 0, prec, seed=3, block=256, budget=3 * eb * 256 * 256, storage=mf.MF_STORE_PARTIAL,
+                  hermitian_reuse=reuse, nvec_hint=nvec)
+        y = _apply(p, X)
+        assert _relerr(y, ref) < (1e-12 if prec == 0 else 2e-5)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
 def test_multivector_cache_modes_bit_identical(mf, prec):
     D, b, nvec = 1000, 256, 8
     eb = 16 if prec == 0 else 8
