@@ -540,7 +540,10 @@ mf_status create_fixed(mf_plan_t* out, int64_t D, int32_t generator, uint64_t se
       return fail(MF_ERR_CUDA);
   }
   if (!p.use_dvr_window && generator != MF_GEN_SINC_DVR_HO && p.prec != MF_PREC_BF16X2) {
-    p.herm_limit = std::min(16e9, 0.1 * (double)mfree);
+    // measured after the cache is allocated, so the slots never crowd it out
+    size_t mfree_now = 0, mtotal_now = 0;
+    if (cudaMemGetInfo(&mfree_now, &mtotal_now) != cudaSuccess) return fail(MF_ERR_CUDA);
+    p.herm_limit = std::min(16e9, 0.1 * (double)mfree_now);
     const std::vector<HermItem> hi = rows_herm_items(D, p.num_sms, &p.herm_ns);
     p.herm_nitems = (int64_t)hi.size();
     if (cudaMalloc((void**)&p.d_herm_items, hi.size() * sizeof(HermItem)) != cudaSuccess) return fail(MF_ERR_OOM);

@@ -40,9 +40,12 @@ void planner_estimate(const mf_problem& pr, const mf_candidate& c, const mf_devi
   //   the contraction itself.
   const double canon = nop * Din * (Din + 1) / 2.0;
   const double frac_cached = e.n_pair > 0 ? (double)pc / (double)e.n_pair : 0.0;
-  const double gen_entries = canon * (1.0 - frac_cached) * (R > 1 ? 2.0 : 1.0);  // row-owner form regenerates
+  // the row-owner form (more than 16 vectors) generates each canonical
+  // entry twice, the Hermitian forms once
+  const double reuse = R > 16 ? 2.0 : 1.0;
+  const double gen_entries = canon * (1.0 - frac_cached) * reuse;
   const double t_gen = dm.gen_entries_per_s > 0 ? gen_entries / dm.gen_entries_per_s : 0.0;
-  const double t_mem = dm.hbm_bytes_per_s > 0 ? canon * frac_cached * Bc * (R > 1 ? 2.0 : 1.0) / dm.hbm_bytes_per_s : 0.0;
+  const double t_mem = dm.hbm_bytes_per_s > 0 ? canon * frac_cached * Bc * reuse / dm.hbm_bytes_per_s : 0.0;
   const double t_mv = dm.flops_per_s > 0 ? e.F_mv / dm.flops_per_s : 0.0;
   e.T_model = std::max(t_gen, std::max(t_mem, t_mv));
   // Pi_mem: a 10 % penalty rising linearly over the last fifth of the
