@@ -43,7 +43,7 @@ __device__ __forceinline__ void proc_tile(typename cplx<T>::t (&yc)[8], const ty
                                           int64_t r0, int64_t c0, int ty, int tx, bool active, uint64_t seed,
                                           T sigma, const dvr_consts& dk) {
   using C = typename cplx<T>::t;
-#pragma unroll 1
+#pragma unroll 2
   for (int a = 0; a < 8; ++a) {
     C yra = czero<T>();
     const int64_t r = r0 + a;
