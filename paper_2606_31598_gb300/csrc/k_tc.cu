@@ -205,7 +205,7 @@ __device__ __forceinline__ void fill_a(unsigned char* A, int64_t R0, int64_t c0,
   const int vr = 8 * g + 2 * (lane & 3), vk = lane >> 2;     // vertical pair origin within a K core
   int64_t slot = -1;
   bool transposed = false;
-  const int64_t n = R0 / b, m = c0 / b;
+  const int64_t n = blk_of(R0, b), m = blk_of(c0, b);
   if (cache || hcache) {
     if (n <= m) slot = slot_of_pair[n * nblk + m];
     else {

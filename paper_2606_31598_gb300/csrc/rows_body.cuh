@@ -25,6 +25,14 @@ template <typename T> __device__ __forceinline__ typename cplx<T>::t zc() {
 }  // namespace rows
 using namespace rows;
 
+// Block index x / b of a row or column (x < 2^31, b a multiple of 128): a
+// shift when b is a power of two (the planner's sizes), else a 32-bit
+// division -- never the long 64-bit division sequence.
+__device__ __forceinline__ int64_t blk_of(int64_t x, int64_t b) {
+  if ((b & (b - 1)) == 0) return x >> (__ffsll((long long)b) - 1);
+  return (int64_t)((uint32_t)x / (uint32_t)b);
+}
+
 // Stored block pair of chunk (R0, c0): the HBM cache slot (>= 0), the host
 // array block -2 - slot (<= -2) or -1 (generated); transposed when the chunk
 // lies below the diagonal and is read from the canonical pair (m, n).
@@ -33,7 +41,7 @@ __device__ __forceinline__ int64_t chunk_slot(int64_t R0, int64_t c0, const void
                                               bool& transposed) {
   transposed = false;
   if (!cache && !hcache) return -1;
-  const int64_t n = R0 / b, m = c0 / b;
+  const int64_t n = blk_of(R0, b), m = blk_of(c0, b);
   if (n <= m) return slot_of_pair[n * nblk + m];
   transposed = true;
   return slot_of_pair[m * nblk + n];
@@ -47,7 +55,7 @@ __device__ __forceinline__ void chunk_load(typename cplx<T>::t (&h)[PER], int64_
                                            int64_t R0, int64_t c0, const typename cplx<T>::t* __restrict__ cache,
                                            const typename cplx<T>::t* __restrict__ hcache, int64_t b) {
   const int tid = threadIdx.x;
-  const int64_t n = R0 / b, m = c0 / b;
+  const int64_t n = blk_of(R0, b), m = blk_of(c0, b);
   const typename cplx<T>::t* blk = slot >= 0 ? cache + slot * b * b : hcache + (-2 - slot) * b * b;
   static_assert(NT % KCH == 0 && NT % RT == 0, "element strides must be whole rows");
   // element e = tid + i NT: (row e / KCH, column e % KCH) advances by whole
@@ -144,7 +152,7 @@ __device__ __forceinline__ void fill_chunk(typename cplx<T>::t* hs, T* win, int6
   // multiple of 128 and chunks are 32-aligned)
   int64_t slot = -1;
   bool transposed = false;
-  int64_t n = R0 / b, m = c0 / b;
+  int64_t n = blk_of(R0, b), m = blk_of(c0, b);
   if (cache || hcache) {
     if (n <= m) {
       slot = slot_of_pair[n * nblk + m];
@@ -312,7 +320,7 @@ __device__ __forceinline__ void chunk_copy_async(typename cplx<T>::t* hb, int64_
   using C = typename cplx<T>::t;
   constexpr int LD = KCH + HPAD;
   const int tid = threadIdx.x;
-  const int64_t n = R0 / b, m = c0 / b;
+  const int64_t n = blk_of(R0, b), m = blk_of(c0, b);
   const C* blk = slot >= 0 ? cache + slot * b * b : hcache + (-2 - slot) * b * b;
   static_assert(NT % KCH == 0 && NT % RT == 0, "element strides must be whole rows");
   if (!transposed) {
