@@ -51,6 +51,7 @@ cudaError_t launch_to_compute(const Plan& p, const double2* x, void* xc, int64_t
 template <typename C>
 __device__ __forceinline__ double2 slot_sum(const C* __restrict__ part, int64_t nslot, int64_t stride, int64_t idx) {
   double sr = 0.0, si = 0.0;
+#pragma unroll 4
   for (int64_t s = 0; s < nslot; ++s) {
     const C v = part[s * stride + idx];
     sr += (double)v.x;
@@ -143,8 +144,10 @@ __global__ void k_cheb_update(const C* __restrict__ part, VecShape sh, int64_t n
   // real time: a_j = 2 (-i)^j J_j; imaginary time: a_j = 2 (-1)^j e^{-z} I_j
   const double aj = (imag_time && (j & 1)) ? -2.0 * J[j] : 2.0 * J[j];
   const int64_t stride = sh.dpad * sh.nb;
+  const double rinv = 1.0 / R;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t row = e / sh.nv, v = e % sh.nv;
+    // one vector needs no index division
+    const int64_t row = sh.nv == 1 ? e : e / sh.nv, v = sh.nv == 1 ? 0 : e - row * sh.nv;
     const int64_t ci = row * sh.nb + v;
     double2 y = slot_sum(part, sh.nslot, stride, ci);
     const double2 q = qcur[e];
@@ -154,7 +157,7 @@ __global__ void k_cheb_update(const C* __restrict__ part, VecShape sh, int64_t n
       y.y = fma(V, q.y, y.y);
     }
     if (hs) add_system_term(y, qcur, row, v, sh.nv, hs);
-    double tr = (y.x - c * q.x) / R, ti = (y.y - c * q.y) / R;
+    double tr = (y.x - c * q.x) * rinv, ti = (y.y - c * q.y) * rinv;
     if (j > 1) {
       const double2 qp = qprev[e];
       tr = 2.0 * tr - qp.x;
