@@ -881,6 +881,7 @@ mf_status mf_external_create(mf_plan_t* out, int64_t D, int64_t block, const voi
     return MF_ERR_INVALID;
   if (!(o.cheb_tol > 0) || o.lanczos_m < 2 || !(o.alpha_safety > 0 && o.alpha_safety <= 1)) return MF_ERR_INVALID;
   if (o.nvec_hint < 1 || o.nvec_hint > 64) return MF_ERR_INVALID;
+  if (o.hermitian_reuse < -1 || o.hermitian_reuse > 1) return MF_ERR_INVALID;
   // block larger than D rounded to the tile: the stored blocks would be
   // smaller than b x b
   if (block > (D + kTile - 1) / kTile * kTile) return MF_ERR_INVALID;
@@ -902,6 +903,7 @@ mf_status mf_sysbath_create(mf_plan_t* out, int64_t d_S, int64_t d_B, int32_t n_
   if (o.precision == MF_PREC_BF16X2) return MF_ERR_UNSUPPORTED;
   if (o.precision != MF_PREC_FP64 && o.precision != MF_PREC_FP32) return MF_ERR_INVALID;
   if (!(o.cheb_tol > 0) || o.lanczos_m < 2 || !(o.alpha_safety > 0 && o.alpha_safety <= 1)) return MF_ERR_INVALID;
+  if (o.hermitian_reuse < -1 || o.hermitian_reuse > 1) return MF_ERR_INVALID;
   // the bath operators are generated on demand (procedural storage)
   o.storage = MF_STORE_PROCEDURAL;
   o.planner_mode = MF_PLANNER_ANALYTIC;
