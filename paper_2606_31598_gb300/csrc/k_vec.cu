@@ -136,6 +136,39 @@ cudaError_t launch_cheb_init(const Plan& p, const double2* psi, double2* q, doub
 // y = H q_k (slot sum + potential); t = (y - c q_k)/R;
 // q_{k+1} = t (k+1 == 1) or 2t - q_{k-1}; acc += a_{k+1} q_{k+1} with
 // a_j = 2 (-i)^j J_j; q_{k+1} overwrites q_{k-1} and its compute copy xc.
+// y = H q_k at element e (partial sums, potential and system term already
+// added), q = q_k[e]: t = (y - c q) / R as (y - c q) * (1 / R);
+// q_{k+1} = t (j == 1) or 2 t - q_{k-1}, written over q_{k-1}; acc += a_j
+// (-i)^j q_{k+1} (real time) or a_j q_{k+1} (imaginary time); the
+// compute-precision copy of q_{k+1} goes to xc[ci].
+template <typename C>
+__device__ __forceinline__ void cheb_term_finish(double2 y, double2 q, int64_t e, int64_t ci, int32_t j, double c,
+                                                 double rinv, double aj, int imag_time, double2* __restrict__ qprev,
+                                                 double2* __restrict__ acc, C* __restrict__ xc) {
+  double tr = (y.x - c * q.x) * rinv, ti = (y.y - c * q.y) * rinv;
+  if (j > 1) {
+    const double2 qp = qprev[e];
+    tr = 2.0 * tr - qp.x;
+    ti = 2.0 * ti - qp.y;
+  }
+  qprev[e] = make_double2(tr, ti);
+  double rr, ri;
+  switch (imag_time ? 0 : (j & 3)) {
+    case 0: rr = tr; ri = ti; break;
+    case 1: rr = ti; ri = -tr; break;
+    case 2: rr = -tr; ri = -ti; break;
+    default: rr = -ti; ri = tr; break;
+  }
+  double2 a = acc[e];
+  a.x = fma(aj, rr, a.x);
+  a.y = fma(aj, ri, a.y);
+  acc[e] = a;
+  C o;
+  o.x = (decltype(o.x))tr;
+  o.y = (decltype(o.y))ti;
+  xc[ci] = o;
+}
+
 template <typename C>
 __global__ void k_cheb_update(const C* __restrict__ part, VecShape sh, int64_t n, int dvr, dvr_consts dk,
                               const double2* __restrict__ qcur, double2* __restrict__ qprev,
@@ -157,29 +190,7 @@ __global__ void k_cheb_update(const C* __restrict__ part, VecShape sh, int64_t n
       y.y = fma(V, q.y, y.y);
     }
     if (hs) add_system_term(y, qcur, row, v, sh.nv, hs);
-    double tr = (y.x - c * q.x) * rinv, ti = (y.y - c * q.y) * rinv;
-    if (j > 1) {
-      const double2 qp = qprev[e];
-      tr = 2.0 * tr - qp.x;
-      ti = 2.0 * ti - qp.y;
-    }
-    qprev[e] = make_double2(tr, ti);
-    // (-i)^j rotation (real time only), then scale by a_j
-    double rr, ri;
-    switch (imag_time ? 0 : (j & 3)) {
-      case 0: rr = tr; ri = ti; break;
-      case 1: rr = ti; ri = -tr; break;
-      case 2: rr = -tr; ri = -ti; break;
-      default: rr = -ti; ri = tr; break;
-    }
-    double2 a = acc[e];
-    a.x = fma(aj, rr, a.x);
-    a.y = fma(aj, ri, a.y);
-    acc[e] = a;
-    C o;
-    o.x = (decltype(o.x))tr;
-    o.y = (decltype(o.y))ti;
-    xc[ci] = o;
+    cheb_term_finish<C>(y, q, e, ci, j, c, rinv, aj, imag_time, qprev, acc, xc);
   }
 }
 

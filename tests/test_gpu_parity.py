@@ -310,3 +310,29 @@ def test_generator_division_and_sqrt_exact_on_this_gpu(mf):
     """The FP32 generator's Markstein-corrected division and square root equal
     IEEE round-to-nearest on every float of their input ranges."""
     assert mf.mf_selfcheck_generator() == (0, 0)
+
+
+@pytest.mark.parametrize("imag", [False, True])
+def test_dvr_fp32_chebyshev_terms_against_oracle(mf, imag):
+    """One-vector FP32 DVR plans run every Chebyshev term as one fused
+    launch (product, then each row tile's update by the CTA that completes
+    it).  D = 10000 spans three 4096-row tiles with a ragged last one; the
+    oracle runs the same recurrence on the same FP32-form entries in FP64."""
+    D = 10000
+    p = _plan(mf, D, mf.MF_GEN_SINC_DVR_HO, 1)
+    emin, emax = p.bounds()
+    c, R = 0.5 * (emax + emin), 0.5 * (emax - emin)
+    op = O.make_op(O.GEN_SINC_DVR_HO, D, form=O.FORM_FP32)
+    psi = W.wavepacket(D)
+    d = _dev(psi)
+    if imag:
+        tau, nt = 2e-4, 24
+        p.cheb_filter(d, 1, tau, nt, True)
+        ref = O.cheb_imag_step(op, psi, tau, c, R, nt, normalize=True)
+    else:
+        dt, nt = 1e-4, 24
+        p.cheb_propagate(d, 1, dt, nt)
+        ref = O.cheb_step(op, psi, dt, c, R, nt)
+    torch.cuda.synchronize()
+    out = d.cpu().numpy()
+    assert np.max(np.abs(out - ref)) < 2e-5 * np.max(np.abs(ref))
