@@ -151,21 +151,21 @@ __device__ __forceinline__ void tmem_load<32>(uint32_t taddr, float* v) {
 }
 
 // Split two complex entries into bf16 hi + lo of their real and imaginary
-// parts; plane p of the pair is word[p] (lower address = first entry).
+// parts; plane p of the pair is word[p] (lower address = first entry).  The
+// two entries go through the packed conversions (each lane rounded to
+// nearest like the scalar conversion) and the packed FP32 subtraction.
+__device__ __forceinline__ uint32_t bf2_bits(__nv_bfloat162 v) { return *reinterpret_cast<uint32_t*>(&v); }
+
 __device__ __forceinline__ void split_pair(float2 h0, float2 h1, uint32_t* w) {
-  const __nv_bfloat16 a_rh = __float2bfloat16_rn(h0.x), b_rh = __float2bfloat16_rn(h1.x);
-  const __nv_bfloat16 a_ih = __float2bfloat16_rn(h0.y), b_ih = __float2bfloat16_rn(h1.y);
-  const __nv_bfloat16 a_rl = __float2bfloat16_rn(h0.x - __bfloat162float(a_rh));
-  const __nv_bfloat16 b_rl = __float2bfloat16_rn(h1.x - __bfloat162float(b_rh));
-  const __nv_bfloat16 a_il = __float2bfloat16_rn(h0.y - __bfloat162float(a_ih));
-  const __nv_bfloat16 b_il = __float2bfloat16_rn(h1.y - __bfloat162float(b_ih));
-  auto pk = [](__nv_bfloat16 a, __nv_bfloat16 b) {
-    return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
-  };
-  w[0] = pk(a_rh, b_rh);
-  w[1] = pk(a_rl, b_rl);
-  w[2] = pk(a_ih, b_ih);
-  w[3] = pk(a_il, b_il);
+  const float2 re = make_float2(h0.x, h1.x), im = make_float2(h0.y, h1.y);
+  const __nv_bfloat162 rh = __floats2bfloat162_rn(re.x, re.y), ih = __floats2bfloat162_rn(im.x, im.y);
+  const float2 rhf = __bfloat1622float2(rh), ihf = __bfloat1622float2(ih);
+  const float2 rd = __fadd2_rn(re, make_float2(-rhf.x, -rhf.y));
+  const float2 id = __fadd2_rn(im, make_float2(-ihf.x, -ihf.y));
+  w[0] = bf2_bits(rh);
+  w[1] = bf2_bits(__floats2bfloat162_rn(rd.x, rd.y));
+  w[2] = bf2_bits(ih);
+  w[3] = bf2_bits(__floats2bfloat162_rn(id.x, id.y));
 }
 
 // entries (r, k) and (r, k + 1), k even: one 32-bit store per plane
