@@ -245,8 +245,11 @@ mf_status mf_plan_destroy(mf_plan_t p);
 /*
  * mf_apply -- y = H x for nvec simultaneous vectors (Eq. blockmatvec and
  * Eq. blockmatvecindex: phi^[n] = sum_m H^[n,m] psi^[m], every block pair
- * included, each canonical pair generated or read once and applied as both
- * H^[n,m] and H^[m,n] = (H^[n,m])^dagger).
+ * included).  Up to 16 vectors (and BF16X2 aside) each canonical pair is
+ * generated or read once and applied as both H^[n,m] and H^[m,n] =
+ * (H^[n,m])^dagger; the row-owner kernels used otherwise (more vectors,
+ * opt.hermitian_reuse = 0, the tensor-core form, the DVR) produce each row's
+ * blocks directly.
  *   y, x : device pointers to complex128 [D][nvec]; y must not overlap x.
  *   nvec : number of vectors, 1 <= nvec <= 64.
  * Asynchronous on the plan's stream.  Errors: MF_ERR_INVALID, MF_ERR_CUDA.
