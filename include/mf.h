@@ -54,7 +54,8 @@ typedef enum {
  * variance 1/(2D) per part, real diagonal, H_cr = conj(H_rc) (global indices:
  * partition invariant, Sec. II).  SINC_DVR_HO is "analytic generation": the
  * Colbert-Miller sinc-DVR kinetic energy on x_i = -L + i*2L/(D-1) plus
- * V = x^2/2 (hbar = m = omega = 1). */
+ * V = x^2/2 (hbar = m = omega = 1).  EXTERNAL: canonical blocks stored by the
+ * caller in host memory (mf_external_create; not accepted by mf_plan_create). */
 typedef enum { MF_GEN_PHILOX_GUE = 0, MF_GEN_SINC_DVR_HO = 1, MF_GEN_EXTERNAL = 2 } mf_generator;
 
 /* Entry precision forms.  FP64: entries, products and sums in double.
