@@ -104,6 +104,9 @@ typedef struct {
                               chunk applied as H and H^dagger while its partial slots
                               fit min(16 GB, 10 % of free memory)), 0 = row-owner
                               kernel (every entry generated or read for each use) */
+  int64_t row_begin;       /* row slice [row_begin, row_end) of a row-distributed plan */
+  int64_t row_end;         /* (Sec. IV.H, row-parallel mode); 0, 0 = all rows; see
+                              mf_plan_create */
 } mf_options;
 
 /* Generic planning instance P_mv of Sec. IV.A (Y = A X with A of size
@@ -275,6 +278,39 @@ mf_status mf_cheb_propagate(mf_plan_t p, void* psi, int64_t nvec, double dt, int
 /* Number of Chebyshev terms mf_cheb_propagate would use for dt at the plan's
  * tolerance (computes bounds and coefficients if needed; synchronises). */
 mf_status mf_cheb_terms(mf_plan_t p, double dt, int32_t* nterms);
+
+/*
+ * Row-distributed propagation (the row-parallel mode of Sec. IV.H: GPU j
+ * owns rows R_j and the cached blocks they touch; every term needs all of
+ * q_k, gathered between terms).  A plan created with opt.row_begin/row_end
+ * (row_begin a multiple of 128, row_end a multiple of 128 or D) applies
+ * H[R_j, :]: mf_apply takes x on all D rows and writes y on the plan's rows
+ * only; its cache holds only the canonical pairs with a block row or column
+ * among its rows; it always uses the row-owner kernels (FP64 or FP32 form).
+ * Philox plans need their bounds set (mf_plan_set_bounds, the same on every
+ * rank); the DVR's are analytic.  A real-time step on one rank:
+ *   mf_rows_cheb_begin(p, dt, order, &nt);          coefficients, term count
+ *   mf_rows_cheb_init(p, psi_full, acc, nvec);      acc = a_0 psi on the slice
+ *   q_full = psi_full, q_prev = (unused for j = 1)
+ *   for j = 1 .. nt-1:
+ *     mf_rows_cheb_term(p, j, q_full, q_prev, q_next, acc, nvec);
+ *         y = H q_j on the slice; q_{j+1} = t or 2 t - q_{j-1},
+ *         t = (y - c q_j)/R; q_prev <- q_j, q_next <- q_{j+1} (slice);
+ *         acc += 2 (-i)^j J_j(R dt) q_{j+1}
+ *     q_full <- all-gather of every rank's q_next (the caller's collective)
+ *   mf_rows_cheb_final(p, acc, psi_slice, nvec, dt); psi = e^{-i c dt} acc
+ * psi_full, q_full: device complex128 [D][nvec]; acc, q_prev, q_next,
+ * psi_slice: device complex128 [row_end - row_begin][nvec], owned by the
+ * caller.  mf_cheb_propagate and mf_cheb_filter return MF_ERR_UNSUPPORTED on
+ * such plans.  Errors: MF_ERR_INVALID (also for a plan without a row slice
+ * or before mf_rows_cheb_begin), MF_ERR_UNSUPPORTED (bounds not set on a
+ * Philox slice), MF_ERR_CUDA.
+ */
+mf_status mf_rows_cheb_begin(mf_plan_t p, double dt, int32_t order, int32_t* nterms);
+mf_status mf_rows_cheb_init(mf_plan_t p, const void* psi_full, void* acc_slice, int64_t nvec);
+mf_status mf_rows_cheb_term(mf_plan_t p, int32_t j, const void* q_full, void* q_prev_slice, void* q_next_slice,
+                            void* acc_slice, int64_t nvec);
+mf_status mf_rows_cheb_final(mf_plan_t p, const void* acc_slice, void* psi_slice, int64_t nvec, double dt);
 
 /*
  * mf_cheb_filter -- imaginary-time Chebyshev filter, the thermal-pure-state

@@ -64,6 +64,8 @@ class mf_options(ctypes.Structure):
         ("device", ctypes.c_int32),
         ("model", ctypes.c_void_p),
         ("hermitian_reuse", ctypes.c_int32),
+        ("row_begin", ctypes.c_int64),
+        ("row_end", ctypes.c_int64),
     ]
 
 
@@ -110,6 +112,12 @@ def lib():
         L.mf_sysbath_create.argtypes = [P(vp), i64, i64, i32, vp, vp, vp, d, P(mf_options)]
         L.mf_external_create.argtypes = [P(vp), i64, i64, vp, ctypes.c_size_t, P(mf_options)]
         L.mf_selfcheck_generator.argtypes = [P(i64), P(i64)]
+        L.mf_rows_cheb_begin.argtypes = [vp, d, i32, P(i32)]
+        L.mf_rows_cheb_init.argtypes = [vp, vp, vp, i64]
+        L.mf_rows_cheb_term.argtypes = [vp, i32, vp, vp, vp, vp, i64]
+        L.mf_rows_cheb_final.argtypes = [vp, vp, vp, i64, d]
+        for name in ("mf_rows_cheb_begin", "mf_rows_cheb_init", "mf_rows_cheb_term", "mf_rows_cheb_final"):
+            getattr(L, name).restype = ctypes.c_int
         L.mf_selfcheck_generator.restype = ctypes.c_int
         L.mf_plan_destroy.argtypes = [vp]
         L.mf_apply.argtypes = [vp, vp, vp, i64]
@@ -466,6 +474,8 @@ class Plan:
             setattr(o, k, v)
         self.options = o
         self.D = int(D)
+        self.row_begin = int(o.row_begin)
+        self.row_end = int(o.row_end) if o.row_end else int(D)
         self.handle = mf_plan_create(D, D if M is None else M, generator, seed, block, cache_budget_bytes, o)
 
     @classmethod
@@ -512,6 +522,23 @@ class Plan:
 
     def cheb_terms(self, dt):
         return mf_cheb_terms(self.handle, dt)
+
+    # row-distributed propagation (plan created with row_begin / row_end)
+    def rows_cheb_begin(self, dt, order=0):
+        n = ctypes.c_int32()
+        _check(lib().mf_rows_cheb_begin(self.handle, float(dt), int(order), ctypes.byref(n)), "mf_rows_cheb_begin")
+        return n.value
+
+    def rows_cheb_init(self, psi_full, acc, nvec):
+        _check(lib().mf_rows_cheb_init(self.handle, _ptr(psi_full), _ptr(acc), int(nvec)), "mf_rows_cheb_init")
+
+    def rows_cheb_term(self, j, q_full, q_prev, q_next, acc, nvec):
+        _check(lib().mf_rows_cheb_term(self.handle, int(j), _ptr(q_full), _ptr(q_prev), _ptr(q_next), _ptr(acc),
+                                       int(nvec)), "mf_rows_cheb_term")
+
+    def rows_cheb_final(self, acc, psi_slice, nvec, dt):
+        _check(lib().mf_rows_cheb_final(self.handle, _ptr(acc), _ptr(psi_slice), int(nvec), float(dt)),
+               "mf_rows_cheb_final")
 
     def cheb_filter(self, psi, nvec, tau, order=0, normalize=True):
         return mf_cheb_filter(self.handle, psi, nvec, tau, order, normalize)

@@ -274,6 +274,7 @@ mf_status mf_batch_create(mf_batch_t* out, int32_t nprob, const int64_t* D, cons
     oi.nvec_hint = nvec[i];
     oi.stream = b->own;
     oi.hermitian_reuse = 0;  // the batched kernel writes one row-owner slot per row
+    oi.row_begin = oi.row_end = 0;
     const double share = cache_budget_bytes == 0 ? 0.0
                          : std::min((double)cache_budget_bytes, 1e18) * (eb * (double)D[i] * D[i] / 2.0) / total_full;
     mf_plan_t p = nullptr;

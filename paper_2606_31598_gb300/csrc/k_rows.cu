@@ -24,13 +24,16 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) rows_simt(int64_t D, in
                                                 typename cplx<T>::t* __restrict__ part,
                                                 const typename cplx<T>::t* __restrict__ cache,
                                                 const int64_t* __restrict__ slot_of_pair, int64_t b, int64_t nblk,
-                                                const typename cplx<T>::t* __restrict__ hcache) {
+                                                const typename cplx<T>::t* __restrict__ hcache, int64_t tile0) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int64_t R0 = (int64_t)blockIdx.x * RT;
+  // tile0: first row tile of a row-distributed plan (0 otherwise); the
+  // partial slots hold the plan's rows only
+  const int64_t R0 = (tile0 + (int64_t)blockIdx.x) * RT;
   const int64_t cbeg = (int64_t)blockIdx.y * ksplit_cols;
   const int64_t cend = cbeg + ksplit_cols < D ? cbeg + ksplit_cols : D;
   row_tile<T, GEN, NV, TR, TV, NT>(smem_raw, R0, cbeg, cend, D, seed, sigma, dk, xc,
-                                   part + ((int64_t)blockIdx.y * dpad + R0) * NV, cache, slot_of_pair, b, nblk, hcache);
+                                   part + ((int64_t)blockIdx.y * dpad + R0 - tile0 * RT) * NV, cache, slot_of_pair, b,
+                                   nblk, hcache);
 }
 
 template <typename T, int GEN, int NV, int TR, int TV, int NT>
@@ -40,11 +43,12 @@ static cudaError_t launch_rows_t(const Plan& p, const void* xc, void* part) {
   auto k = rows_simt<T, GEN, NV, TR, TV, NT>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  dim3 grid((unsigned)p.ntile, (unsigned)p.rows_nsplit);
+  const int64_t ntiles = p.sliced ? p.slice_nt : p.ntile;
+  dim3 grid((unsigned)ntiles, (unsigned)p.rows_nsplit);
   const T sigma = sizeof(T) == 4 ? (T)p.sigma32 : (T)p.sigma64;
-  k<<<grid, NT, sm, p.stream>>>(p.D, p.ntile * (int64_t)kTile, p.rows_split_cols, p.seed, sigma, p.dvr,
+  k<<<grid, NT, sm, p.stream>>>(p.D, ntiles * (int64_t)kTile, p.rows_split_cols, p.seed, sigma, p.dvr,
                                 (const C*)xc, (C*)part, (const C*)p.d_cache, p.d_pair_slot, p.b, p.nblk,
-                                (const C*)p.d_hblocks);
+                                (const C*)p.d_hblocks, p.sliced ? p.slice_t0 : 0);
   return cudaGetLastError();
 }
 

@@ -72,16 +72,19 @@ __device__ __forceinline__ void add_system_term(double2& s, const double2* __res
   }
 }
 
+// row0: first output row of a row-distributed plan (0 otherwise); y and the
+// slots hold the plan's rows, x all of them.
 template <typename C>
 __global__ void k_reduce(const C* __restrict__ part, VecShape sh, int64_t n, int dvr, dvr_consts dk,
-                         const double2* __restrict__ x, double2* __restrict__ y, const double2* __restrict__ hs) {
+                         const double2* __restrict__ x, double2* __restrict__ y, const double2* __restrict__ hs,
+                         int64_t row0) {
   const int64_t stride = sh.dpad * sh.nb;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t row = e / sh.nv, v = e % sh.nv;
     double2 s = slot_sum(part, sh.nslot, stride, row * sh.nb + v);
     if (dvr) {
-      const double V = dvr_V(dk, row);
-      const double2 xv = x[e];
+      const double V = dvr_V(dk, row0 + row);
+      const double2 xv = x[e + row0 * sh.nv];
       s.x = fma(V, xv.x, s.x);
       s.y = fma(V, xv.y, s.y);
     }
@@ -91,12 +94,15 @@ __global__ void k_reduce(const C* __restrict__ part, VecShape sh, int64_t n, int
 }
 
 cudaError_t launch_reduce(const Plan& p, const void* part, const double2* x, double2* y, VecShape s) {
-  const int64_t n = p.D * s.nv;
+  const int64_t rows = p.sliced ? p.row1 - p.row0 : p.D, row0 = p.sliced ? p.row0 : 0;
+  const int64_t n = rows * s.nv;
   const int dvr = p.gen == MF_GEN_SINC_DVR_HO;
   if (p.prec == MF_PREC_FP64)
-    k_reduce<double2><<<grid_for(n), 256, 0, p.stream>>>((const double2*)part, s, n, dvr, p.dvr, x, y, p.d_sb_HS);
+    k_reduce<double2><<<grid_for(n), 256, 0, p.stream>>>((const double2*)part, s, n, dvr, p.dvr, x, y, p.d_sb_HS,
+                                                         row0);
   else
-    k_reduce<float2><<<grid_for(n), 256, 0, p.stream>>>((const float2*)part, s, n, dvr, p.dvr, x, y, p.d_sb_HS);
+    k_reduce<float2><<<grid_for(n), 256, 0, p.stream>>>((const float2*)part, s, n, dvr, p.dvr, x, y, p.d_sb_HS,
+                                                        row0);
   return cudaGetLastError();
 }
 
@@ -204,6 +210,62 @@ cudaError_t launch_cheb_update(const Plan& p, const void* part, const double2* q
   else
     k_cheb_update<float2><<<grid_for(n), 256, 0, p.stream>>>((const float2*)part, s, n, dvr, p.dvr, qcur, qprev,
                                                              acc, (float2*)xc, p.d_J, k_next, c, R, imag_time, p.d_sb_HS);
+  return cudaGetLastError();
+}
+
+// Row-distributed Chebyshev term (row-parallel mode, Sec. IV.H): the plan's
+// slice of one term.  y = H q_j on the plan's rows, q = q_j on all rows (the
+// caller gathers it); t = (y - c q) / R; q_{j+1} = t (j == 1) or 2 t -
+// q_{j-1}; q_prev <- q_j and q_next <- q_{j+1} on the slice (q_next is what
+// the caller gathers for the next term); acc += a_j (-i)^j q_{j+1}.
+__global__ void k_cheb_rows_init(const double2* __restrict__ psi, int64_t off, double2* __restrict__ acc, int64_t n,
+                                 const double* __restrict__ J) {
+  const double a0 = J[0];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const double2 a = psi[off + e];
+    acc[e] = make_double2(a0 * a.x, a0 * a.y);
+  }
+}
+
+__global__ void k_cheb_rows_term(const double2* __restrict__ y, const double2* __restrict__ qfull, int64_t off,
+                                 double2* __restrict__ qprev, double2* __restrict__ qnext, double2* __restrict__ acc,
+                                 int64_t n, const double* __restrict__ J, int32_t j, double c, double rinv) {
+  const double aj = 2.0 * J[j];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const double2 yv = y[e], q = qfull[off + e];
+    double tr = (yv.x - c * q.x) * rinv, ti = (yv.y - c * q.y) * rinv;
+    if (j > 1) {
+      const double2 qp = qprev[e];
+      tr = 2.0 * tr - qp.x;
+      ti = 2.0 * ti - qp.y;
+    }
+    qprev[e] = q;
+    qnext[e] = make_double2(tr, ti);
+    double rr, ri;
+    switch (j & 3) {
+      case 0: rr = tr; ri = ti; break;
+      case 1: rr = ti; ri = -tr; break;
+      case 2: rr = -tr; ri = -ti; break;
+      default: rr = -ti; ri = tr; break;
+    }
+    double2 a = acc[e];
+    a.x = fma(aj, rr, a.x);
+    a.y = fma(aj, ri, a.y);
+    acc[e] = a;
+  }
+}
+
+cudaError_t launch_cheb_rows_init(const Plan& p, const double2* psi, double2* acc, int64_t nvec) {
+  const int64_t n = (p.row1 - p.row0) * nvec;
+  k_cheb_rows_init<<<grid_for(n), 256, 0, p.stream>>>(psi, p.row0 * nvec, acc, n, p.d_J);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cheb_rows_term(const Plan& p, const double2* y, const double2* qfull, double2* qprev,
+                                  double2* qnext, double2* acc, int64_t nvec, int32_t j, double c, double R) {
+  const int64_t n = (p.row1 - p.row0) * nvec;
+  k_cheb_rows_term<<<grid_for(n), 256, 0, p.stream>>>(y, qfull, p.row0 * nvec, qprev, qnext, acc, n, p.d_J, j, c,
+                                                      1.0 / R);
   return cudaGetLastError();
 }
 

@@ -94,6 +94,7 @@ bool use_rows_herm(const Plan& p, int64_t nb) {
 VecShape shape_for(const Plan& p, int64_t nvec) {
   if (p.prec == MF_PREC_BF16X2)
     return VecShape{nvec, tc_nvec_bucket(nvec), p.rows_nsplit, p.ntile * (int64_t)kTile};
+  if (p.sliced) return VecShape{nvec, rows_nvec_bucket(nvec), p.rows_nsplit, p.slice_nt * (int64_t)kTile};
   if (nvec == 1 && !p.sb_nop) return VecShape{1, 1, p.nslot, p.dpad};
   const int64_t nb = rows_nvec_bucket(nvec);
   if (use_rows_herm(p, nb)) return VecShape{nvec, nb, p.herm_ns + p.ntile, p.ntile * (int64_t)kTile};
@@ -155,7 +156,7 @@ mf_status apply_kernel(Plan& p, int64_t nvec) {
     MF_CUDA(cudaEventRecord(p.ev[p.ev_used].first, p.stream));
   }
   const int64_t nbr = rows_nvec_bucket(nvec);
-  const bool herm = (nvec > 1 || p.sb_nop) && p.prec != MF_PREC_BF16X2 && use_rows_herm(p, nbr);
+  const bool herm = !p.sliced && (nvec > 1 || p.sb_nop) && p.prec != MF_PREC_BF16X2 && use_rows_herm(p, nbr);
   if (herm) {
     const VecShape sh = shape_for(p, nvec);
     MF_CUDA(cudaMemsetAsync(p.d_part, 0, (size_t)sh.nslot * sh.dpad * sh.nb * compute_elem_bytes(p.prec), p.stream));
@@ -170,7 +171,7 @@ mf_status apply_kernel(Plan& p, int64_t nvec) {
     MF_CUDA(launch_tc_apply(p, p.d_xc, p.d_part, p.d_tcb, tc_nvec_bucket(nvec)));
   else if (nvec > 1 && herm)
     MF_CUDA(launch_rows_herm(p, p.d_xc, 0, p.d_part, nbr, 1, nullptr));
-  else if (nvec > 1)
+  else if (nvec > 1 || p.sliced)
     MF_CUDA(launch_rows_apply(p, p.d_xc, p.d_part, nbr));
   else if (p.use_dvr_window)
     MF_CUDA(launch_dvr_apply(p, p.d_xc, p.d_part, 1));
@@ -224,6 +225,8 @@ double tridiag_eig(const std::vector<double>& a, const std::vector<double>& b, i
 
 mf_status compute_bounds(Plan& p) {
   if (p.have_bounds) return MF_OK;
+  // a row slice cannot run Lanczos on its own: the caller sets the bounds
+  if (p.sliced && p.gen != MF_GEN_SINC_DVR_HO) return MF_ERR_UNSUPPORTED;
   if (p.gen == MF_GEN_SINC_DVR_HO) {
     // symbol of the sinc-DVR kinetic operator is k^2/2 on |k| <= pi/dx, so
     // 0 <= T <= pi^2/(2 dx^2); 0 <= V <= L^2/2 on the grid.
@@ -375,20 +378,35 @@ mf_status create_fixed(mf_plan_t* out, int64_t D, int32_t generator, uint64_t se
   p.nblk = (D + p.b - 1) / p.b;
   p.npair = p.nblk * (p.nblk + 1) / 2;
   p.ntile = (D + kTile - 1) / kTile;
+  // row-distributed plan: the pairs its rows touch (block row n or block
+  // column m among its blocks) are the ones it may cache
+  p.sliced = o.row_end > 0;
+  int64_t nb0 = 0, nb1 = p.nblk, npair_use = p.npair;
+  if (p.sliced) {
+    p.row0 = o.row_begin;
+    p.row1 = o.row_end;
+    p.slice_t0 = p.row0 / kTile;
+    p.slice_nt = (p.row1 + kTile - 1) / kTile - p.slice_t0;
+    nb0 = p.row0 / p.b;
+    nb1 = (p.row1 + p.b - 1) / p.b;
+    npair_use = 0;
+    for (int64_t n = 0; n < p.nblk; ++n)
+      for (int64_t m = n; m < p.nblk; ++m) npair_use += ((n >= nb0 && n < nb1) || (m >= nb0 && m < nb1)) ? 1 : 0;
+  }
 
   // storage (Sec. III.A, IV.G): P_cache = min(N_pair, floor(M_cache / (B_c b^2)))
   const size_t eb = compute_elem_bytes(p.prec);
   size_t budget = cache_budget_bytes;
   if (budget == SIZE_MAX) budget = (size_t)(o.f_cache * (double)mfree);
   const double blk_bytes = (double)eb * (double)p.b * (double)p.b;
-  int64_t pc = (int64_t)std::min<double>((double)p.npair, std::floor((double)budget / blk_bytes));
+  int64_t pc = (int64_t)std::min<double>((double)npair_use, std::floor((double)budget / blk_bytes));
   int32_t storage = o.storage;
   if (storage == MF_STORE_PROCEDURAL && generator != MF_GEN_EXTERNAL) {
     pc = 0;
   } else if (storage == MF_STORE_FULL) {
-    if (pc < p.npair) return fail(MF_ERR_OOM);
+    if (pc < npair_use) return fail(MF_ERR_OOM);
   }
-  if (pc == p.npair) storage = MF_STORE_FULL;
+  if (pc == npair_use) storage = MF_STORE_FULL;
   else if (generator == MF_GEN_EXTERNAL) storage = MF_STORE_PARTIAL;  // the rest stays in host memory
   else if (pc == 0) storage = MF_STORE_PROCEDURAL;
   p.storage = storage;
@@ -397,7 +415,7 @@ mf_status create_fixed(mf_plan_t* out, int64_t D, int32_t generator, uint64_t se
 
   // memory feasibility (Eq. planner_memory_constraint): M_op + M_work <= alpha M_free
   const int64_t nv = std::max(1, o.nvec_hint);
-  p.use_dvr_window = generator == MF_GEN_SINC_DVR_HO && pc == 0 && p.prec != MF_PREC_BF16X2;
+  p.use_dvr_window = generator == MF_GEN_SINC_DVR_HO && pc == 0 && p.prec != MF_PREC_BF16X2 && !p.sliced;
   if (p.use_dvr_window && p.prec == MF_PREC_FP32) {
     const DvrRowsShape s = dvr_rows_shape(D, p.num_sms);
     p.dvr_rows = (int)s.rows;
@@ -437,9 +455,9 @@ mf_status create_fixed(mf_plan_t* out, int64_t D, int32_t generator, uint64_t se
     // shrink the cache until the plan fits
     const double room = o.alpha_safety * (double)mfree - m_work;
     pc = room > 0 ? (int64_t)std::floor(room / blk_bytes) : 0;
-    pc = std::min(pc, p.npair);
+    pc = std::min(pc, npair_use);
     p.pairs_cached = pc;
-    p.storage = pc == p.npair ? MF_STORE_FULL
+    p.storage = pc == npair_use ? MF_STORE_FULL
                 : (pc == 0 && generator != MF_GEN_EXTERNAL ? MF_STORE_PROCEDURAL : MF_STORE_PARTIAL);
     if (m_work > o.alpha_safety * (double)mfree) return fail(MF_ERR_OOM);
   }
@@ -456,8 +474,9 @@ mf_status create_fixed(mf_plan_t* out, int64_t D, int32_t generator, uint64_t se
   p.pair_slot.assign((size_t)(p.nblk * p.nblk), -1);
   std::vector<int2> pairs;
   for (int64_t n = 0, s = 0; n < p.nblk && s < p.pairs_cached; ++n)
-    for (int64_t m = n; m < p.nblk && s < p.pairs_cached; ++m, ++s) {
-      p.pair_slot[(size_t)(n * p.nblk + m)] = s;
+    for (int64_t m = n; m < p.nblk && s < p.pairs_cached; ++m) {
+      if (!((n >= nb0 && n < nb1) || (m >= nb0 && m < nb1))) continue;
+      p.pair_slot[(size_t)(n * p.nblk + m)] = s++;
       pairs.push_back(make_int2((int)n, (int)m));
     }
   if (generator == MF_GEN_EXTERNAL) {
@@ -506,7 +525,7 @@ mf_status create_fixed(mf_plan_t* out, int64_t D, int32_t generator, uint64_t se
 
   // work list of canonical tiles, cached and procedural items interleaved so
   // HBM streaming and generation overlap on the SMs (Eq. runtime_overlap)
-  if (!p.use_dvr_window) {
+  if (!p.use_dvr_window && !p.sliced) {
     std::vector<WorkItem> cached, proc;
     const int64_t tpb = p.b / kTile;
     for (int64_t ti = 0; ti < p.ntile; ++ti)
@@ -539,7 +558,7 @@ mf_status create_fixed(mf_plan_t* out, int64_t D, int32_t generator, uint64_t se
                         p.stream) != cudaSuccess)
       return fail(MF_ERR_CUDA);
   }
-  if (!p.use_dvr_window && generator != MF_GEN_SINC_DVR_HO && p.prec != MF_PREC_BF16X2) {
+  if (!p.use_dvr_window && !p.sliced && generator != MF_GEN_SINC_DVR_HO && p.prec != MF_PREC_BF16X2) {
     // measured after the cache is allocated, so the slots never crowd it out
     size_t mfree_now = 0, mtotal_now = 0;
     if (cudaMemGetInfo(&mfree_now, &mtotal_now) != cudaSuccess) return fail(MF_ERR_CUDA);
@@ -681,6 +700,8 @@ void mf_options_default(mf_options* o) {
   o->device = 0;
   o->model = nullptr;
   o->hermitian_reuse = -1;
+  o->row_begin = 0;
+  o->row_end = 0;
 }
 
 const char* mf_status_string(mf_status s) {
@@ -717,6 +738,20 @@ mf_status mf_plan_create(mf_plan_t* out, int64_t D, int64_t M, int32_t generator
   if (o.hermitian_reuse < -1 || o.hermitian_reuse > 1) return MF_ERR_INVALID;
   if ((o.planner_mode == MF_PLANNER_LEARNED || o.planner_mode == MF_PLANNER_HYBRID) && !o.model)
     return MF_ERR_INVALID;
+
+  // row-distributed plan: one explicit candidate on the slice's rows
+  if (o.row_begin != 0 || o.row_end != 0) {
+    if (o.row_begin < 0 || o.row_end <= o.row_begin || o.row_end > D || o.row_begin % kTile != 0 ||
+        (o.row_end % kTile != 0 && o.row_end != D))
+      return MF_ERR_INVALID;
+    if (o.precision == MF_PREC_BF16X2) return MF_ERR_UNSUPPORTED;
+    const int64_t Dt = (D + kTile - 1) / kTile * kTile;
+    const int64_t b = block > 0 ? block : std::min<int64_t>(2048, Dt);
+    mf_options os = o;
+    if (os.storage == MF_STORE_AUTO) os.storage = cache_budget_bytes > 0 ? MF_STORE_PARTIAL : MF_STORE_PROCEDURAL;
+    os.planner_mode = MF_PLANNER_ANALYTIC;
+    return create_fixed(out, D, generator, seed, b, cache_budget_bytes, os);
+  }
 
   // one explicit candidate: no planning
   if (block > 0 && o.storage != MF_STORE_AUTO && o.planner_mode == MF_PLANNER_ANALYTIC)
@@ -887,6 +922,7 @@ mf_status mf_external_create(mf_plan_t* out, int64_t D, int64_t block, const voi
   if (block > (D + kTile - 1) / kTile * kTile) return MF_ERR_INVALID;
   // P_cache from the budget (Eq. partial_cache_pairs); STORE_FULL insists
   if (o.storage != MF_STORE_FULL) o.storage = MF_STORE_PARTIAL;
+  o.row_begin = o.row_end = 0;
   o.planner_mode = MF_PLANNER_ANALYTIC;
   return create_fixed(out, D, MF_GEN_EXTERNAL, 0, block, cache_budget_bytes, o, blocks);
 }
@@ -906,6 +942,7 @@ mf_status mf_sysbath_create(mf_plan_t* out, int64_t d_S, int64_t d_B, int32_t n_
   if (o.hermitian_reuse < -1 || o.hermitian_reuse > 1) return MF_ERR_INVALID;
   // the bath operators are generated on demand (procedural storage)
   o.storage = MF_STORE_PROCEDURAL;
+  o.row_begin = o.row_end = 0;
   o.planner_mode = MF_PLANNER_ANALYTIC;
   o.nvec_hint = (int32_t)std::max<int64_t>(2, d_S);
   const int64_t Dt = (d_B + kTile - 1) / kTile * kTile;
@@ -958,9 +995,11 @@ mf_status mf_apply(mf_plan_t h, void* y, const void* x, int64_t nvec) {
   if (!h || !y || !x || nvec < 1 || nvec > 64) return MF_ERR_INVALID;
   Plan& p = h->p;
   if (p.sb_nop && nvec != p.sb_dS) return MF_ERR_INVALID;
-  const size_t bytes = (size_t)p.D * (size_t)nvec * sizeof(double2);
+  // x holds all rows; y the plan's rows (a slice for a row-distributed plan)
+  const size_t xbytes = (size_t)p.D * (size_t)nvec * sizeof(double2);
+  const size_t ybytes = (size_t)(p.sliced ? p.row1 - p.row0 : p.D) * (size_t)nvec * sizeof(double2);
   const char *yb = (const char*)y, *xb = (const char*)x;
-  if (yb < xb + bytes && xb < yb + bytes) return MF_ERR_INVALID;
+  if (yb < xb + xbytes && xb < yb + ybytes) return MF_ERR_INVALID;
   DeviceGuard guard(p.device);
   return apply_internal(p, (double2*)y, (const double2*)x, nvec);
 }
@@ -998,6 +1037,7 @@ mf_status mf_cheb_propagate(mf_plan_t h, void* psi, int64_t nvec, double dt, int
   if (!h || !psi || nvec < 1 || nvec > 64 || !(dt > 0) || !std::isfinite(dt) || order < 0) return MF_ERR_INVALID;
   Plan& p = h->p;
   if (p.sb_nop && nvec != p.sb_dS) return MF_ERR_INVALID;
+  if (p.sliced) return MF_ERR_UNSUPPORTED;  // row groups use mf_rows_cheb_*
   DeviceGuard guard(p.device);
   mf_status st = compute_bounds(p);
   if (st != MF_OK) return st;
@@ -1021,6 +1061,54 @@ mf_status mf_cheb_propagate(mf_plan_t h, void* psi, int64_t nvec, double dt, int
   return MF_OK;
 }
 
+mf_status mf_rows_cheb_begin(mf_plan_t h, double dt, int32_t order, int32_t* nterms) {
+  if (!h || !nterms || !(dt > 0) || !std::isfinite(dt) || order < 0) return MF_ERR_INVALID;
+  Plan& p = h->p;
+  if (!p.sliced) return MF_ERR_INVALID;
+  DeviceGuard guard(p.device);
+  mf_status st = compute_bounds(p);
+  if (st != MF_OK) return st;
+  const double R = 0.5 * (p.emax - p.emin);
+  return coefficients(p, R * dt, order, nterms, 0);
+}
+
+mf_status mf_rows_cheb_init(mf_plan_t h, const void* psi_full, void* acc_slice, int64_t nvec) {
+  if (!h || !psi_full || !acc_slice || nvec < 1 || nvec > 64) return MF_ERR_INVALID;
+  Plan& p = h->p;
+  if (!p.sliced || p.J_arg < 0) return MF_ERR_INVALID;
+  DeviceGuard guard(p.device);
+  MF_CUDA(launch_cheb_rows_init(p, (const double2*)psi_full, (double2*)acc_slice, nvec));
+  return MF_OK;
+}
+
+mf_status mf_rows_cheb_term(mf_plan_t h, int32_t j, const void* q_full, void* q_prev_slice, void* q_next_slice,
+                            void* acc_slice, int64_t nvec) {
+  if (!h || !q_full || !q_prev_slice || !q_next_slice || !acc_slice || nvec < 1 || nvec > 64 || j < 1)
+    return MF_ERR_INVALID;
+  Plan& p = h->p;
+  if (!p.sliced || p.J_arg < 0 || j > p.J_K) return MF_ERR_INVALID;
+  DeviceGuard guard(p.device);
+  mf_status st = ensure_workspace(p, nvec);
+  if (st != MF_OK) return st;
+  // y = H q_j on the slice, into the plan's own vector workspace
+  double2* y = p.d_q[2];
+  if ((st = apply_internal(p, y, (const double2*)q_full, nvec)) != MF_OK) return st;
+  const double c = 0.5 * (p.emax + p.emin), R = 0.5 * (p.emax - p.emin);
+  MF_CUDA(launch_cheb_rows_term(p, y, (const double2*)q_full, (double2*)q_prev_slice, (double2*)q_next_slice,
+                                (double2*)acc_slice, nvec, j, c, R));
+  return MF_OK;
+}
+
+mf_status mf_rows_cheb_final(mf_plan_t h, const void* acc_slice, void* psi_slice, int64_t nvec, double dt) {
+  if (!h || !acc_slice || !psi_slice || nvec < 1 || nvec > 64 || !std::isfinite(dt)) return MF_ERR_INVALID;
+  Plan& p = h->p;
+  if (!p.sliced || !p.have_bounds) return MF_ERR_INVALID;
+  DeviceGuard guard(p.device);
+  const double c = 0.5 * (p.emax + p.emin);
+  MF_CUDA(launch_cheb_final(p, (const double2*)acc_slice, (double2*)psi_slice, (p.row1 - p.row0) * nvec, c, dt));
+  return MF_OK;
+}
+
 mf_status mf_cheb_filter_terms(mf_plan_t h, double tau, int32_t* nterms) {
   if (!h || !nterms || !(tau >= 0) || !std::isfinite(tau)) return MF_ERR_INVALID;
   Plan& p = h->p;
@@ -1039,6 +1127,7 @@ mf_status mf_cheb_filter(mf_plan_t h, void* psi, int64_t nvec, double tau, int32
   if (!h || !psi || nvec < 1 || nvec > 64 || !(tau >= 0) || !std::isfinite(tau) || order < 0) return MF_ERR_INVALID;
   Plan& p = h->p;
   if (p.sb_nop && nvec != p.sb_dS) return MF_ERR_INVALID;
+  if (p.sliced) return MF_ERR_UNSUPPORTED;
   DeviceGuard guard(p.device);
   mf_status st = compute_bounds(p);
   if (st != MF_OK) return st;

@@ -72,6 +72,10 @@ struct Plan {
   HermItem* d_herm_items = nullptr;
   int64_t herm_nitems = 0, herm_ns = 0;
   double herm_limit = 0.0;  // largest partial-slot buffer (bytes) the path may use
+  // row-distributed plan: output rows [row0, row1), row tiles slice_t0 ..
+  // slice_t0 + slice_nt - 1 (row-owner kernels only)
+  bool sliced = false;
+  int64_t row0 = 0, row1 = 0, slice_t0 = 0, slice_nt = 0;
   // DVR launch shape
   int dvr_rows = 512, dvr_cols = 4096;
   // workspace (sized for nvec_cap vectors)
@@ -171,6 +175,10 @@ cudaError_t launch_cheb_update(const Plan& p, const void* part, const double2* q
                                int imag_time);
 cudaError_t launch_cheb_final(const Plan& p, const double2* acc, double2* psi, int64_t n, double c, double dt);
 cudaError_t launch_bessel(const Plan& p, double z, int32_t K, double* J);
+// Row-distributed Chebyshev pieces (slice of the plan's rows, see k_vec.cu).
+cudaError_t launch_cheb_rows_init(const Plan& p, const double2* psi, double2* acc, int64_t nvec);
+cudaError_t launch_cheb_rows_term(const Plan& p, const double2* y, const double2* qfull, double2* qprev,
+                                  double2* qnext, double2* acc, int64_t nvec, int32_t j, double c, double R);
 // Imaginary-time filter pieces: scaled I_k(z) and the final copy with optional
 // per-column renormalisation (reduction scratch in d_red: 64*64 + 64 doubles).
 cudaError_t launch_bessel_i(const Plan& p, double z, int32_t K, double* I);
