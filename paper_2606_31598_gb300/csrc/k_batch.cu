@@ -70,9 +70,17 @@ __global__ void __launch_bounds__(256) k_batch_apply(const BatchItem* __restrict
         row_tile_async<T, GEN, 4, 1, 2, 256>(smem_raw, R0, 0, P.D, P.seed, sigma, P.dk, xc, (C*)P.part + R0 * 4,
                                              cache, P.slot, P.b, P.nblk);
         break;
+      case 6:
+        row_tile_async<T, GEN, 6, 1, 3, 256>(smem_raw, R0, 0, P.D, P.seed, sigma, P.dk, xc, (C*)P.part + R0 * 6,
+                                             cache, P.slot, P.b, P.nblk);
+        break;
       case 8:
         row_tile_async<T, GEN, 8, 2, 2, 256>(smem_raw, R0, 0, P.D, P.seed, sigma, P.dk, xc, (C*)P.part + R0 * 8,
                                              cache, P.slot, P.b, P.nblk);
+        break;
+      case 12:
+        row_tile_async<T, GEN, 12, 2, 3, 256>(smem_raw, R0, 0, P.D, P.seed, sigma, P.dk, xc, (C*)P.part + R0 * 12,
+                                              cache, P.slot, P.b, P.nblk);
         break;
       default:
         row_tile_async<T, GEN, 16, 2, 4, 256>(smem_raw, R0, 0, P.D, P.seed, sigma, P.dk, xc, (C*)P.part + R0 * 16,

@@ -58,7 +58,9 @@ static cudaError_t launch_rows_g(const Plan& p, const void* xc, void* part, int6
   switch (nvec) {
     case 2: return launch_rows_t<T, GEN, 2, 1, 1, 256>(p, xc, part);
     case 4: return launch_rows_t<T, GEN, 4, 1, 2, 256>(p, xc, part);
+    case 6: return launch_rows_t<T, GEN, 6, 1, 3, 256>(p, xc, part);
     case 8: return launch_rows_t<T, GEN, 8, 2, 2, 256>(p, xc, part);
+    case 12: return launch_rows_t<T, GEN, 12, 2, 3, 256>(p, xc, part);
     case 16: return launch_rows_t<T, GEN, 16, 2, 4, 256>(p, xc, part);
     case 32: return launch_rows_t<T, GEN, 32, 4, 4, 256>(p, xc, part);
     case 64:
@@ -68,12 +70,13 @@ static cudaError_t launch_rows_g(const Plan& p, const void* xc, void* part, int6
   return cudaErrorNotSupported;
 }
 
-// Vector counts the row kernels are compiled for; other counts are padded up
-// by the caller to the next one.
+// Vector counts the row kernels are compiled for (2, 4, 6, 8, 12, 16, 32,
+// 64); other counts are padded up by the caller to the next one.
 int64_t rows_nvec_bucket(int64_t nvec) {
-  int64_t b = 2;
-  while (b < nvec) b *= 2;
-  return b;
+  static const int64_t kB[] = {2, 4, 6, 8, 12, 16, 32, 64};
+  for (int64_t b : kB)
+    if (nvec <= b) return b;
+  return 64;
 }
 
 cudaError_t launch_rows_apply(const Plan& p, const void* xc, void* part, int64_t nvec_bucket) {

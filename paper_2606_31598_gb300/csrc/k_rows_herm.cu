@@ -1,6 +1,7 @@
 // k_rows_herm.cu -- multi-vector generate-and-apply with Hermitian reuse.
 //
-// Y = H X for 2..16 vectors (Sec. IV.A, Eq. generic_multivector), each
+// Y = H X for 2..16 vectors (compiled for 2, 4, 6, 8, 12, 16; Sec. IV.A,
+// Eq. generic_multivector), each
 // canonical entry generated (or read from the block cache) once and applied
 // twice, as H^[n,m] and as H^[m,n] = (H^[n,m])^dagger (Sec. III.A).  A CTA
 // owns a 128-row tile ti and a range of columns c >= 128 ti (the upper part
@@ -27,7 +28,7 @@ namespace {
 // columns x VT vectors over the rows of part p (register tile: each staged
 // value read once per CT or VT products); the P parts are combined later.
 template <typename T, int NV> struct Dag {
-  static constexpr int VT = NV < 4 ? NV : 4;                         // vectors per thread
+  static constexpr int VT = NV % 3 == 0 ? 3 : (NV < 4 ? NV : 4);     // vectors per thread
   static constexpr int CT = (NV == 16 && sizeof(T) == 4) ? 4 : 2;    // columns per thread
   static constexpr int TPP = (KCH / CT) * (NV / VT);                 // threads per part
 };
@@ -186,7 +187,9 @@ cudaError_t launch_g(const Plan& p, const void* xc, int64_t xstride, void* part,
   switch (nb) {
     case 2: return launch_t<T, G, 2, 1, 1, 256>(p, xc, xstride, part, nop, seeds);
     case 4: return launch_t<T, G, 4, 1, 2, 256>(p, xc, xstride, part, nop, seeds);
+    case 6: return launch_t<T, G, 6, 1, 3, 256>(p, xc, xstride, part, nop, seeds);
     case 8: return launch_t<T, G, 8, 2, 2, 256>(p, xc, xstride, part, nop, seeds);
+    case 12: return launch_t<T, G, 12, 2, 3, 256>(p, xc, xstride, part, nop, seeds);
     case 16: return launch_t<T, G, 16, 2, 4, 256>(p, xc, xstride, part, nop, seeds);
   }
   return cudaErrorNotSupported;

@@ -141,7 +141,9 @@ static cudaError_t launch_sb_g(const Plan& p, const void* xo, int64_t ostride, v
   switch (nb) {
     case 2: return launch_sb_t<T, 2, 1, 1, 256>(p, xo, ostride, part);
     case 4: return launch_sb_t<T, 4, 1, 2, 256>(p, xo, ostride, part);
+    case 6: return launch_sb_t<T, 6, 1, 3, 256>(p, xo, ostride, part);
     case 8: return launch_sb_t<T, 8, 2, 2, 256>(p, xo, ostride, part);
+    case 12: return launch_sb_t<T, 12, 2, 3, 256>(p, xo, ostride, part);
     case 16: return launch_sb_t<T, 16, 2, 4, 256>(p, xo, ostride, part);
     case 32: return launch_sb_t<T, 32, 4, 4, 256>(p, xo, ostride, part);
     case 64:
