@@ -109,14 +109,12 @@ mf_status ensure_workspace(Plan& p, int64_t nvec) {
   free_dev(p.d_tcb);
   for (auto& q : p.d_q) free_dev(q);
   const size_t eb = compute_elem_bytes(p.prec);
-  const VecShape one = shape_for(p, 1);
-  size_t part_bytes = (size_t)one.nslot * (size_t)one.dpad * eb;
-  size_t rows = (size_t)std::max(one.dpad, p.D);
-  size_t xc_bytes = rows * eb;
-  if (nvec > 1 || p.prec == MF_PREC_BF16X2 || p.sb_nop) {
-    const VecShape m = shape_for(p, nvec);
-    part_bytes = std::max(part_bytes, (size_t)m.nslot * (size_t)m.dpad * (size_t)m.nb * eb);
-    xc_bytes = std::max(xc_bytes, (size_t)std::max<int64_t>(m.dpad, p.D) * (size_t)m.nb * eb);
+  // the larger of the one-vector shape and the nvec shape, each with its
+  // padded vector count (a row slice pads even one vector to two)
+  size_t part_bytes = 0, xc_bytes = 0;
+  for (const VecShape& s : {shape_for(p, 1), shape_for(p, nvec)}) {
+    part_bytes = std::max(part_bytes, (size_t)s.nslot * (size_t)s.dpad * (size_t)s.nb * eb);
+    xc_bytes = std::max(xc_bytes, (size_t)std::max<int64_t>(s.dpad, p.D) * (size_t)s.nb * eb);
   }
   MF_CUDA(cudaMalloc(&p.d_part, part_bytes));
   MF_CUDA(cudaMalloc(&p.d_xc, xc_bytes));
