@@ -44,7 +44,7 @@ struct BatchItem {
 namespace {
 
 template <typename T, int GEN>
-__global__ void __launch_bounds__(256) k_batch_apply(const BatchItem* __restrict__ items, int n_items,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_batch_apply(const BatchItem* __restrict__ items, int n_items,
                                                      const BatchProb* __restrict__ probs, int* __restrict__ counter) {
   using C = typename cplx<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];

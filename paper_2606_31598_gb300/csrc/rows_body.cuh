@@ -220,6 +220,31 @@ __device__ __forceinline__ void tile_cmac(typename cplx<T>::t (&acc)[TR][TV], co
     }
 }
 
+// acc[i][j] += h[i] x[j] for real h (the sinc-DVR kinetic entries, whose
+// imaginary parts are exactly zero whether generated or read from the cache):
+// two fused operations per product instead of four.
+template <typename T, int TR, int TV>
+__device__ __forceinline__ void tile_rmac(typename cplx<T>::t (&acc)[TR][TV], const typename cplx<T>::t (&h)[TR],
+                                          const typename cplx<T>::t (&x)[TV]) {
+#pragma unroll
+  for (int i = 0; i < TR; ++i)
+#pragma unroll
+    for (int j = 0; j < TV; ++j) {
+      acc[i][j].x = fma(h[i].x, x[j].x, acc[i][j].x);
+      acc[i][j].y = fma(h[i].x, x[j].y, acc[i][j].y);
+    }
+}
+
+// The product of one staged entry column with the thread's rows of X.
+template <typename T, int GEN, int TR, int TV>
+__device__ __forceinline__ void tile_mac(typename cplx<T>::t (&acc)[TR][TV], const typename cplx<T>::t (&h)[TR],
+                                         const typename cplx<T>::t (&x)[TV]) {
+  if constexpr (GEN == MF_GEN_SINC_DVR_HO)
+    tile_rmac<T, TR, TV>(acc, h, x);
+  else
+    tile_cmac<T, TR, TV>(acc, h, x);
+}
+
 // Y[R0 : R0+RT, :] over columns [cbeg, cend) -> out[row][v] (row-major,
 // NV vectors per row).  Called by all NT threads of the CTA; smem_raw holds
 // rows_smem_bytes<T, NV>() bytes.
@@ -284,7 +309,7 @@ __device__ __forceinline__ void row_tile(unsigned char* smem_raw, int64_t R0, in
       for (int i = 0; i < TR; ++i) h[i] = hs[(r0 + i) * LD + k];
 #pragma unroll
       for (int j = 0; j < TV; ++j) x[j] = xs[k * NV + tv + j * (NV / TV)];
-      tile_cmac<T, TR, TV>(acc, h, x);
+      tile_mac<T, GEN, TR, TV>(acc, h, x);
     }
     __syncthreads();
   }
@@ -296,9 +321,10 @@ __device__ __forceinline__ void row_tile(unsigned char* smem_raw, int64_t R0, in
 
 // ---------------------------------------------------------------------------
 // Asynchronous variant of row_tile for the persistent batched kernel: two
-// chunk buffers; a stored chunk is copied into the free buffer with cp.async
-// (no registers held) while the current chunk is contracted; a generated
-// chunk is generated into it after the contraction.  Chunks read transposed
+// chunk buffers and two buffers for the chunk's rows of X; a stored chunk and
+// the next rows of X are copied into the free buffers with cp.async (no
+// registers held) while the current chunk is contracted; a generated chunk is
+// generated into its buffer after the contraction.  Chunks read transposed
 // from the canonical pair are stored raw and conjugated as they are used.
 // smem_raw holds rows_smem_bytes_async<T, NV>() bytes.
 // ---------------------------------------------------------------------------
@@ -343,6 +369,29 @@ __device__ __forceinline__ void chunk_copy_async(typename cplx<T>::t* hb, int64_
   cp_async_commit();
 }
 
+// Rows c0 .. c0+KCH-1 of X (NV vectors each, contiguous and 16-byte aligned
+// since c0 is a multiple of KCH and NV is even) into xs[KCH][NV] in 16-byte
+// pieces; rows at or past cend are zero-filled by plain stores.
+template <typename T, int NV, int NT>
+__device__ __forceinline__ void xchunk_copy_async(typename cplx<T>::t* xs, const typename cplx<T>::t* __restrict__ xc,
+                                                  int64_t c0, int64_t cend) {
+  using C = typename cplx<T>::t;
+  static_assert(NV % 2 == 0, "a 16-byte piece must not straddle two rows");
+  constexpr int EPP = 16 / (int)sizeof(C);  // elements per piece
+  constexpr int NP = KCH * NV / EPP;
+  const C* src = xc + c0 * NV;
+  for (int pc = threadIdx.x; pc < NP; pc += NT) {
+    const int e = pc * EPP;
+    if (c0 + e / NV < cend) {
+      const unsigned sa = (unsigned)__cvta_generic_to_shared(xs + e);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(src + e) : "memory");
+    } else {
+#pragma unroll
+      for (int i = 0; i < EPP; ++i) xs[e + i] = zc<T>();
+    }
+  }
+}
+
 template <typename T, int GEN, int NV, int TR, int TV, int NT>
 __device__ __forceinline__ void row_tile_async(unsigned char* smem_raw, int64_t R0, int64_t cbeg, int64_t cend,
                                                uint64_t seed, T sigma, const dvr_consts& dk,
@@ -355,8 +404,9 @@ __device__ __forceinline__ void row_tile_async(unsigned char* smem_raw, int64_t 
   constexpr int LD = KCH + HPAD;
   C* hs0 = reinterpret_cast<C*>(smem_raw);
   C* hs1 = hs0 + RT * LD;
-  C* xs = hs1 + RT * LD;                         // [KCH][NV]
-  T* win = reinterpret_cast<T*>(xs + KCH * NV);  // [RT + KCH]
+  C* xs0 = hs1 + RT * LD;                         // [KCH][NV]
+  C* xs1 = xs0 + KCH * NV;                        // [KCH][NV]
+  T* win = reinterpret_cast<T*>(xs1 + KCH * NV);  // [RT + KCH]
   const int tid = threadIdx.x;
   const int tv = tid % (NV / TV), tr = tid / (NV / TV);
   const int r0 = tr * TR;
@@ -366,36 +416,41 @@ __device__ __forceinline__ void row_tile_async(unsigned char* smem_raw, int64_t 
 #pragma unroll
     for (int j = 0; j < TV; ++j) acc[i][j] = zc<T>();
   if (cbeg >= cend) return;
-  // chunk 0 into buffer 0
+  // chunk 0 and its rows of X into buffers 0
   bool conj0 = false, conj1 = false;  // chunk in buffer 0 / 1 read transposed (conjugate on use)
   {
     bool t0 = false;
     const int64_t s0 = chunk_slot(R0, cbeg, cache, nullptr, slot_of_pair, b, nblk, t0);
+    xchunk_copy_async<T, NV, NT>(xs0, xc, cbeg, cend);
     if (s0 != -1) {
       chunk_copy_async<T, NT>(hs0, s0, t0, R0, cbeg, cache, nullptr, b);
       conj0 = t0;
-      cp_async_wait_all();
     } else {
+      cp_async_commit();
       fill_chunk_gen<T, GEN, NT>(hs0, win, R0, cbeg, seed, sigma, dk);
     }
+    cp_async_wait_all();
+    __syncthreads();
   }
   int k = 0;
   for (int64_t c0 = cbeg; c0 < cend; c0 += KCH, ++k) {
     C* cur = (k & 1) ? hs1 : hs0;
     C* nxt = (k & 1) ? hs0 : hs1;
+    const C* xcur = (k & 1) ? xs1 : xs0;
+    C* xnxt = (k & 1) ? xs0 : xs1;
     const bool cj = (k & 1) ? conj1 : conj0;
-    for (int e = tid; e < KCH * NV; e += NT) {
-      const int64_t c = c0 + e / NV;
-      xs[e] = c < cend ? xc[c * NV + e % NV] : zc<T>();
-    }
+    // the free buffers were last read before the previous barrier
     const int64_t c1 = c0 + KCH;
     bool t1 = false;
     int64_t s1 = -1;
     if (c1 < cend) {
       s1 = chunk_slot(R0, c1, cache, nullptr, slot_of_pair, b, nblk, t1);
-      if (s1 != -1) chunk_copy_async<T, NT>(nxt, s1, t1, R0, c1, cache, nullptr, b);
+      xchunk_copy_async<T, NV, NT>(xnxt, xc, c1, cend);
+      if (s1 != -1)
+        chunk_copy_async<T, NT>(nxt, s1, t1, R0, c1, cache, nullptr, b);
+      else
+        cp_async_commit();
     }
-    __syncthreads();
 #pragma unroll 4
     for (int kk = 0; kk < KCH; ++kk) {
       C h[TR], x[TV];
@@ -405,13 +460,11 @@ __device__ __forceinline__ void row_tile_async(unsigned char* smem_raw, int64_t 
         if (cj) h[i].y = -h[i].y;
       }
 #pragma unroll
-      for (int j = 0; j < TV; ++j) x[j] = xs[kk * NV + tv + j * (NV / TV)];
-      tile_cmac<T, TR, TV>(acc, h, x);
+      for (int j = 0; j < TV; ++j) x[j] = xcur[kk * NV + tv + j * (NV / TV)];
+      tile_mac<T, GEN, TR, TV>(acc, h, x);
     }
-    if (c1 < cend && s1 == -1) {
-      __syncthreads();  // the DVR window table and xs are free again
-      fill_chunk_gen<T, GEN, NT>(nxt, win, R0, c1, seed, sigma, dk);
-    }
+    // (the window table was last read before the previous barrier)
+    if (c1 < cend && s1 == -1) fill_chunk_gen<T, GEN, NT>(nxt, win, R0, c1, seed, sigma, dk);
     if (k & 1)
       conj0 = s1 != -1 && t1;
     else
@@ -427,7 +480,7 @@ __device__ __forceinline__ void row_tile_async(unsigned char* smem_raw, int64_t 
 
 template <typename T, int NV>
 __host__ __device__ constexpr size_t rows_smem_bytes_async() {
-  return sizeof(typename cplx<T>::t) * (2 * (size_t)RT * (KCH + HPAD) + (size_t)KCH * NV) + sizeof(T) * (RT + KCH);
+  return sizeof(typename cplx<T>::t) * (2 * (size_t)RT * (KCH + HPAD) + 2 * (size_t)KCH * NV) + sizeof(T) * (RT + KCH);
 }
 
 template <typename T, int NV>

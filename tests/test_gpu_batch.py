@@ -18,12 +18,30 @@ def mf():
     return mf
 
 
+@pytest.mark.parametrize("cache", ["none", "partial", "full"])
 @pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 3e-5)])
-def test_batch_matches_per_problem_and_oracle(mf, prec, tol):
-    Ds = [1000, 2048, 700, 130, 1536]
+def test_batch_matches_per_problem_and_oracle(mf, prec, tol, cache):
+    """Generated chunks (no cache), a mix of stored and generated block
+    pairs (partial) and stored pairs only (full); ragged D leaves a partial
+    last chunk of columns and a partial last row tile."""
+    # (a partial cache needs at least two block pairs: no D = 130 there)
+    Ds = [1000, 2048, 700, 130 if cache != "partial" else 1200, 1536]
     nv = [1, 3, 16, 2, 5]
     seeds = [0, 1, 2, 3, 4]
-    b = mf.Batch(Ds, nv, seeds, mf.MF_GEN_PHILOX_GUE, precision=prec)
+    eb = 16 if prec == 0 else 8
+    full = sum(eb * D * D for D in Ds)  # every block pair, with headroom
+    budget = {"none": 0, "partial": full // 5, "full": 4 * full}[cache]
+    b = mf.Batch(Ds, nv, seeds, mf.MF_GEN_PHILOX_GUE, cache_budget_bytes=budget, precision=prec,
+                 storage={"none": mf.MF_STORE_PROCEDURAL, "partial": mf.MF_STORE_PARTIAL,
+                          "full": mf.MF_STORE_FULL}[cache])
+    cached = [mf.mf_plan_describe(b.plan(i))["pairs_cached"] for i in range(len(Ds))]
+    npair = [mf.mf_plan_describe(b.plan(i))["n_pair"] for i in range(len(Ds))]
+    if cache == "none":
+        assert sum(cached) == 0
+    elif cache == "full":
+        assert cached == npair
+    else:
+        assert any(0 < c < n for c, n in zip(cached, npair)), (cached, npair)
     total = int(b.offsets[-1])
     rng = np.random.default_rng(0)
     parts = [W.random_state(D, k, seed=10 + i).reshape(D, k) for i, (D, k) in enumerate(zip(Ds, nv))]
