@@ -376,6 +376,46 @@ def time_applies(plan, x, y, nvec, reps):
     return a.elapsed_time(b) / 1e3 / reps
 
 
+def run_dvrmv(args):
+    """Sinc-DVR D = 131072, FP32 form, procedural, 1..16 vectors: the
+    one-vector row-split kernel and the multi-vector window kernel (vector
+    buckets 2, 4, 8, 16).  Algorithmic work 4 FLOP per kinetic entry and
+    vector (real entry times complex x); peak 152 SMs x 128 FMA lanes x 2 x
+    the SM clock sampled during the run."""
+    import torch
+    import paper_2606_31598_gb300 as mf
+    import workloads as W
+    D = 131072
+    stream = torch.cuda.current_stream().cuda_stream
+    props = torch.cuda.get_device_properties(0)
+    out = {"workload": "sinc-DVR D=%d, FP32 form, procedural, several vectors" % D}
+    nvecs = [args.dvrmv_nvec] if args.dvrmv_nvec else [1, 2, 4, 8, 16]
+    t1 = None
+    for nv in nvecs:
+        plan = mf.Plan(D, mf.MF_GEN_SINC_DVR_HO, seed=1, precision=mf.MF_PREC_FP32, nvec_hint=nv, stream=stream)
+        x = torch.from_numpy(W.random_state(D, nv, seed=4)).cuda()
+        y = torch.empty_like(x)
+        clock = ClockSampler(0)
+        clock.start()
+        plan.profile(True)
+        t = time_applies(plan, x, y, nv, max(1, args.steps))
+        kern_ms, kern_n = plan.profile_read()
+        clk = clock.stop()
+        plan.profile(False)
+        per = kern_ms / 1e3 / max(1, kern_n)
+        mhz = clk.get("sm_mhz") or 2070.0
+        peak = props.multi_processor_count * 128 * 2 * mhz * 1e6
+        flops = 4.0 * D * D * nv
+        if nv == 1:
+            t1 = t
+        out["nvec_%d" % nv] = {"apply_s": t, "kernel_s": per, "kernel_tflops": flops / per / 1e12,
+                               "fp32_fma_peak_tflops": peak / 1e12, "frac": flops / per / peak,
+                               "vs_one_vector_products": (nv * t1 / t) if t1 else None, "clocks": clk}
+        plan.close()
+    print(json.dumps(out))
+    return 0
+
+
 def run_multivector(args):
     """Philox ensemble D = 262144, 64 vectors, block 2048, 120 GB partial
     cache (P_cache = 3576 of 8256 canonical pairs): BF16X2 on tcgen05 against
@@ -740,13 +780,17 @@ def main():
     ap.add_argument("--sb-db", type=int, default=65536, help="sysbath: bath dimension d_B")
     ap.add_argument("--ext-dim", type=int, default=65536, help="external: D")
     ap.add_argument("--workload", default="dvr",
-                    choices=["dvr", "multivector", "batch", "philox", "sysbath", "external"],
-                    help="dvr: the benchmark line; multivector: the 64-vector tensor-core workload report")
+                    choices=["dvr", "dvrmv", "multivector", "batch", "philox", "sysbath", "external"],
+                    help="dvr: the benchmark line; dvrmv: the DVR product for 1..16 vectors; "
+                         "multivector: the 64-vector tensor-core workload report")
+    ap.add_argument("--dvrmv-nvec", type=int, default=0, help="dvrmv: one vector count only (0: 1, 2, 4, 8, 16)")
     ap.add_argument("--fp64", action="store_true", help="multivector: also time the FP64 procedural form")
     ap.add_argument("--mv-dim", type=int, default=262144, help="multivector: D (smaller D keeps the cached fraction)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "dvrmv":
+        return run_dvrmv(args)
     if args.workload == "multivector":
         return run_multivector(args)
     if args.workload == "batch":

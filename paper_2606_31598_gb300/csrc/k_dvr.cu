@@ -221,15 +221,122 @@ __global__ void __launch_bounds__(256, 2) dvr_rows_f32(int64_t D, int64_t dpad, 
   }
 }
 
-DvrRowsShape dvr_rows_shape(int64_t D, int num_sms) {
+// ---------------------------------------------------------------------------
+// FP32 form, NV = 2, 4, 8 or 16 vectors: the same persistent row split with
+// a lane owning 16 rows of ONE vector.  The 32 lanes of a warp are 32 / NV
+// row groups x NV vectors (lane L: group L / NV, vector L % NV), so a row
+// tile has RB = 8 * 16 * 32 / NV rows and every lane keeps 16 accumulators,
+// whatever NV.  Lanes of one row group read the same window entries
+// (broadcast); the chunk's x is staged vector-major, xs[v][KC + 2], so a lane
+// reads its 16 columns with eight 16-byte loads (the pad of 2 elements per
+// vector row spreads the NV rows over the banks).  KC = 8192 / NV columns
+// per chunk keeps the staged x at 64 KB.  Per 16 x 16 block a lane issues
+// 256 packed FMAs against 16 shared-memory loads, as in the one-vector kernel.
+// part[slot][row][v] as the row-owner kernels lay it out.
+// ---------------------------------------------------------------------------
+template <int NV>
+struct DvrMv {
+  static constexpr int GPW = 32 / NV;                  // row groups per warp
+  static constexpr int RB = kDvrWarps * kDvrP * GPW;   // rows per row tile
+  static constexpr int KC = 8192 / NV;                 // staged columns per chunk
+  static constexpr int XLD = KC + 2;                   // staged row length (elements)
+  static constexpr int NTB = RB + KC - 1;              // window entries per chunk
+  static constexpr int TB_FLOATS = ((NTB + 1 + 15) / 16) * 20;
+  static constexpr size_t SMEM = (size_t)TB_FLOATS * sizeof(float) + (size_t)NV * XLD * sizeof(float2);
+};
+
+template <int NV>
+__global__ void __launch_bounds__(256, 2) dvr_rows_mv_f32(int64_t D, int64_t dpad, int64_t nslot, int64_t nbc,
+                                                          int64_t nblocks, dvr_consts dk,
+                                                          const float2* __restrict__ xc, float2* __restrict__ part) {
+  using S = DvrMv<NV>;
+  constexpr int P = kDvrP, U = kDvrU, KC = S::KC, BPC = KC / U;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* tb = reinterpret_cast<float*>(smem_raw);
+  float2* xs = reinterpret_cast<float2*>(tb + S::TB_FLOATS);
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int grp = lane / NV, v = lane % NV;
+  const int64_t G = gridDim.x, b = blockIdx.x;
+  const int64_t lo = split_lo(b, nblocks, G), hi = split_lo(b + 1, nblocks, G);
+  const int rl0 = P * (S::GPW * w + grp);  // first tile row of the lane
+  const int jb0 = rl0 + KC - U;            // window start of the chunk's first block
+  const float2* xv_base = xs + v * S::XLD;
+  float2 acc[P];
+  for (int64_t cur = lo; cur < hi;) {
+    const int64_t rt = cur / nbc, cb = cur - rt * nbc;
+    const int64_t chunk = cb / BPC;
+    const int64_t seg_end = min(hi, rt * nbc + min((chunk + 1) * BPC, nbc));
+    if (cur == lo || cb == 0) {
+#pragma unroll
+      for (int a = 0; a < P; ++a) acc[a] = make_float2(0.f, 0.f);
+    }
+    const int64_t R0 = rt * S::RB, C0 = chunk * KC;
+    __syncthreads();  // the previous segment is done with the staged chunk
+    for (int e = tid; e < KC * NV; e += 256) {
+      const int c = e / NV, vv = e % NV;
+      const int64_t g = C0 + c;
+      xs[vv * S::XLD + c] = g < D ? xc[g * NV + vv] : make_float2(0.f, 0.f);
+    }
+    const long long kmin = (long long)(R0 - C0) - KC + 1;
+    for (int j = tid; j <= S::NTB; j += 256) tb[dvr_wpad(j)] = j < S::NTB ? dvr_T_f32(dk, kmin + j) : 0.f;
+    __syncthreads();
+    const int cc_beg = (int)(cb - chunk * BPC) * U, cc_end = cc_beg + (int)(seg_end - cur) * U;
+#pragma unroll 1
+    for (int cc = cc_beg; cc < cc_end; cc += U) {
+      const int jb = jb0 - cc;  // a multiple of 16
+      float win[32];
+#pragma unroll
+      for (int g = 0; g < 2; ++g) {
+        const float4* q = reinterpret_cast<const float4*>(tb + dvr_wpad(jb + 16 * g));
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const float4 t4 = q[i];
+          win[16 * g + 4 * i] = t4.x;
+          win[16 * g + 4 * i + 1] = t4.y;
+          win[16 * g + 4 * i + 2] = t4.z;
+          win[16 * g + 4 * i + 3] = t4.w;
+        }
+      }
+      float2 xv[U];
+      const float4* xq = reinterpret_cast<const float4*>(xv_base + cc);
+#pragma unroll
+      for (int i = 0; i < U / 2; ++i) {
+        const float4 t4 = xq[i];
+        xv[2 * i] = make_float2(t4.x, t4.y);
+        xv[2 * i + 1] = make_float2(t4.z, t4.w);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int a = 0; a < P; ++a) {
+          const float t = win[a - u + U - 1];
+          acc[a] = __ffma2_rn(make_float2(t, t), xv[u], acc[a]);
+        }
+    }
+    cur = seg_end;
+    const int64_t rt_end = (rt + 1) * nbc;
+    if (cur == hi || cur == rt_end) {
+      const int64_t slot = b - split_owner(rt * nbc, nblocks, G);
+      const int64_t row = R0 + rl0;
+#pragma unroll
+      for (int a = 0; a < P; ++a) part[(slot * dpad + row + a) * NV + v] = acc[a];
+      if (cur == rt_end)
+        for (int64_t s = slot + 1; s < nslot; ++s)
+#pragma unroll
+          for (int a = 0; a < P; ++a) part[(s * dpad + row + a) * NV + v] = make_float2(0.f, 0.f);
+    }
+  }
+}
+
+static DvrRowsShape rows_split_shape(int64_t D, int64_t rb, int64_t kc, int num_sms) {
   DvrRowsShape s{};
-  s.rows = kDvrRB;
-  s.cols = kDvrKC;
-  s.rtiles = (D + kDvrRB - 1) / kDvrRB;
+  s.rows = rb;
+  s.cols = kc;
+  s.rtiles = (D + rb - 1) / rb;
   s.nbc = (D + kDvrU - 1) / kDvrU;
   s.nblocks = s.rtiles * s.nbc;
   s.grid = std::min<int64_t>(2 * (int64_t)num_sms, s.nblocks);
-  s.dpad = s.rtiles * kDvrRB;
+  s.dpad = s.rtiles * rb;
   s.nslot = 1;
   for (int64_t rt = 0; rt < s.rtiles; ++rt) {
     const int64_t f = split_owner(rt * s.nbc, s.nblocks, s.grid);
@@ -238,6 +345,41 @@ DvrRowsShape dvr_rows_shape(int64_t D, int num_sms) {
   }
   return s;
 }
+
+int64_t dvr_mv_bucket(int64_t nvec) { return nvec <= 2 ? 2 : nvec <= 4 ? 4 : nvec <= 8 ? 8 : 16; }
+
+DvrRowsShape dvr_mv_shape(int64_t D, int64_t nb, int num_sms) {
+  switch (nb) {
+    case 2: return rows_split_shape(D, DvrMv<2>::RB, DvrMv<2>::KC, num_sms);
+    case 4: return rows_split_shape(D, DvrMv<4>::RB, DvrMv<4>::KC, num_sms);
+    case 8: return rows_split_shape(D, DvrMv<8>::RB, DvrMv<8>::KC, num_sms);
+    default: return rows_split_shape(D, DvrMv<16>::RB, DvrMv<16>::KC, num_sms);
+  }
+}
+
+template <int NV>
+static cudaError_t launch_mv_t(const Plan& p, const void* xc, void* part) {
+  const DvrRowsShape s = dvr_mv_shape(p.D, NV, p.num_sms);
+  auto k = dvr_rows_mv_f32<NV>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DvrMv<NV>::SMEM);
+  if (e != cudaSuccess) return e;
+  k<<<(unsigned)s.grid, 256, DvrMv<NV>::SMEM, p.stream>>>(p.D, s.dpad, s.nslot, s.nbc, s.nblocks, p.dvr,
+                                                          (const float2*)xc, (float2*)part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dvr_mv(const Plan& p, const void* xc, void* part, int64_t nb) {
+  if (p.prec != MF_PREC_FP32) return cudaErrorNotSupported;
+  switch (nb) {
+    case 2: return launch_mv_t<2>(p, xc, part);
+    case 4: return launch_mv_t<4>(p, xc, part);
+    case 8: return launch_mv_t<8>(p, xc, part);
+    case 16: return launch_mv_t<16>(p, xc, part);
+  }
+  return cudaErrorNotSupported;
+}
+
+DvrRowsShape dvr_rows_shape(int64_t D, int num_sms) { return rows_split_shape(D, kDvrRB, kDvrKC, num_sms); }
 
 template <typename T, int P>
 static size_t dvr_smem_bytes(int kc) {

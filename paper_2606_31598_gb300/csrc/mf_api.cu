@@ -76,8 +76,9 @@ void release(Plan& p) {
 }
 
 // Vector shape of the path used for nvec vectors: the Hermitian or DVR
-// window path for one vector, the row-owner path (padded to a compiled
-// vector count) for several.
+// window path for one vector; for several, the DVR window kernel (FP32
+// procedural DVR, 2..16 vectors) or the row-owner path, padded to a
+// compiled vector count.
 // The Hermitian-reuse multi-vector path (each canonical entry applied as H
 // and H^dagger) is used for the Philox ensemble and stored blocks with up to
 // 16 vectors while its partial slots (one per owner item and per row tile)
@@ -91,11 +92,21 @@ bool use_rows_herm(const Plan& p, int64_t nb) {
   return bytes <= p.herm_limit;
 }
 
+// The DVR window kernel for 2..16 vectors (FP32 form, procedural plans).
+bool use_dvr_mv(const Plan& p, int64_t nvec) {
+  return p.use_dvr_window && p.prec == MF_PREC_FP32 && !p.sb_nop && nvec >= 2 && nvec <= 16;
+}
+
 VecShape shape_for(const Plan& p, int64_t nvec) {
   if (p.prec == MF_PREC_BF16X2)
     return VecShape{nvec, tc_nvec_bucket(nvec), p.rows_nsplit, p.ntile * (int64_t)kTile};
   if (p.sliced) return VecShape{nvec, rows_nvec_bucket(nvec), p.rows_nsplit, p.slice_nt * (int64_t)kTile};
   if (nvec == 1 && !p.sb_nop) return VecShape{1, 1, p.nslot, p.dpad};
+  if (use_dvr_mv(p, nvec)) {
+    const int64_t nb = dvr_mv_bucket(nvec);
+    const DvrRowsShape s = dvr_mv_shape(p.D, nb, p.num_sms);
+    return VecShape{nvec, nb, s.nslot, s.dpad};
+  }
   const int64_t nb = rows_nvec_bucket(nvec);
   if (use_rows_herm(p, nb)) return VecShape{nvec, nb, p.herm_ns + p.ntile, p.ntile * (int64_t)kTile};
   return VecShape{nvec, nb, p.rows_nsplit, p.ntile * (int64_t)kTile};
@@ -169,6 +180,8 @@ mf_status apply_kernel(Plan& p, int64_t nvec) {
     MF_CUDA(launch_tc_apply(p, p.d_xc, p.d_part, p.d_tcb, tc_nvec_bucket(nvec)));
   else if (nvec > 1 && herm)
     MF_CUDA(launch_rows_herm(p, p.d_xc, 0, p.d_part, nbr, 1, nullptr));
+  else if (use_dvr_mv(p, nvec))
+    MF_CUDA(launch_dvr_mv(p, p.d_xc, p.d_part, dvr_mv_bucket(nvec)));
   else if (nvec > 1 || p.sliced)
     MF_CUDA(launch_rows_apply(p, p.d_xc, p.d_part, nbr));
   else if (p.use_dvr_window)

@@ -141,6 +141,11 @@ struct DvrRowsShape {
   int64_t rows, cols, rtiles, nbc, nblocks, grid, nslot, dpad;
 };
 DvrRowsShape dvr_rows_shape(int64_t D, int num_sms);
+// Multi-vector DVR window kernel (FP32 form): vector buckets 2, 4, 8, 16,
+// its row split for nb vectors and the launch (xc [rows][nb] -> part).
+int64_t dvr_mv_bucket(int64_t nvec);
+DvrRowsShape dvr_mv_shape(int64_t D, int64_t nb, int num_sms);
+cudaError_t launch_dvr_mv(const Plan& p, const void* xc, void* part, int64_t nb);
 // Fill the cache blocks listed in d_pairs (block pair (n, m) per cache slot).
 cudaError_t launch_cache_fill_pairs(const Plan& p, const int2* d_pairs, int64_t npairs);
 // Multi-vector row-owner apply (nvec bucket 2..64).

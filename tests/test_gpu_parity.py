@@ -312,27 +312,62 @@ def test_generator_division_and_sqrt_exact_on_this_gpu(mf):
     assert mf.mf_selfcheck_generator() == (0, 0)
 
 
+@pytest.mark.parametrize("nvec", [1, 3])
 @pytest.mark.parametrize("imag", [False, True])
-def test_dvr_fp32_chebyshev_terms_against_oracle(mf, imag):
-    """One-vector FP32 DVR plans run every Chebyshev term as one fused
-    launch (product, then each row tile's update by the CTA that completes
-    it).  D = 10000 spans three 4096-row tiles with a ragged last one; the
+def test_dvr_fp32_chebyshev_terms_against_oracle(mf, imag, nvec):
+    """FP32 DVR plans, real- and imaginary-time Chebyshev steps through the
+    window kernels: D = 10000 spans three 4096-row tiles with a ragged last
+    one (one vector) or five 2048-row tiles (3 vectors, padded to 4); the
     oracle runs the same recurrence on the same FP32-form entries in FP64."""
     D = 10000
-    p = _plan(mf, D, mf.MF_GEN_SINC_DVR_HO, 1)
+    p = _plan(mf, D, mf.MF_GEN_SINC_DVR_HO, 1, nvec_hint=nvec)
     emin, emax = p.bounds()
     c, R = 0.5 * (emax + emin), 0.5 * (emax - emin)
     op = O.make_op(O.GEN_SINC_DVR_HO, D, form=O.FORM_FP32)
-    psi = W.wavepacket(D)
+    psi = W.wavepacket(D) if nvec == 1 else W.random_state(D, nvec, seed=12).reshape(D, nvec)
     d = _dev(psi)
     if imag:
         tau, nt = 2e-4, 24
-        p.cheb_filter(d, 1, tau, nt, True)
+        p.cheb_filter(d, nvec, tau, nt, True)
         ref = O.cheb_imag_step(op, psi, tau, c, R, nt, normalize=True)
     else:
         dt, nt = 1e-4, 24
-        p.cheb_propagate(d, 1, dt, nt)
+        p.cheb_propagate(d, nvec, dt, nt)
         ref = O.cheb_step(op, psi, dt, c, R, nt)
     torch.cuda.synchronize()
     out = d.cpu().numpy()
     assert np.max(np.abs(out - ref)) < 2e-5 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("nvec", [2, 4, 5, 8, 13, 16])
+def test_dvr_multivector_window_kernel(mf, nvec):
+    """FP32 DVR products of 2..16 vectors by the multi-vector window kernel
+    (vector buckets 2, 4, 8, 16; its row tiles are 4096 / bucket x 16 rows,
+    its chunks 8192 / bucket columns): D = 5000 spans several row tiles and
+    column chunks of every bucket with ragged tails.  Every column against
+    the oracle's FFT form of the FP32 form's entries and against the
+    one-vector kernel."""
+    D = 5000
+    p = _plan(mf, D, mf.MF_GEN_SINC_DVR_HO, 1, nvec_hint=nvec)
+    rng = np.random.default_rng(20 + nvec)
+    X = (rng.standard_normal((D, nvec)) + 1j * rng.standard_normal((D, nvec))) / np.sqrt(2.0 * D)
+    Y = _apply(p, X)
+    op = O.make_op(O.GEN_SINC_DVR_HO, D, form=O.FORM_FP32)
+    for v in range(nvec):
+        ref = O.dvr_apply_fft(op, X[:, v])
+        assert _relerr(Y[:, v], ref) < 2e-5, v
+        assert _relerr(Y[:, v], _apply(p, np.ascontiguousarray(X[:, v]))) < 2e-5, v
+
+
+@pytest.mark.parametrize("nvec", [2, 16])
+def test_dvr_multivector_full_size_against_fft(mf, nvec):
+    """D = 131072 (the benchmark's grid) with 2 and 16 vectors: every row of
+    the first and last columns against the oracle's FFT form."""
+    D = 131072
+    p = _plan(mf, D, mf.MF_GEN_SINC_DVR_HO, 1, nvec_hint=nvec)
+    rng = np.random.default_rng(31)
+    X = (rng.standard_normal((D, nvec)) + 1j * rng.standard_normal((D, nvec))) / np.sqrt(2.0 * D)
+    Y = _apply(p, X)
+    op = O.make_op(O.GEN_SINC_DVR_HO, D, form=O.FORM_FP32)
+    for v in (0, nvec - 1):
+        assert _relerr(Y[:, v], O.dvr_apply_fft(op, X[:, v])) < 2e-5, v
