@@ -146,11 +146,12 @@ def cpu_oracle_sample(target_s=10.0, max_rows=None):
     import workloads as W
     op = O.make_op(O.GEN_SINC_DVR_HO, D)
     x = W.wavepacket(D)
-    rows = np.linspace(0, D - 1, 256).astype(np.int64)
+    O.apply_rows(op, x, np.arange(64, dtype=np.int64))  # thread pool start-up
+    rows = np.linspace(0, D - 1, 1024).astype(np.int64)
     t0 = time.perf_counter()
     O.apply_rows(op, x, rows)
     t = time.perf_counter() - t0
-    n = int(min(max_rows or D, max(256, 256 * target_s / max(t, 1e-6))))
+    n = int(min(max_rows or D, max(1024, 1024 * target_s / max(t, 1e-6))))
     rows = np.linspace(0, D - 1, n).astype(np.int64)
     t0 = time.perf_counter()
     O.apply_rows(op, x, rows)
@@ -770,7 +771,7 @@ def run_external(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mf", choices=["mf", "reference"])
     ap.add_argument("--batch-n", type=int, default=256, help="batch: number of problems")
