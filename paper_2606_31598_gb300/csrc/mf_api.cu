@@ -73,6 +73,8 @@ void release(Plan& p) {
   free_dev(p.d_sb_M);
   free_dev(p.d_sb_HS);
   free_dev(p.d_sb_xo);
+  p.part_cap = p.xc_cap = p.tcb_cap = p.sb_xo_cap = 0;
+  for (auto& c : p.q_cap) c = 0;
 }
 
 // Vector shape of the path used for nvec vectors: the Hermitian or DVR
@@ -112,33 +114,44 @@ VecShape shape_for(const Plan& p, int64_t nvec) {
   return VecShape{nvec, nb, p.rows_nsplit, p.ntile * (int64_t)kTile};
 }
 
-// Workspace for nvec vectors: partial slots, compute copy, three FP64 vectors.
+// Workspace for nvec vectors: partial slots and compute copy (the larger of
+// the one-vector and nvec shapes, each with its padded vector count), the
+// tensor-core operand tiles, three FP64 vectors and the system-bath mixed
+// inputs.  Each buffer grows when a call needs more than it holds; a smaller
+// vector count can need more partial slots than a larger one, since it may
+// take another kernel.
 mf_status ensure_workspace(Plan& p, int64_t nvec) {
-  if (nvec <= p.nvec_cap) return MF_OK;
-  free_dev(p.d_part);
-  free_dev(p.d_xc);
-  free_dev(p.d_tcb);
-  for (auto& q : p.d_q) free_dev(q);
   const size_t eb = compute_elem_bytes(p.prec);
-  // the larger of the one-vector shape and the nvec shape, each with its
-  // padded vector count (a row slice pads even one vector to two)
+  const VecShape m = shape_for(p, nvec);
   size_t part_bytes = 0, xc_bytes = 0;
-  for (const VecShape& s : {shape_for(p, 1), shape_for(p, nvec)}) {
+  for (const VecShape& s : {shape_for(p, 1), m}) {
     part_bytes = std::max(part_bytes, (size_t)s.nslot * (size_t)s.dpad * (size_t)s.nb * eb);
     xc_bytes = std::max(xc_bytes, (size_t)std::max<int64_t>(s.dpad, p.D) * (size_t)s.nb * eb);
   }
-  MF_CUDA(cudaMalloc(&p.d_part, part_bytes));
-  MF_CUDA(cudaMalloc(&p.d_xc, xc_bytes));
-  if (p.prec == MF_PREC_BF16X2) MF_CUDA(cudaMalloc(&p.d_tcb, tc_operand_bytes(p.D, shape_for(p, nvec).nb)));
-  MF_CUDA(cudaMemset(p.d_xc, 0, xc_bytes));
-  for (auto& q : p.d_q) MF_CUDA(cudaMalloc((void**)&q, (size_t)p.D * (size_t)nvec * sizeof(double2)));
+  const size_t tcb_bytes = p.prec == MF_PREC_BF16X2 ? tc_operand_bytes(p.D, m.nb) : 0;
+  const size_t q_bytes = (size_t)p.D * (size_t)nvec * sizeof(double2);
+  const int64_t sb_rows = std::max<int64_t>(m.dpad, p.D);
+  const size_t xo_bytes = p.sb_nop ? (size_t)p.sb_nop * (size_t)sb_rows * (size_t)m.nb * eb : 0;
+  auto grow = [](void** ptr, size_t& cap, size_t need, bool zero) -> mf_status {
+    if (need <= cap) return MF_OK;
+    if (*ptr) cudaFree(*ptr);
+    *ptr = nullptr;
+    cap = 0;
+    MF_CUDA(cudaMalloc(ptr, need));
+    if (zero) MF_CUDA(cudaMemset(*ptr, 0, need));
+    cap = need;
+    return MF_OK;
+  };
+  mf_status st = MF_OK;
+  if ((st = grow(&p.d_part, p.part_cap, part_bytes, false)) != MF_OK) return st;
+  if ((st = grow(&p.d_xc, p.xc_cap, xc_bytes, true)) != MF_OK) return st;
+  if (tcb_bytes && (st = grow(&p.d_tcb, p.tcb_cap, tcb_bytes, false)) != MF_OK) return st;
+  for (int i = 0; i < 3; ++i)
+    if ((st = grow((void**)&p.d_q[i], p.q_cap[i], q_bytes, false)) != MF_OK) return st;
   if (p.sb_nop) {
-    const VecShape m = shape_for(p, nvec);
-    free_dev(p.d_sb_xo);
-    p.sb_rows = std::max<int64_t>(m.dpad, p.D);
-    MF_CUDA(cudaMalloc(&p.d_sb_xo, (size_t)p.sb_nop * (size_t)p.sb_rows * (size_t)m.nb * eb));
+    if ((st = grow(&p.d_sb_xo, p.sb_xo_cap, xo_bytes, false)) != MF_OK) return st;
+    p.sb_rows = sb_rows;
   }
-  p.nvec_cap = nvec;
   return MF_OK;
 }
 
@@ -985,7 +998,6 @@ mf_status mf_sysbath_create(mf_plan_t* out, int64_t d_S, int64_t d_B, int32_t n_
     return fail(MF_ERR_CUDA);
   p.sb_nop = nop;
   p.sb_dS = (int32_t)d_S;
-  p.nvec_cap = 0;  // the workspace is re-sized with the mixed inputs on first use
   p.have_bounds = false;
   // dense-work estimate of the composite: n_op bath operators per product
   p.w_hpsi = (double)nop * (double)d_B * (double)d_B;

@@ -78,8 +78,9 @@ struct Plan {
   int64_t row0 = 0, row1 = 0, slice_t0 = 0, slice_nt = 0;
   // DVR launch shape
   int dvr_rows = 512, dvr_cols = 4096;
-  // workspace (sized for nvec_cap vectors)
-  int64_t nvec_cap = 0;
+  // workspace buffers and the bytes each holds (grown on demand)
+  size_t part_cap = 0, xc_cap = 0, tcb_cap = 0, sb_xo_cap = 0;
+  size_t q_cap[3] = {0, 0, 0};
   int64_t nslot = 0;              // partial-sum slots per output row
   int64_t dpad = 0;               // rows per slot (D padded to the kernel's row tile)
   bool use_dvr_window = false;    // DVR procedural path (Toeplitz window kernel)
