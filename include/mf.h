@@ -251,9 +251,10 @@ mf_status mf_plan_destroy(mf_plan_t p);
  * Eq. blockmatvecindex: phi^[n] = sum_m H^[n,m] psi^[m], every block pair
  * included).  Up to 16 vectors (and BF16X2 aside) each canonical pair is
  * generated or read once and applied as both H^[n,m] and H^[m,n] =
- * (H^[n,m])^dagger; the row-owner kernels used otherwise (more vectors,
- * opt.hermitian_reuse = 0, the tensor-core form, the DVR) produce each row's
- * blocks directly.
+ * (H^[n,m])^dagger; the procedural sinc-DVR in the FP32 form uses its
+ * Toeplitz-window kernels (1 to 16 vectors); the row-owner kernels used
+ * otherwise (more vectors, opt.hermitian_reuse = 0, the tensor-core form,
+ * stored DVR blocks, row slices) produce each row's blocks directly.
  *   y, x : device pointers to complex128 [D][nvec]; y must not overlap x.
  *   nvec : number of vectors, 1 <= nvec <= 64.
  * Asynchronous on the plan's stream.  Errors: MF_ERR_INVALID, MF_ERR_CUDA.

@@ -1,6 +1,8 @@
 // k_rows.cu -- multi-vector generate-and-apply, row-owner form (SIMT).
 //
-// For nvec >= 2 the product Y = H X (Sec. IV.A, Eq. generic_multivector) is
+// The product Y = H X (Sec. IV.A, Eq. generic_multivector) for the cases the
+// Hermitian-reuse and DVR window kernels do not take (more than 16 vectors,
+// hermitian_reuse = 0, stored DVR blocks, the FP64 DVR form, row slices) is
 // computed by CTAs that own a 128-row output tile and sweep a column range
 // in chunks of 32 columns (Eq. blockmatvec: phi^[n] = sum_m H^[n,m] psi^[m],
 // scheduled by output block rows as in Sec. III.B).  Each chunk H[128 x 32]

@@ -90,3 +90,74 @@ def test_sweep_apply_matches_oracle(mf, case):
         err = float(np.max(np.abs(Y - ref)) / np.max(np.abs(ref)))
         assert err < bar, (nv, err)
     p.close()
+
+
+def _cheb_cases(n=16, seed=77):
+    rng = np.random.default_rng(seed)
+    out = []
+    edges = [2, 129, 513]
+    for i in range(n):
+        D = edges[i] if i < len(edges) else int(rng.integers(2, 901))
+        out.append((i, int(rng.integers(0, 2)), int(rng.integers(0, 2)), int(rng.integers(0, 3)), D,
+                    int(rng.choice(NVECS)), float(rng.uniform(0.2, 1.0))))
+    return out
+
+
+@pytest.mark.parametrize("case", _cheb_cases(), ids=lambda c: "c%d-g%d-p%d-s%d-D%d-v%d-t%.2f" % c)
+def test_sweep_chebyshev_matches_oracle(mf, case):
+    """One Chebyshev step of exp(-i dt H) (Sec. VII) at drawn shapes; dt is
+    capped so R dt <= 8 (a few tens of terms) and the oracle runs the same
+    recurrence on the same form's entries with the plan's bounds."""
+    _, gen, prec, storage, D, nvec, dt = case
+    p = _make_plan(mf, gen, prec, storage, D, nvec)
+    emin, emax = p.bounds()
+    c, R = 0.5 * (emax + emin), 0.5 * (emax - emin)
+    dt = min(dt, 8.0 / R)
+    nt = p.cheb_terms(dt)
+    X = W.random_state(D, nvec, seed=5).reshape(D, nvec)
+    d = torch.from_numpy(np.ascontiguousarray(X)).cuda()
+    p.cheb_propagate(d, nvec, dt, nt)
+    torch.cuda.synchronize()
+    got = d.cpu().numpy()
+    op = O.make_op(gen, D, seed=11, form=O.FORM_FP64 if prec == 0 else O.FORM_FP32)
+    ref = O.cheb_step(op, X, dt, c, R, nt)
+    err = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+    assert err < (1e-11 if prec == 0 else 2e-5), err
+    p.close()
+
+
+def _slice_cases(n=12, seed=99):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        D = int(rng.integers(129, 1501))
+        ntile = -(-D // 128)
+        world = int(rng.integers(2, min(4, ntile) + 1))
+        out.append((i, int(rng.integers(0, 2)), int(rng.integers(0, 2)), D, world, int(rng.choice(NVECS))))
+    return out
+
+
+@pytest.mark.parametrize("case", _slice_cases(), ids=lambda c: "c%d-g%d-p%d-D%d-w%d-v%d" % c)
+def test_sweep_row_slices_reassemble_the_product(mf, case):
+    """Row-slice plans (row-parallel mode of Sec. IV.H) at drawn sizes and
+    rank counts, every other slice with a partial cache of its block pairs:
+    the slices' products stacked are the oracle's product."""
+    from paper_2606_31598_gb300 import rowgroup
+    _, gen, prec, D, world, nvec = case
+    eb = 16 if prec == 0 else 8
+    X = W.random_state(D, nvec, seed=6).reshape(D, nvec)
+    xd = torch.from_numpy(np.ascontiguousarray(X)).cuda()
+    parts = []
+    for k, (r0, r1) in enumerate(rowgroup.slices(D, world)):
+        budget = eb * 128 * 128 * 2 if k % 2 else 0
+        p = mf.Plan(D, gen, seed=11, block=128, precision=prec, cache_budget_bytes=budget,
+                    storage=mf.MF_STORE_PARTIAL if budget else mf.MF_STORE_PROCEDURAL, row_begin=r0, row_end=r1)
+        y = torch.empty((r1 - r0, nvec), dtype=torch.complex128, device="cuda")
+        p.apply(y, xd, nvec)
+        torch.cuda.synchronize()
+        parts.append(y.cpu().numpy())
+        p.close()
+    got = np.concatenate(parts)
+    ref = O.apply(O.make_op(gen, D, seed=11, form=O.FORM_FP64 if prec == 0 else O.FORM_FP32), X)
+    err = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+    assert err < (1e-12 if prec == 0 else 2e-5), err
