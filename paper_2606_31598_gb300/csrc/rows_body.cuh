@@ -1,9 +1,12 @@
 // rows_body.cuh -- the row-owner generate-and-apply tile (device code) shared
 // by the split-K launcher (k_rows.cu) and the batched persistent kernel
-// (k_batch.cu): CTAs own a 128-row output tile and sweep a column range in
-// chunks of 32 columns; each chunk of H is generated (canonical entries,
-// conjugates below the diagonal, DVR window table) or copied from the block
-// cache into shared memory and contracted with the chunk's rows of X.
+// (k_batch.cu), whose chunk generation, register-tile products and block
+// lookup the Hermitian-reuse (k_rows_herm.cu), system-bath (k_sysbath.cu)
+// and tcgen05 (k_tc.cu) kernels also use: CTAs own a 128-row output tile and
+// sweep a column range in chunks of 32 columns; each chunk of H is generated
+// (canonical entries, conjugates below the diagonal, DVR window table) or
+// copied from the block cache into shared memory and contracted with the
+// chunk's rows of X.
 #pragma once
 #include "mf_internal.h"
 
@@ -248,7 +251,7 @@ __device__ __forceinline__ void tile_mac(typename cplx<T>::t (&acc)[TR][TV], con
 // Y[R0 : R0+RT, :] over columns [cbeg, cend) -> out[row][v] (row-major,
 // NV vectors per row).  Called by all NT threads of the CTA; smem_raw holds
 // rows_smem_bytes<T, NV>() bytes.
-template <typename T, int GEN, int NV, int TR, int TV, int NT, bool PIPE = true>
+template <typename T, int GEN, int NV, int TR, int TV, int NT>
 __device__ __forceinline__ void row_tile(unsigned char* smem_raw, int64_t R0, int64_t cbeg, int64_t cend, int64_t D,
                                          uint64_t seed, T sigma, const dvr_consts& dk,
                                          const typename cplx<T>::t* __restrict__ xc,
@@ -276,7 +279,7 @@ __device__ __forceinline__ void row_tile(unsigned char* smem_raw, int64_t R0, in
   // FP32 with up to 16 accumulators per thread: the next stored chunk's
   // loads are issued into registers before this chunk's products, so the
   // cache (or host) latency overlaps them
-  constexpr bool kPipe = PIPE && sizeof(T) == 4 && TR * TV <= 16;
+  constexpr bool kPipe = sizeof(T) == 4 && TR * TV <= 16;
   constexpr int PER = RT * KCH / NT;
   C hreg[kPipe ? PER : 1];
   bool ptrans = false;
