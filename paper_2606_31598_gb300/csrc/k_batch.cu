@@ -34,7 +34,7 @@ struct BatchProb {
   double2* acc;
   double2* psi;
   const double* J;
-  double c, R, ph_r, ph_i;
+  double c, rinv, ph_r, ph_i;  // centre, 1 / half-width, e^{-i c dt}
 };
 
 struct BatchItem {
@@ -115,7 +115,8 @@ __global__ void k_batch_init(const BatchProb* __restrict__ probs, int parity) {
   }
 }
 
-// y = part + V q; t = (y - c q)/R; q_next = t or 2t - q_prev; acc += a_j q_next
+// y = part + V q; t = (y - c q)/R (as a product with 1/R, like the one-plan
+// update); q_next = t or 2t - q_prev; acc += a_j q_next
 template <typename C>
 __global__ void k_batch_update(const BatchProb* __restrict__ probs, int parity, int32_t j, int gen_dvr) {
   const BatchProb& P = probs[blockIdx.y];
@@ -124,7 +125,7 @@ __global__ void k_batch_update(const BatchProb* __restrict__ probs, int parity, 
   double2* qp = P.q[1 - parity];
   const C* part = (const C*)P.part;
   C* xc = (C*)P.xc;
-  const double aj = 2.0 * P.J[j], c = P.c, R = P.R;
+  const double aj = 2.0 * P.J[j], c = P.c, rinv = P.rinv;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t row = e / P.nv, v = e % P.nv, ci = row * P.nb + v;
     const C pv = part[ci];
@@ -135,7 +136,7 @@ __global__ void k_batch_update(const BatchProb* __restrict__ probs, int parity, 
       yr = fma(V, q.x, yr);
       yi = fma(V, q.y, yi);
     }
-    double tr = (yr - c * q.x) / R, ti = (yi - c * q.y) / R;
+    double tr = (yr - c * q.x) * rinv, ti = (yi - c * q.y) * rinv;
     if (j > 1) {
       const double2 o = qp[e];
       tr = 2.0 * tr - o.x;
@@ -407,7 +408,7 @@ mf_status mf_batch_propagate(mf_batch_t b, void* psi, double dt, int32_t nsteps,
       q.psi = (double2*)psi + b->offsets[i];
       q.J = P.d_J;
       q.c = 0.5 * (P.emax + P.emin);
-      q.R = 0.5 * (P.emax - P.emin);
+      q.rinv = 1.0 / (0.5 * (P.emax - P.emin));
       q.ph_r = std::cos(q.c * dt);
       q.ph_i = -std::sin(q.c * dt);
     }

@@ -179,11 +179,10 @@ template <typename C>
 __global__ void k_cheb_update(const C* __restrict__ part, VecShape sh, int64_t n, int dvr, dvr_consts dk,
                               const double2* __restrict__ qcur, double2* __restrict__ qprev,
                               double2* __restrict__ acc, C* __restrict__ xc, const double* __restrict__ J,
-                              int32_t j, double c, double R, int imag_time, const double2* __restrict__ hs) {
+                              int32_t j, double c, double rinv, int imag_time, const double2* __restrict__ hs) {
   // real time: a_j = 2 (-i)^j J_j; imaginary time: a_j = 2 (-1)^j e^{-z} I_j
   const double aj = (imag_time && (j & 1)) ? -2.0 * J[j] : 2.0 * J[j];
   const int64_t stride = sh.dpad * sh.nb;
-  const double rinv = 1.0 / R;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
     // one vector needs no index division
     const int64_t row = sh.nv == 1 ? e : e / sh.nv, v = sh.nv == 1 ? 0 : e - row * sh.nv;
@@ -204,12 +203,15 @@ cudaError_t launch_cheb_update(const Plan& p, const void* part, const double2* q
                                void* xc, VecShape s, int32_t k_next, double c, double R, int imag_time) {
   const int64_t n = p.D * s.nv;
   const int dvr = p.gen == MF_GEN_SINC_DVR_HO;
+  const double rinv = 1.0 / R;  // once on the host: the FP64 pipe is GB300's slowest
   if (p.prec == MF_PREC_FP64)
     k_cheb_update<double2><<<grid_for(n), 256, 0, p.stream>>>((const double2*)part, s, n, dvr, p.dvr, qcur, qprev,
-                                                              acc, (double2*)xc, p.d_J, k_next, c, R, imag_time, p.d_sb_HS);
+                                                              acc, (double2*)xc, p.d_J, k_next, c, rinv, imag_time,
+                                                              p.d_sb_HS);
   else
     k_cheb_update<float2><<<grid_for(n), 256, 0, p.stream>>>((const float2*)part, s, n, dvr, p.dvr, qcur, qprev,
-                                                             acc, (float2*)xc, p.d_J, k_next, c, R, imag_time, p.d_sb_HS);
+                                                             acc, (float2*)xc, p.d_J, k_next, c, rinv, imag_time,
+                                                             p.d_sb_HS);
   return cudaGetLastError();
 }
 
