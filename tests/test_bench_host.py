@@ -1,0 +1,46 @@
+"""Host-side pieces of bench.py that need no GPU: the bounded CPU-oracle
+sample behind cpu_baseline and the reference arm, the clock sampler's
+behaviour without nvidia-smi readings, the committed profile's traffic
+record, and the whole-job arithmetic."""
+import os
+import re
+
+import pytest
+
+import bench
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_cpu_oracle_sample_is_bounded_and_positive():
+    from oracle import build as obuild
+    obuild.build()
+    v, n, t = bench.cpu_oracle_sample(target_s=0.3)
+    assert v > 0 and n >= 1024 and t > 0
+    assert abs(v - n * bench.D / t) <= 1e-6 * v
+    # the sample is sized from a probe: it should land near the target, not
+    # at the 131072-row cap
+    assert n < bench.D
+
+
+def test_clock_sampler_without_readings():
+    c = bench.ClockSampler(0)
+    c.proc = None  # as when nvidia-smi is absent
+    out = c.stop()
+    assert out["samples"] == 0 and out["sm_mhz"] is None and out["reasons"] == []
+
+
+def test_profile_traffic_record_parses():
+    """The dominant kernel's summary carries a per-launch DRAM figure and the
+    hash of the source it was taken on; bench.py reports the figure only
+    while the hash matches."""
+    txt = open(os.path.join(ROOT, "profiles", "dvr_rows_f32_D131072.md")).read()
+    assert re.search(r"traffic_bytes_per_launch:\s*[0-9.eE+]+", txt)
+    assert re.search(r"source_sha256:\s*[0-9a-f]{64}", txt)
+    t = bench.traffic_from_profile()
+    assert t is None or 1e5 < t < 1e8
+
+
+@pytest.mark.parametrize("world", [1, 2, 8])
+def test_job_value_is_whole_job_throughput(world):
+    assert bench.job_value(world, 10, 1e9, 2.0) == pytest.approx(world * 10 * 1e9 / 2.0)
