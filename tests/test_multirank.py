@@ -33,7 +33,7 @@ def _worker(rank, world, port, out):
 def test_two_gloo_ranks_share_the_job_time():
     import torch.multiprocessing as mp
     world, port = 2, _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)
@@ -101,7 +101,7 @@ def test_row_group_propagation_on_two_gloo_ranks():
     import torch.multiprocessing as mp
     from oracle import oracle as O
     world, port = 2, _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_row_worker, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)
