@@ -161,3 +161,89 @@ def test_sweep_row_slices_reassemble_the_product(mf, case):
     ref = O.apply(O.make_op(gen, D, seed=11, form=O.FORM_FP64 if prec == 0 else O.FORM_FP32), X)
     err = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
     assert err < (1e-12 if prec == 0 else 2e-5), err
+
+
+def _herm(rng, n):
+    M = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    return 0.5 * (M + M.conj().T)
+
+
+def _sysbath_cases(n=12, seed=7):
+    rng = np.random.default_rng(seed)
+    edges = [2, 129, 255]
+    out = []
+    for i in range(n):
+        d_B = edges[i] if i < len(edges) else int(rng.integers(2, 901))
+        out.append((i, int(rng.integers(1, 17)), d_B, int(rng.integers(0, 4)), int(rng.integers(0, 2))))
+    return out
+
+
+@pytest.mark.parametrize("case", _sysbath_cases(), ids=lambda c: "c%d-dS%d-dB%d-n%d-p%d" % c)
+def test_sweep_sysbath_matches_oracle(mf, case):
+    """System-bath plans (Sec. VII composite) at drawn d_S, d_B and numbers
+    of coupling terms, against the oracle's matrix-free statement."""
+    _, d_S, d_B, n_int, prec = case
+    rng = np.random.default_rng(d_S * 1000 + d_B)
+    H_S = _herm(rng, d_S)
+    A = np.stack([_herm(rng, d_S) for _ in range(n_int)]) if n_int else np.zeros((0, d_S, d_S))
+    seeds = [31 + 7 * k for k in range(n_int + 1)]
+    g = 0.3
+    p = mf.Plan.sysbath(d_S, d_B, seeds, H_S, A, g, precision=prec)
+    X = rng.standard_normal((d_B, d_S)) + 1j * rng.standard_normal((d_B, d_S))
+    ref = O.sysbath_apply(d_S, d_B, seeds, H_S, A, g, X, form=O.FORM_FP64 if prec == 0 else O.FORM_FP32)
+    xd = torch.from_numpy(np.ascontiguousarray(X)).cuda()
+    yd = torch.empty_like(xd)
+    p.apply(yd, xd, d_S)
+    torch.cuda.synchronize()
+    err = float(np.max(np.abs(yd.cpu().numpy() - ref)) / np.max(np.abs(ref)))
+    assert err < (1e-12 if prec == 0 else 2e-5), err
+    p.close()
+
+
+def _external_cases(n=12, seed=8):
+    rng = np.random.default_rng(seed)
+    edges = [2, 128, 257]
+    out = []
+    for i in range(n):
+        D = edges[i] if i < len(edges) else int(rng.integers(2, 1201))
+        b = int(rng.choice([128, 256]))
+        if b > -(-D // 128) * 128:
+            b = 128  # the block may not exceed D rounded up to the tile
+        nblk = -(-D // b)
+        npair = nblk * (nblk + 1) // 2
+        out.append((i, D, b, int(rng.integers(0, npair + 1)), int(rng.integers(0, 3)), int(rng.choice(NVECS)),
+                    int(rng.choice(NVECS))))
+    return out
+
+
+@pytest.mark.parametrize("case", _external_cases(), ids=lambda c: "c%d-D%d-b%d-k%d-p%d-v%d-v%d" % c)
+def test_sweep_external_blocks_match_dense_product(mf, case):
+    """Externally stored blocks (Sec. II) at drawn sizes, block sizes and
+    numbers of pairs copied to HBM (the rest read from host memory), every
+    precision form, two vector counts per plan, against the dense product of
+    the assembled blocks."""
+    _, D, b, kpairs, prec, nvec, nvec2 = case
+    rng = np.random.default_rng(D + 17 * b)
+    M = rng.standard_normal((D, D)) + 1j * rng.standard_normal((D, D))
+    H = (M + M.conj().T) / np.sqrt(8.0 * D)
+    nblk = -(-D // b)
+    P = np.zeros((nblk * b, nblk * b), dtype=np.complex128)
+    P[:D, :D] = H
+    dt = np.complex128 if prec == 0 else np.complex64
+    blocks = np.ascontiguousarray(
+        np.stack([P[n * b:(n + 1) * b, m * b:(m + 1) * b] for n, m in O.external_pairs(D, b)]).astype(dt))
+    eb = 16 if prec == 0 else 8
+    p = mf.Plan.external(D, b, blocks, cache_budget_bytes=kpairs * eb * b * b, precision=prec)
+    assert p.describe()["pairs_cached"] == kpairs
+    Hd = O.external_dense(D, b, blocks)
+    bar = {0: 1e-12, 1: 2e-5, 2: 1e-4}[prec]
+    for k, nv in enumerate((nvec, nvec2)):
+        X = rng.standard_normal((D, nv)) + 1j * rng.standard_normal((D, nv))
+        xd = torch.from_numpy(np.ascontiguousarray(X)).cuda()
+        yd = torch.empty_like(xd)
+        p.apply(yd, xd, nv)
+        torch.cuda.synchronize()
+        ref = Hd @ X
+        err = float(np.max(np.abs(yd.cpu().numpy() - ref)) / np.max(np.abs(ref)))
+        assert err < bar, (nv, err)
+    p.close()
