@@ -247,3 +247,87 @@ def test_sweep_external_blocks_match_dense_product(mf, case):
         err = float(np.max(np.abs(yd.cpu().numpy() - ref)) / np.max(np.abs(ref)))
         assert err < bar, (nv, err)
     p.close()
+
+
+def _filter_cases(n=8, seed=12):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        D = [2, 129][i] if i < 2 else int(rng.integers(2, 1201))
+        out.append((i, int(rng.integers(0, 2)), int(rng.integers(0, 2)), int(rng.integers(0, 3)), D,
+                    int(rng.choice(NVECS)), i % 2))
+    return out
+
+
+@pytest.mark.parametrize("case", _filter_cases(), ids=lambda c: "c%d-g%d-p%d-s%d-D%d-v%d-n%d" % c)
+def test_sweep_imaginary_time_filter(mf, case):
+    """exp(-tau (H - E_min)) at drawn shapes (tau so that R tau <= 6), with
+    and without per-column renormalisation, against the oracle's recurrence
+    with the plan's bounds.  Bars relative to the input as in the filter
+    tests (divided by the smallest filtered column norm when normalised)."""
+    _, gen, prec, storage, D, nvec, normalize = case
+    p = _make_plan(mf, gen, prec, storage, D, nvec)
+    emin, emax = p.bounds()
+    c, R = 0.5 * (emax + emin), 0.5 * (emax - emin)
+    tau = 6.0 / R
+    nt = O.cheb_imag_terms(R * tau, 1e-15)
+    op = O.make_op(gen, D, seed=11, form=O.FORM_FP64 if prec == 0 else O.FORM_FP32)
+    psi = W.random_state(D, nvec, seed=9).reshape(D, nvec)
+    raw = O.cheb_imag_step(op, psi, tau, c, R, nt, normalize=False).reshape(D, nvec)
+    d = torch.from_numpy(np.ascontiguousarray(psi)).cuda()
+    p.cheb_filter(d, nvec, tau, nt, bool(normalize))
+    torch.cuda.synchronize()
+    out = d.cpu().numpy().reshape(D, nvec)
+    tol = (1e-13 if prec == 0 else 1e-5) * np.max(np.abs(psi))
+    ref = raw
+    if normalize:
+        ref = raw / np.linalg.norm(raw, axis=0)
+        tol /= np.min(np.linalg.norm(raw, axis=0))
+        assert np.max(np.abs(np.linalg.norm(out, axis=0) - 1)) < 1e-12
+    assert np.max(np.abs(out - ref)) < tol
+    p.close()
+
+
+def _batch_cases(n=6, seed=21):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        k = int(rng.integers(2, 7))
+        Ds = [int(d) for d in rng.integers(2, 1201, k)]
+        if i == 0:
+            Ds[0] = 2
+        nv = [int(v) for v in rng.integers(1, 17, k)]
+        out.append((i, int(rng.integers(0, 2)), int(rng.integers(0, 2)), int(rng.integers(0, 2)), tuple(Ds), tuple(nv)))
+    return out
+
+
+@pytest.mark.parametrize("case", _batch_cases(), ids=lambda c: "c%d-g%d-p%d-full%d" % c[:4])
+def test_sweep_batched_problems(mf, case):
+    """Batches of 2..6 problems of drawn D (from 2) and vector counts, all
+    generated or all fully cached, one Chebyshev step each in one persistent
+    launch per term: every problem against the oracle's recurrence with its
+    own plan's bounds and the batch's common term count."""
+    _, gen, prec, full, Ds, nv = case
+    # the budget is shared in proportion to D^2; a full cache of a small
+    # problem still takes whole 128 x 128 blocks, so give room to spare (the
+    # plans allocate only the blocks they hold)
+    budget = int(1e12) if full else 0
+    b = mf.Batch(list(Ds), list(nv), list(range(len(Ds))), gen, cache_budget_bytes=budget, precision=prec,
+                 storage=mf.MF_STORE_FULL if full else mf.MF_STORE_PROCEDURAL)
+    parts = [W.random_state(D, k, seed=40 + i).reshape(D, k) for i, (D, k) in enumerate(zip(Ds, nv))]
+    d = torch.from_numpy(np.concatenate([q.ravel() for q in parts])).cuda()
+    dt = 0.5 if gen == 0 else 2e-3
+    nt = b.propagate(d, dt, 1)
+    torch.cuda.synchronize()
+    out = d.cpu().numpy()
+    for i, (D, k) in enumerate(zip(Ds, nv)):
+        h = b.plan(i)
+        if full:
+            assert mf.mf_plan_describe(h)["storage"] == "full"
+        emin, emax = mf.mf_spectral_bounds(h)
+        c, R = 0.5 * (emax + emin), 0.5 * (emax - emin)
+        op = O.make_op(gen, D, seed=i, form=O.FORM_FP64 if prec == 0 else O.FORM_FP32)
+        ref = O.cheb_step(op, parts[i], dt, c, R, nt)
+        got = out[b.offsets[i]:b.offsets[i + 1]].reshape(D, k)
+        assert np.max(np.abs(got - ref)) < (1e-11 if prec == 0 else 3e-5), i
+    b.close()
