@@ -103,7 +103,8 @@ typedef struct {
   int32_t hermitian_reuse; /* 2..16 vectors: -1 = automatic (default; each canonical
                               chunk applied as H and H^dagger while its partial slots
                               fit min(16 GB, 10 % of free memory)), 0 = row-owner
-                              kernel (every entry generated or read for each use) */
+                              kernel (every entry generated or read for each use);
+                              not used by the sinc-DVR generator */
   int64_t row_begin;       /* row slice [row_begin, row_end) of a row-distributed plan */
   int64_t row_end;         /* (Sec. IV.H, row-parallel mode); 0, 0 = all rows; see
                               mf_plan_create */
