@@ -181,10 +181,22 @@ def _check(st, what=""):
     return st
 
 
-def _ptr(t):
-    """Device pointer of a torch tensor, or an int address."""
+def _vec(t, n, what):
+    """Device address of a vector argument: a contiguous complex128 CUDA
+    tensor holding at least n elements (n = 0: size not checked).  An int is
+    taken as a raw device address, unchecked.  Anything else raises
+    MF_ERR_INVALID before the library sees it: the kernels read and write
+    rows x nvec complex128 elements from the address they are given."""
     if isinstance(t, int):
         return t
+    import torch
+    ok = (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.complex128 and t.is_contiguous()
+          and t.numel() >= n)
+    if not ok:
+        got = ("%s %s on %s, %d elements" % (tuple(t.shape), t.dtype, t.device, t.numel())
+               if isinstance(t, torch.Tensor) else type(t).__name__)
+        raise MFError(MF_ERR_INVALID, "%s: expected a contiguous complex128 CUDA tensor of at least %d elements, "
+                      "got %s" % (what, n, got))
     return t.data_ptr()
 
 
@@ -248,11 +260,12 @@ def mf_selfcheck_generator():
 
 
 def mf_apply(plan, y, x, nvec=1):
-    return _check(lib().mf_apply(plan, _ptr(y), _ptr(x), int(nvec)), "mf_apply")
+    return _check(lib().mf_apply(plan, _vec(y, 0, "mf_apply y"), _vec(x, 0, "mf_apply x"), int(nvec)), "mf_apply")
 
 
 def mf_cheb_propagate(plan, psi, nvec, dt, order=0):
-    return _check(lib().mf_cheb_propagate(plan, _ptr(psi), int(nvec), float(dt), int(order)),
+    return _check(lib().mf_cheb_propagate(plan, _vec(psi, 0, "mf_cheb_propagate psi"), int(nvec), float(dt),
+                                          int(order)),
                   "mf_cheb_propagate")
 
 
@@ -263,7 +276,8 @@ def mf_cheb_terms(plan, dt):
 
 
 def mf_cheb_filter(plan, psi, nvec, tau, order=0, normalize=True):
-    return _check(lib().mf_cheb_filter(plan, _ptr(psi), int(nvec), float(tau), int(order), int(bool(normalize))),
+    return _check(lib().mf_cheb_filter(plan, _vec(psi, 0, "mf_cheb_filter psi"), int(nvec), float(tau), int(order),
+                                       int(bool(normalize))),
                   "mf_cheb_filter")
 
 
@@ -301,7 +315,8 @@ def mf_debug_entries(plan, r0, c0, rows, cols, out_host):
 
 def mf_apply_dvr_noalloc(D, dvr_L, x, y, stream=None):
     """Allocation-free DVR apply (FP32 form, one vector); see include/mf.h."""
-    return _check(lib().mf_apply_dvr_noalloc(int(D), float(dvr_L), _ptr(x), _ptr(y), stream),
+    return _check(lib().mf_apply_dvr_noalloc(int(D), float(dvr_L), _vec(x, int(D), "mf_apply_dvr_noalloc x"),
+                                             _vec(y, int(D), "mf_apply_dvr_noalloc y"), stream),
                   "mf_apply_dvr_noalloc")
 
 
@@ -425,7 +440,8 @@ class Batch:
 
     def propagate(self, psi, dt, nsteps=1, order=0):
         nt = ctypes.c_int32()
-        _check(lib().mf_batch_propagate(self.handle, _ptr(psi), float(dt), int(nsteps), int(order), ctypes.byref(nt)),
+        psi_p = _vec(psi, int(self.offsets[-1]), "Batch.propagate psi")
+        _check(lib().mf_batch_propagate(self.handle, psi_p, float(dt), int(nsteps), int(order), ctypes.byref(nt)),
                "mf_batch_propagate")
         return nt.value
 
@@ -514,10 +530,18 @@ class Plan:
         self.handle = mf_sysbath_create(d_S, d_B, seeds, H_S, A, g, o)
         return self
 
+    def _rows(self):
+        """Output rows of this plan: its row slice, else all D rows."""
+        return getattr(self, "row_end", self.D) - getattr(self, "row_begin", 0)
+
     def apply(self, y, x, nvec=1):
+        n = max(0, int(nvec))
+        _vec(x, self.D * n, "Plan.apply x")
+        _vec(y, self._rows() * n, "Plan.apply y")
         return mf_apply(self.handle, y, x, nvec)
 
     def cheb_propagate(self, psi, nvec, dt, order=0):
+        _vec(psi, self.D * max(0, int(nvec)), "Plan.cheb_propagate psi")
         return mf_cheb_propagate(self.handle, psi, nvec, dt, order)
 
     def cheb_terms(self, dt):
@@ -530,17 +554,27 @@ class Plan:
         return n.value
 
     def rows_cheb_init(self, psi_full, acc, nvec):
-        _check(lib().mf_rows_cheb_init(self.handle, _ptr(psi_full), _ptr(acc), int(nvec)), "mf_rows_cheb_init")
+        n = max(0, int(nvec))
+        _check(lib().mf_rows_cheb_init(self.handle, _vec(psi_full, self.D * n, "rows_cheb_init psi_full"),
+                                       _vec(acc, self._rows() * n, "rows_cheb_init acc"), int(nvec)),
+               "mf_rows_cheb_init")
 
     def rows_cheb_term(self, j, q_full, q_prev, q_next, acc, nvec):
-        _check(lib().mf_rows_cheb_term(self.handle, int(j), _ptr(q_full), _ptr(q_prev), _ptr(q_next), _ptr(acc),
+        n = max(0, int(nvec))
+        rn = self._rows() * n
+        _check(lib().mf_rows_cheb_term(self.handle, int(j), _vec(q_full, self.D * n, "rows_cheb_term q_full"),
+                                       _vec(q_prev, rn, "rows_cheb_term q_prev"),
+                                       _vec(q_next, rn, "rows_cheb_term q_next"), _vec(acc, rn, "rows_cheb_term acc"),
                                        int(nvec)), "mf_rows_cheb_term")
 
     def rows_cheb_final(self, acc, psi_slice, nvec, dt):
-        _check(lib().mf_rows_cheb_final(self.handle, _ptr(acc), _ptr(psi_slice), int(nvec), float(dt)),
+        rn = self._rows() * max(0, int(nvec))
+        _check(lib().mf_rows_cheb_final(self.handle, _vec(acc, rn, "rows_cheb_final acc"),
+                                        _vec(psi_slice, rn, "rows_cheb_final psi_slice"), int(nvec), float(dt)),
                "mf_rows_cheb_final")
 
     def cheb_filter(self, psi, nvec, tau, order=0, normalize=True):
+        _vec(psi, self.D * max(0, int(nvec)), "Plan.cheb_filter psi")
         return mf_cheb_filter(self.handle, psi, nvec, tau, order, normalize)
 
     def cheb_filter_terms(self, tau):

@@ -69,3 +69,20 @@ def test_null_handles_are_invalid(mf):
     assert L.mf_cheb_propagate(None, None, 1, 0.1, 0) == mf.MF_ERR_INVALID
     assert L.mf_plan_destroy(None) == mf.MF_OK
     assert L.mf_sync(None) == mf.MF_ERR_INVALID
+
+
+def test_vector_arguments_are_checked_before_the_library(mf):
+    """The binding hands the kernels bare device addresses, so it refuses
+    what would make them read or write the wrong memory: host tensors, other
+    element types, strided views and tensors too small for rows x nvec."""
+    torch = pytest.importorskip("torch")
+    from paper_2606_31598_gb300 import _vec
+    assert _vec(1234, 10, "raw address") == 1234
+    bad = [torch.zeros(8, dtype=torch.complex128),               # host memory
+           torch.zeros(8, dtype=torch.complex64),                # element type
+           torch.zeros((4, 4), dtype=torch.complex128).t(),      # strided view
+           "not a tensor"]
+    for t in bad:
+        with pytest.raises(mf.MFError) as e:
+            _vec(t, 4, "x")
+        assert e.value.status == mf.MF_ERR_INVALID
