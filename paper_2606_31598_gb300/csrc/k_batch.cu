@@ -253,97 +253,99 @@ extern "C" {
 mf_status mf_batch_create(mf_batch_t* out, int32_t nprob, const int64_t* D, const int32_t* nvec,
                           const uint64_t* seeds, int32_t generator, size_t cache_budget_bytes,
                           const mf_options* opt) {
-  if (!out || nprob < 1 || !D || !nvec || !seeds) return MF_ERR_INVALID;
-  *out = nullptr;
-  mf_options o;
-  if (opt) o = *opt; else mf_options_default(&o);
-  if (o.precision == MF_PREC_BF16X2) return MF_ERR_UNSUPPORTED;
-  for (int32_t i = 0; i < nprob; ++i)
-    if (D[i] < 2 || nvec[i] < 1 || nvec[i] > 16) return MF_ERR_INVALID;
-  mf_batch* b = new (std::nothrow) mf_batch();
-  if (!b) return MF_ERR_OOM;
-  b->gen = generator;
-  b->prec = o.precision;
-  b->user = (cudaStream_t)o.stream;
-  if (cudaSetDevice(o.device) != cudaSuccess ||
-      cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, o.device) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&b->own, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) != cudaSuccess) {
-    batch_release(b);
-    return MF_ERR_CUDA;
-  }
-  // cache budget shared in proportion to each problem's full canonical cache
-  const double eb = o.precision == MF_PREC_FP64 ? 16.0 : 8.0;
-  double total_full = 0.0;
-  for (int32_t i = 0; i < nprob; ++i) total_full += eb * (double)D[i] * (double)D[i] / 2.0;
-  b->offsets.push_back(0);
-  for (int32_t i = 0; i < nprob; ++i) {
-    mf_options oi = o;
-    oi.nvec_hint = nvec[i];
-    oi.stream = b->own;
-    oi.hermitian_reuse = 0;  // the batched kernel writes one row-owner slot per row
-    oi.row_begin = oi.row_end = 0;
-    const double share = cache_budget_bytes == 0 ? 0.0
-                         : std::min((double)cache_budget_bytes, 1e18) * (eb * (double)D[i] * D[i] / 2.0) / total_full;
-    mf_plan_t p = nullptr;
-    mf_status st = mf_plan_create(&p, D[i], D[i], generator, seeds[i], 0, (size_t)share, &oi);
-    if (st != MF_OK && st != MF_WARN_DENSE_WORK) {
+  return guard([&]() -> mf_status {
+    if (!out || nprob < 1 || !D || !nvec || !seeds) return MF_ERR_INVALID;
+    *out = nullptr;
+    mf_options o;
+    if (opt) o = *opt; else mf_options_default(&o);
+    if (o.precision == MF_PREC_BF16X2) return MF_ERR_UNSUPPORTED;
+    for (int32_t i = 0; i < nprob; ++i)
+      if (D[i] < 2 || nvec[i] < 1 || nvec[i] > 16) return MF_ERR_INVALID;
+    mf_batch* b = new (std::nothrow) mf_batch();
+    if (!b) return MF_ERR_OOM;
+    b->gen = generator;
+    b->prec = o.precision;
+    b->user = (cudaStream_t)o.stream;
+    if (cudaSetDevice(o.device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, o.device) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&b->own, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) != cudaSuccess) {
       batch_release(b);
-      return st;
+      return MF_ERR_CUDA;
     }
-    b->plans.push_back(p);
-    if ((st = plan_workspace(p->p, std::max<int64_t>(2, nvec[i]))) != MF_OK || (st = plan_bounds(p->p)) != MF_OK) {
+    // cache budget shared in proportion to each problem's full canonical cache
+    const double eb = o.precision == MF_PREC_FP64 ? 16.0 : 8.0;
+    double total_full = 0.0;
+    for (int32_t i = 0; i < nprob; ++i) total_full += eb * (double)D[i] * (double)D[i] / 2.0;
+    b->offsets.push_back(0);
+    for (int32_t i = 0; i < nprob; ++i) {
+      mf_options oi = o;
+      oi.nvec_hint = nvec[i];
+      oi.stream = b->own;
+      oi.hermitian_reuse = 0;  // the batched kernel writes one row-owner slot per row
+      oi.row_begin = oi.row_end = 0;
+      const double share = cache_budget_bytes == 0 ? 0.0
+                           : std::min((double)cache_budget_bytes, 1e18) * (eb * (double)D[i] * D[i] / 2.0) / total_full;
+      mf_plan_t p = nullptr;
+      mf_status st = mf_plan_create(&p, D[i], D[i], generator, seeds[i], 0, (size_t)share, &oi);
+      if (st != MF_OK && st != MF_WARN_DENSE_WORK) {
+        batch_release(b);
+        return st;
+      }
+      b->plans.push_back(p);
+      if ((st = plan_workspace(p->p, std::max<int64_t>(2, nvec[i]))) != MF_OK || (st = plan_bounds(p->p)) != MF_OK) {
+        batch_release(b);
+        return st;
+      }
+      b->offsets.push_back(b->offsets.back() + D[i] * nvec[i]);
+      b->max_elems = std::max<int64_t>(b->max_elems, D[i] * rows_nvec_bucket(std::max<int32_t>(2, nvec[i])));
+    }
+    // work list: every (problem, row tile), most expensive first
+    std::vector<BatchItem> items;
+    std::vector<double> cost;
+    for (int32_t i = 0; i < nprob; ++i) {
+      const Plan& P = b->plans[i]->p;
+      for (int64_t t = 0; t < P.ntile; ++t) {
+        items.push_back(BatchItem{i, (int32_t)t});
+        cost.push_back((double)P.D * (double)rows_nvec_bucket(std::max<int32_t>(2, nvec[i])));
+      }
+    }
+    std::vector<size_t> idx(items.size());
+    for (size_t k = 0; k < idx.size(); ++k) idx[k] = k;
+    std::stable_sort(idx.begin(), idx.end(), [&](size_t a, size_t c) { return cost[a] > cost[c]; });
+    std::vector<BatchItem> sorted;
+    for (size_t k : idx) sorted.push_back(items[k]);
+    b->n_items = (int)sorted.size();
+    b->smem = o.precision == MF_PREC_FP64 ? rows_smem_bytes_async<double, 16>() : rows_smem_bytes_async<float, 16>();
+    cudaError_t e = cudaMalloc((void**)&b->d_items, sorted.size() * sizeof(BatchItem));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(b->d_items, sorted.data(), sorted.size() * sizeof(BatchItem), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_counter, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_probs, (size_t)nprob * sizeof(BatchProb));
+    // persistent grid: resident CTAs per SM x SMs
+    int per_sm = 0;
+    if (e == cudaSuccess) {
+      if (o.precision == MF_PREC_FP64) {
+        auto k = generator == MF_GEN_PHILOX_GUE ? k_batch_apply<double, MF_GEN_PHILOX_GUE>
+                                                : k_batch_apply<double, MF_GEN_SINC_DVR_HO>;
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, b->smem);
+      } else {
+        auto k = generator == MF_GEN_PHILOX_GUE ? k_batch_apply<float, MF_GEN_PHILOX_GUE>
+                                                : k_batch_apply<float, MF_GEN_SINC_DVR_HO>;
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, b->smem);
+      }
+    }
+    if (e != cudaSuccess) {
       batch_release(b);
-      return st;
+      return e == cudaErrorMemoryAllocation ? MF_ERR_OOM : MF_ERR_CUDA;
     }
-    b->offsets.push_back(b->offsets.back() + D[i] * nvec[i]);
-    b->max_elems = std::max<int64_t>(b->max_elems, D[i] * rows_nvec_bucket(std::max<int32_t>(2, nvec[i])));
-  }
-  // work list: every (problem, row tile), most expensive first
-  std::vector<BatchItem> items;
-  std::vector<double> cost;
-  for (int32_t i = 0; i < nprob; ++i) {
-    const Plan& P = b->plans[i]->p;
-    for (int64_t t = 0; t < P.ntile; ++t) {
-      items.push_back(BatchItem{i, (int32_t)t});
-      cost.push_back((double)P.D * (double)rows_nvec_bucket(std::max<int32_t>(2, nvec[i])));
-    }
-  }
-  std::vector<size_t> idx(items.size());
-  for (size_t k = 0; k < idx.size(); ++k) idx[k] = k;
-  std::stable_sort(idx.begin(), idx.end(), [&](size_t a, size_t c) { return cost[a] > cost[c]; });
-  std::vector<BatchItem> sorted;
-  for (size_t k : idx) sorted.push_back(items[k]);
-  b->n_items = (int)sorted.size();
-  b->smem = o.precision == MF_PREC_FP64 ? rows_smem_bytes_async<double, 16>() : rows_smem_bytes_async<float, 16>();
-  cudaError_t e = cudaMalloc((void**)&b->d_items, sorted.size() * sizeof(BatchItem));
-  if (e == cudaSuccess)
-    e = cudaMemcpy(b->d_items, sorted.data(), sorted.size() * sizeof(BatchItem), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_counter, sizeof(int));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_probs, (size_t)nprob * sizeof(BatchProb));
-  // persistent grid: resident CTAs per SM x SMs
-  int per_sm = 0;
-  if (e == cudaSuccess) {
-    if (o.precision == MF_PREC_FP64) {
-      auto k = generator == MF_GEN_PHILOX_GUE ? k_batch_apply<double, MF_GEN_PHILOX_GUE>
-                                              : k_batch_apply<double, MF_GEN_SINC_DVR_HO>;
-      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
-      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, b->smem);
-    } else {
-      auto k = generator == MF_GEN_PHILOX_GUE ? k_batch_apply<float, MF_GEN_PHILOX_GUE>
-                                              : k_batch_apply<float, MF_GEN_SINC_DVR_HO>;
-      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
-      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, b->smem);
-    }
-  }
-  if (e != cudaSuccess) {
-    batch_release(b);
-    return e == cudaErrorMemoryAllocation ? MF_ERR_OOM : MF_ERR_CUDA;
-  }
-  b->persist_grid = std::max(1, per_sm) * b->num_sms;
-  *out = b;
-  return MF_OK;
+    b->persist_grid = std::max(1, per_sm) * b->num_sms;
+    *out = b;
+    return MF_OK;
+  });
 }
 
 mf_status mf_batch_destroy(mf_batch_t b) {
@@ -360,91 +362,93 @@ mf_status mf_batch_offsets(mf_batch_t b, int64_t* offsets) {
 }
 
 mf_status mf_batch_propagate(mf_batch_t b, void* psi, double dt, int32_t nsteps, int32_t order, int32_t* nterms_out) {
-  if (!b || !psi || !(dt > 0) || !std::isfinite(dt) || nsteps < 1 || order < 0) return MF_ERR_INVALID;
-  const bool same = b->graph && b->g_dt == dt && b->g_steps == nsteps && b->g_order == order && b->g_psi == psi;
-  if (!same) {
-    // per-problem coefficients for its own R dt; a common term count (the
-    // largest one needed, so every problem meets the tolerance)
-    int32_t nt = order;
-    std::vector<int32_t> need(b->plans.size());
-    for (size_t i = 0; i < b->plans.size(); ++i) {
-      Plan& P = b->plans[i]->p;
-      const double R = 0.5 * (P.emax - P.emin);
-      mf_status st = plan_coefficients(P, R * dt, order, &need[i]);
-      if (st != MF_OK) return st;
-      nt = std::max(nt, need[i]);
-    }
-    if (order == 0) {
+  return guard([&]() -> mf_status {
+    if (!b || !psi || !(dt > 0) || !std::isfinite(dt) || nsteps < 1 || order < 0) return MF_ERR_INVALID;
+    const bool same = b->graph && b->g_dt == dt && b->g_steps == nsteps && b->g_order == order && b->g_psi == psi;
+    if (!same) {
+      // per-problem coefficients for its own R dt; a common term count (the
+      // largest one needed, so every problem meets the tolerance)
+      int32_t nt = order;
+      std::vector<int32_t> need(b->plans.size());
       for (size_t i = 0; i < b->plans.size(); ++i) {
         Plan& P = b->plans[i]->p;
         const double R = 0.5 * (P.emax - P.emin);
-        int32_t dummy = 0;
-        mf_status st = plan_coefficients(P, R * dt, nt, &dummy);
+        mf_status st = plan_coefficients(P, R * dt, order, &need[i]);
         if (st != MF_OK) return st;
+        nt = std::max(nt, need[i]);
       }
+      if (order == 0) {
+        for (size_t i = 0; i < b->plans.size(); ++i) {
+          Plan& P = b->plans[i]->p;
+          const double R = 0.5 * (P.emax - P.emin);
+          int32_t dummy = 0;
+          mf_status st = plan_coefficients(P, R * dt, nt, &dummy);
+          if (st != MF_OK) return st;
+        }
+      }
+      std::vector<BatchProb> probs(b->plans.size());
+      for (size_t i = 0; i < b->plans.size(); ++i) {
+        Plan& P = b->plans[i]->p;
+        BatchProb& q = probs[i];
+        q.D = P.D;
+        q.ntile = P.ntile;
+        q.b = P.b;
+        q.nblk = P.nblk;
+        q.nv = b->offsets[i + 1] - b->offsets[i];
+        q.nv /= P.D;
+        q.nb = rows_nvec_bucket(std::max<int64_t>(2, q.nv));
+        q.seed = P.seed;
+        q.sigma32 = P.sigma32;
+        q.sigma64 = P.sigma64;
+        q.dk = P.dvr;
+        q.xc = P.d_xc;
+        q.part = P.d_part;
+        q.cache = P.pairs_cached > 0 ? P.d_cache : nullptr;
+        q.slot = P.d_pair_slot;
+        q.q[0] = P.d_q[0];
+        q.q[1] = P.d_q[1];
+        q.acc = P.d_q[2];
+        q.psi = (double2*)psi + b->offsets[i];
+        q.J = P.d_J;
+        q.c = 0.5 * (P.emax + P.emin);
+        q.rinv = 1.0 / (0.5 * (P.emax - P.emin));
+        q.ph_r = std::cos(q.c * dt);
+        q.ph_i = -std::sin(q.c * dt);
+      }
+      if (cudaStreamSynchronize(b->own) != cudaSuccess) return MF_ERR_CUDA;
+      if (cudaMemcpy(b->d_probs, probs.data(), probs.size() * sizeof(BatchProb), cudaMemcpyHostToDevice) != cudaSuccess)
+        return MF_ERR_CUDA;
+      // capture the whole propagation once
+      if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+      }
+      cudaGraph_t g = nullptr;
+      if (cudaStreamBeginCapture(b->own, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return MF_ERR_CUDA;
+      cudaError_t e = b->prec == MF_PREC_FP64 ? enqueue_propagation<double>(b, nsteps, nt, b->own)
+                                              : enqueue_propagation<float>(b, nsteps, nt, b->own);
+      cudaError_t e2 = cudaStreamEndCapture(b->own, &g);
+      if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return MF_ERR_CUDA;
+      }
+      e = cudaGraphInstantiate(&b->graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return MF_ERR_CUDA;
+      b->g_dt = dt;
+      b->g_steps = nsteps;
+      b->g_order = order;
+      b->g_psi = psi;
+      b->g_terms = nt;
     }
-    std::vector<BatchProb> probs(b->plans.size());
-    for (size_t i = 0; i < b->plans.size(); ++i) {
-      Plan& P = b->plans[i]->p;
-      BatchProb& q = probs[i];
-      q.D = P.D;
-      q.ntile = P.ntile;
-      q.b = P.b;
-      q.nblk = P.nblk;
-      q.nv = b->offsets[i + 1] - b->offsets[i];
-      q.nv /= P.D;
-      q.nb = rows_nvec_bucket(std::max<int64_t>(2, q.nv));
-      q.seed = P.seed;
-      q.sigma32 = P.sigma32;
-      q.sigma64 = P.sigma64;
-      q.dk = P.dvr;
-      q.xc = P.d_xc;
-      q.part = P.d_part;
-      q.cache = P.pairs_cached > 0 ? P.d_cache : nullptr;
-      q.slot = P.d_pair_slot;
-      q.q[0] = P.d_q[0];
-      q.q[1] = P.d_q[1];
-      q.acc = P.d_q[2];
-      q.psi = (double2*)psi + b->offsets[i];
-      q.J = P.d_J;
-      q.c = 0.5 * (P.emax + P.emin);
-      q.rinv = 1.0 / (0.5 * (P.emax - P.emin));
-      q.ph_r = std::cos(q.c * dt);
-      q.ph_i = -std::sin(q.c * dt);
-    }
-    if (cudaStreamSynchronize(b->own) != cudaSuccess) return MF_ERR_CUDA;
-    if (cudaMemcpy(b->d_probs, probs.data(), probs.size() * sizeof(BatchProb), cudaMemcpyHostToDevice) != cudaSuccess)
+    // order the graph after the caller's stream and the caller's stream after it
+    if (cudaEventRecord(b->ev_in, b->user) != cudaSuccess || cudaStreamWaitEvent(b->own, b->ev_in, 0) != cudaSuccess ||
+        cudaGraphLaunch(b->graph, b->own) != cudaSuccess || cudaEventRecord(b->ev_out, b->own) != cudaSuccess ||
+        cudaStreamWaitEvent(b->user, b->ev_out, 0) != cudaSuccess)
       return MF_ERR_CUDA;
-    // capture the whole propagation once
-    if (b->graph) {
-      cudaGraphExecDestroy(b->graph);
-      b->graph = nullptr;
-    }
-    cudaGraph_t g = nullptr;
-    if (cudaStreamBeginCapture(b->own, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return MF_ERR_CUDA;
-    cudaError_t e = b->prec == MF_PREC_FP64 ? enqueue_propagation<double>(b, nsteps, nt, b->own)
-                                            : enqueue_propagation<float>(b, nsteps, nt, b->own);
-    cudaError_t e2 = cudaStreamEndCapture(b->own, &g);
-    if (e != cudaSuccess || e2 != cudaSuccess) {
-      if (g) cudaGraphDestroy(g);
-      return MF_ERR_CUDA;
-    }
-    e = cudaGraphInstantiate(&b->graph, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) return MF_ERR_CUDA;
-    b->g_dt = dt;
-    b->g_steps = nsteps;
-    b->g_order = order;
-    b->g_psi = psi;
-    b->g_terms = nt;
-  }
-  // order the graph after the caller's stream and the caller's stream after it
-  if (cudaEventRecord(b->ev_in, b->user) != cudaSuccess || cudaStreamWaitEvent(b->own, b->ev_in, 0) != cudaSuccess ||
-      cudaGraphLaunch(b->graph, b->own) != cudaSuccess || cudaEventRecord(b->ev_out, b->own) != cudaSuccess ||
-      cudaStreamWaitEvent(b->user, b->ev_out, 0) != cudaSuccess)
-    return MF_ERR_CUDA;
-  if (nterms_out) *nterms_out = b->g_terms;
-  return MF_OK;
+    if (nterms_out) *nterms_out = b->g_terms;
+    return MF_OK;
+  });
 }
 
 mf_status mf_batch_plan(mf_batch_t b, int32_t i, mf_plan_t* plan) {

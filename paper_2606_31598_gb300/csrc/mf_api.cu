@@ -743,266 +743,274 @@ const char* mf_status_string(mf_status s) {
 
 mf_status mf_plan_create(mf_plan_t* out, int64_t D, int64_t M, int32_t generator, uint64_t seed, int64_t block,
                          size_t cache_budget_bytes, const mf_options* opt) {
-  if (!out) return MF_ERR_INVALID;
-  *out = nullptr;
-  mf_options o;
-  if (opt) o = *opt; else mf_options_default(&o);
-  if (D < 2 || M != D || D > (int64_t)1 << 31) return MF_ERR_INVALID;
-  if (generator != MF_GEN_PHILOX_GUE && generator != MF_GEN_SINC_DVR_HO) return MF_ERR_INVALID;
-  if (o.precision != MF_PREC_FP64 && o.precision != MF_PREC_FP32 && o.precision != MF_PREC_BF16X2)
-    return MF_ERR_INVALID;
-  if (block < 0 || (block > 0 && block % kTile != 0)) return MF_ERR_INVALID;
-  // the FP32 steps of the DVR generator square an exact float(i - j)
-  if (generator == MF_GEN_SINC_DVR_HO && o.precision != MF_PREC_FP64 && D > ((int64_t)1 << 24)) return MF_ERR_INVALID;
-  if (o.storage < MF_STORE_AUTO || o.storage > MF_STORE_FULL) return MF_ERR_INVALID;
-  if (o.planner_mode < MF_PLANNER_ANALYTIC || o.planner_mode > MF_PLANNER_HYBRID) return MF_ERR_INVALID;
-  if (!(o.cheb_tol > 0) || o.lanczos_m < 2 || !(o.alpha_safety > 0 && o.alpha_safety <= 1)) return MF_ERR_INVALID;
-  if (o.nvec_hint < 1 || o.nvec_hint > 64 || o.autotune_k < 1 || o.autotune_repeats < 1 || o.autotune_warmup < 0)
-    return MF_ERR_INVALID;
-  if (o.hermitian_reuse < -1 || o.hermitian_reuse > 1) return MF_ERR_INVALID;
-  if ((o.planner_mode == MF_PLANNER_LEARNED || o.planner_mode == MF_PLANNER_HYBRID) && !o.model)
-    return MF_ERR_INVALID;
-
-  // row-distributed plan: one explicit candidate on the slice's rows
-  if (o.row_begin != 0 || o.row_end != 0) {
-    if (o.row_begin < 0 || o.row_end <= o.row_begin || o.row_end > D || o.row_begin % kTile != 0 ||
-        (o.row_end % kTile != 0 && o.row_end != D))
+  return guard([&]() -> mf_status {
+    if (!out) return MF_ERR_INVALID;
+    *out = nullptr;
+    mf_options o;
+    if (opt) o = *opt; else mf_options_default(&o);
+    if (D < 2 || M != D || D > (int64_t)1 << 31) return MF_ERR_INVALID;
+    if (generator != MF_GEN_PHILOX_GUE && generator != MF_GEN_SINC_DVR_HO) return MF_ERR_INVALID;
+    if (o.precision != MF_PREC_FP64 && o.precision != MF_PREC_FP32 && o.precision != MF_PREC_BF16X2)
       return MF_ERR_INVALID;
-    if (o.precision == MF_PREC_BF16X2) return MF_ERR_UNSUPPORTED;
+    if (block < 0 || (block > 0 && block % kTile != 0)) return MF_ERR_INVALID;
+    // the FP32 steps of the DVR generator square an exact float(i - j)
+    if (generator == MF_GEN_SINC_DVR_HO && o.precision != MF_PREC_FP64 && D > ((int64_t)1 << 24)) return MF_ERR_INVALID;
+    if (o.storage < MF_STORE_AUTO || o.storage > MF_STORE_FULL) return MF_ERR_INVALID;
+    if (o.planner_mode < MF_PLANNER_ANALYTIC || o.planner_mode > MF_PLANNER_HYBRID) return MF_ERR_INVALID;
+    if (!(o.cheb_tol > 0) || o.lanczos_m < 2 || !(o.alpha_safety > 0 && o.alpha_safety <= 1)) return MF_ERR_INVALID;
+    if (o.nvec_hint < 1 || o.nvec_hint > 64 || o.autotune_k < 1 || o.autotune_repeats < 1 || o.autotune_warmup < 0)
+      return MF_ERR_INVALID;
+    if (o.hermitian_reuse < -1 || o.hermitian_reuse > 1) return MF_ERR_INVALID;
+    if ((o.planner_mode == MF_PLANNER_LEARNED || o.planner_mode == MF_PLANNER_HYBRID) && !o.model)
+      return MF_ERR_INVALID;
+
+    // row-distributed plan: one explicit candidate on the slice's rows
+    if (o.row_begin != 0 || o.row_end != 0) {
+      if (o.row_begin < 0 || o.row_end <= o.row_begin || o.row_end > D || o.row_begin % kTile != 0 ||
+          (o.row_end % kTile != 0 && o.row_end != D))
+        return MF_ERR_INVALID;
+      if (o.precision == MF_PREC_BF16X2) return MF_ERR_UNSUPPORTED;
+      const int64_t Dt = (D + kTile - 1) / kTile * kTile;
+      const int64_t b = block > 0 ? block : std::min<int64_t>(2048, Dt);
+      mf_options os = o;
+      if (os.storage == MF_STORE_AUTO) os.storage = cache_budget_bytes > 0 ? MF_STORE_PARTIAL : MF_STORE_PROCEDURAL;
+      os.planner_mode = MF_PLANNER_ANALYTIC;
+      return create_fixed(out, D, generator, seed, b, cache_budget_bytes, os);
+    }
+
+    // one explicit candidate: no planning
+    if (block > 0 && o.storage != MF_STORE_AUTO && o.planner_mode == MF_PLANNER_ANALYTIC)
+      return create_fixed(out, D, generator, seed, block, cache_budget_bytes, o);
+
+    DeviceGuard guard(o.device);
+    if (cudaSetDevice(o.device) != cudaSuccess) return MF_ERR_CUDA;
+    int num_sms = 0;
+    if (cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, o.device) != cudaSuccess) return MF_ERR_CUDA;
+    size_t mfree = 0, mtotal = 0;
+    if (cudaMemGetInfo(&mfree, &mtotal) != cudaSuccess) return MF_ERR_CUDA;
+    const double budget = cache_budget_bytes == SIZE_MAX ? o.f_cache * (double)mfree : (double)cache_budget_bytes;
+    const size_t eb = compute_elem_bytes(o.precision);
+
+    // candidate block sizes (Sec. IV.F) and storage modes (Sec. IV.G)
     const int64_t Dt = (D + kTile - 1) / kTile * kTile;
-    const int64_t b = block > 0 ? block : std::min<int64_t>(2048, Dt);
-    mf_options os = o;
-    if (os.storage == MF_STORE_AUTO) os.storage = cache_budget_bytes > 0 ? MF_STORE_PARTIAL : MF_STORE_PROCEDURAL;
-    os.planner_mode = MF_PLANNER_ANALYTIC;
-    return create_fixed(out, D, generator, seed, b, cache_budget_bytes, os);
-  }
+    std::vector<int64_t> blocks;
+    if (block > 0) blocks.push_back(std::min(block, Dt));
+    else
+      for (int64_t b = 256; b <= 4096; b *= 2)
+        if (b <= Dt) blocks.push_back(b);
+    if (blocks.empty()) blocks.push_back(Dt);
+    std::vector<int32_t> stores;
+    if (o.storage != MF_STORE_AUTO) stores.push_back(o.storage);
+    else stores = {MF_STORE_PROCEDURAL, MF_STORE_PARTIAL, MF_STORE_FULL};
 
-  // one explicit candidate: no planning
-  if (block > 0 && o.storage != MF_STORE_AUTO && o.planner_mode == MF_PLANNER_ANALYTIC)
-    return create_fixed(out, D, generator, seed, block, cache_budget_bytes, o);
-
-  DeviceGuard guard(o.device);
-  if (cudaSetDevice(o.device) != cudaSuccess) return MF_ERR_CUDA;
-  int num_sms = 0;
-  if (cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, o.device) != cudaSuccess) return MF_ERR_CUDA;
-  size_t mfree = 0, mtotal = 0;
-  if (cudaMemGetInfo(&mfree, &mtotal) != cudaSuccess) return MF_ERR_CUDA;
-  const double budget = cache_budget_bytes == SIZE_MAX ? o.f_cache * (double)mfree : (double)cache_budget_bytes;
-  const size_t eb = compute_elem_bytes(o.precision);
-
-  // candidate block sizes (Sec. IV.F) and storage modes (Sec. IV.G)
-  const int64_t Dt = (D + kTile - 1) / kTile * kTile;
-  std::vector<int64_t> blocks;
-  if (block > 0) blocks.push_back(std::min(block, Dt));
-  else
-    for (int64_t b = 256; b <= 4096; b *= 2)
-      if (b <= Dt) blocks.push_back(b);
-  if (blocks.empty()) blocks.push_back(Dt);
-  std::vector<int32_t> stores;
-  if (o.storage != MF_STORE_AUTO) stores.push_back(o.storage);
-  else stores = {MF_STORE_PROCEDURAL, MF_STORE_PARTIAL, MF_STORE_FULL};
-
-  mf_problem pr{D, D, o.nvec_hint, 1, 1, (double)eb, (double)mfree, 1};
-  const mf_device_model dm = device_model(o.precision, generator, num_sms);
-  struct Ranked {
-    mf_candidate c;
-    mf_estimate e;
-  };
-  std::vector<Ranked> ranked;
-  for (int64_t b : blocks)
-    for (int32_t st : stores) {
-      mf_candidate c{b, st, -1, 1, 1, 4};
-      mf_estimate e{};
-      planner_estimate(pr, c, dm, o.alpha_safety, budget, e);
-      if (st == MF_STORE_PARTIAL && (e.pairs_cached == 0 || e.pairs_cached == e.n_pair)) continue;
-      if (st == MF_STORE_FULL && (double)e.n_pair * e.M_block > budget) continue;
-      if (!e.feasible && st != MF_STORE_PROCEDURAL) continue;
-      ranked.push_back({c, e});
-    }
-  if (ranked.empty()) return MF_ERR_OOM;
-  std::stable_sort(ranked.begin(), ranked.end(),
-                   [](const Ranked& a, const Ranked& b) { return a.e.S_model < b.e.S_model; });
-
-  auto budget_for = [&](const Ranked& r) -> size_t {
-    if (r.c.storage == MF_STORE_PROCEDURAL) return 0;
-    return (size_t)((double)r.e.pairs_cached * r.e.M_block);
-  };
-  auto build = [&](const Ranked& r, mf_plan_t* h) {
-    mf_options oc = o;
-    oc.storage = r.c.storage;
-    return create_fixed(h, D, generator, seed, r.c.block, budget_for(r), oc);
-  };
-
-  if (o.planner_mode == MF_PLANNER_ANALYTIC) {
-    mf_status st = MF_ERR_OOM;
-    for (const Ranked& r : ranked) {  // best feasible by the model
-      st = build(r, out);
-      if (st == MF_OK || st == MF_WARN_DENSE_WORK) {
-        (*out)->p.s_model = r.e.S_model;
-        (*out)->p.trials.push_back(trial_json((*out)->p, pr, r.c, r.e, -1.0, budget, (double)mtotal));
-        return st;
+    mf_problem pr{D, D, o.nvec_hint, 1, 1, (double)eb, (double)mfree, 1};
+    const mf_device_model dm = device_model(o.precision, generator, num_sms);
+    struct Ranked {
+      mf_candidate c;
+      mf_estimate e;
+    };
+    std::vector<Ranked> ranked;
+    for (int64_t b : blocks)
+      for (int32_t st : stores) {
+        mf_candidate c{b, st, -1, 1, 1, 4};
+        mf_estimate e{};
+        planner_estimate(pr, c, dm, o.alpha_safety, budget, e);
+        if (st == MF_STORE_PARTIAL && (e.pairs_cached == 0 || e.pairs_cached == e.n_pair)) continue;
+        if (st == MF_STORE_FULL && (double)e.n_pair * e.M_block > budget) continue;
+        if (!e.feasible && st != MF_STORE_PROCEDURAL) continue;
+        ranked.push_back({c, e});
       }
-    }
-    return st;
-  }
+    if (ranked.empty()) return MF_ERR_OOM;
+    std::stable_sort(ranked.begin(), ranked.end(),
+                     [](const Ranked& a, const Ranked& b) { return a.e.S_model < b.e.S_model; });
 
-  // Algorithm 2: measure the K_bench best candidates, keep the fastest job
-  // score S_bench = W t_mv (Eq. bench_score, Eq. bench_argmin); Algorithm 3
-  // (learned/hybrid) reorders the candidates by the surrogate first.
-  if (o.planner_mode == MF_PLANNER_LEARNED || o.planner_mode == MF_PLANNER_HYBRID) {
-    std::vector<double> pred(ranked.size(), 0.0);
-    for (size_t i = 0; i < ranked.size(); ++i) {
-      double t = 0.0;
-      mf_status st = surrogate_predict(o.model, generator, o.precision, pr, ranked[i].c, ranked[i].e, budget,
-                                       (double)mtotal, num_sms, &t);
-      if (st != MF_OK) return st;
-      pred[i] = t * (double)ranked[i].e.waves;
-    }
-    std::vector<size_t> idx(ranked.size());
-    for (size_t i = 0; i < idx.size(); ++i) idx[i] = i;
-    std::stable_sort(idx.begin(), idx.end(), [&](size_t a, size_t b) { return pred[a] < pred[b]; });
-    std::vector<Ranked> re;
-    for (size_t i : idx) re.push_back(ranked[i]);
-    ranked.swap(re);
-    if (o.planner_mode == MF_PLANNER_LEARNED) {
+    auto budget_for = [&](const Ranked& r) -> size_t {
+      if (r.c.storage == MF_STORE_PROCEDURAL) return 0;
+      return (size_t)((double)r.e.pairs_cached * r.e.M_block);
+    };
+    auto build = [&](const Ranked& r, mf_plan_t* h) {
+      mf_options oc = o;
+      oc.storage = r.c.storage;
+      return create_fixed(h, D, generator, seed, r.c.block, budget_for(r), oc);
+    };
+
+    if (o.planner_mode == MF_PLANNER_ANALYTIC) {
       mf_status st = MF_ERR_OOM;
-      for (const Ranked& r : ranked) {
+      for (const Ranked& r : ranked) {  // best feasible by the model
         st = build(r, out);
         if (st == MF_OK || st == MF_WARN_DENSE_WORK) {
-          (*out)->p.planner_used = MF_PLANNER_LEARNED;
           (*out)->p.s_model = r.e.S_model;
+          (*out)->p.trials.push_back(trial_json((*out)->p, pr, r.c, r.e, -1.0, budget, (double)mtotal));
           return st;
         }
       }
       return st;
     }
-  }
-  const size_t K = std::min<size_t>((size_t)o.autotune_k, ranked.size());
-  mf_plan_t best = nullptr;
-  mf_status best_st = MF_ERR_OOM;
-  double best_score = 1e300;
-  std::vector<std::string> log;
-  for (size_t i = 0; i < K; ++i) {
-    mf_plan_t h = nullptr;
-    mf_status st = build(ranked[i], &h);
-    if (st != MF_OK && st != MF_WARN_DENSE_WORK) continue;
-    double t = 0.0;
-    mf_status ms = measure_plan(h->p, o.nvec_hint, o.autotune_warmup, o.autotune_repeats, &t);
-    if (ms != MF_OK) {
-      mf_plan_destroy(h);
-      if (ms == MF_ERR_CUDA) return ms;
-      continue;
+
+    // Algorithm 2: measure the K_bench best candidates, keep the fastest job
+    // score S_bench = W t_mv (Eq. bench_score, Eq. bench_argmin); Algorithm 3
+    // (learned/hybrid) reorders the candidates by the surrogate first.
+    if (o.planner_mode == MF_PLANNER_LEARNED || o.planner_mode == MF_PLANNER_HYBRID) {
+      std::vector<double> pred(ranked.size(), 0.0);
+      for (size_t i = 0; i < ranked.size(); ++i) {
+        double t = 0.0;
+        mf_status st = surrogate_predict(o.model, generator, o.precision, pr, ranked[i].c, ranked[i].e, budget,
+                                         (double)mtotal, num_sms, &t);
+        if (st != MF_OK) return st;
+        pred[i] = t * (double)ranked[i].e.waves;
+      }
+      std::vector<size_t> idx(ranked.size());
+      for (size_t i = 0; i < idx.size(); ++i) idx[i] = i;
+      std::stable_sort(idx.begin(), idx.end(), [&](size_t a, size_t b) { return pred[a] < pred[b]; });
+      std::vector<Ranked> re;
+      for (size_t i : idx) re.push_back(ranked[i]);
+      ranked.swap(re);
+      if (o.planner_mode == MF_PLANNER_LEARNED) {
+        mf_status st = MF_ERR_OOM;
+        for (const Ranked& r : ranked) {
+          st = build(r, out);
+          if (st == MF_OK || st == MF_WARN_DENSE_WORK) {
+            (*out)->p.planner_used = MF_PLANNER_LEARNED;
+            (*out)->p.s_model = r.e.S_model;
+            return st;
+          }
+        }
+        return st;
+      }
     }
-    log.push_back(trial_json(h->p, pr, ranked[i].c, ranked[i].e, t, budget, (double)mtotal));
-    const double score = (double)ranked[i].e.waves * t;
-    if (score < best_score) {
-      if (best) mf_plan_destroy(best);
-      best = h;
-      best_st = st;
-      best_score = score;
-      best->p.s_model = ranked[i].e.S_model;
-      best->p.t_measured = t;
-    } else {
-      mf_plan_destroy(h);
+    const size_t K = std::min<size_t>((size_t)o.autotune_k, ranked.size());
+    mf_plan_t best = nullptr;
+    mf_status best_st = MF_ERR_OOM;
+    double best_score = 1e300;
+    std::vector<std::string> log;
+    for (size_t i = 0; i < K; ++i) {
+      mf_plan_t h = nullptr;
+      mf_status st = build(ranked[i], &h);
+      if (st != MF_OK && st != MF_WARN_DENSE_WORK) continue;
+      double t = 0.0;
+      mf_status ms = measure_plan(h->p, o.nvec_hint, o.autotune_warmup, o.autotune_repeats, &t);
+      if (ms != MF_OK) {
+        mf_plan_destroy(h);
+        if (ms == MF_ERR_CUDA) return ms;
+        continue;
+      }
+      log.push_back(trial_json(h->p, pr, ranked[i].c, ranked[i].e, t, budget, (double)mtotal));
+      const double score = (double)ranked[i].e.waves * t;
+      if (score < best_score) {
+        if (best) mf_plan_destroy(best);
+        best = h;
+        best_st = st;
+        best_score = score;
+        best->p.s_model = ranked[i].e.S_model;
+        best->p.t_measured = t;
+      } else {
+        mf_plan_destroy(h);
+      }
     }
-  }
-  if (!best) return MF_ERR_OOM;
-  best->p.trials = log;
-  best->p.planner_used = o.planner_mode;
-  *out = best;
-  return best_st;
+    if (!best) return MF_ERR_OOM;
+    best->p.trials = log;
+    best->p.planner_used = o.planner_mode;
+    *out = best;
+    return best_st;
+  });
 }
 
 mf_status mf_plan_trials(mf_plan_t h, char* buf, size_t len, size_t* needed) {
-  if (!h) return MF_ERR_INVALID;
-  std::string all;
-  for (const auto& t : h->p.trials) {
-    all += t;
-    all += "\n";
-  }
-  if (needed) *needed = all.size() + 1;
-  if (!buf) return MF_OK;
-  if (len == 0) return MF_ERR_INVALID;
-  std::strncpy(buf, all.c_str(), len - 1);
-  buf[len - 1] = '\0';
-  return all.size() + 1 <= len ? MF_OK : MF_ERR_INVALID;
+  return guard([&]() -> mf_status {
+    if (!h) return MF_ERR_INVALID;
+    std::string all;
+    for (const auto& t : h->p.trials) {
+      all += t;
+      all += "\n";
+    }
+    if (needed) *needed = all.size() + 1;
+    if (!buf) return MF_OK;
+    if (len == 0) return MF_ERR_INVALID;
+    std::strncpy(buf, all.c_str(), len - 1);
+    buf[len - 1] = '\0';
+    return all.size() + 1 <= len ? MF_OK : MF_ERR_INVALID;
+  });
 }
 
 mf_status mf_external_create(mf_plan_t* out, int64_t D, int64_t block, const void* blocks,
                              size_t cache_budget_bytes, const mf_options* opt) {
-  if (!out) return MF_ERR_INVALID;
-  *out = nullptr;
-  mf_options o;
-  if (opt) o = *opt; else mf_options_default(&o);
-  if (D < 2 || D > (int64_t)1 << 31 || !blocks || block < kTile || block % kTile != 0) return MF_ERR_INVALID;
-  if ((uintptr_t)blocks % 16 != 0) return MF_ERR_INVALID;  // the kernels read 16-byte words
-  if (o.precision != MF_PREC_FP64 && o.precision != MF_PREC_FP32 && o.precision != MF_PREC_BF16X2)
-    return MF_ERR_INVALID;
-  if (!(o.cheb_tol > 0) || o.lanczos_m < 2 || !(o.alpha_safety > 0 && o.alpha_safety <= 1)) return MF_ERR_INVALID;
-  if (o.nvec_hint < 1 || o.nvec_hint > 64) return MF_ERR_INVALID;
-  if (o.hermitian_reuse < -1 || o.hermitian_reuse > 1) return MF_ERR_INVALID;
-  // block larger than D rounded to the tile: the stored blocks would be
-  // smaller than b x b
-  if (block > (D + kTile - 1) / kTile * kTile) return MF_ERR_INVALID;
-  // P_cache from the budget (Eq. partial_cache_pairs); STORE_FULL insists
-  if (o.storage != MF_STORE_FULL) o.storage = MF_STORE_PARTIAL;
-  o.row_begin = o.row_end = 0;
-  o.planner_mode = MF_PLANNER_ANALYTIC;
-  return create_fixed(out, D, MF_GEN_EXTERNAL, 0, block, cache_budget_bytes, o, blocks);
+  return guard([&]() -> mf_status {
+    if (!out) return MF_ERR_INVALID;
+    *out = nullptr;
+    mf_options o;
+    if (opt) o = *opt; else mf_options_default(&o);
+    if (D < 2 || D > (int64_t)1 << 31 || !blocks || block < kTile || block % kTile != 0) return MF_ERR_INVALID;
+    if ((uintptr_t)blocks % 16 != 0) return MF_ERR_INVALID;  // the kernels read 16-byte words
+    if (o.precision != MF_PREC_FP64 && o.precision != MF_PREC_FP32 && o.precision != MF_PREC_BF16X2)
+      return MF_ERR_INVALID;
+    if (!(o.cheb_tol > 0) || o.lanczos_m < 2 || !(o.alpha_safety > 0 && o.alpha_safety <= 1)) return MF_ERR_INVALID;
+    if (o.nvec_hint < 1 || o.nvec_hint > 64) return MF_ERR_INVALID;
+    if (o.hermitian_reuse < -1 || o.hermitian_reuse > 1) return MF_ERR_INVALID;
+    // block larger than D rounded to the tile: the stored blocks would be
+    // smaller than b x b
+    if (block > (D + kTile - 1) / kTile * kTile) return MF_ERR_INVALID;
+    // P_cache from the budget (Eq. partial_cache_pairs); STORE_FULL insists
+    if (o.storage != MF_STORE_FULL) o.storage = MF_STORE_PARTIAL;
+    o.row_begin = o.row_end = 0;
+    o.planner_mode = MF_PLANNER_ANALYTIC;
+    return create_fixed(out, D, MF_GEN_EXTERNAL, 0, block, cache_budget_bytes, o, blocks);
+  });
 }
 
 mf_status mf_sysbath_create(mf_plan_t* out, int64_t d_S, int64_t d_B, int32_t n_int, const uint64_t* seeds,
                             const void* H_S, const void* A, double g, const mf_options* opt) {
-  if (!out) return MF_ERR_INVALID;
-  *out = nullptr;
-  mf_options o;
-  if (opt) o = *opt; else mf_options_default(&o);
-  if (d_S < 1 || d_S > 64 || d_B < 2 || d_B > (int64_t)1 << 31 || n_int < 0 || n_int > 15 || !seeds || !H_S ||
-      (n_int > 0 && !A) || !std::isfinite(g))
-    return MF_ERR_INVALID;
-  if (o.precision == MF_PREC_BF16X2) return MF_ERR_UNSUPPORTED;
-  if (o.precision != MF_PREC_FP64 && o.precision != MF_PREC_FP32) return MF_ERR_INVALID;
-  if (!(o.cheb_tol > 0) || o.lanczos_m < 2 || !(o.alpha_safety > 0 && o.alpha_safety <= 1)) return MF_ERR_INVALID;
-  if (o.hermitian_reuse < -1 || o.hermitian_reuse > 1) return MF_ERR_INVALID;
-  // the bath operators are generated on demand (procedural storage)
-  o.storage = MF_STORE_PROCEDURAL;
-  o.row_begin = o.row_end = 0;
-  o.planner_mode = MF_PLANNER_ANALYTIC;
-  o.nvec_hint = (int32_t)std::max<int64_t>(2, d_S);
-  const int64_t Dt = (d_B + kTile - 1) / kTile * kTile;
-  mf_status st = create_fixed(out, d_B, MF_GEN_PHILOX_GUE, seeds[0], std::min<int64_t>(1024, Dt), 0, o);
-  if (st != MF_OK) return st;
-  Plan& p = (*out)->p;
-  DeviceGuard guard(p.device);
-  const int nop = 1 + n_int;
-  std::vector<double2> M((size_t)nop * d_S * d_S, make_double2(0.0, 0.0));
-  for (int64_t v = 0; v < d_S; ++v) M[(size_t)(v * d_S + v)] = make_double2(1.0, 0.0);
-  const double2* Ah = (const double2*)A;
-  for (int a = 0; a < n_int; ++a)
-    for (int64_t e = 0; e < d_S * d_S; ++e) {
-      const double2 x = Ah[(size_t)a * d_S * d_S + e];
-      M[(size_t)(a + 1) * d_S * d_S + e] = make_double2(g * x.x, g * x.y);
-    }
-  auto fail = [&](mf_status s) {
-    mf_plan_destroy(*out);
+  return guard([&]() -> mf_status {
+    if (!out) return MF_ERR_INVALID;
     *out = nullptr;
-    return s;
-  };
-  if (cudaMalloc((void**)&p.d_sb_seeds, nop * sizeof(uint64_t)) != cudaSuccess ||
-      cudaMalloc((void**)&p.d_sb_M, M.size() * sizeof(double2)) != cudaSuccess ||
-      cudaMalloc((void**)&p.d_sb_HS, (size_t)d_S * d_S * sizeof(double2)) != cudaSuccess)
-    return fail(MF_ERR_OOM);
-  if (cudaMemcpy(p.d_sb_seeds, seeds, nop * sizeof(uint64_t), cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(p.d_sb_M, M.data(), M.size() * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(p.d_sb_HS, H_S, (size_t)d_S * d_S * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess)
-    return fail(MF_ERR_CUDA);
-  p.sb_nop = nop;
-  p.sb_dS = (int32_t)d_S;
-  p.have_bounds = false;
-  // dense-work estimate of the composite: n_op bath operators per product
-  p.w_hpsi = (double)nop * (double)d_B * (double)d_B;
-  p.dense_warn = p.w_hpsi > o.dense_work_limit;
-  return MF_OK;
+    mf_options o;
+    if (opt) o = *opt; else mf_options_default(&o);
+    if (d_S < 1 || d_S > 64 || d_B < 2 || d_B > (int64_t)1 << 31 || n_int < 0 || n_int > 15 || !seeds || !H_S ||
+        (n_int > 0 && !A) || !std::isfinite(g))
+      return MF_ERR_INVALID;
+    if (o.precision == MF_PREC_BF16X2) return MF_ERR_UNSUPPORTED;
+    if (o.precision != MF_PREC_FP64 && o.precision != MF_PREC_FP32) return MF_ERR_INVALID;
+    if (!(o.cheb_tol > 0) || o.lanczos_m < 2 || !(o.alpha_safety > 0 && o.alpha_safety <= 1)) return MF_ERR_INVALID;
+    if (o.hermitian_reuse < -1 || o.hermitian_reuse > 1) return MF_ERR_INVALID;
+    // the bath operators are generated on demand (procedural storage)
+    o.storage = MF_STORE_PROCEDURAL;
+    o.row_begin = o.row_end = 0;
+    o.planner_mode = MF_PLANNER_ANALYTIC;
+    o.nvec_hint = (int32_t)std::max<int64_t>(2, d_S);
+    const int64_t Dt = (d_B + kTile - 1) / kTile * kTile;
+    mf_status st = create_fixed(out, d_B, MF_GEN_PHILOX_GUE, seeds[0], std::min<int64_t>(1024, Dt), 0, o);
+    if (st != MF_OK) return st;
+    Plan& p = (*out)->p;
+    DeviceGuard guard(p.device);
+    const int nop = 1 + n_int;
+    std::vector<double2> M((size_t)nop * d_S * d_S, make_double2(0.0, 0.0));
+    for (int64_t v = 0; v < d_S; ++v) M[(size_t)(v * d_S + v)] = make_double2(1.0, 0.0);
+    const double2* Ah = (const double2*)A;
+    for (int a = 0; a < n_int; ++a)
+      for (int64_t e = 0; e < d_S * d_S; ++e) {
+        const double2 x = Ah[(size_t)a * d_S * d_S + e];
+        M[(size_t)(a + 1) * d_S * d_S + e] = make_double2(g * x.x, g * x.y);
+      }
+    auto fail = [&](mf_status s) {
+      mf_plan_destroy(*out);
+      *out = nullptr;
+      return s;
+    };
+    if (cudaMalloc((void**)&p.d_sb_seeds, nop * sizeof(uint64_t)) != cudaSuccess ||
+        cudaMalloc((void**)&p.d_sb_M, M.size() * sizeof(double2)) != cudaSuccess ||
+        cudaMalloc((void**)&p.d_sb_HS, (size_t)d_S * d_S * sizeof(double2)) != cudaSuccess)
+      return fail(MF_ERR_OOM);
+    if (cudaMemcpy(p.d_sb_seeds, seeds, nop * sizeof(uint64_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(p.d_sb_M, M.data(), M.size() * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(p.d_sb_HS, H_S, (size_t)d_S * d_S * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess)
+      return fail(MF_ERR_CUDA);
+    p.sb_nop = nop;
+    p.sb_dS = (int32_t)d_S;
+    p.have_bounds = false;
+    // dense-work estimate of the composite: n_op bath operators per product
+    p.w_hpsi = (double)nop * (double)d_B * (double)d_B;
+    p.dense_warn = p.w_hpsi > o.dense_work_limit;
+    return MF_OK;
+  });
 }
 
 mf_status mf_plan_destroy(mf_plan_t h) {

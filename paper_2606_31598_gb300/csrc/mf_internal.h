@@ -5,6 +5,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <new>
 #include <string>
 #include <utility>
 #include <vector>
@@ -167,6 +168,21 @@ int64_t tc_nvec_bucket(int64_t nvec);
 // Vector layouts: the FP64 master x/y is [D][nv]; the compute copy xc and the
 // partial slots use a padded vector stride nb >= nv ([D][nb], [slot][dpad][nb])
 // with zeros in the padding.  nslot/dpad describe the path in use.
+// C++ exceptions must not cross the C boundary: entry points that build host
+// containers (pair lists, work items, candidate lists, JSON records) run
+// their body through guard(), which maps a host allocation failure to
+// MF_ERR_OOM and anything else thrown to MF_ERR_INVALID.
+template <typename F>
+mf_status guard(F&& body) {
+  try {
+    return body();
+  } catch (const std::bad_alloc&) {
+    return MF_ERR_OOM;
+  } catch (...) {
+    return MF_ERR_INVALID;
+  }
+}
+
 struct VecShape {
   int64_t nv, nb, nslot, dpad;
 };
