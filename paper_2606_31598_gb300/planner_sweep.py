@@ -143,7 +143,19 @@ def run_sweep(out_path, small=False, warm=1, reps=3, max_minutes=1e9, log=print)
     return records
 
 
+# The records of the sweep measured on GB300 (480-problem grid, 30-minute
+# cap: 465 problems, 4185 records), shipped so that the surrogate can be
+# fitted, and the regret report re-derived, without re-measuring:
+#   python -m paper_2606_31598_gb300.planner_sweep --evaluate-only --out <this file>
+RECORDS_GB300 = os.path.join(os.path.dirname(os.path.abspath(__file__)), "planner_records_gb300.jsonl.gz")
+
+
 def load(path):
+    """Sweep records (one JSON object per line; gzip if the name ends .gz)."""
+    if path.endswith(".gz"):
+        import gzip
+        with gzip.open(path, "rt") as f:
+            return [json.loads(l) for l in f if l.strip()]
     with open(path) as f:
         return [json.loads(l) for l in f if l.strip()]
 

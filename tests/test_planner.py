@@ -180,3 +180,20 @@ def test_regret_definition():
     assert abs(an["mean"] - 1.0) < 1e-12 and an["zero_regret_frac"] == 0.0
     tr, te = PS.split(recs, 0.25, seed=0)
     assert {r["problem"] for r in tr}.isdisjoint({r["problem"] for r in te})
+
+
+def test_shipped_gb300_records_give_the_reported_analytic_regret():
+    """The sweep records measured on GB300 ship with the package; the
+    analytic planner's held-out regret recomputed from them (same seed-0
+    split of problems) is the one reported for the sweep, and every problem
+    has the measured best among its candidates."""
+    from paper_2606_31598_gb300 import planner_sweep as ps
+    recs = ps.load(ps.RECORDS_GB300)
+    assert len(recs) == 4185
+    assert len({r["problem"] for r in recs}) == 465
+    train, test = ps.split(recs, 0.2, 0)
+    a_test, a_train = ps.regret(test, None), ps.regret(train, None)
+    assert a_test["problems"] == 93 and a_train["problems"] == 372
+    assert abs(a_test["mean"] - 0.11672) < 1e-4 and abs(a_test["max"] - 1.06904) < 1e-4
+    assert abs(a_train["mean"] - 0.07975) < 1e-4
+    assert all(r["t_mv"] > 0 and len(r["features"]) == 10 for r in recs)
