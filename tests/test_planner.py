@@ -197,3 +197,37 @@ def test_shipped_gb300_records_give_the_reported_analytic_regret():
     assert abs(a_test["mean"] - 0.11672) < 1e-4 and abs(a_test["max"] - 1.06904) < 1e-4
     assert abs(a_train["mean"] - 0.07975) < 1e-4
     assert all(r["t_mv"] > 0 and len(r["features"]) == 10 for r in recs)
+
+
+def test_learned_choice_beats_the_analytic_one_on_the_shipped_records():
+    """Algorithm 3 on the GB300 records, on the CPU: the oracle's FP64 form
+    of the surrogate (10 -> 64 -> 64 -> 3 log-times, masked squared loss,
+    Adam) fitted to the training problems picks, on the 93 held-out
+    problems, plans whose mean regret is well below the analytic planner's."""
+    from oracle import mlp_oracle as MO
+    from paper_2606_31598_gb300 import planner_sweep as ps
+    train, test = ps.split(ps.load(ps.RECORDS_GB300), 0.2, 0)
+    X = np.array([r["features"] for r in train], np.float64)
+    Y = np.zeros((len(train), 3))
+    M = np.zeros((len(train), 3))
+    for i, r in enumerate(train):
+        k = ps.STRATEGIES.index(r["storage"])
+        Y[i, k] = math.log(r["t_mv"])
+        M[i, k] = 1.0
+    F, H, O = 10, 64, 3
+    rng = np.random.default_rng(0)
+    p = np.concatenate([(rng.standard_normal(F * H) / np.sqrt(F)), np.zeros(H),
+                        (rng.standard_normal(H * H) / np.sqrt(H)), np.zeros(H),
+                        (rng.standard_normal(H * O) / np.sqrt(H)), np.zeros(O)])
+    mu, sd = MO.zscore(X)
+    p, curve = MO.train_adam(p, mu, sd, X, Y, M, F, H, O, epochs=800, lr=3e-3)
+    assert curve[-1] < 0.05 * curve[0]
+
+    class Net:
+        def predict(self, Xq):
+            return MO.forward(p, mu, sd, Xq, F, H, O)[3]
+
+    learned, analytic = ps.regret(test, Net()), ps.regret(test, None)
+    # (fitted here: 0.5 % against 11.7 %; the library's FP32 surrogate after
+    # 3000 epochs on the GPU: 0.24 %)
+    assert learned["mean"] < 0.02 and learned["mean"] < 0.25 * analytic["mean"], (learned, analytic)
