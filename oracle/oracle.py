@@ -4,8 +4,8 @@ Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
 leg may import this module.  It never imports the product package.
 
 Every routine forwards to ``mf_oracle.c`` (plain FP64 C); the few numpy steps
-here are library primitives (dense matrix products) used as stated steps of a
-definition, with no blocking or reordering beyond the definition.
+here are library primitives (dense matrix products, FFTs) used as stated steps
+of a definition, with no blocking or reordering beyond the definition.
 """
 import ctypes
 import os
@@ -215,19 +215,26 @@ def cheb_step(op, psi, dt, c, R, nterms, block=0, nthreads=0):
     return P.reshape(shape)
 
 
-def cheb_step_dense(H, psi, dt, c, R, nterms):
-    """The same recurrence with a materialised H (small D): q_{k+1} =
-    2 (H q_k - c q_k)/R - q_{k-1}, matrix products by numpy."""
+def cheb_step_fn(apply_fn, psi, dt, c, R, nterms):
+    """The Chebyshev step with the product y = apply_fn(q) of any operator
+    form: q_{k+1} = 2 (H q_k - c q_k)/R - q_{k-1}, acc += a_k q_k, final
+    phase e^{-i c dt}."""
     a = cheb_coeffs(R * dt, nterms)
     q_prev = None
     q = np.array(psi, dtype=np.complex128)
     acc = a[0] * q
     for k in range(1, nterms):
-        t = (H @ q - c * q) / R
+        t = (apply_fn(q) - c * q) / R
         qn = t if k == 1 else 2.0 * t - q_prev
         q_prev, q = q, qn
         acc = acc + a[k] * q
     return np.exp(-1j * c * dt) * acc
+
+
+def cheb_step_dense(H, psi, dt, c, R, nterms):
+    """The same recurrence with a materialised H (small D), matrix products
+    by numpy."""
+    return cheb_step_fn(lambda q: H @ q, psi, dt, c, R, nterms)
 
 
 # ------------------------------------------------------------- BF16X2 form --
@@ -273,6 +280,51 @@ def apply_bf16x2(op, x, H32=None):
         V = np.array([potential(op, i) for i in range(op.D)])
         Y = Y + V[:, None] * X
     return Y.reshape(x.shape)
+
+
+class DvrToeplitz:
+    """The sinc-DVR operator at any D (the benchmark's D = 131072 included)
+    as Toeplitz products by the FFT.  T is symmetric Toeplitz in k = r - c,
+    so T x is the first D entries of the circular convolution of the 2D
+    embedding [t(0..D-1), 0, t(D-1..1)] with [x, 0] (a library FFT as one
+    step).  apply64: the FP64 form.  apply_bf16x2: the BF16X2 form as
+    apply_bf16x2 states it -- FP32-form entries split hi/lo, x rounded to
+    complex64 and its parts split hi/lo, the three kept partial products
+    (the split of T(k) depends on k only, so each is a Toeplitz product).
+    Both add V_i x_i in FP64 with the FP64 x."""
+
+    def __init__(self, D, L=None):
+        self.D = D
+        op64 = make_op(GEN_SINC_DVR_HO, D, L=L)
+        op32 = make_op(GEN_SINC_DVR_HO, D, form=FORM_FP32, L=L)
+        t64 = kinetic_window(op64, 0, 0, D, 1)[:, 0]
+        th, tl = split_bf16(kinetic_window(op32, 0, 0, D, 1)[:, 0].astype(np.float32))
+        self.V = np.array([potential(op64, i) for i in range(D)])
+
+        def embed(t):
+            return np.fft.fft(np.concatenate([t, [0.0], t[:0:-1]]))
+
+        self.f64 = embed(t64)
+        self.fhi = embed(th.astype(np.float64))
+        self.flo = embed(tl.astype(np.float64))
+
+    def _toeplitz(self, ft, v):
+        vp = np.concatenate([v, np.zeros(self.D, dtype=np.complex128)])
+        return np.fft.ifft(ft * np.fft.fft(vp))[:self.D]
+
+    def apply64(self, x):
+        x = np.asarray(x, dtype=np.complex128).reshape(self.D)
+        return self._toeplitz(self.f64, x) + self.V * x
+
+    def apply_bf16x2(self, x):
+        x = np.asarray(x, dtype=np.complex128).reshape(self.D)
+        x32 = x.astype(np.complex64)
+        rh, rl = split_bf16(x32.real)
+        ih, il = split_bf16(x32.imag)
+        xh = rh.astype(np.float64) + 1j * ih.astype(np.float64)
+        xl = rl.astype(np.float64) + 1j * il.astype(np.float64)
+        return (self._toeplitz(self.fhi, xh) + self._toeplitz(self.fhi, xl) + self._toeplitz(self.flo, xh)
+                + self.V * x)
 
 
 # ------------------------------------------------------- system-bath form ---
