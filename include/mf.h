@@ -160,6 +160,15 @@ typedef struct {
 mf_status mf_planner_estimate(const mf_problem* prob, const mf_candidate* cand, const mf_device_model* model,
                               double alpha, double cache_budget_bytes, mf_estimate* out);
 
+/*
+ * mf_planner_device_model -- the throughputs mf_plan_create's analytic
+ * planner (Algorithm 1) feeds its runtime model for a precision form and a
+ * generator on a GPU with num_sms SMs (the values measured on GB300; host
+ * only).  Errors: MF_ERR_INVALID for a NULL out, num_sms < 1 or an unknown
+ * precision or generator.
+ */
+mf_status mf_planner_device_model(int32_t precision, int32_t generator, int32_t num_sms, mf_device_model* out);
+
 /* Fill *o with the defaults listed above.  Never fails. */
 void mf_options_default(mf_options* o);
 

@@ -133,6 +133,8 @@ def lib():
         L.mf_apply_dvr_noalloc.argtypes = [i64, d, vp, vp, vp]
         L.mf_plan_profile.argtypes = [vp, i32]
         L.mf_planner_estimate.argtypes = [P(mf_problem), P(mf_candidate), P(mf_device_model), d, d, P(mf_estimate)]
+        L.mf_planner_device_model.argtypes = [i32, i32, i32, P(mf_device_model)]
+        L.mf_planner_device_model.restype = ctypes.c_int
         L.mf_plan_trials.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t, P(ctypes.c_size_t)]
         fp = P(ctypes.c_float)
         L.mf_mlp_create.argtypes = [P(vp), i32, i32, i32, u64]
@@ -326,6 +328,14 @@ def mf_planner_estimate(problem, candidate, model=None, alpha=0.9, cache_budget_
     _check(lib().mf_planner_estimate(ctypes.byref(problem), ctypes.byref(candidate),
                                      ctypes.byref(model) if model is not None else None, float(alpha),
                                      float(cache_budget_bytes), ctypes.byref(out)), "mf_planner_estimate")
+    return out
+
+
+def mf_planner_device_model(precision, generator, num_sms=152):
+    """The runtime-model throughputs the analytic planner uses (host only)."""
+    out = mf_device_model()
+    _check(lib().mf_planner_device_model(int(precision), int(generator), int(num_sms), ctypes.byref(out)),
+           "mf_planner_device_model")
     return out
 
 

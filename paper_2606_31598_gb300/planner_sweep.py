@@ -64,11 +64,8 @@ def candidates(mf, gen, prec, D, nvec, budget, blocks):
 
 
 def _device_model(mf, prec, gen):
-    # the same throughputs the library's analytic planner assumes
-    clk, sms = 1.9e9, 152
-    fl = 1.2e12 if prec == mf.MF_PREC_FP64 else sms * 128 * 2 * clk
-    g = 1e15 if gen == mf.MF_GEN_SINC_DVR_HO else (1.5e10 if prec == mf.MF_PREC_FP64 else 4e11)
-    return mf.mf_device_model(fl, 6.7e12, g)
+    # the throughputs the library's analytic planner uses (GB300, 152 SMs)
+    return mf.mf_planner_device_model(prec, gen, 152)
 
 
 def measure(mf, torch, gen, prec, D, nvec, b, storage, budget_used, warm, reps):
