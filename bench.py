@@ -233,7 +233,7 @@ def run_mf(args):
     props = torch.cuda.get_device_properties(dev)
     x0 = rank_task(rank)
 
-    plan = mf.Plan(D, mf.MF_GEN_SINC_DVR_HO, precision=mf.MF_PREC_FP32, stream=stream)
+    plan = mf.Plan(D, mf.MF_GEN_SINC_DVR_HO, precision=mf.MF_PREC_FP32, stream=stream, device=local)
     desc = plan.describe()
     emin, emax = plan.bounds()
     tau = substep_tau(plan)
@@ -297,7 +297,7 @@ def run_mf(args):
     # closed-form coherent state
     err = {}
     if rank == 0:
-        plan64 = mf.Plan(D, mf.MF_GEN_SINC_DVR_HO, precision=mf.MF_PREC_FP64, stream=stream)
+        plan64 = mf.Plan(D, mf.MF_GEN_SINC_DVR_HO, precision=mf.MF_PREC_FP64, stream=stream, device=local)
         plan64.set_bounds(emin, emax)
         a = torch.from_numpy(psi0).to(dev)
         b = torch.from_numpy(psi0).to(dev)
