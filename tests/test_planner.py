@@ -266,3 +266,19 @@ def test_device_model_rejects_bad_input(mf):
         mf.mf_planner_device_model(7, 0, 152)
     with pytest.raises(mf.MFError):
         mf.mf_planner_device_model(1, 0, 0)
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_library_model_prefers_the_cache_for_philox_vectors_and_generation_for_dvr(mf, prec):
+    """With the library's runtime-model rates, 16 Philox vectors with room for
+    the whole canonical cache are planned with it (measured on GB300: full
+    cache about 2x faster than generation), while the DVR stays procedural
+    (its window table makes generation nearly free)."""
+    D, R = 65536, 16
+    pr = mf.mf_problem(D, D, R, 1, 1, 8.0, 250e9, 1)
+    budget = 40e9
+    for gen, want_cache in ((0, True), (1, False)):
+        dm = mf.mf_planner_device_model(prec, gen, 152)
+        proc = _est(mf, pr, mf.mf_candidate(2048, 0, -1, 1, 1, 4), model=dm, budget=budget)
+        full = _est(mf, pr, mf.mf_candidate(2048, 2, -1, 1, 1, 4), model=dm, budget=budget)
+        assert (full.S_model < proc.S_model) == want_cache, (gen, full.S_model, proc.S_model)
