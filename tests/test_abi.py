@@ -86,3 +86,43 @@ def test_vector_arguments_are_checked_before_the_library(mf):
         with pytest.raises(mf.MFError) as e:
             _vec(t, 4, "x")
         assert e.value.status == mf.MF_ERR_INVALID
+
+
+def test_every_entry_point_rejects_null_handles_and_bad_arguments(mf):
+    """Each call checks its arguments on the host before any CUDA call, so
+    on a machine without a GPU every one of these returns MF_ERR_INVALID."""
+    L = mf.lib()
+    INV = mf.MF_ERR_INVALID
+    d = ctypes.c_double()
+    i32 = ctypes.c_int32()
+    i64 = ctypes.c_int64()
+    vp = ctypes.c_void_p()
+    checks = {
+        "mf_cheb_filter": L.mf_cheb_filter(None, None, 1, 0.1, 0, 1),
+        "mf_cheb_terms": L.mf_cheb_terms(None, 0.1, ctypes.byref(i32)),
+        "mf_cheb_filter_terms": L.mf_cheb_filter_terms(None, 0.1, ctypes.byref(i32)),
+        "mf_spectral_bounds": L.mf_spectral_bounds(None, ctypes.byref(d), ctypes.byref(d)),
+        "mf_plan_set_bounds": L.mf_plan_set_bounds(None, 0.0, 1.0),
+        "mf_plan_describe": L.mf_plan_describe(None, None, 0),
+        "mf_debug_entries": L.mf_debug_entries(None, 0, 0, 1, 1, None),
+        "mf_plan_profile": L.mf_plan_profile(None, 1),
+        "mf_plan_profile_read": L.mf_plan_profile_read(None, ctypes.byref(d), ctypes.byref(i64)),
+        "mf_plan_trials": L.mf_plan_trials(None, None, 0, None),
+        "mf_rows_cheb_begin": L.mf_rows_cheb_begin(None, 0.1, 0, ctypes.byref(i32)),
+        "mf_rows_cheb_init": L.mf_rows_cheb_init(None, None, None, 1),
+        "mf_rows_cheb_term": L.mf_rows_cheb_term(None, 1, None, None, None, None, 1),
+        "mf_rows_cheb_final": L.mf_rows_cheb_final(None, None, None, 1, 0.1),
+        "mf_batch_propagate": L.mf_batch_propagate(None, None, 0.1, 1, 0, None),
+        "mf_batch_offsets": L.mf_batch_offsets(None, None),
+        "mf_batch_plan": L.mf_batch_plan(None, 0, ctypes.byref(vp)),
+        "mf_batch_info": L.mf_batch_info(None, None, None),
+        "mf_batch_create (no problems)": L.mf_batch_create(ctypes.byref(vp), 0, None, None, None, 0, 0, None),
+        "mf_mlp_param_count": L.mf_mlp_param_count(None, ctypes.byref(i64)),
+        "mf_mlp_predict": L.mf_mlp_predict(None, None, 1, None),
+        "mf_external_create (block 100)": L.mf_external_create(ctypes.byref(vp), 300, 100, None, 0, None),
+        "mf_sysbath_create (d_S 0)": L.mf_sysbath_create(ctypes.byref(vp), 0, 100, 0, None, None, None, 0.1, None),
+        "mf_apply_dvr_noalloc (D 1)": L.mf_apply_dvr_noalloc(1, 0.0, None, None, None),
+    }
+    bad = {k: v for k, v in checks.items() if v != INV}
+    assert not bad, bad
+    assert L.mf_batch_destroy(None) == mf.MF_OK
