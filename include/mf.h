@@ -23,6 +23,9 @@
  *    errors are returned as MF_ERR_CUDA by the call that hit them; kernel-side
  *    failures (device error word) are returned by the next mf_sync.
  *  - Hermitian generators require M == D.  y must not alias x.
+ *  - A plan (or batch) is used by one host thread at a time: its calls share
+ *    the plan's workspace, partial slots and events.  Distinct plans are
+ *    independent and may be driven from different threads and streams.
  */
 #ifndef MF_H
 #define MF_H
