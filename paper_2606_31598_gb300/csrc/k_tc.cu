@@ -3,24 +3,28 @@
 //
 // Row-owner form of Y = H X (Sec. IV.A, Eq. generic_multivector; output
 // block rows as in Sec. III.B): a CTA owns 128 output rows and sweeps its
-// column range in chunks of 32 columns.  For every chunk
-//   * all warps generate H[128 x 32] (Philox canonical entries, conjugates
-//     below the diagonal, DVR window table) or read it from the FP32 block
-//     cache, split each real part into bf16 hi + lo and store the four planes
-//     (re hi, re lo, im hi, im lo) straight into shared memory in the
-//     canonical no-swizzle K-major layout the tensor core reads;
-//   * one thread streams the chunk's operand tiles of X (pre-split per apply
-//     into the same layout: B1 = [Re X | Im X], B2 = [-Im X | Re X], hi and
-//     lo) with bulk asynchronous copies completing on an mbarrier;
+// column range in chunks of 32 columns with 16 generator warps and one
+// copy/MMA warp.  For every chunk
+//   * the generator warps generate H[128 x 32] (Philox canonical entries,
+//     conjugates below the diagonal, DVR window table) or read it from the
+//     FP32 block cache, split each real part into bf16 hi + lo and store the
+//     four planes (re hi, re lo, im hi, im lo) straight into shared memory in
+//     the canonical no-swizzle K-major layout the tensor core reads;
+//   * one thread of the copy/MMA warp streams the chunk's operand tiles of X
+//     (pre-split per apply into the same layout: B1 = [Re X | Im X],
+//     B2 = [-Im X | Re X], hi and lo) with bulk asynchronous copies
+//     completing on an mbarrier;
 //   * the same thread issues twelve tcgen05.mma (two K steps of 16, six split
 //     products each: A_re_hi B1_hi, A_re_hi B1_lo, A_re_lo B1_hi and the same
 //     for A_im with B2) accumulating D[128 x 2 NV] = [Re Y | Im Y] in TMEM;
 //     tcgen05.commit arrives on the stage's mbarrier when they finish.
 // Two shared-memory stages let the generation of chunk k+1 run on the SIMT
-// pipes while the tensor core works on chunk k.  The epilogue reads TMEM
-// with tcgen05.ld and writes the split-K partial slot.  Every wait is
-// bounded; on time-out the kernel records the stage in the plan's error word,
-// drains its own outstanding work (again bounded), frees TMEM and returns.
+// pipes while the tensor core works on chunk k.  Every 32 chunks the TMEM
+// accumulator is drained (tcgen05.ld) into an FP32 accumulator in shared
+// memory with round-to-nearest adds; the epilogue writes that accumulator to
+// the split-K partial slot.  Every wait is bounded; on time-out the kernel
+// records the stage in the plan's error word, drains its own outstanding work
+// (again bounded), frees TMEM and returns.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
