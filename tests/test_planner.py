@@ -242,21 +242,7 @@ def test_library_model_on_the_shipped_records(mf):
     from paper_2606_31598_gb300 import planner_sweep as ps
     recs = ps.load(ps.RECORDS_GB300)
     train, test = ps.split(recs, 0.2, 0)
-
-    def rescore(rs):
-        out = []
-        for r in rs:
-            eb = 16.0 if r["precision"] == mf.MF_PREC_FP64 else 8.0
-            pr = mf.mf_problem(r["D"], r["D"], r["nvec"], 1, 1, eb, 250e9, 1)
-            c = mf.mf_candidate(r["block"], ps.STRATEGIES.index(r["storage"]), -1, 1, 1, 4)
-            e = mf.mf_planner_estimate(pr, c, mf.mf_planner_device_model(r["precision"], r["generator"], 152),
-                                       0.9, r["budget_gb"] * 1e9)
-            q = dict(r)
-            q["S_model"] = e.S_model
-            out.append(q)
-        return out
-
-    held, tr = ps.regret(rescore(test), None), ps.regret(rescore(train), None)
+    held, tr = ps.regret(ps.rescore(test), None), ps.regret(ps.rescore(train), None)
     assert held["mean"] < 0.01 and tr["mean"] < 0.02, (held, tr)
     assert 0.0024 < held["mean"]
 
