@@ -282,6 +282,37 @@ def apply_bf16x2(op, x, H32=None):
     return Y.reshape(x.shape)
 
 
+def apply_rows_bf16x2(op, x, rows):
+    """Rows of y = H x in the BF16X2 form (as apply_bf16x2 states it) for any
+    D: each sampled row of the FP32-form operator is generated on its own
+    (a 1 x D window), split hi/lo, and multiplied with the split FP32 copy of
+    x, the three kept partial products summed exactly in FP64; the DVR
+    potential is added in FP64 to the FP64 x.  For full-size checks where
+    the dense operator cannot be formed."""
+    x = np.asarray(x, dtype=np.complex128)
+    X = x.reshape(op.D, -1)
+    op32 = make_op(op.gen, op.D, seed=op.seed, form=FORM_FP32, L=op.L or None)
+    X32 = X.astype(np.complex64)
+    Xr_h, Xr_l = split_bf16(X32.real)
+    Xi_h, Xi_l = split_bf16(X32.imag)
+    f = lambda a: a.astype(np.float64)
+    out = np.zeros((len(rows), X.shape[1]), dtype=np.complex128)
+    for i, r in enumerate(rows):
+        h = window_native(op32, int(r), 0, 1, op.D)
+        Ar_h, Ar_l = split_bf16(h.real)
+        Ai_h, Ai_l = split_bf16(h.imag)
+
+        def prod(ah, al, bh, bl):
+            return f(ah) @ f(bh) + f(ah) @ f(bl) + f(al) @ f(bh)
+
+        yr = prod(Ar_h, Ar_l, Xr_h, Xr_l) - prod(Ai_h, Ai_l, Xi_h, Xi_l)
+        yi = prod(Ar_h, Ar_l, Xi_h, Xi_l) + prod(Ai_h, Ai_l, Xr_h, Xr_l)
+        out[i] = (yr + 1j * yi)[0]
+        if op.gen == GEN_SINC_DVR_HO:
+            out[i] += potential(op, int(r)) * X[int(r)]
+    return out
+
+
 class DvrToeplitz:
     """The sinc-DVR operator at any D (the benchmark's D = 131072 included)
     as Toeplitz products by the FFT.  T is symmetric Toeplitz in k = r - c,

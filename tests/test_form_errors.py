@@ -62,3 +62,17 @@ def test_bf16x2_form_error_on_the_dvr_workload():
     x = (rng.standard_normal(D) + 1j * rng.standard_normal(D)) / np.sqrt(2.0 * D)
     y64 = T.apply64(x)
     assert np.max(np.abs(T.apply_bf16x2(x) - y64)) < 5e-6 * np.max(np.abs(y64))
+
+
+@pytest.mark.parametrize("gen", [O.GEN_PHILOX_GUE, O.GEN_SINC_DVR_HO])
+def test_row_sampled_bf16x2_form_matches_the_dense_statement(gen):
+    """apply_rows_bf16x2 (one generated row at a time, any D) against the
+    dense BF16X2 statement at D = 700 with 5 vectors, rows at both ends,
+    the diagonal blocks and a ragged tail."""
+    D = 700
+    op = O.make_op(gen, D, seed=3)
+    X = W.random_state(D, 5, seed=4).reshape(D, 5)
+    rows = [0, 1, 127, 128, 350, 698, 699]
+    ref = O.apply_bf16x2(op, X)[rows]
+    got = O.apply_rows_bf16x2(op, X, rows)
+    assert np.max(np.abs(got - ref)) < 1e-13 * np.max(np.abs(ref))
