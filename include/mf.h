@@ -165,9 +165,10 @@ mf_status mf_planner_estimate(const mf_problem* prob, const mf_candidate* cand, 
 
 /*
  * mf_planner_device_model -- the throughputs mf_plan_create's analytic
- * planner (Algorithm 1) feeds its runtime model for a precision form and a
- * generator on a GPU with num_sms SMs (the values measured on GB300; host
- * only).  Errors: MF_ERR_INVALID for a NULL out, num_sms < 1 or an unknown
+ * planner (Algorithm 1) feeds its runtime model (Eq. runtime_overlap: the
+ * slowest of generation, cache streaming and contraction) for a precision
+ * form and a generator on a GPU with num_sms SMs (the values measured on
+ * GB300; host only).  Errors: MF_ERR_INVALID for a NULL out, num_sms < 1 or an unknown
  * precision or generator.
  */
 mf_status mf_planner_device_model(int32_t precision, int32_t generator, int32_t num_sms, mf_device_model* out);
