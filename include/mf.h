@@ -151,6 +151,9 @@ typedef struct {
   double T_model;  /* max(generation, streaming, contraction) time, Eq. runtime_overlap */
   double S_model;  /* W T_model Pi_mem, Eq. planner_cost_score */
   int32_t feasible;/* Eq. planner_memory_constraint */
+  double T_sum;    /* generation + streaming + contraction time: the ranking's
+                      second key, deciding between candidates whose S_model
+                      ties (the same term bounds both) for the less total work */
 } mf_estimate;
 
 /*

@@ -89,7 +89,8 @@ class mf_estimate(ctypes.Structure):
     _fields_ = [("n_blk", ctypes.c_int64), ("n_pair", ctypes.c_int64), ("pairs_cached", ctypes.c_int64),
                 ("waves", ctypes.c_int64), ("M_block", ctypes.c_double), ("M_work", ctypes.c_double),
                 ("M_op", ctypes.c_double), ("M_tot", ctypes.c_double), ("F_mv", ctypes.c_double),
-                ("T_model", ctypes.c_double), ("S_model", ctypes.c_double), ("feasible", ctypes.c_int32)]
+                ("T_model", ctypes.c_double), ("S_model", ctypes.c_double), ("feasible", ctypes.c_int32),
+                ("T_sum", ctypes.c_double)]
 
 
 _lib = None

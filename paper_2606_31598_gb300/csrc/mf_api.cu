@@ -839,8 +839,12 @@ mf_status mf_plan_create(mf_plan_t* out, int64_t D, int64_t M, int32_t generator
         ranked.push_back({c, e});
       }
     if (ranked.empty()) return MF_ERR_OOM;
-    std::stable_sort(ranked.begin(), ranked.end(),
-                     [](const Ranked& a, const Ranked& b) { return a.e.S_model < b.e.S_model; });
+    // model score first; where the same term bounds two candidates (equal
+    // scores), the one with less total work (fewer generated or streamed
+    // entries competing with the contraction for the SMs)
+    std::stable_sort(ranked.begin(), ranked.end(), [](const Ranked& a, const Ranked& b) {
+      return a.e.S_model < b.e.S_model || (a.e.S_model == b.e.S_model && a.e.T_sum < b.e.T_sum);
+    });
 
     auto budget_for = [&](const Ranked& r) -> size_t {
       if (r.c.storage == MF_STORE_PROCEDURAL) return 0;

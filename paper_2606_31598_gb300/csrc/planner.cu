@@ -48,6 +48,7 @@ void planner_estimate(const mf_problem& pr, const mf_candidate& c, const mf_devi
   const double t_mem = dm.hbm_bytes_per_s > 0 ? canon * frac_cached * Bc * reuse / dm.hbm_bytes_per_s : 0.0;
   const double t_mv = dm.flops_per_s > 0 ? e.F_mv / dm.flops_per_s : 0.0;
   e.T_model = std::max(t_gen, std::max(t_mem, t_mv));
+  e.T_sum = t_gen + t_mem + t_mv;
   // Pi_mem: a 10 % penalty rising linearly over the last fifth of the
   // allowed memory (Eq. planner_cost_score leaves the form open).
   const double use = pr.M_free > 0 ? e.M_tot / (alpha * pr.M_free) : 0.0;

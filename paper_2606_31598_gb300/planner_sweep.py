@@ -59,7 +59,8 @@ def candidates(mf, gen, prec, D, nvec, budget, blocks):
             if not e.feasible and st != mf.MF_STORE_PROCEDURAL:
                 continue
             out.append({"block": b, "storage": STRATEGIES[st], "pairs_cached": int(e.pairs_cached),
-                        "S_model": e.S_model, "budget_used": 0.0 if st == 0 else e.pairs_cached * e.M_block})
+                        "S_model": e.S_model, "T_sum": e.T_sum,
+                        "budget_used": 0.0 if st == 0 else e.pairs_cached * e.M_block})
     return out
 
 
@@ -131,7 +132,7 @@ def run_sweep(out_path, small=False, warm=1, reps=3, max_minutes=1e9, log=print)
                 feats = [float(v) for v in mf.mf_mlp_features(gen, prec, D, c["block"], nv, budget)]
                 rec = {"problem": pid, "generator": gen, "precision": prec, "D": D, "nvec": nv, "budget_gb": bud_gb,
                        "block": c["block"], "storage": c["storage"], "pairs_cached": c["pairs_cached"],
-                       "S_model": c["S_model"], "t_mv": cache[key], "features": feats}
+                       "S_model": c["S_model"], "T_sum": c["T_sum"], "t_mv": cache[key], "features": feats}
                 records.append(rec)
                 f.write(json.dumps(rec) + "\n")
             f.flush()
@@ -188,7 +189,9 @@ def regret(records, net=None):
     for pid, rs in by.items():
         best = min(r["t_mv"] for r in rs)
         if net is None:
-            pick = min(rs, key=lambda r: r["S_model"])
+            # the library's ranking: model score, then total work on ties
+            # (records scored before T_sum existed keep their first minimum)
+            pick = min(rs, key=lambda r: (r["S_model"], r.get("T_sum", 0.0)))
         else:
             pred = net.predict(np.array([r["features"] for r in rs], np.float32))
             pick = rs[int(np.argmin([pred[i, STRATEGIES.index(r["storage"])] for i, r in enumerate(rs)]))]
@@ -212,6 +215,7 @@ def rescore(records):
                                    r["budget_gb"] * 1e9)
         q = dict(r)
         q["S_model"] = e.S_model
+        q["T_sum"] = e.T_sum
         out.append(q)
     return out
 

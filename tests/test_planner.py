@@ -234,17 +234,18 @@ def test_learned_choice_beats_the_analytic_one_on_the_shipped_records():
 
 
 def test_library_model_on_the_shipped_records(mf):
-    """Algorithm 1 with the library's current runtime-model throughputs
-    (mf_planner_device_model), re-scored on every shipped GB300 record: the
-    held-out regret is 0.7 % (the sweep's own scores, made with a 4e11/s
-    Philox generation rate and the FP32 rate for BF16X2, gave 11.7 %), and
-    the learned planner's 0.24 % on the same problems is still lower."""
+    """Algorithm 1 as the library now ranks (runtime-model throughputs from
+    mf_planner_device_model; ties between equal model scores broken by the
+    total work T_sum), re-scored on every shipped GB300 record: 0.11 %
+    held-out regret (max 2.5 %) and 0.27 % on the training problems.  The
+    sweep's own scores (a 4e11/s Philox generation rate, the FP32 rate for
+    BF16X2, no tie-break) gave 11.7 %; the learned planner trained on the
+    same measurements reached 0.24 % (max 6.8 %)."""
     from paper_2606_31598_gb300 import planner_sweep as ps
     recs = ps.load(ps.RECORDS_GB300)
     train, test = ps.split(recs, 0.2, 0)
     held, tr = ps.regret(ps.rescore(test), None), ps.regret(ps.rescore(train), None)
-    assert held["mean"] < 0.01 and tr["mean"] < 0.02, (held, tr)
-    assert 0.0024 < held["mean"]
+    assert held["mean"] < 0.003 and held["max"] < 0.05 and tr["mean"] < 0.005, (held, tr)
 
 
 def test_device_model_rejects_bad_input(mf):
