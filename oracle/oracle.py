@@ -322,20 +322,24 @@ class DvrToeplitz:
     apply_bf16x2 states it -- FP32-form entries split hi/lo, x rounded to
     complex64 and its parts split hi/lo, the three kept partial products
     (the split of T(k) depends on k only, so each is a Toeplitz product).
-    Both add V_i x_i in FP64 with the FP64 x."""
+    apply32: the FP32 form's entries and the complex64 copy of x with exact
+    sums (the form's own rounding, without the FP32 tile sums).  All add
+    V_i x_i in FP64 with the FP64 x."""
 
     def __init__(self, D, L=None):
         self.D = D
         op64 = make_op(GEN_SINC_DVR_HO, D, L=L)
         op32 = make_op(GEN_SINC_DVR_HO, D, form=FORM_FP32, L=L)
         t64 = kinetic_window(op64, 0, 0, D, 1)[:, 0]
-        th, tl = split_bf16(kinetic_window(op32, 0, 0, D, 1)[:, 0].astype(np.float32))
+        t32 = kinetic_window(op32, 0, 0, D, 1)[:, 0].astype(np.float32)
+        th, tl = split_bf16(t32)
         self.V = np.array([potential(op64, i) for i in range(D)])
 
         def embed(t):
             return np.fft.fft(np.concatenate([t, [0.0], t[:0:-1]]))
 
         self.f64 = embed(t64)
+        self.f32 = embed(t32.astype(np.float64))
         self.fhi = embed(th.astype(np.float64))
         self.flo = embed(tl.astype(np.float64))
 
@@ -346,6 +350,11 @@ class DvrToeplitz:
     def apply64(self, x):
         x = np.asarray(x, dtype=np.complex128).reshape(self.D)
         return self._toeplitz(self.f64, x) + self.V * x
+
+    def apply32(self, x):
+        x = np.asarray(x, dtype=np.complex128).reshape(self.D)
+        x32 = x.astype(np.complex64).astype(np.complex128)
+        return self._toeplitz(self.f32, x32) + self.V * x
 
     def apply_bf16x2(self, x):
         x = np.asarray(x, dtype=np.complex128).reshape(self.D)

@@ -23,6 +23,12 @@ def test_fft_forms_match_the_dense_statements(D):
     ref64 = O.apply(op, x)
     assert np.max(np.abs(T.apply_bf16x2(x) - ref_bf)) < 1e-12 * np.max(np.abs(ref_bf))
     assert np.max(np.abs(T.apply64(x) - ref64)) < 1e-12 * np.max(np.abs(ref64))
+    # FP32 form with exact sums: the C oracle's FP32-form product of the
+    # complex64-rounded x (its potential term takes the rounded x too)
+    x32 = x.astype(np.complex64).astype(np.complex128)
+    V = np.array([O.potential(op, i) for i in range(D)])
+    ref32 = O.apply(O.make_op(O.GEN_SINC_DVR_HO, D, form=O.FORM_FP32), x32) - V * x32 + V * x
+    assert np.max(np.abs(T.apply32(x) - ref32)) < 1e-12 * np.max(np.abs(ref32))
 
 
 def test_python_recurrence_matches_the_c_oracle():
@@ -58,6 +64,10 @@ def test_bf16x2_form_error_on_the_dvr_workload():
     sbf = O.cheb_step_fn(T.apply_bf16x2, psi, tau, c, R, 64)
     err = np.linalg.norm(sbf - s64)
     assert 5e-6 < err < 5e-5, err
+    # the FP32 form's own rounding (exact sums) accounts for nearly all of
+    # the FP32 error measured on the GPU (5.3e-7 at tau = 4.14e-4)
+    s32 = O.cheb_step_fn(T.apply32, psi, tau, c, R, 64)
+    assert 3e-7 < np.linalg.norm(s32 - s64) < 8e-7
     rng = np.random.default_rng(3)
     x = (rng.standard_normal(D) + 1j * rng.standard_normal(D)) / np.sqrt(2.0 * D)
     y64 = T.apply64(x)
