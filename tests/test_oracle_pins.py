@@ -450,3 +450,76 @@ def test_dvr_fft_product_matches_direct_sum(D):
     x = rng.standard_normal(D) + 1j * rng.standard_normal(D)
     ref = O.apply(op, x)
     assert np.max(np.abs(O.dvr_apply_fft(op, x) - ref)) < 1e-11 * np.max(np.abs(ref))
+
+
+# ------------------------------------------------------------ BF16 split ----
+def _bf16_sweep():
+    """float32 bit patterns that exercise bfloat16 rounding: exact ties with
+    an even and an odd kept mantissa, one unit either side of a tie, +-0,
+    subnormals, the largest finite values (ties there round to infinity),
+    powers of two and random finite patterns of both signs."""
+    rng = np.random.default_rng(11)
+    hi = rng.integers(0, 0x7F7F, 4000, dtype=np.uint64) << 16
+    pats = [hi | 0x8000, hi | 0x7FFF, hi | 0x8001, hi, hi | 0xFFFF]
+    pats.append(np.array([0x00000000, 0x00000001, 0x00008000, 0x00018000, 0x007FFFFF, 0x00800000,
+                          0x7F7F0000, 0x7F7F7FFF, 0x7F7F8000, 0x7F7EFFFF, 0x7F7E8000, 0x3F800000,
+                          0x3F808000, 0x3F818000], dtype=np.uint64))
+    pats.append(rng.integers(0, 0x7F800000, 20000, dtype=np.uint64))
+    u = np.concatenate(pats).astype(np.uint32)
+    return np.concatenate([u, u | np.uint32(0x80000000)]).view(np.float32)
+
+
+def _bf16_value(bits32):
+    """float64 value of a bfloat16 bit pattern held in the high half of a
+    32-bit word; the pattern just past the largest finite value stands for
+    2^128, the value IEEE rounding compares against before overflowing."""
+    b = bits32 & 0x7FFFFFFF
+    if b == 0x7F800000:
+        v = 2.0 ** 128
+    else:
+        v = float(np.uint32(b).view(np.float32))
+    return -v if bits32 & 0x80000000 else v
+
+
+def test_bf16_rounding_against_torch_and_the_definition():
+    """oracle.bf16_rn against an independent rounding (torch's float32 ->
+    bfloat16 conversion, round to nearest even) on every pattern of the
+    sweep, and against the definition itself on a subset: the result is one
+    of the two bfloat16 neighbours of x, the nearer one, the one with an
+    even last mantissa bit on a tie."""
+    torch = pytest.importorskip("torch")
+    x = _bf16_sweep()
+    got = O.bf16_rn(x)
+    ref = torch.from_numpy(x.copy()).to(torch.bfloat16).to(torch.float32).numpy()
+    assert np.array_equal(got.view(np.uint32), ref.view(np.uint32))
+    assert np.all((got.view(np.uint32) & 0xFFFF) == 0)
+    for xv, gv in zip(x[::7], got[::7]):
+        u = int(np.float32(xv).view(np.uint32))
+        lo = u & 0xFFFF0000
+        up = lo + 0x10000
+        a, b = _bf16_value(lo), _bf16_value(up)
+        dx = abs(float(xv) - a), abs(float(xv) - b)
+        if dx[0] < dx[1]:
+            want = lo
+        elif dx[1] < dx[0]:
+            want = up
+        else:
+            want = lo if ((lo >> 16) & 1) == 0 else up
+        assert int(np.float32(gv).view(np.uint32)) == want, hex(u)
+
+
+def test_bf16_split_reconstructs_float32():
+    """split_bf16: hi = bf16(x), lo = bf16(x - hi) with x - hi exact in
+    float32, and hi + lo within 2^-17 |x| of x (each rounding keeps 8
+    significant bits, so the two together carry 16)."""
+    rng = np.random.default_rng(12)
+    x = np.concatenate([rng.standard_normal(50000).astype(np.float32),
+                        (rng.standard_normal(50000) * 1e-3).astype(np.float32),
+                        _bf16_sweep()[:40000]])
+    x = x[np.isfinite(x) & (np.abs(x) < 1e38) & (np.abs(x) > 1e-30)]
+    hi, lo = O.split_bf16(x)
+    r = x.astype(np.float64) - hi.astype(np.float64)
+    assert np.array_equal(r.astype(np.float32).astype(np.float64), r)
+    assert np.array_equal(lo, O.bf16_rn(r.astype(np.float32)))
+    err = np.abs(hi.astype(np.float64) + lo.astype(np.float64) - x.astype(np.float64))
+    assert np.all(err <= 2.0 ** -17 * np.abs(x.astype(np.float64)))
