@@ -20,8 +20,19 @@
  *    NULL = the legacy default stream) and is asynchronous unless stated.
  *  - Every call returns an mf_status.  Argument errors are detected on the host
  *    before anything is enqueued and leave the plan unchanged.  CUDA launch
- *    errors are returned as MF_ERR_CUDA by the call that hit them; kernel-side
- *    failures (device error word) are returned by the next mf_sync.
+ *    errors are returned as MF_ERR_CUDA by the call that hit them.  Kernel-side
+ *    failures (the plan's device error word: a bounded wait that ran out) are
+ *    returned by mf_sync, or by the next mf_apply / mf_cheb_propagate /
+ *    mf_cheb_filter / mf_rows_cheb_term on the plan once the earlier work has
+ *    finished (read without blocking); that call then enqueues nothing.  The
+ *    word is cleared when it is reported, so the plan stays usable.
+ *  - Fault injection for tests of these paths (host side only, no GPU fault is
+ *    ever caused): the environment variable MF_FAULT="<site>:<n>" makes the
+ *    n-th event of <site>, counted from the moment the variable took that
+ *    value, fail: "alloc" (a device allocation of the library reports out of
+ *    memory), "launch" (an apply kernel launch reports a launch failure,
+ *    nothing is launched), "plan" (a candidate plan the planner builds fails,
+ *    so the planner moves on to the next one).
  *  - Hermitian generators require M == D.  y must not alias x.
  *  - A plan (or batch) is used by one host thread at a time: its calls share
  *    the plan's workspace, partial slots and events.  Distinct plans are
@@ -111,6 +122,11 @@ typedef struct {
   int64_t row_begin;       /* row slice [row_begin, row_end) of a row-distributed plan */
   int64_t row_end;         /* (Sec. IV.H, row-parallel mode); 0, 0 = all rows; see
                               mf_plan_create */
+  int32_t spin_limit;      /* polls of one bounded wait inside the tensor-core kernels
+                              (0 = 2^22, a few hundred ms); when one runs out the kernel
+                              stops, frees its tensor memory and reports MF_ERR_TIMEOUT
+                              (the waits for its own copies and MMAs already issued keep
+                              the 2^22 bound whatever this value) */
 } mf_options;
 
 /* Generic planning instance P_mv of Sec. IV.A (Y = A X with A of size
@@ -446,7 +462,10 @@ mf_status mf_batch_propagate(mf_batch_t b, void* psi, double dt, int32_t nsteps,
 mf_status mf_batch_plan(mf_batch_t b, int32_t i, mf_plan_t* plan);
 mf_status mf_batch_info(mf_batch_t b, int32_t* n_items, int32_t* persist_grid);
 
-/* Wait for the plan's stream and report any device-side error word. */
+/* Wait for the plan's stream and report the device error word: MF_OK, or
+ * MF_ERR_TIMEOUT when a bounded wait ran out (codes 100..199, see
+ * mf_plan_describe's "last_device_error"), MF_ERR_CUDA for any other code.
+ * The word is cleared once reported. */
 mf_status mf_sync(mf_plan_t p);
 
 /*
@@ -483,12 +502,18 @@ mf_status mf_debug_entries(mf_plan_t p, int64_t r0, int64_t c0, int64_t rows, in
  * that every GPU loading the library holds until the process exits; no
  * cudaMalloc, cudaFree or other allocating call is made.  The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture.  Every call
- * on a device shares the one array and leaves its contents behind (nothing in
- * it needs clearing: the kernels write every scratch value they read), so
- * calls that overlap on the GPU -- on different streams, or from different
- * threads -- race and must be serialised by the caller.  Asynchronous;
- * errors: MF_ERR_INVALID, MF_ERR_CUDA.
+ * device current and keeps it.  CUDA loads device code lazily by default, so
+ * that first call also loads the kernels and the array and may need device
+ * memory: make it once, as a warm-up, before the caller's memory is reserved
+ * and before any stream capture.  The kept address does not survive a device
+ * reset (cudaDeviceReset or a re-created primary context): do not call this
+ * entry point on a device after resetting it.  Every call on a device shares
+ * the one array and leaves its contents behind (nothing in it needs clearing:
+ * the kernels write every scratch value they read), so calls that overlap on
+ * the GPU -- on different streams, or from different threads -- race and
+ * must be serialised by the caller.  Asynchronous; errors: MF_ERR_INVALID
+ * (also for a non-finite dvr_L), MF_ERR_OOM (the first call could not load
+ * the code or the array), MF_ERR_CUDA.
  */
 mf_status mf_apply_dvr_noalloc(int64_t D, double dvr_L, const void* x, void* y, void* stream);
 

@@ -66,6 +66,7 @@ class mf_options(ctypes.Structure):
         ("hermitian_reuse", ctypes.c_int32),
         ("row_begin", ctypes.c_int64),
         ("row_end", ctypes.c_int64),
+        ("spin_limit", ctypes.c_int32),
     ]
 
 

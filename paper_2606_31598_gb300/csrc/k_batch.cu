@@ -318,11 +318,11 @@ mf_status mf_batch_create(mf_batch_t* out, int32_t nprob, const int64_t* D, cons
     for (size_t k : idx) sorted.push_back(items[k]);
     b->n_items = (int)sorted.size();
     b->smem = o.precision == MF_PREC_FP64 ? rows_smem_bytes_async<double, 16>() : rows_smem_bytes_async<float, 16>();
-    cudaError_t e = cudaMalloc((void**)&b->d_items, sorted.size() * sizeof(BatchItem));
+    cudaError_t e = dev_malloc((void**)&b->d_items, sorted.size() * sizeof(BatchItem));
     if (e == cudaSuccess)
       e = cudaMemcpy(b->d_items, sorted.data(), sorted.size() * sizeof(BatchItem), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_counter, sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_probs, (size_t)nprob * sizeof(BatchProb));
+    if (e == cudaSuccess) e = dev_malloc((void**)&b->d_counter, sizeof(int));
+    if (e == cudaSuccess) e = dev_malloc((void**)&b->d_probs, (size_t)nprob * sizeof(BatchProb));
     // persistent grid: resident CTAs per SM x SMs
     int per_sm = 0;
     if (e == cudaSuccess) {

@@ -9,6 +9,12 @@
 // kernels' scratch (the FP32 copy of x and the partial-sum slots) lives in
 // one file-scope device array of fixed size that every GPU loading this
 // library holds until the process exits.
+//
+// CUDA loads a library's device code and arrays lazily by default, on first
+// use: the first call on a device loads the three kernels and the array and
+// may need device memory for that.  A caller makes that first call once, as
+// a warm-up, before its memory is reserved (and before any stream capture);
+// later calls load and allocate nothing.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -30,7 +36,10 @@ std::mutex g_mu;
 void* g_addr[kMaxDevices] = {};
 
 // Device address of the scratch array on the current device, looked up once
-// per device with that device current.
+// per device with that device current and kept for the life of the process.
+// A device reset (cudaDeviceReset, or the primary context destroyed and
+// created again) makes the kept address stale; callers that reset a device
+// must not call this entry point on it afterwards.
 cudaError_t scratch_address(int dev, void** out) {
   std::lock_guard<std::mutex> lock(g_mu);
   if (!g_addr[dev]) {
@@ -43,18 +52,24 @@ cudaError_t scratch_address(int dev, void** out) {
   return cudaSuccess;
 }
 
+mf_status status_of(cudaError_t e) {
+  if (e == cudaSuccess) return MF_OK;
+  return e == cudaErrorMemoryAllocation ? MF_ERR_OOM : MF_ERR_CUDA;
+}
+
 }  // namespace
 
 extern "C" mf_status mf_apply_dvr_noalloc(int64_t D, double dvr_L, const void* x, void* y, void* stream) {
   using namespace mf;
-  if (D < 2 || D > kNoAllocMaxD || !x || !y || !(dvr_L >= 0.0)) return MF_ERR_INVALID;
+  if (D < 2 || D > kNoAllocMaxD || !x || !y || !(dvr_L >= 0.0) || !std::isfinite(dvr_L)) return MF_ERR_INVALID;
   const size_t bytes = (size_t)D * sizeof(double2);
   const char *xb = (const char*)x, *yb = (const char*)y;
   if (yb < xb + bytes && xb < yb + bytes) return MF_ERR_INVALID;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MF_ERR_CUDA;
 
-  // the same launch shape the plan path picks for this D (FP32 form)
+  // the constants and launch shape the plan path sets up for this D (FP32
+  // form, procedural): the same helpers, so the two cannot drift apart
   Plan p;
   p.D = D;
   p.gen = MF_GEN_SINC_DVR_HO;
@@ -62,33 +77,23 @@ extern "C" mf_status mf_apply_dvr_noalloc(int64_t D, double dvr_L, const void* x
   p.stream = (cudaStream_t)stream;
   p.device = dev;
   if (cudaDeviceGetAttribute(&p.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return MF_ERR_CUDA;
-  const double L = dvr_L > 0 ? dvr_L : 0.9 * std::sqrt(2.0 * (double)D);
-  p.dvr.L = L;
-  p.dvr.dx = (2.0 * L) / (double)(D - 1);
-  p.dvr.dx2 = p.dvr.dx * p.dvr.dx;
-  p.dvr.t0_64 = 0x1.a51a6625307d3p+0 / p.dvr.dx2;
-  p.dvr.t0_32 = (float)p.dvr.t0_64;
-  p.dvr.c32 = (float)(1.0 / p.dvr.dx2);
+  dvr_setup(p.dvr, D, dvr_L);
   p.use_dvr_window = true;
-  const DvrRowsShape s = dvr_rows_shape(D, p.num_sms);
-  p.dvr_rows = (int)s.rows;
-  p.dvr_cols = (int)s.cols;
-  p.nslot = s.nslot;
-  p.dpad = s.dpad;
+  dvr_fp32_window_shape(p);
 
   const size_t xc_bytes = ((size_t)p.dpad * sizeof(float2) + 255) & ~(size_t)255;
   const size_t part_bytes = (size_t)p.nslot * (size_t)p.dpad * sizeof(float2);
   if (xc_bytes + part_bytes > kNoAllocScratchBytes) return MF_ERR_INVALID;
 
   void* base = nullptr;
-  if (scratch_address(dev, &base) != cudaSuccess) return MF_ERR_CUDA;
+  mf_status st = status_of(scratch_address(dev, &base));
+  if (st != MF_OK) return st;
   void* xc = base;
   void* part = (char*)base + xc_bytes;
   // every partial slot row the reduction reads is written by the apply kernel
   // first, so no part of the scratch needs clearing between calls
   const VecShape sh{1, 1, p.nslot, p.dpad};
-  if (launch_to_compute(p, (const double2*)x, xc, D, sh) != cudaSuccess) return MF_ERR_CUDA;
-  if (launch_dvr_apply(p, xc, part, 1) != cudaSuccess) return MF_ERR_CUDA;
-  if (launch_reduce(p, part, (const double2*)x, (double2*)y, sh) != cudaSuccess) return MF_ERR_CUDA;
-  return MF_OK;
+  if ((st = status_of(launch_to_compute(p, (const double2*)x, xc, D, sh))) != MF_OK) return st;
+  if ((st = status_of(launch_dvr_apply(p, xc, part, 1))) != MF_OK) return st;
+  return status_of(launch_reduce(p, part, (const double2*)x, (double2*)y, sh));
 }

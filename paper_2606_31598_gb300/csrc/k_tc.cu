@@ -39,7 +39,10 @@ constexpr int NGEN = 16;                     // generator warps (fill the A plan
 constexpr int MMA_WARP = NGEN;               // the copy/MMA-issuing warp
 constexpr int NTHREADS = (NGEN + 1) * 32;
 constexpr int A_PLANE = RT * KC * 2;  // bytes of one bf16 plane of the chunk (8 KB)
-constexpr uint32_t kSpinLimit = 1u << 22;
+// Waits for work this CTA issued itself (its bulk copies, its committed
+// MMAs) always complete; they keep this bound whatever the plan's spin limit,
+// so that a CTA never leaves with a copy or an MMA in flight.
+constexpr uint32_t kDrainSpin = kDefaultSpin;
 // The tensor core's FP32 accumulation is not round-to-nearest over long
 // chains, so TMEM accumulates SEG chunks (SEG * 12 MMAs) at a time and is
 // then drained into an FP32 accumulator in shared memory with ordinary
@@ -81,9 +84,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// bounded wait; false on time-out
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (uint32_t i = 0; i < kSpinLimit; ++i)
+// bounded wait of at most `limit` polls; false on time-out
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit) {
+  for (uint32_t i = 0; i < limit; ++i)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
@@ -290,7 +293,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     tc_rows(int64_t D, int64_t dpad, int64_t split_cols, uint64_t seed, float sigma, dvr_consts dk,
             const unsigned char* __restrict__ gB, float2* __restrict__ part, const float2* __restrict__ cache,
             const int64_t* __restrict__ slot_of_pair, int64_t b, int64_t nblk, int* __restrict__ err,
-            const float2* __restrict__ hcache) {
+            const float2* __restrict__ hcache, uint32_t spin) {
   constexpr int N = 2 * NV;             // MMA N: [Re | Im] of NV vectors
   constexpr int B_TILE = N * KC * 2;    // bytes of one bf16 B tile
   constexpr int B_CHUNK = 4 * B_TILE;   // B1 hi, B1 lo, B2 hi, B2 lo
@@ -346,19 +349,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           unsigned char* A = smem + s * STAGE;
           unsigned char* B = A + 4 * A_PLANE;
           // the stage's previous MMAs (chunk kc - 2) must be done before its X tiles are replaced
-          if (kc >= 2 && !mbar_wait(&mma_bar[s], (uint32_t)(((kc - 2) >> 1) & 1))) {
+          if (kc >= 2 && !mbar_wait(&mma_bar[s], (uint32_t)(((kc - 2) >> 1) & 1), spin)) {
             atomicCAS(err, 0, 100 + s);
             abort_flag = 1;
             break;
           }
           mbar_expect_tx(&b_full[s], (uint32_t)B_CHUNK);
           bulk_g2s(B, gB + ((cbeg + (int64_t)kc * KC) / KC) * (int64_t)B_CHUNK, (uint32_t)B_CHUNK, &b_full[s]);
-          const bool a_ok = mbar_wait(&a_full[s], (uint32_t)((kc >> 1) & 1));
-          const bool b_ok = mbar_wait(&b_full[s], (uint32_t)((kc >> 1) & 1));
+          const bool a_ok = mbar_wait(&a_full[s], (uint32_t)((kc >> 1) & 1), spin);
+          // the copy just issued: wait for it in any case
+          const bool b_ok = mbar_wait(&b_full[s], (uint32_t)((kc >> 1) & 1), kDrainSpin);
           if (!a_ok || !b_ok) {
             atomicCAS(err, 0, a_ok ? 111 : 110);
             abort_flag = 1;
-            if (!b_ok) mbar_wait(&b_full[s], (uint32_t)((kc >> 1) & 1));  // bounded wait for the copy in flight
             break;
           }
           tc_fence_after();
@@ -382,7 +385,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           last = kc;
         }
         // the segment's MMAs complete in issue order: wait for the last one
-        if (last >= 0 && !mbar_wait(&mma_bar[last & 1], (uint32_t)((last >> 1) & 1))) {
+        if (last >= 0 && !mbar_wait(&mma_bar[last & 1], (uint32_t)((last >> 1) & 1), kDrainSpin)) {
           atomicCAS(err, 0, 120);
           abort_flag = 1;
         }
@@ -394,7 +397,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int s = kc & 1;
         if (kc >= 2) {
           bool ok = true;
-          if (lane == 0) ok = mbar_wait(&mma_bar[s], (uint32_t)(((kc - 2) >> 1) & 1));
+          if (lane == 0) ok = mbar_wait(&mma_bar[s], (uint32_t)(((kc - 2) >> 1) & 1), spin);
           ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
           if (!ok) {
             if (lane == 0) {
@@ -485,7 +488,7 @@ cudaError_t launch_tc_t(const Plan& p, const void* xc, void* part, void* gB, int
   k<<<grid, NTHREADS, smem, p.stream>>>(p.D, p.ntile * (int64_t)kTile, p.rows_split_cols, p.seed, p.sigma32, p.dvr,
                                         (const unsigned char*)gB, (float2*)part,
                                         p.pairs_cached > 0 ? (const float2*)p.d_cache : nullptr, p.d_pair_slot, p.b,
-                                        p.nblk, err, (const float2*)p.d_hblocks);
+                                        p.nblk, err, (const float2*)p.d_hblocks, p.spin);
   return cudaGetLastError();
 }
 

@@ -11,7 +11,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -19,6 +21,57 @@
 #include "mf_internal.h"
 
 using namespace mf;
+
+namespace mf {
+
+namespace {
+std::mutex g_fault_mu;
+std::string g_fault_value;  // MF_FAULT as last seen
+long long g_fault_count = 0;  // events of its site since it took that value
+}  // namespace
+
+bool fault_hit(const char* site) {
+  const char* v = std::getenv("MF_FAULT");
+  if (!v || !*v) return false;
+  std::lock_guard<std::mutex> lock(g_fault_mu);
+  if (g_fault_value != v) {
+    g_fault_value = v;
+    g_fault_count = 0;
+  }
+  const char* colon = std::strchr(v, ':');
+  const size_t n = colon ? (size_t)(colon - v) : std::strlen(v);
+  if (std::strlen(site) != n || std::strncmp(site, v, n) != 0) return false;
+  const long long want = colon ? std::atoll(colon + 1) : 1;
+  return ++g_fault_count == want;
+}
+
+cudaError_t dev_malloc(void** ptr, size_t bytes) {
+  if (fault_hit("alloc")) {
+    *ptr = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(ptr, bytes);
+}
+
+void dvr_setup(dvr_consts& k, int64_t D, double L) {
+  k.L = L > 0 ? L : 0.9 * std::sqrt(2.0 * (double)D);
+  k.dx = (2.0 * k.L) / (double)(D - 1);
+  k.dx2 = k.dx * k.dx;
+  const double PI2_6 = 0x1.a51a6625307d3p+0;  // pi^2 / 6 rounded to double
+  k.t0_64 = PI2_6 / k.dx2;
+  k.t0_32 = (float)k.t0_64;
+  k.c32 = (float)(1.0 / k.dx2);
+}
+
+void dvr_fp32_window_shape(Plan& p) {
+  const DvrRowsShape s = dvr_rows_shape(p.D, p.num_sms);
+  p.dvr_rows = (int)s.rows;
+  p.dvr_cols = (int)s.cols;
+  p.nslot = s.nslot;
+  p.dpad = s.dpad;
+}
+
+}  // namespace mf
 
 namespace {
 
@@ -50,6 +103,52 @@ void free_dev(T*& ptr) {
   ptr = nullptr;
 }
 
+// cudaMalloc through the fault-injection site, typed.
+template <typename T>
+cudaError_t dmalloc(T** ptr, size_t bytes) {
+  void* v = nullptr;
+  const cudaError_t e = dev_malloc(&v, bytes);
+  *ptr = (T*)v;
+  return e;
+}
+
+mf_status status_of_device_code(int code) {
+  if (code == 0) return MF_OK;
+  if (code >= kErrTimeoutFirst && code <= kErrTimeoutLast) return MF_ERR_TIMEOUT;
+  return MF_ERR_CUDA;
+}
+
+bool capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  return cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone;
+}
+
+// The device error word an earlier call left, read without blocking: only
+// once the copy enqueued after that call has completed.  A nonzero word is
+// cleared and reported; the calling entry point then enqueues nothing.
+mf_status pending_device_error(Plan& p) {
+  if (!p.err_pending || capturing(p.stream)) return MF_OK;
+  const cudaError_t q = cudaEventQuery(p.err_ev);
+  if (q == cudaErrorNotReady) return MF_OK;
+  if (q != cudaSuccess) return MF_ERR_CUDA;
+  p.err_pending = false;
+  const int code = *(volatile int*)p.h_err;
+  if (code == 0) return MF_OK;
+  p.last_dev_err = code;
+  if (cudaMemsetAsync(p.d_err, 0, sizeof(int), p.stream) != cudaSuccess) return MF_ERR_CUDA;
+  return status_of_device_code(code);
+}
+
+// After a call whose kernels may set the word: enqueue its copy to the host.
+mf_status post_device_error_copy(Plan& p) {
+  if (!p.has_waits || capturing(p.stream)) return MF_OK;
+  if (cudaMemcpyAsync(p.h_err, p.d_err, sizeof(int), cudaMemcpyDeviceToHost, p.stream) != cudaSuccess ||
+      cudaEventRecord(p.err_ev, p.stream) != cudaSuccess)
+    return MF_ERR_CUDA;
+  p.err_pending = true;
+  return MF_OK;
+}
+
 void release(Plan& p) {
   for (auto& e : p.ev) {
     cudaEventDestroy(e.first);
@@ -67,6 +166,11 @@ void release(Plan& p) {
   free_dev(p.d_J);
   free_dev(p.d_red);
   free_dev(p.d_err);
+  if (p.h_err) cudaFreeHost(p.h_err);
+  p.h_err = nullptr;
+  if (p.err_ev) cudaEventDestroy(p.err_ev);
+  p.err_ev = nullptr;
+  p.err_pending = false;
   if (p.h_registered) cudaHostUnregister(const_cast<void*>(p.h_blocks));
   p.h_registered = false;
   free_dev(p.d_sb_seeds);
@@ -137,7 +241,7 @@ mf_status ensure_workspace(Plan& p, int64_t nvec) {
     if (*ptr) cudaFree(*ptr);
     *ptr = nullptr;
     cap = 0;
-    MF_CUDA(cudaMalloc(ptr, need));
+    MF_CUDA(dev_malloc(ptr, need));
     if (zero) MF_CUDA(cudaMemset(*ptr, 0, need));
     cap = need;
     return MF_OK;
@@ -159,7 +263,7 @@ mf_status ensure_J(Plan& p, int32_t K) {
   if (K + 1 <= p.J_cap) return MF_OK;
   free_dev(p.d_J);
   const int32_t cap = std::max<int32_t>(K + 1, 256);
-  MF_CUDA(cudaMalloc((void**)&p.d_J, (size_t)cap * sizeof(double)));
+  MF_CUDA(dmalloc(&p.d_J, (size_t)cap * sizeof(double)));
   p.J_cap = cap;
   p.J_arg = -1.0;
   return MF_OK;
@@ -177,6 +281,7 @@ mf_status apply_kernel(Plan& p, int64_t nvec) {
     }
     MF_CUDA(cudaEventRecord(p.ev[p.ev_used].first, p.stream));
   }
+  if (fault_hit("launch")) return MF_ERR_CUDA;
   const int64_t nbr = rows_nvec_bucket(nvec);
   const bool herm = !p.sliced && (nvec > 1 || p.sb_nop) && p.prec != MF_PREC_BF16X2 && use_rows_herm(p, nbr);
   if (herm) {
@@ -268,7 +373,7 @@ mf_status compute_bounds(Plan& p) {
   if (st != MF_OK) return st;
   double2 *v = p.d_q[0], *vp = p.d_q[1], *w = p.d_q[2];
   double* d_s = nullptr;
-  MF_CUDA(cudaMalloc((void**)&d_s, 2 * sizeof(double)));
+  MF_CUDA(dmalloc(&d_s, 2 * sizeof(double)));
   auto dot = [&](const double2* a, const double2* b, double* out) -> mf_status {
     MF_CUDA(launch_dot(p, a, b, n, d_s));
     MF_CUDA(cudaMemcpyAsync(out, d_s, sizeof(double), cudaMemcpyDeviceToHost, p.stream));
@@ -387,14 +492,10 @@ mf_status create_fixed(mf_plan_t* out, int64_t D, int32_t generator, uint64_t se
   // generator constants
   p.sigma64 = std::sqrt(0.5 / (double)D);
   p.sigma32 = sqrtf(0.5f / (float)D);
-  const double L = o.dvr_L > 0 ? o.dvr_L : 0.9 * std::sqrt(2.0 * (double)D);
-  p.dvr.L = L;
-  p.dvr.dx = (2.0 * L) / (double)(D - 1);
-  p.dvr.dx2 = p.dvr.dx * p.dvr.dx;
-  const double PI2_6 = 0x1.a51a6625307d3p+0;
-  p.dvr.t0_64 = PI2_6 / p.dvr.dx2;
-  p.dvr.t0_32 = (float)p.dvr.t0_64;
-  p.dvr.c32 = (float)(1.0 / p.dvr.dx2);
+  dvr_setup(p.dvr, D, o.dvr_L);
+  // the tensor-core kernels are the ones with bounded waits
+  p.has_waits = p.prec == MF_PREC_BF16X2;
+  p.spin = o.spin_limit > 0 ? (uint32_t)o.spin_limit : kDefaultSpin;
 
   // partition (Sec. II / IV.F): b multiple of the tile, at most D rounded up
   const int64_t Dt = (D + kTile - 1) / kTile * kTile;
@@ -441,11 +542,7 @@ mf_status create_fixed(mf_plan_t* out, int64_t D, int32_t generator, uint64_t se
   const int64_t nv = std::max(1, o.nvec_hint);
   p.use_dvr_window = generator == MF_GEN_SINC_DVR_HO && pc == 0 && p.prec != MF_PREC_BF16X2 && !p.sliced;
   if (p.use_dvr_window && p.prec == MF_PREC_FP32) {
-    const DvrRowsShape s = dvr_rows_shape(D, p.num_sms);
-    p.dvr_rows = (int)s.rows;
-    p.dvr_cols = (int)s.cols;
-    p.nslot = s.nslot;
-    p.dpad = s.dpad;
+    dvr_fp32_window_shape(p);
   } else if (p.use_dvr_window) {
     const int P = 8;
     p.dvr_rows = 32 * P;
@@ -490,9 +587,14 @@ mf_status create_fixed(mf_plan_t* out, int64_t D, int32_t generator, uint64_t se
   p.w_hpsi = (double)D * (double)D;
   p.dense_warn = p.w_hpsi > o.dense_work_limit;
 
-  if (cudaMalloc((void**)&p.d_err, sizeof(int)) != cudaSuccess) return fail(MF_ERR_OOM);
+  if (dmalloc(&p.d_err, sizeof(int)) != cudaSuccess) return fail(MF_ERR_OOM);
   if (cudaMemsetAsync(p.d_err, 0, sizeof(int), p.stream) != cudaSuccess) return fail(MF_ERR_CUDA);
-  if (cudaMalloc((void**)&p.d_red, kRedDoubles * sizeof(double)) != cudaSuccess) return fail(MF_ERR_OOM);
+  if (dmalloc(&p.d_red, kRedDoubles * sizeof(double)) != cudaSuccess) return fail(MF_ERR_OOM);
+  if (p.has_waits) {
+    if (cudaHostAlloc((void**)&p.h_err, sizeof(int), cudaHostAllocDefault) != cudaSuccess) return fail(MF_ERR_OOM);
+    *p.h_err = 0;
+    if (cudaEventCreateWithFlags(&p.err_ev, cudaEventDisableTiming) != cudaSuccess) return fail(MF_ERR_CUDA);
+  }
 
   // cache: the first P_cache canonical pairs in row order
   p.pair_slot.assign((size_t)(p.nblk * p.nblk), -1);
@@ -530,7 +632,7 @@ mf_status create_fixed(mf_plan_t* out, int64_t D, int32_t generator, uint64_t se
   }
   if (p.pairs_cached > 0) {
     p.cache_bytes = (size_t)p.pairs_cached * (size_t)blk_bytes;
-    cudaError_t e = cudaMalloc(&p.d_cache, p.cache_bytes);
+    cudaError_t e = dev_malloc(&p.d_cache, p.cache_bytes);
     if (e != cudaSuccess) return fail(MF_ERR_OOM);
   }
   if (p.pairs_cached > 0 && generator == MF_GEN_EXTERNAL) {
@@ -539,7 +641,7 @@ mf_status create_fixed(mf_plan_t* out, int64_t D, int32_t generator, uint64_t se
   } else if (p.pairs_cached > 0) {
     cudaError_t e;
     int2* d_pairs = nullptr;
-    if (cudaMalloc((void**)&d_pairs, pairs.size() * sizeof(int2)) != cudaSuccess) return fail(MF_ERR_OOM);
+    if (dmalloc(&d_pairs, pairs.size() * sizeof(int2)) != cudaSuccess) return fail(MF_ERR_OOM);
     cudaMemcpyAsync(d_pairs, pairs.data(), pairs.size() * sizeof(int2), cudaMemcpyHostToDevice, p.stream);
     e = launch_cache_fill_pairs(p, d_pairs, (int64_t)pairs.size());
     cudaStreamSynchronize(p.stream);
@@ -577,7 +679,7 @@ mf_status create_fixed(mf_plan_t* out, int64_t D, int32_t generator, uint64_t se
       work.push_back(take_c ? cached[ic++] : proc[ip++]);
     }
     p.nwork = (int64_t)work.size();
-    if (cudaMalloc((void**)&p.d_work, work.size() * sizeof(WorkItem)) != cudaSuccess) return fail(MF_ERR_OOM);
+    if (dmalloc(&p.d_work, work.size() * sizeof(WorkItem)) != cudaSuccess) return fail(MF_ERR_OOM);
     if (cudaMemcpyAsync(p.d_work, work.data(), work.size() * sizeof(WorkItem), cudaMemcpyHostToDevice,
                         p.stream) != cudaSuccess)
       return fail(MF_ERR_CUDA);
@@ -589,14 +691,14 @@ mf_status create_fixed(mf_plan_t* out, int64_t D, int32_t generator, uint64_t se
     p.herm_limit = std::min(16e9, 0.1 * (double)mfree_now);
     const std::vector<HermItem> hi = rows_herm_items(D, p.num_sms, &p.herm_ns);
     p.herm_nitems = (int64_t)hi.size();
-    if (cudaMalloc((void**)&p.d_herm_items, hi.size() * sizeof(HermItem)) != cudaSuccess) return fail(MF_ERR_OOM);
+    if (dmalloc(&p.d_herm_items, hi.size() * sizeof(HermItem)) != cudaSuccess) return fail(MF_ERR_OOM);
     if (cudaMemcpyAsync(p.d_herm_items, hi.data(), hi.size() * sizeof(HermItem), cudaMemcpyHostToDevice,
                         p.stream) != cudaSuccess)
       return fail(MF_ERR_CUDA);
   }
   if (p.pairs_cached > 0 || generator == MF_GEN_EXTERNAL) {
     const size_t nb = p.pair_slot.size() * sizeof(int64_t);
-    if (cudaMalloc((void**)&p.d_pair_slot, nb) != cudaSuccess) return fail(MF_ERR_OOM);
+    if (dmalloc(&p.d_pair_slot, nb) != cudaSuccess) return fail(MF_ERR_OOM);
     if (cudaMemcpyAsync(p.d_pair_slot, p.pair_slot.data(), nb, cudaMemcpyHostToDevice, p.stream) != cudaSuccess)
       return fail(MF_ERR_CUDA);
   }
@@ -634,8 +736,8 @@ namespace {
 mf_status measure_plan(Plan& p, int64_t nvec, int warm, int reps, double* t_mean) {
   double2 *x = nullptr, *y = nullptr;
   const size_t bytes = (size_t)p.D * (size_t)nvec * sizeof(double2);
-  if (cudaMalloc((void**)&x, bytes) != cudaSuccess) return MF_ERR_OOM;
-  if (cudaMalloc((void**)&y, bytes) != cudaSuccess) {
+  if (dmalloc(&x, bytes) != cudaSuccess) return MF_ERR_OOM;
+  if (dmalloc(&y, bytes) != cudaSuccess) {
     cudaFree(x);
     return MF_ERR_OOM;
   }
@@ -744,6 +846,7 @@ void mf_options_default(mf_options* o) {
   o->hermitian_reuse = -1;
   o->row_begin = 0;
   o->row_end = 0;
+  o->spin_limit = 0;
 }
 
 const char* mf_status_string(mf_status s) {
@@ -779,6 +882,7 @@ mf_status mf_plan_create(mf_plan_t* out, int64_t D, int64_t M, int32_t generator
     if (o.nvec_hint < 1 || o.nvec_hint > 64 || o.autotune_k < 1 || o.autotune_repeats < 1 || o.autotune_warmup < 0)
       return MF_ERR_INVALID;
     if (o.hermitian_reuse < -1 || o.hermitian_reuse > 1) return MF_ERR_INVALID;
+    if (!(o.dvr_L >= 0.0) || !std::isfinite(o.dvr_L) || o.spin_limit < 0) return MF_ERR_INVALID;
     if ((o.planner_mode == MF_PLANNER_LEARNED || o.planner_mode == MF_PLANNER_HYBRID) && !o.model)
       return MF_ERR_INVALID;
 
@@ -851,6 +955,7 @@ mf_status mf_plan_create(mf_plan_t* out, int64_t D, int64_t M, int32_t generator
       return (size_t)((double)r.e.pairs_cached * r.e.M_block);
     };
     auto build = [&](const Ranked& r, mf_plan_t* h) {
+      if (fault_hit("plan")) return MF_ERR_OOM;  // injected: this candidate fails to build
       mf_options oc = o;
       oc.storage = r.c.storage;
       return create_fixed(h, D, generator, seed, r.c.block, budget_for(r), oc);
@@ -966,7 +1071,7 @@ mf_status mf_external_create(mf_plan_t* out, int64_t D, int64_t block, const voi
     if (o.precision != MF_PREC_FP64 && o.precision != MF_PREC_FP32 && o.precision != MF_PREC_BF16X2)
       return MF_ERR_INVALID;
     if (!(o.cheb_tol > 0) || o.lanczos_m < 2 || !(o.alpha_safety > 0 && o.alpha_safety <= 1)) return MF_ERR_INVALID;
-    if (o.nvec_hint < 1 || o.nvec_hint > 64) return MF_ERR_INVALID;
+    if (o.nvec_hint < 1 || o.nvec_hint > 64 || o.spin_limit < 0) return MF_ERR_INVALID;
     if (o.hermitian_reuse < -1 || o.hermitian_reuse > 1) return MF_ERR_INVALID;
     // block larger than D rounded to the tile: the stored blocks would be
     // smaller than b x b
@@ -1017,9 +1122,9 @@ mf_status mf_sysbath_create(mf_plan_t* out, int64_t d_S, int64_t d_B, int32_t n_
       *out = nullptr;
       return s;
     };
-    if (cudaMalloc((void**)&p.d_sb_seeds, nop * sizeof(uint64_t)) != cudaSuccess ||
-        cudaMalloc((void**)&p.d_sb_M, M.size() * sizeof(double2)) != cudaSuccess ||
-        cudaMalloc((void**)&p.d_sb_HS, (size_t)d_S * d_S * sizeof(double2)) != cudaSuccess)
+    if (dmalloc(&p.d_sb_seeds, nop * sizeof(uint64_t)) != cudaSuccess ||
+        dmalloc(&p.d_sb_M, M.size() * sizeof(double2)) != cudaSuccess ||
+        dmalloc(&p.d_sb_HS, (size_t)d_S * d_S * sizeof(double2)) != cudaSuccess)
       return fail(MF_ERR_OOM);
     if (cudaMemcpy(p.d_sb_seeds, seeds, nop * sizeof(uint64_t), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(p.d_sb_M, M.data(), M.size() * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -1054,7 +1159,10 @@ mf_status mf_apply(mf_plan_t h, void* y, const void* x, int64_t nvec) {
   const char *yb = (const char*)y, *xb = (const char*)x;
   if (yb < xb + xbytes && xb < yb + ybytes) return MF_ERR_INVALID;
   DeviceGuard guard(p.device);
-  return apply_internal(p, (double2*)y, (const double2*)x, nvec);
+  mf_status st = pending_device_error(p);
+  if (st != MF_OK) return st;
+  if ((st = apply_internal(p, (double2*)y, (const double2*)x, nvec)) != MF_OK) return st;
+  return post_device_error_copy(p);
 }
 
 mf_status mf_spectral_bounds(mf_plan_t h, double* emin, double* emax) {
@@ -1092,7 +1200,9 @@ mf_status mf_cheb_propagate(mf_plan_t h, void* psi, int64_t nvec, double dt, int
   if (p.sb_nop && nvec != p.sb_dS) return MF_ERR_INVALID;
   if (p.sliced) return MF_ERR_UNSUPPORTED;  // row groups use mf_rows_cheb_*
   DeviceGuard guard(p.device);
-  mf_status st = compute_bounds(p);
+  mf_status st = pending_device_error(p);
+  if (st != MF_OK) return st;
+  st = compute_bounds(p);
   if (st != MF_OK) return st;
   const double c = 0.5 * (p.emax + p.emin), R = 0.5 * (p.emax - p.emin);
   int32_t nt = 0;
@@ -1111,7 +1221,7 @@ mf_status mf_cheb_propagate(mf_plan_t h, void* psi, int64_t nvec, double dt, int
     std::swap(q_cur, q_prev);
   }
   MF_CUDA(launch_cheb_final(p, acc, (double2*)psi, p.D * nvec, c, dt));
-  return MF_OK;
+  return post_device_error_copy(p);
 }
 
 mf_status mf_rows_cheb_begin(mf_plan_t h, double dt, int32_t order, int32_t* nterms) {
@@ -1141,15 +1251,16 @@ mf_status mf_rows_cheb_term(mf_plan_t h, int32_t j, const void* q_full, void* q_
   Plan& p = h->p;
   if (!p.sliced || p.J_arg < 0 || j > p.J_K) return MF_ERR_INVALID;
   DeviceGuard guard(p.device);
-  mf_status st = ensure_workspace(p, nvec);
+  mf_status st = pending_device_error(p);
   if (st != MF_OK) return st;
+  if ((st = ensure_workspace(p, nvec)) != MF_OK) return st;
   // y = H q_j on the slice, into the plan's own vector workspace
   double2* y = p.d_q[2];
   if ((st = apply_internal(p, y, (const double2*)q_full, nvec)) != MF_OK) return st;
   const double c = 0.5 * (p.emax + p.emin), R = 0.5 * (p.emax - p.emin);
   MF_CUDA(launch_cheb_rows_term(p, y, (const double2*)q_full, (double2*)q_prev_slice, (double2*)q_next_slice,
                                 (double2*)acc_slice, nvec, j, c, R));
-  return MF_OK;
+  return post_device_error_copy(p);
 }
 
 mf_status mf_rows_cheb_final(mf_plan_t h, const void* acc_slice, void* psi_slice, int64_t nvec, double dt) {
@@ -1182,8 +1293,9 @@ mf_status mf_cheb_filter(mf_plan_t h, void* psi, int64_t nvec, double tau, int32
   if (p.sb_nop && nvec != p.sb_dS) return MF_ERR_INVALID;
   if (p.sliced) return MF_ERR_UNSUPPORTED;
   DeviceGuard guard(p.device);
-  mf_status st = compute_bounds(p);
+  mf_status st = pending_device_error(p);
   if (st != MF_OK) return st;
+  if ((st = compute_bounds(p)) != MF_OK) return st;
   const double c = 0.5 * (p.emax + p.emin), R = 0.5 * (p.emax - p.emin);
   int32_t nt = 0;
   st = coefficients(p, R * tau, order, &nt, 1);
@@ -1205,7 +1317,7 @@ mf_status mf_cheb_filter(mf_plan_t h, void* psi, int64_t nvec, double tau, int32
     MF_CUDA(launch_filter_final(p, acc, (double2*)psi, p.D * nvec, 1, normalize != 0));
   else
     MF_CUDA(launch_filter_final(p, acc, (double2*)psi, p.D, nvec, normalize != 0));
-  return MF_OK;
+  return post_device_error_copy(p);
 }
 
 mf_status mf_plan_profile(mf_plan_t h, int32_t enable) {
@@ -1240,9 +1352,13 @@ mf_status mf_sync(mf_plan_t h) {
   if (cudaMemcpyAsync(&err, p.d_err, sizeof(int), cudaMemcpyDeviceToHost, p.stream) != cudaSuccess)
     return MF_ERR_CUDA;
   if (cudaStreamSynchronize(p.stream) != cudaSuccess) return MF_ERR_CUDA;
-  if (err == 1) return MF_ERR_TIMEOUT;
-  if (err != 0) return MF_ERR_CUDA;
-  return MF_OK;
+  p.err_pending = false;
+  if (err == 0) return MF_OK;
+  p.last_dev_err = err;
+  if (cudaMemsetAsync(p.d_err, 0, sizeof(int), p.stream) != cudaSuccess ||
+      cudaStreamSynchronize(p.stream) != cudaSuccess)
+    return MF_ERR_CUDA;
+  return status_of_device_code(err);
 }
 
 mf_status mf_plan_describe(mf_plan_t h, char* buf, size_t len) {
@@ -1256,13 +1372,13 @@ mf_status mf_plan_describe(mf_plan_t h, char* buf, size_t len) {
       "\"pairs_cached\": %lld, \"cache_bytes\": %zu, \"path\": \"%s\", \"tile\": %d, \"dvr_rows\": %d, "
       "\"dvr_cols\": %d, \"n_slot\": %lld, \"n_work\": %lld, \"w_hpsi\": %.6g, \"dense_warn\": %s, "
       "\"dvr_L\": %.17g, \"dvr_dx\": %.17g, \"have_bounds\": %s, \"emin\": %.17g, \"emax\": %.17g, "
-      "\"num_sms\": %d, \"sb_nop\": %d, \"sb_dS\": %d}",
+      "\"num_sms\": %d, \"sb_nop\": %d, \"sb_dS\": %d, \"spin_limit\": %u, \"last_device_error\": %d}",
       (long long)p.D, gen_name(p.gen), (unsigned long long)p.seed, prec_name(p.prec), (long long)p.b,
       (long long)p.nblk, (long long)p.npair, store_name(p.storage), p.cache_budget, (long long)p.pairs_cached,
       p.cache_bytes, p.sb_nop ? "sysbath_rows" : (p.use_dvr_window ? "dvr_window" : "herm_tile"), kTile, p.dvr_rows,
       p.dvr_cols,
       (long long)p.nslot, (long long)p.nwork, p.w_hpsi, p.dense_warn ? "true" : "false", p.dvr.L, p.dvr.dx,
-      p.have_bounds ? "true" : "false", p.emin, p.emax, p.num_sms, p.sb_nop, p.sb_dS);
+      p.have_bounds ? "true" : "false", p.emin, p.emax, p.num_sms, p.sb_nop, p.sb_dS, p.spin, p.last_dev_err);
   if (n < 0) return MF_ERR_INVALID;
   std::strncpy(buf, tmp, len - 1);
   buf[len - 1] = '\0';
@@ -1277,7 +1393,7 @@ mf_status mf_debug_entries(mf_plan_t h, int64_t r0, int64_t c0, int64_t rows, in
   DeviceGuard guard(p.device);
   const size_t bytes = (size_t)rows * (size_t)cols * compute_elem_bytes(p.prec);
   void* d = nullptr;
-  MF_CUDA(cudaMalloc(&d, bytes));
+  MF_CUDA(dev_malloc(&d, bytes));
   cudaError_t e = launch_debug_entries(p, r0, c0, rows, cols, d);
   if (e == cudaSuccess) e = cudaMemcpyAsync(out_host, d, bytes, cudaMemcpyDeviceToHost, p.stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(p.stream);

@@ -17,6 +17,17 @@ namespace mf {
 
 constexpr int kTile = 128;  // CTA tile edge of the Hermitian (canonical-pair) kernels
 
+// Device error word codes: kernels set the word with atomicCAS(word, 0, code)
+// when a bounded wait runs out; the code says which wait (100..199).
+constexpr int kErrTimeoutFirst = 100, kErrTimeoutLast = 199;
+constexpr uint32_t kDefaultSpin = 1u << 22;  // polls of a bounded wait
+
+// Host-side fault injection (MF_FAULT="<site>:<n>", see include/mf.h): true
+// when this event of the site is the n-th since the variable took its value.
+bool fault_hit(const char* site);
+// cudaMalloc through the "alloc" injection site.
+cudaError_t dev_malloc(void** ptr, size_t bytes);
+
 // One CTA work item of the Hermitian apply: canonical tile (ti <= tj) in units
 // of kTile, and the byte offset of its block in the HBM cache (-1 when the
 // block pair is generated procedurally).
@@ -93,6 +104,12 @@ struct Plan {
   int32_t J_cap = 0;
   double* d_red = nullptr;        // small reduction scratch (dots/norms)
   int* d_err = nullptr;           // device error word
+  int* h_err = nullptr;           // pinned host copy of the word, read without blocking
+  cudaEvent_t err_ev = nullptr;   // recorded after the copy into h_err
+  bool err_pending = false;       // a copy into h_err was enqueued and not yet read
+  bool has_waits = false;         // the plan's kernels have bounded waits (tensor-core form)
+  uint32_t spin = kDefaultSpin;   // polls of one bounded wait (mf_options.spin_limit)
+  int last_dev_err = 0;           // last device error code reported
   // spectral bounds
   bool have_bounds = false;
   double emin = 0.0, emax = 0.0;
@@ -124,6 +141,13 @@ struct Plan {
   void* d_sb_xo = nullptr;         // [nop][rows][nb] mixed inputs X M_o^T (compute precision)
   int64_t sb_rows = 0;             // rows of each mixed input
 };
+
+// Generator constants of the sinc-DVR operator on D points of [-L, L]
+// (L <= 0 selects 0.9 sqrt(2D)), and the launch shape of the FP32 Toeplitz
+// window kernel for one vector (dvr_rows, dvr_cols, nslot, dpad).  Shared by
+// plan creation and the allocation-free entry point.
+void dvr_setup(dvr_consts& k, int64_t D, double L);
+void dvr_fp32_window_shape(Plan& p);
 
 // Plan services shared with the batched path (mf_api.cu).
 mf_status plan_workspace(Plan& p, int64_t nvec);

@@ -48,22 +48,36 @@ def slices(D, world, tile=128):
     return out
 
 
-def dist_allgather(group=None):
+def dist_allgather(group=None, host=False):
     """An allgather for torch.distributed (NCCL on GPUs, gloo on CPU) that
-    accepts slices of unequal length (padded to the longest, then trimmed)."""
+    accepts slices of unequal length (padded to the longest, then trimmed).
+    The slice lengths are fixed by the plans, so they are exchanged once, on
+    the first call, and again only if this rank's length changes.  host=True
+    gathers host copies (for a CPU-only backend such as gloo driving device
+    tensors) and returns the result on the input's device."""
     import torch
     import torch.distributed as dist
 
+    known = {"local": None, "sizes": None}
+
     def gather(t):
+        dev = t.device
+        if host:
+            t = t.cpu()
         world = dist.get_world_size(group)
-        n = torch.tensor([t.shape[0]], device=t.device)
-        sizes = [torch.zeros_like(n) for _ in range(world)]
-        dist.all_gather(sizes, n, group=group)
-        m = int(max(int(s.item()) for s in sizes))
+        if known["local"] != t.shape[0]:
+            n = torch.tensor([t.shape[0]], device=t.device)
+            sizes = [torch.zeros_like(n) for _ in range(world)]
+            dist.all_gather(sizes, n, group=group)
+            known["local"] = t.shape[0]
+            known["sizes"] = [int(s.item()) for s in sizes]
+        sizes = known["sizes"]
+        m = max(sizes)
         pad = torch.zeros((m,) + tuple(t.shape[1:]), dtype=t.dtype, device=t.device)
         pad[: t.shape[0]] = t
         parts = [torch.empty_like(pad) for _ in range(world)]
         dist.all_gather(parts, pad, group=group)
-        return torch.cat([p[: int(s.item())] for p, s in zip(parts, sizes)], dim=0)
+        out = torch.cat([p[:s] for p, s in zip(parts, sizes)], dim=0)
+        return out.to(dev) if host else out
 
     return gather

@@ -1,7 +1,8 @@
 """Row-distributed plans (row-parallel mode, Sec. IV.H) on one GPU: plans for
 row slices apply H[rows, :] to the whole vector and cache only the pairs
-their rows touch; several slice plans stepped in lockstep, with the gathers
-emulated by concatenation, give the single plan's Chebyshev step.
+their rows touch; slice plans stepped in lockstep (gathers emulated by
+concatenation), and two processes driving rowgroup.propagate over a gloo
+all-gather, give the oracle's Chebyshev step.
 
 Bars: FP64 form 1e-12 of max|y| (summation order), FP32 form 2e-5."""
 import numpy as np
@@ -49,24 +50,31 @@ def test_slices_reassemble_the_product(mf, gen, prec, nvec):
     assert _rel(got, ref) < (1e-12 if prec == 0 else 2e-5)
 
 
-def test_lockstep_row_group_step_matches_one_plan(mf):
+def _padded_bounds(op, pad=0.05):
+    """Spectral bounds from the oracle's dense eigenvalues, padded by 5 % of
+    the half-width (any enclosure gives the same exp(-i dt H) psi)."""
+    ev = np.linalg.eigvalsh(O.dense(op))
+    half = 0.5 * (ev[-1] - ev[0])
+    return ev[0] - pad * half, ev[-1] + pad * half
+
+
+def test_lockstep_row_group_step_matches_oracle(mf):
     """Two slice plans stepped term by term (gather = concatenation) against
-    one plan's exp(-i dt H) psi; the Philox slices get the same bounds."""
+    the oracle's Chebyshev step with the same bounds and term count."""
     from paper_2606_31598_gb300 import rowgroup
     D, nvec, dt = 1000, 2, 0.8
-    full = mf.Plan(D, 0, seed=6, precision=0, cheb_tol=1e-13)
-    emin, emax = full.bounds()
+    op = O.make_op(O.GEN_PHILOX_GUE, D, seed=6)
+    emin, emax = _padded_bounds(op)
+    c, R = 0.5 * (emax + emin), 0.5 * (emax - emin)
     psi = W.random_state(D, nvec, seed=5).reshape(D, nvec)
-    ref_d = torch.from_numpy(psi.copy()).cuda()
-    full.cheb_propagate(ref_d, nvec, dt, 0)
-    nt_full = full.cheb_terms(dt)
     plans = []
     for r0, r1 in rowgroup.slices(D, 2):
         p = mf.Plan(D, 0, seed=6, precision=0, cheb_tol=1e-13, row_begin=r0, row_end=r1)
         p.set_bounds(emin, emax)
         plans.append(p)
     nts = [p.rows_cheb_begin(dt) for p in plans]
-    assert nts[0] == nts[1] == nt_full
+    assert nts[0] == nts[1] and nts[0] > 8
+    nt = nts[0]
     psi_d = torch.from_numpy(psi).cuda()
     st = []
     for p in plans:
@@ -75,7 +83,7 @@ def test_lockstep_row_group_step_matches_one_plan(mf):
         p.rows_cheb_init(psi_d, acc, nvec)
         st.append([acc, torch.zeros_like(acc), torch.empty_like(acc)])
     q_full = psi_d
-    for j in range(1, nt_full):
+    for j in range(1, nt):
         for p, (acc, qp, qn) in zip(plans, st):
             p.rows_cheb_term(j, q_full, qp, qn, acc, nvec)
         q_full = torch.cat([s[2] for s in st])
@@ -86,7 +94,78 @@ def test_lockstep_row_group_step_matches_one_plan(mf):
         outs.append(o)
     torch.cuda.synchronize()
     got = torch.cat(outs).cpu().numpy()
-    assert np.max(np.abs(got - ref_d.cpu().numpy())) < 1e-11
+    ref = O.cheb_step(op, psi, dt, c, R, nt)
+    assert np.max(np.abs(got - ref)) < 1e-11
+
+
+def _free_port():
+    import socket
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, case, out):
+    """One rank of a row group: its slice plan on the one GPU, the library's
+    slice calls through rowgroup.propagate, a gloo all-gather of host copies
+    between terms."""
+    import os
+    import torch.distributed as dist
+    import paper_2606_31598_gb300 as mf
+    from paper_2606_31598_gb300 import rowgroup
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        torch.cuda.set_device(0)
+        gen, prec, D, nvec, dt, bounds, psi = case
+        r0, r1 = rowgroup.slices(D, world)[rank]
+        budget = (2 * 16 * 256 * 256) if rank == 1 else 0
+        p = mf.Plan(D, gen, seed=6, block=256, precision=prec, cheb_tol=1e-13, cache_budget_bytes=budget,
+                    row_begin=r0, row_end=r1)
+        if bounds is not None:
+            p.set_bounds(*bounds)
+        res = rowgroup.propagate(p, torch.from_numpy(psi).cuda(), nvec, dt,
+                                 rowgroup.dist_allgather(host=True))
+        torch.cuda.synchronize()
+        out[rank] = (r0, r1, res.cpu().numpy(), p.describe()["pairs_cached"])
+        p.close()
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("gen,prec", [(0, 0), (1, 1)])
+def test_row_group_on_two_processes_over_the_library(mf, gen, prec):
+    """Two processes, each with its row-slice plan of the library (one with a
+    partial cache of the pairs its rows touch), drive rowgroup.propagate with
+    a gloo all-gather of host copies of the slices: both end with the
+    oracle's exp(-i dt H) psi."""
+    import torch.multiprocessing as tmp
+    D, nvec = (1000, 2) if gen == 0 else (3000, 1)
+    form = O.FORM_FP64 if prec == 0 else O.FORM_FP32
+    op = O.make_op(gen, D, seed=6, form=form)
+    if gen == 0:
+        bounds = _padded_bounds(O.make_op(gen, D, seed=6))
+        dt = 0.8
+    else:
+        dx = 2 * W.dvr_default_L(D) / (D - 1)
+        bounds = None  # analytic on every rank
+        emin, emax = 0.0, np.pi ** 2 / (2 * dx * dx) + 0.5 * W.dvr_default_L(D) ** 2
+        dt = 2e-3
+    psi = W.random_state(D, nvec, seed=8).reshape(D, nvec)
+    world, port = 2, _free_port()
+    case = (gen, prec, D, nvec, dt, bounds, psi)
+    with tmp.get_context("spawn").Manager() as m:
+        out = m.dict()
+        tmp.spawn(_rank_main, args=(world, port, case, out), nprocs=world, join=True)
+        res = dict(out)
+    emin, emax = bounds if bounds is not None else (emin, emax)
+    c, R = 0.5 * (emax + emin), 0.5 * (emax - emin)
+    nt = O.cheb_terms(R * dt, 1e-13)
+    ref = O.cheb_step(op, psi, dt, c, R, nt)
+    tol = 1e-11 if prec == 0 else 2e-5 * np.max(np.abs(ref))
+    for r in (0, 1):
+        assert np.max(np.abs(res[r][2] - ref)) < tol
+    assert res[1][3] > 0  # the second rank's slice cached its pairs
 
 
 def test_slice_plans_refuse_what_they_cannot_do(mf):
