@@ -557,9 +557,15 @@ mf_status create_fixed(mf_plan_t* out, int64_t D, int32_t generator, uint64_t se
     p.dpad = p.ntile * kTile;
   }
   // multi-vector row-owner path: enough (row tile, column range) CTAs for
-  // two waves, column ranges a multiple of the 32-column chunk
+  // two waves, column ranges a multiple of the 32-column chunk and at most
+  // kMaxSplitCols long, so that no FP32 partial sum runs over more terms
+  // (the sums across ranges are FP64; at D = 262144 with 64 vectors one
+  // FP32 chain over the whole row left 2.4e-5 of max|y| against the FP32
+  // form's exact sums)
   {
+    constexpr int64_t kMaxSplitCols = 16384;
     int64_t ns = std::max<int64_t>(1, std::min<int64_t>(64, (2 * (int64_t)p.num_sms + p.ntile - 1) / p.ntile));
+    ns = std::max<int64_t>(ns, (D + kMaxSplitCols - 1) / kMaxSplitCols);
     int64_t cols = ((D + ns - 1) / ns + 31) / 32 * 32;
     p.rows_split_cols = cols;
     p.rows_nsplit = (D + cols - 1) / cols;
