@@ -177,6 +177,11 @@ void release(Plan& p) {
   free_dev(p.d_sb_M);
   free_dev(p.d_sb_HS);
   free_dev(p.d_sb_xo);
+  free_dev(p.d_tch_units);
+  free_dev(p.d_tch_off);
+  free_dev(p.d_tch_counter);
+  free_dev(p.d_tch_slots);
+  p.tch_slots_cap = 0;
   p.part_cap = p.xc_cap = p.tcb_cap = p.sb_xo_cap = 0;
   for (auto& c : p.q_cap) c = 0;
 }
@@ -198,14 +203,24 @@ bool use_rows_herm(const Plan& p, int64_t nb) {
   return bytes <= p.herm_limit;
 }
 
+// The Hermitian-reuse tensor-core walk: chosen at plan creation for BF16X2
+// Philox plans over all rows (opt.hermitian_reuse != 0) whose unit slots
+// for 64 vectors fit the plan's limit; such a plan keeps its cache in the
+// walk's tile format, so every BF16X2 product of the plan takes the walk.
+double tch_slot_bytes(const Plan& p, int64_t nb) { return (double)p.tch_rows * 2.0 * (double)nb * 4.0; }
+bool use_tch(const Plan& p, int64_t) { return p.tch; }
+
 // The DVR window kernel for 2..16 vectors (FP32 form, procedural plans).
 bool use_dvr_mv(const Plan& p, int64_t nvec) {
   return p.use_dvr_window && p.prec == MF_PREC_FP32 && !p.sb_nop && nvec >= 2 && nvec <= 16;
 }
 
 VecShape shape_for(const Plan& p, int64_t nvec) {
-  if (p.prec == MF_PREC_BF16X2)
-    return VecShape{nvec, tc_nvec_bucket(nvec), p.rows_nsplit, p.ntile * (int64_t)kTile};
+  if (p.prec == MF_PREC_BF16X2) {
+    const int64_t nb = tc_nvec_bucket(nvec);
+    // the unit walk hands its FP64 row sums on as two FP32 slots (hi, lo)
+    return VecShape{nvec, nb, use_tch(p, nb) ? 2 : p.rows_nsplit, p.ntile * (int64_t)kTile};
+  }
   if (p.sliced) return VecShape{nvec, rows_nvec_bucket(nvec), p.rows_nsplit, p.slice_nt * (int64_t)kTile};
   if (nvec == 1 && !p.sb_nop) return VecShape{1, 1, p.nslot, p.dpad};
   if (use_dvr_mv(p, nvec)) {
@@ -232,7 +247,10 @@ mf_status ensure_workspace(Plan& p, int64_t nvec) {
     part_bytes = std::max(part_bytes, (size_t)s.nslot * (size_t)s.dpad * (size_t)s.nb * eb);
     xc_bytes = std::max(xc_bytes, (size_t)std::max<int64_t>(s.dpad, p.D) * (size_t)s.nb * eb);
   }
-  const size_t tcb_bytes = p.prec == MF_PREC_BF16X2 ? tc_operand_bytes(p.D, m.nb) : 0;
+  const bool tch = p.prec == MF_PREC_BF16X2 && use_tch(p, m.nb);
+  const size_t tcb_bytes =
+      p.prec == MF_PREC_BF16X2 ? (tch ? tch_operand_bytes(p.D, m.nb) : tc_operand_bytes(p.D, m.nb)) : 0;
+  const size_t tch_bytes = tch ? (size_t)tch_slot_bytes(p, m.nb) : 0;
   const size_t q_bytes = (size_t)p.D * (size_t)nvec * sizeof(double2);
   const int64_t sb_rows = std::max<int64_t>(m.dpad, p.D);
   const size_t xo_bytes = p.sb_nop ? (size_t)p.sb_nop * (size_t)sb_rows * (size_t)m.nb * eb : 0;
@@ -250,6 +268,7 @@ mf_status ensure_workspace(Plan& p, int64_t nvec) {
   if ((st = grow(&p.d_part, p.part_cap, part_bytes, false)) != MF_OK) return st;
   if ((st = grow(&p.d_xc, p.xc_cap, xc_bytes, true)) != MF_OK) return st;
   if (tcb_bytes && (st = grow(&p.d_tcb, p.tcb_cap, tcb_bytes, false)) != MF_OK) return st;
+  if (tch_bytes && (st = grow(&p.d_tch_slots, p.tch_slots_cap, tch_bytes, false)) != MF_OK) return st;
   for (int i = 0; i < 3; ++i)
     if ((st = grow((void**)&p.d_q[i], p.q_cap[i], q_bytes, false)) != MF_OK) return st;
   if (p.sb_nop) {
@@ -294,7 +313,9 @@ mf_status apply_kernel(Plan& p, int64_t nvec) {
       MF_CUDA(launch_rows_herm(p, p.d_sb_xo, p.sb_rows * nbr, p.d_part, nbr, p.sb_nop, p.d_sb_seeds));
     else
       MF_CUDA(launch_sb_rows(p, p.d_sb_xo, p.sb_rows * nbr, p.d_part, nbr));
-  } else if (p.prec == MF_PREC_BF16X2)
+  } else if (p.prec == MF_PREC_BF16X2 && use_tch(p, tc_nvec_bucket(nvec)))
+    MF_CUDA(launch_tch_apply(p, p.d_xc, p.d_part, p.d_tcb, tc_nvec_bucket(nvec)));
+  else if (p.prec == MF_PREC_BF16X2)
     MF_CUDA(launch_tc_apply(p, p.d_xc, p.d_part, p.d_tcb, tc_nvec_bucket(nvec)));
   else if (nvec > 1 && herm)
     MF_CUDA(launch_rows_herm(p, p.d_xc, 0, p.d_part, nbr, 1, nullptr));
@@ -571,9 +592,22 @@ mf_status create_fixed(mf_plan_t* out, int64_t D, int32_t generator, uint64_t se
     p.rows_nsplit = (D + cols - 1) / cols;
   }
   const int64_t nbk = p.prec == MF_PREC_BF16X2 ? tc_nvec_bucket(nv) : (nv > 1 ? rows_nvec_bucket(nv) : 1);
+  // Hermitian tensor-core walk: Philox BF16X2 plans over all rows
+  std::vector<int2> tch_units;
+  std::vector<int64_t> tch_off;
+  if (p.prec == MF_PREC_BF16X2 && generator == MF_GEN_PHILOX_GUE && !p.sliced && o.hermitian_reuse != 0) {
+    p.tch_rows = tch_layout(p.ntile, p.num_sms, &p.tch_s, &p.tch_U, tch_units, tch_off);
+    p.tch_nunits = (int64_t)tch_units.size();
+    // the unit slots for the largest vector bucket must fit beside the cache
+    const double room = std::max(0.0, (double)mfree - (double)pc * blk_bytes);
+    p.tch_limit = std::min(24e9, 0.15 * room);
+    p.tch = (double)p.tch_rows * 2.0 * 64.0 * 4.0 <= p.tch_limit;
+  }
   const double part_b = (nv > 1 || p.prec == MF_PREC_BF16X2) ? std::max((double)p.nslot * p.dpad, (double)p.rows_nsplit * p.ntile * kTile * nbk)
                                : (double)p.nslot * p.dpad;
-  const double m_work = part_b * eb + 3.0 * D * nv * 16.0 + (double)std::max(p.dpad, p.ntile * kTile) * nbk * eb;
+  const double m_tch = p.tch ? (double)p.tch_rows * 2.0 * (double)nbk * 4.0 + (double)tch_operand_bytes(D, nbk) : 0.0;
+  const double m_work =
+      part_b * eb + 3.0 * D * nv * 16.0 + (double)std::max(p.dpad, p.ntile * kTile) * nbk * eb + m_tch;
   p.m_work = m_work;
   const double m_op = (double)pc * blk_bytes;
   if (m_op + m_work > o.alpha_safety * (double)mfree) {
@@ -649,7 +683,8 @@ mf_status create_fixed(mf_plan_t* out, int64_t D, int32_t generator, uint64_t se
     int2* d_pairs = nullptr;
     if (dmalloc(&d_pairs, pairs.size() * sizeof(int2)) != cudaSuccess) return fail(MF_ERR_OOM);
     cudaMemcpyAsync(d_pairs, pairs.data(), pairs.size() * sizeof(int2), cudaMemcpyHostToDevice, p.stream);
-    e = launch_cache_fill_pairs(p, d_pairs, (int64_t)pairs.size());
+    e = p.tch ? launch_tch_cache_fill(p, d_pairs, (int64_t)pairs.size())
+              : launch_cache_fill_pairs(p, d_pairs, (int64_t)pairs.size());
     cudaStreamSynchronize(p.stream);
     cudaFree(d_pairs);
     if (e != cudaSuccess) return fail(MF_ERR_CUDA);
@@ -699,6 +734,17 @@ mf_status create_fixed(mf_plan_t* out, int64_t D, int32_t generator, uint64_t se
     p.herm_nitems = (int64_t)hi.size();
     if (dmalloc(&p.d_herm_items, hi.size() * sizeof(HermItem)) != cudaSuccess) return fail(MF_ERR_OOM);
     if (cudaMemcpyAsync(p.d_herm_items, hi.data(), hi.size() * sizeof(HermItem), cudaMemcpyHostToDevice,
+                        p.stream) != cudaSuccess)
+      return fail(MF_ERR_CUDA);
+  }
+  if (p.tch) {
+    if (dmalloc(&p.d_tch_units, tch_units.size() * sizeof(int2)) != cudaSuccess ||
+        dmalloc(&p.d_tch_off, tch_off.size() * sizeof(int64_t)) != cudaSuccess ||
+        dmalloc(&p.d_tch_counter, sizeof(int)) != cudaSuccess)
+      return fail(MF_ERR_OOM);
+    if (cudaMemcpyAsync(p.d_tch_units, tch_units.data(), tch_units.size() * sizeof(int2), cudaMemcpyHostToDevice,
+                        p.stream) != cudaSuccess ||
+        cudaMemcpyAsync(p.d_tch_off, tch_off.data(), tch_off.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
                         p.stream) != cudaSuccess)
       return fail(MF_ERR_CUDA);
   }
@@ -1378,13 +1424,16 @@ mf_status mf_plan_describe(mf_plan_t h, char* buf, size_t len) {
       "\"pairs_cached\": %lld, \"cache_bytes\": %zu, \"path\": \"%s\", \"tile\": %d, \"dvr_rows\": %d, "
       "\"dvr_cols\": %d, \"n_slot\": %lld, \"n_work\": %lld, \"w_hpsi\": %.6g, \"dense_warn\": %s, "
       "\"dvr_L\": %.17g, \"dvr_dx\": %.17g, \"have_bounds\": %s, \"emin\": %.17g, \"emax\": %.17g, "
-      "\"num_sms\": %d, \"sb_nop\": %d, \"sb_dS\": %d, \"spin_limit\": %u, \"last_device_error\": %d}",
+      "\"num_sms\": %d, \"sb_nop\": %d, \"sb_dS\": %d, \"spin_limit\": %u, \"last_device_error\": %d, \"tc_walk\": \"%s\", "
+      "\"tch_unit\": %d, \"tch_units\": %lld, \"cache_format\": \"%s\"}",
       (long long)p.D, gen_name(p.gen), (unsigned long long)p.seed, prec_name(p.prec), (long long)p.b,
       (long long)p.nblk, (long long)p.npair, store_name(p.storage), p.cache_budget, (long long)p.pairs_cached,
       p.cache_bytes, p.sb_nop ? "sysbath_rows" : (p.use_dvr_window ? "dvr_window" : "herm_tile"), kTile, p.dvr_rows,
       p.dvr_cols,
       (long long)p.nslot, (long long)p.nwork, p.w_hpsi, p.dense_warn ? "true" : "false", p.dvr.L, p.dvr.dx,
-      p.have_bounds ? "true" : "false", p.emin, p.emax, p.num_sms, p.sb_nop, p.sb_dS, p.spin, p.last_dev_err);
+      p.have_bounds ? "true" : "false", p.emin, p.emax, p.num_sms, p.sb_nop, p.sb_dS, p.spin, p.last_dev_err,
+      p.prec != MF_PREC_BF16X2 ? "none" : (p.tch ? "hermitian" : "row_owner"), p.tch_s,
+      (long long)p.tch_nunits, p.tch ? "bf16x2_tiles" : (p.prec == MF_PREC_FP64 ? "complex128" : "complex64"));
   if (n < 0) return MF_ERR_INVALID;
   std::strncpy(buf, tmp, len - 1);
   buf[len - 1] = '\0';

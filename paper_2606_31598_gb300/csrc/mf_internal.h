@@ -84,6 +84,18 @@ struct Plan {
   HermItem* d_herm_items = nullptr;
   int64_t herm_nitems = 0, herm_ns = 0;
   double herm_limit = 0.0;  // largest partial-slot buffer (bytes) the path may use
+  // BF16X2 Hermitian tensor-core walk (k_tch.cu): units of tch_s x tch_s
+  // tiles, their order and slot row offsets, the unit counter and the slots
+  bool tch = false;                // the plan's BF16X2 apply uses it (its cache is then in the
+                                   // walk's bf16 tile format, not FP32 complex)
+  int32_t tch_s = 0, tch_U = 0;
+  int64_t tch_nunits = 0, tch_rows = 0;
+  int2* d_tch_units = nullptr;
+  int64_t* d_tch_off = nullptr;
+  int* d_tch_counter = nullptr;
+  void* d_tch_slots = nullptr;     // [tch_rows][2 nb] FP32
+  size_t tch_slots_cap = 0;
+  double tch_limit = 0.0;          // largest slot buffer (bytes) the walk may use
   // row-distributed plan: output rows [row0, row1), row tiles slice_t0 ..
   // slice_t0 + slice_nt - 1 (row-owner kernels only)
   bool sliced = false;
@@ -188,6 +200,16 @@ int64_t rows_nvec_bucket(int64_t nvec);
 cudaError_t launch_tc_apply(const Plan& p, const void* xc, void* part, void* gB, int64_t nv_bucket);
 size_t tc_operand_bytes(int64_t D, int64_t nv_bucket);
 int64_t tc_nvec_bucket(int64_t nvec);
+// Hermitian-reuse tensor-core apply (k_tch.cu): unit layout for T tile rows
+// (returns the slot rows), operand bytes, and the launch (operand split,
+// persistent unit walk, gather into two slots of part).
+int64_t tch_layout(int64_t T, int num_sms, int32_t* s_out, int32_t* U_out, std::vector<int2>& units,
+                   std::vector<int64_t>& off2d);
+size_t tch_operand_bytes(int64_t D, int64_t nv_bucket);
+cudaError_t launch_tch_apply(const Plan& p, const void* xc, void* part, void* gB, int64_t nv_bucket);
+// Fill the cache of a Hermitian tensor-core plan in its consumer format
+// (every tile of the listed block pairs as the kernel's four bf16 planes).
+cudaError_t launch_tch_cache_fill(const Plan& p, const int2* d_pairs, int64_t npairs);
 
 // Vector layouts: the FP64 master x/y is [D][nv]; the compute copy xc and the
 // partial slots use a padded vector stride nb >= nv ([D][nb], [slot][dpad][nb])

@@ -52,6 +52,25 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
+// Six MMAs of one K step of a BF16 hi + lo split product into one
+// accumulator, issued from one asm block (one predicate for the first MMA's
+// accumulate flag, the others accumulate): A descriptors a0 a0 a1 a2 a2 a3
+// with B descriptors b0 b1 b0 b2 b3 b2, i.e. a0 (b0 + b1) + a1 b0 and
+// a2 (b2 + b3) + a3 b2.
+__device__ __forceinline__ void mma_bf16_x6(uint32_t d, uint64_t a0, uint64_t a1, uint64_t a2, uint64_t a3,
+                                            uint64_t b0, uint64_t b1, uint64_t b2, uint64_t b3, uint32_t idesc,
+                                            uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.b32 p, %10, 0;\n setp.eq.b32 q, %10, %10;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %5, %9, p;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %6, %9, q;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %2, %5, %9, q;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %3, %7, %9, q;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %3, %8, %9, q;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %4, %7, %9, q;\n}\n" ::"r"(d),
+      "l"(a0), "l"(a1), "l"(a2), "l"(a3), "l"(b0), "l"(b1), "l"(b2), "l"(b3), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
