@@ -15,6 +15,13 @@ Under torchrun (N > 1) every rank propagates an independent wavepacket
 (parameter-parallel tasks, no collective on the data path) and the job value
 is the sum of work over the max time across ranks.  ``--impl reference``
 times the CPU oracle on bounded row samples of the same product.
+
+At N = 1 the line also carries, under "workloads", the other
+configurations, each timed on its own with its roofline, CPU oracle baseline
+and error against the FP64 form: the Philox ensemble at D = 4096 in the FP64
+form (one product and a 32-term step), the 64-vector Philox workload at
+D = 262144 with its 120 GB cache (BF16X2 and FP32 forms, one Chebyshev step)
+and the 256 batched problems (one step).  --headline-only leaves them out.
 """
 import argparse
 import hashlib
@@ -314,7 +321,17 @@ def run_mf(args):
         xg = -L + (2 * L / (D - 1)) * np.arange(D)
         exact = coherent_state(xg, x0, tau)
         exact = exact / np.linalg.norm(exact)
+        # the BF16 hi+lo split form of the same step (tcgen05 kernel)
+        plan16 = mf.Plan(D, mf.MF_GEN_SINC_DVR_HO, precision=mf.MF_PREC_BF16X2, stream=stream, device=local)
+        plan16.set_bounds(emin, emax)
+        c16 = torch.from_numpy(psi0).to(dev)
+        plan16.cheb_propagate(c16, 1, tau, TERMS)
+        torch.cuda.synchronize()
+        plan16.sync()
+        c16 = c16.cpu().numpy()
+        plan16.close()
         err = {"fp32_vs_fp64_form": float(np.linalg.norm(a - b)), "fp32_vs_closed_form": float(np.linalg.norm(a - exact)),
+               "bf16x2_vs_fp64_form": float(np.linalg.norm(c16 - b)),
                "fp64_vs_closed_form": float(np.linalg.norm(b - exact)),
                "norm_drift_after_timed_steps": float(abs(np.linalg.norm(psi_timed) - 1.0)),
                "measure": "2-norm of the state difference after one step (unit-norm states)"}
@@ -355,11 +372,252 @@ def run_mf(args):
         cb_value, cb_rows, cb_t = cpu_oracle_sample(target_s=10.0)
         line["cpu_baseline"] = {"value": cb_value, "unit": "entries/s", "cores": cpu_threads(), "kind": "oracle",
                                 "sample": "%d of %d output rows of one FP64 H psi (%.1f s)" % (cb_rows, D, cb_t)}
+        plan.close()
+        plan = None
+        if world == 1 and not args.headline_only:
+            # the other configurations, each with its own timing, roofline,
+            # CPU oracle baseline and error (one GPU, after the headline)
+            peaks = measured_peaks()
+            line["workloads"] = {}
+            for key, fn in (("philox_D4096_fp64", lambda: sub_small_philox(stream)),
+                            ("philox_D262144_64vec_120GB", lambda: sub_multivector(stream, peaks)),
+                            ("batch_256_problems", lambda: sub_batch(stream))):
+                t0 = time.perf_counter()
+                line["workloads"][key] = fn()
+                line["workloads"][key]["wall_s"] = time.perf_counter() - t0
+                torch.cuda.empty_cache()
         print(json.dumps(line))
-    plan.close()
+    if plan is not None:
+        plan.close()
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def measured_peaks():
+    """HBM copy GB/s and BF16 TFLOP/s (burst, sustained) measured on this
+    pool's GPUs (MEASURED_PEAKS.json beside this file), else the fallback
+    figures; the dict says which."""
+    try:
+        m = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return {"hbm_gbs": float(m["hbm_gbs"]), "bf16_tflops": float(m["bf16_tflops"]),
+                "bf16_tflops_sustained": float(m["bf16_tflops_sustained"]), "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
+
+
+def events_time(fn, reps):
+    """Mean seconds of fn() over reps calls (CUDA events, synchronised)."""
+    import torch
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / 1e3 / reps
+
+
+def sub_small_philox(stream):
+    """Plain method, small size: Philox ensemble D = 4096 (seed 1) in the FP64
+    form (complex128), block 512, procedural; one H psi plus one 32-term
+    Chebyshev step of t = 1 per step, psi random (seed 1).  GPU and CPU
+    oracle run the same step in full; the error is against the oracle."""
+    import torch
+    import paper_2606_31598_gb300 as mf
+    import workloads as W
+    from oracle import oracle as O
+    D, B, NT = 4096, 512, 32
+    plan = mf.Plan(D, mf.MF_GEN_PHILOX_GUE, seed=1, block=B, precision=mf.MF_PREC_FP64,
+                   storage=mf.MF_STORE_PROCEDURAL, stream=stream)
+    emin, emax = plan.bounds()
+    c, R = 0.5 * (emax + emin), 0.5 * (emax - emin)
+    psi0 = W.random_state(D, 1, seed=1)
+    x = torch.from_numpy(psi0).cuda()
+    y = torch.empty_like(x)
+    psi = torch.empty_like(x)
+
+    def step():
+        plan.apply(y, x, 1)
+        psi.copy_(x)
+        plan.cheb_propagate(psi, 1, 1.0, NT)
+
+    step()
+    plan.profile(True)
+    reps = 10
+    t = events_time(step, reps)
+    kern_ms, kern_n = plan.profile_read()
+    plan.profile(False)
+    op = O.make_op(O.GEN_PHILOX_GUE, D, seed=1)
+    t0 = time.perf_counter()
+    ref_y = O.apply(op, psi0, block=B)
+    ref_psi = O.cheb_step(op, psi0, 1.0, c, R, NT, block=B)
+    t_cpu = time.perf_counter() - t0
+    yh, ph = y.cpu().numpy(), psi.cpu().numpy()
+    entries = float(NT) * D * D  # one product plus 31 in the step
+    plan.close()
+    return {"workload": "Philox GUE D=4096 (seed 1), FP64 form, block 512, procedural, 1 vector; one H psi "
+                        "plus one 32-term Chebyshev step of t=1",
+            "step_s": t, "entries_per_s": entries / t, "products_per_step": NT, "steps_per_s": 1.0 / t,
+            "kernel_ms_per_launch": kern_ms / max(1, kern_n),
+            "error": {"apply_rel_vs_oracle": float(np.max(np.abs(yh - ref_y)) / np.max(np.abs(ref_y))),
+                      "step_abs_vs_oracle": float(np.max(np.abs(ph - ref_psi))),
+                      "measure": "FP64 form against the CPU oracle's FP64 statement (same bounds and terms)"},
+            "roofline": {"bound": "fp64", "achieved_canonical_entries_per_s": NT * D * (D + 1) / 2.0 / t,
+                         "note": "the FP64 form generates each canonical entry with FP64 Philox-to-Gaussian "
+                                 "arithmetic on GB300's FP64 pipe (1/64 of the FP32 rate); %.3f ms per product "
+                                 "launch, 8.4e6 canonical entries" % (kern_ms / max(1, kern_n))},
+            "cpu_baseline": {"value": entries / t_cpu, "unit": "entries/s", "cores": cpu_threads(), "kind": "oracle",
+                             "sample": "the whole step (one product plus the 32-term step) in FP64 (%.2f s)" % t_cpu}}
+
+
+def sub_multivector(stream, peaks):
+    """The 64-vector workload: Philox D = 262144 (seed 1), 64 unit vectors
+    (seed 2), block 2048, 120 GB partial cache (3576 of 8256 canonical
+    pairs), BF16X2 (tcgen05, Hermitian reuse) and FP32 forms; one Chebyshev
+    step of dt = 1 at tolerance 1e-12 in the BF16X2 form.  Errors against the
+    FP64 form on 1024 sampled rows computed by the oracle; the CPU baseline
+    is the oracle's FP64 product on those rows, extrapolated to all D rows."""
+    import torch
+    import paper_2606_31598_gb300 as mf
+    import workloads as W
+    from oracle import oracle as O
+    D, R, B, BUDGET = 262144, 64, 2048, int(120e9)
+    X = torch.from_numpy(W.random_state(D, R, seed=2)).cuda()
+    Y = torch.empty_like(X)
+    rows = np.unique(np.concatenate([np.linspace(0, D - 1, 1020).astype(np.int64),
+                                     np.array([2047, 2048, 63488, 212992], dtype=np.int64)]))
+    out = {"workload": "Philox GUE D=262144 (seed 1), 64 vectors (seed 2), block 2048, 120 GB partial cache"}
+    res = {}
+    for name, prec in (("bf16x2", mf.MF_PREC_BF16X2), ("fp32", mf.MF_PREC_FP32)):
+        t0 = time.perf_counter()
+        plan = mf.Plan(D, mf.MF_GEN_PHILOX_GUE, seed=1, block=B, cache_budget_bytes=BUDGET, precision=prec,
+                       storage=mf.MF_STORE_PARTIAL, nvec_hint=R, stream=stream, cheb_tol=1e-12)
+        torch.cuda.synchronize()
+        t_create = time.perf_counter() - t0
+        desc = plan.describe()
+        plan.apply(Y, X, R)
+        plan.profile(True)
+        reps = 3 if name == "bf16x2" else 1
+        t = events_time(lambda: plan.apply(Y, X, R), reps)
+        kern_ms, kern_n = plan.profile_read()
+        plan.profile(False)
+        plan.sync()
+        r = {"apply_s": t, "entries_per_s": float(D) * D * R / t, "kernel_ms": kern_ms / max(1, kern_n),
+             "create_s": t_create, "pairs_cached": desc["pairs_cached"], "walk": desc.get("tc_walk")}
+        r["_rows"] = Y[torch.from_numpy(rows).cuda()].cpu().numpy()
+        if name == "bf16x2":
+            nt = plan.cheb_terms(1.0)
+            psi = X.clone()
+            t_step = events_time(lambda: plan.cheb_propagate(psi, R, 1.0, 0), 1)
+            plan.sync()
+            r.update({"cheb_terms": nt, "cheb_step_s": t_step, "cheb_steps_per_s": 1.0 / t_step,
+                      "cheb_terms_per_s": (nt - 1) / t_step})
+            del psi
+        res[name] = r
+        plan.close()
+        torch.cuda.empty_cache()
+    Xh = X.cpu().numpy()
+    del X, Y
+    torch.cuda.empty_cache()
+    op64 = O.make_op(O.GEN_PHILOX_GUE, D, seed=1)
+    t0 = time.perf_counter()
+    ref = O.apply_rows(op64, Xh, rows)
+    t_cpu = time.perf_counter() - t0
+    scale = np.max(np.abs(ref))
+    for name in res:
+        res[name]["err_vs_fp64_form"] = float(np.max(np.abs(res[name].pop("_rows") - ref)) / scale)
+    # composite bound of the BF16X2 product (Sec. IV.B runtime model with
+    # measured rates): tensor work, cached bytes, generation
+    npair, pc = 8256, res["bf16x2"]["pairs_cached"]
+    canon = D * (D + 1) / 2.0
+    cached = pc * float(B) * B
+    t_tc = 24.0 * R * D * D / (peaks["bf16_tflops_sustained"] * 1e12)
+    t_hbm = 8.0 * cached / (peaks["hbm_gbs"] * 1e9)
+    t_gen = (canon - cached) * PHILOX_INSTR_PER_ENTRY / (152 * 128 * 2.07e9)
+    bound = max(t_tc, t_hbm, t_gen)
+    tb = res["bf16x2"]["kernel_ms"] / 1e3
+    out.update(res)
+    out["roofline"] = {
+        "bound": {t_tc: "tensor", t_hbm: "hbm", t_gen: "generation"}[bound], "t_bound_s": bound,
+        "t_tensor_s": t_tc, "t_hbm_s": t_hbm, "t_generation_s": t_gen, "achieved_s": tb, "frac": bound / tb,
+        "tensor_tflops": 24.0 * R * D * D / tb / 1e12, "peak_tensor_tflops": peaks["bf16_tflops_sustained"],
+        "peak_source": peaks["source"],
+        "basis": "tensor: 3 bf16 products x 8 real FLOP x 64 vectors x D^2 at the sustained BF16 peak; hbm: the "
+                 "cached canonical entries (8 B each) at the measured copy rate; generation: the procedural "
+                 "canonical entries x %d thread instructions (ncu count of the one-vector generator) at the "
+                 "issue rate 152 x 128 x 2070 MHz" % PHILOX_INSTR_PER_ENTRY}
+    out["speedup_bf16x2_vs_fp32"] = res["fp32"]["apply_s"] / res["bf16x2"]["apply_s"]
+    out["cpu_baseline"] = {"value": len(rows) * float(D) * R / t_cpu, "unit": "entries/s", "cores": cpu_threads(),
+                           "kind": "oracle", "sample": "%d of %d output rows of one FP64 H X with 64 vectors "
+                                                      "(%.1f s), rate extrapolated to all rows" % (len(rows), D, t_cpu)}
+    return out
+
+
+def sub_batch(stream):
+    """256 batched Philox problems (the workload draw: D log-uniform in
+    [1024, 32768] rounded to 128, 1..16 vectors, seeds 0..255), plans chosen
+    per problem by the measured autotuner, FP32 form, one persistent launch
+    per Chebyshev term under a captured CUDA graph; one step of dt = 1.  The
+    error is problem 0's step against the oracle (same bounds and terms); the
+    CPU baseline is the oracle's FP64 product of the first 8 problems."""
+    import torch
+    import paper_2606_31598_gb300 as mf
+    import workloads as W
+    from oracle import oracle as O
+    probs = W.batch_problems(256)
+    Ds = [p[0] for p in probs]
+    nv = [p[1] for p in probs]
+    seeds = [p[2] for p in probs]
+    t0 = time.perf_counter()
+    b = mf.Batch(Ds, nv, seeds, mf.MF_GEN_PHILOX_GUE, cache_budget_bytes=int(200e9), precision=mf.MF_PREC_FP32,
+                 planner_mode=mf.MF_PLANNER_AUTOTUNE, autotune_k=4, autotune_repeats=2, stream=stream)
+    torch.cuda.synchronize()
+    t_create = time.perf_counter() - t0
+    parts = [W.random_state(D, k, seed=100 + i).reshape(D, k) for i, (D, k) in enumerate(zip(Ds, nv))]
+    host = torch.from_numpy(np.concatenate([q.ravel() for q in parts]))
+    packed = host.cuda()
+    nt = b.propagate(packed, 1.0, 1)  # captures the graph for this buffer; later calls replay it
+    torch.cuda.synchronize()
+    t = events_time(lambda: b.propagate(packed, 1.0, 1), 3)
+    packed.copy_(host)
+    b.propagate(packed, 1.0, 1)
+    torch.cuda.synchronize()
+    got0 = packed[int(b.offsets[0]):int(b.offsets[1])].cpu().numpy().reshape(Ds[0], nv[0])
+    lo, hi = mf.mf_spectral_bounds(b.plan(0))
+    c, R = 0.5 * (hi + lo), 0.5 * (hi - lo)
+    ref0 = O.cheb_step(O.make_op(O.GEN_PHILOX_GUE, Ds[0], seed=seeds[0], form=O.FORM_FP32), parts[0], 1.0, c, R, nt)
+    entries = float(sum(D * D * k for D, k in zip(Ds, nv)))
+    hbm_bytes = gen_entries = flops = 0.0
+    stores = {}
+    for i, (D, k) in enumerate(zip(Ds, nv)):
+        d = mf.mf_plan_describe(b.plan(i))
+        stores[d["storage"]] = stores.get(d["storage"], 0) + 1
+        cached = min(float(D) * D, 2.0 * d["pairs_cached"] * d["block"] ** 2)
+        hbm_bytes += 8.0 * cached
+        gen_entries += float(D) * D - cached
+        flops += 8.0 * D * D * k
+    n_items, grid = b.info()
+    b.close()
+    t0 = time.perf_counter()
+    cpu_entries = 0.0
+    for i in range(8):
+        O.apply(O.make_op(O.GEN_PHILOX_GUE, Ds[i], seed=seeds[i]), parts[i])
+        cpu_entries += float(Ds[i]) * Ds[i] * nv[i]
+    t_cpu = time.perf_counter() - t0
+    applies = nt - 1
+    return {"workload": "256 batched Philox problems, D in [1024, 32768], 1-16 vectors, FP32, autotuned plans",
+            "create_s": t_create, "terms_per_step": nt, "step_s": t, "steps_per_s": 1.0 / t,
+            "entries_per_s": entries * applies / t, "sum_D2_nvec": entries, "work_items": n_items,
+            "persistent_grid": grid, "storage_chosen": stores,
+            "error": {"problem0_step_abs_vs_oracle": float(np.max(np.abs(got0 - ref0))),
+                      "measure": "FP32 form against the oracle's statement of the same form, same bounds/terms"},
+            "roofline": batch_roofline(hbm_bytes, gen_entries, flops, t / applies),
+            "cpu_baseline": {"value": cpu_entries / t_cpu, "unit": "entries/s", "cores": cpu_threads(),
+                             "kind": "oracle", "sample": "one FP64 product of each of the first 8 problems "
+                                                        "(%.1f s)" % t_cpu}}
 
 
 def time_applies(plan, x, y, nvec, reps):
@@ -555,6 +813,10 @@ def run_philox(args):
 # (~8), the sin/cos polynomials with the quadrant logic (~24), the scale (3)
 # and the 8 FMAs applying the entry as H and H^dagger.
 PHILOX_OPS_PER_ENTRY = 30 + 12 + 24 + 8 + 24 + 3 + 8
+# Thread instructions per canonical entry of the FP32 Philox generator as ncu
+# counted them in the one-vector kernel (the generation term of the bound of
+# the 64-vector workload).
+PHILOX_INSTR_PER_ENTRY = 108
 
 
 def batch_roofline(hbm_bytes, gen_entries, flops, t_apply):
@@ -787,6 +1049,8 @@ def main():
     ap.add_argument("--dvrmv-nvec", type=int, default=0, help="dvrmv: one vector count only (0: 1, 2, 4, 8, 16)")
     ap.add_argument("--fp64", action="store_true", help="multivector: also time the FP64 procedural form")
     ap.add_argument("--mv-dim", type=int, default=262144, help="multivector: D (smaller D keeps the cached fraction)")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="dvr: the headline line alone, without the other configurations' sub-results")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
