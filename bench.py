@@ -686,13 +686,17 @@ def run_multivector(args):
     D, R, B = args.mv_dim, 64, 2048
     nblk = (D + B - 1) // B
     # the same cached fraction of canonical pairs as 120 GB at D = 262144
+    # (--mv-cache none: every block generated)
     BUDGET = int(120e9 if D == 262144 else 3576 / 8256 * nblk * (nblk + 1) / 2 * B * B * 8 + 1)
+    if args.mv_cache == "none":
+        BUDGET = 0
     stream = torch.cuda.current_stream().cuda_stream
     X = torch.from_numpy(W.random_state(D, R, seed=2)).cuda()
     Y = torch.empty_like(X)
     out = {"workload": "Philox GUE D=%d, 64 vectors, block 2048, %.1f GB partial cache" % (D, BUDGET / 1e9)}
     plan = mf.Plan(D, mf.MF_GEN_PHILOX_GUE, seed=1, block=B, cache_budget_bytes=BUDGET, precision=mf.MF_PREC_BF16X2,
-                   storage=mf.MF_STORE_PARTIAL, nvec_hint=R, stream=stream, cheb_tol=1e-12)
+                   storage=mf.MF_STORE_PARTIAL if BUDGET else mf.MF_STORE_PROCEDURAL, nvec_hint=R, stream=stream,
+                   cheb_tol=1e-12, hermitian_reuse=0 if args.mv_rowowner else -1)
     desc = plan.describe()
     t_bf = time_applies(plan, X, Y, R, 3)
     Ybf = Y.clone()
@@ -714,7 +718,7 @@ def run_multivector(args):
     nterms = plan.cheb_terms(1.0)
     plan.close()
     p32 = mf.Plan(D, mf.MF_GEN_PHILOX_GUE, seed=1, block=B, cache_budget_bytes=BUDGET, precision=mf.MF_PREC_FP32,
-                  storage=mf.MF_STORE_PARTIAL, nvec_hint=R, stream=stream)
+                  storage=mf.MF_STORE_PARTIAL if BUDGET else mf.MF_STORE_PROCEDURAL, nvec_hint=R, stream=stream)
     t_32 = time_applies(p32, X, Y, R, 1)
     Y32 = Y.clone()
     p32.close()
@@ -1048,6 +1052,10 @@ def main():
                          "multivector: the 64-vector tensor-core workload report")
     ap.add_argument("--dvrmv-nvec", type=int, default=0, help="dvrmv: one vector count only (0: 1, 2, 4, 8, 16)")
     ap.add_argument("--fp64", action="store_true", help="multivector: also time the FP64 procedural form")
+    ap.add_argument("--mv-cache", default="partial", choices=["partial", "none"],
+                    help="multivector: the 120 GB-share partial cache, or every block generated")
+    ap.add_argument("--mv-rowowner", action="store_true",
+                    help="multivector: the row-owner tcgen05 kernel (hermitian_reuse = 0) for the BF16X2 form")
     ap.add_argument("--mv-dim", type=int, default=262144, help="multivector: D (smaller D keeps the cached fraction)")
     ap.add_argument("--headline-only", action="store_true",
                     help="dvr: the headline line alone, without the other configurations' sub-results")
