@@ -477,6 +477,29 @@ mf_status mf_sync(mf_plan_t p);
 mf_status mf_plan_describe(mf_plan_t p, char* buf, size_t len);
 
 /*
+ * mf_plan_serialize / mf_plan_deserialize -- the plan record of a
+ * continuation run (Sec. VII resumes propagations with the plan selected
+ * earlier): the selected block size, storage mode and pairs cached, the
+ * generator, seed and precision form, the numerical options and, once
+ * computed, the spectral bounds, as NUL-terminated text ("mf_plan v1" and
+ * key=value lines; doubles as exact hexadecimal floats).
+ *   serialize   : *needed receives the size including the NUL; buf may be
+ *                 NULL to query it; MF_ERR_INVALID when buf is too small;
+ *                 MF_ERR_UNSUPPORTED for system-bath and externally stored
+ *                 plans (their operator data is the caller's).
+ *   deserialize : builds the recorded plan directly -- no planner, no
+ *                 measurement, no Lanczos run when the record holds bounds --
+ *                 so products and propagations equal the original plan's bit
+ *                 for bit on the same GPU model.  opt supplies the stream and
+ *                 device (NULL = defaults); the recorded fields override its
+ *                 numerical options.  rec is read up to len bytes or its NUL.
+ *                 Errors: MF_ERR_INVALID (malformed record or out-of-range
+ *                 field; nothing allocated), MF_ERR_OOM, MF_ERR_CUDA.
+ */
+mf_status mf_plan_serialize(mf_plan_t p, char* buf, size_t len, size_t* needed);
+mf_status mf_plan_deserialize(mf_plan_t* out, const char* rec, size_t len, const mf_options* opt);
+
+/*
  * mf_debug_entries -- copy the generator's entries H[r0:r0+rows, c0:c0+cols]
  * as produced on the GPU in the plan's precision form to HOST memory out:
  * complex64 (FP32 and BF16X2 plans, the FP32 entry before splitting) or

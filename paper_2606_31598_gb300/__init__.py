@@ -138,6 +138,10 @@ def lib():
         L.mf_planner_device_model.argtypes = [i32, i32, i32, P(mf_device_model)]
         L.mf_planner_device_model.restype = ctypes.c_int
         L.mf_plan_trials.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t, P(ctypes.c_size_t)]
+        L.mf_plan_serialize.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t, P(ctypes.c_size_t)]
+        L.mf_plan_deserialize.argtypes = [P(vp), ctypes.c_char_p, ctypes.c_size_t, P(mf_options)]
+        L.mf_plan_serialize.restype = ctypes.c_int
+        L.mf_plan_deserialize.restype = ctypes.c_int
         fp = P(ctypes.c_float)
         L.mf_mlp_create.argtypes = [P(vp), i32, i32, i32, u64]
         L.mf_mlp_destroy.argtypes = [vp]
@@ -350,6 +354,23 @@ def mf_plan_trials(plan):
     return [json.loads(l) for l in buf.value.decode().splitlines() if l.strip()]
 
 
+def mf_plan_serialize(plan):
+    """The plan record (bytes, without the NUL) for a later mf_plan_deserialize."""
+    need = ctypes.c_size_t()
+    _check(lib().mf_plan_serialize(plan, None, 0, ctypes.byref(need)), "mf_plan_serialize")
+    buf = ctypes.create_string_buffer(max(1, need.value))
+    _check(lib().mf_plan_serialize(plan, buf, len(buf), None), "mf_plan_serialize")
+    return buf.value
+
+
+def mf_plan_deserialize(record, options=None):
+    h = ctypes.c_void_p()
+    opt = options if options is not None else mf_options_default(stream=current_stream())
+    rec = bytes(record)
+    _check(lib().mf_plan_deserialize(ctypes.byref(h), rec, len(rec), ctypes.byref(opt)), "mf_plan_deserialize")
+    return h
+
+
 def _fptr(a):
     return None if a is None else a.ctypes.data
 
@@ -526,6 +547,30 @@ class Plan:
         self._blocks = blocks
         self.handle = mf_external_create(D, block, blocks, cache_budget_bytes, o)
         return self
+
+    @classmethod
+    def deserialize(cls, record, **opts):
+        """A plan rebuilt from mf_plan_serialize's record (no planning);
+        opts may set the stream and device."""
+        self = cls.__new__(cls)
+        o = mf_options_default()
+        if "stream" not in opts:
+            opts["stream"] = current_stream()
+        for k, v in opts.items():
+            setattr(o, k, v)
+        self.handle = mf_plan_deserialize(record, o)
+        d = mf_plan_describe(self.handle)
+        self.options = o
+        self.options.precision = {"fp64": MF_PREC_FP64, "fp32": MF_PREC_FP32, "bf16x2": MF_PREC_BF16X2}[d["precision"]]
+        self.D = int(d["D"])
+        fields = dict(l.split(b"=", 1) for l in bytes(record).splitlines()[1:] if b"=" in l)
+        self.row_begin = int(fields.get(b"row_begin", b"0"))
+        re_ = int(fields.get(b"row_end", b"0"))
+        self.row_end = re_ if re_ else self.D
+        return self
+
+    def serialize(self):
+        return mf_plan_serialize(self.handle)
 
     @classmethod
     def sysbath(cls, d_S, d_B, seeds, H_S, A, g, **opts):

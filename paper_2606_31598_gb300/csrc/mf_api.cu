@@ -1413,10 +1413,174 @@ mf_status mf_sync(mf_plan_t h) {
   return status_of_device_code(err);
 }
 
+// Plan record for continuation runs (the selected plan reused without
+// planning, Sec. VII): a versioned text of "key=value" lines, integers in
+// decimal and doubles as exact hexadecimal floats.
+mf_status mf_plan_serialize(mf_plan_t h, char* buf, size_t len, size_t* needed) {
+  return guard([&]() -> mf_status {
+    if (!h) return MF_ERR_INVALID;
+    const Plan& p = h->p;
+    if (p.gen == MF_GEN_EXTERNAL || p.sb_nop) return MF_ERR_UNSUPPORTED;
+    std::string t = "mf_plan v1\n";
+    auto put_i = [&](const char* k, long long v) {
+      char b[96];
+      std::snprintf(b, sizeof(b), "%s=%lld\n", k, v);
+      t += b;
+    };
+    auto put_d = [&](const char* k, double v) {
+      char b[96];
+      std::snprintf(b, sizeof(b), "%s=%a\n", k, v);
+      t += b;
+    };
+    put_i("D", p.D);
+    put_i("generator", p.gen);
+    t += "seed=" + std::to_string((unsigned long long)p.seed) + "\n";
+    put_i("precision", p.prec);
+    put_i("block", p.b);
+    put_i("storage", p.storage);
+    put_i("pairs_cached", p.pairs_cached);
+    put_d("dvr_L", p.dvr.L);
+    put_i("nvec_hint", p.opt.nvec_hint);
+    put_d("cheb_tol", p.opt.cheb_tol);
+    put_i("lanczos_m", p.opt.lanczos_m);
+    put_d("bounds_pad", p.opt.bounds_pad);
+    put_d("alpha_safety", p.opt.alpha_safety);
+    put_d("f_cache", p.opt.f_cache);
+    put_d("dense_work_limit", p.opt.dense_work_limit);
+    put_i("hermitian_reuse", p.opt.hermitian_reuse);
+    put_i("row_begin", p.opt.row_begin);
+    put_i("row_end", p.opt.row_end);
+    put_i("spin_limit", p.opt.spin_limit);
+    put_i("have_bounds", p.have_bounds ? 1 : 0);
+    put_d("emin", p.emin);
+    put_d("emax", p.emax);
+    put_i("planner", p.planner_used);
+    put_d("s_model", p.s_model);
+    put_d("t_measured", p.t_measured);
+    put_i("num_sms", p.num_sms);
+    if (needed) *needed = t.size() + 1;
+    if (!buf) return MF_OK;
+    if (len == 0) return MF_ERR_INVALID;
+    std::strncpy(buf, t.c_str(), len - 1);
+    buf[len - 1] = '\0';
+    return t.size() + 1 <= len ? MF_OK : MF_ERR_INVALID;
+  });
+}
+
+mf_status mf_plan_deserialize(mf_plan_t* out, const char* rec, size_t len, const mf_options* opt) {
+  return guard([&]() -> mf_status {
+    if (!out || !rec) return MF_ERR_INVALID;
+    *out = nullptr;
+    const std::string text(rec, strnlen(rec, len));
+    if (text.compare(0, 11, "mf_plan v1\n") != 0) return MF_ERR_INVALID;
+    std::vector<std::pair<std::string, std::string>> kv;
+    size_t pos = 11;
+    while (pos < text.size()) {
+      size_t eol = text.find('\n', pos);
+      if (eol == std::string::npos) eol = text.size();
+      const std::string line = text.substr(pos, eol - pos);
+      pos = eol + 1;
+      if (line.empty()) continue;
+      const size_t eq = line.find('=');
+      if (eq == std::string::npos || eq == 0) return MF_ERR_INVALID;
+      kv.emplace_back(line.substr(0, eq), line.substr(eq + 1));
+    }
+    auto find = [&](const char* k) -> const std::string* {
+      for (const auto& e : kv)
+        if (e.first == k) return &e.second;
+      return nullptr;
+    };
+    bool bad = false;
+    auto get_i = [&](const char* k) -> long long {
+      const std::string* v = find(k);
+      if (!v || v->empty()) { bad = true; return 0; }
+      char* end = nullptr;
+      const long long r = std::strtoll(v->c_str(), &end, 10);
+      if (*end) bad = true;
+      return r;
+    };
+    auto get_u = [&](const char* k) -> unsigned long long {
+      const std::string* v = find(k);
+      if (!v || v->empty()) { bad = true; return 0; }
+      char* end = nullptr;
+      const unsigned long long r = std::strtoull(v->c_str(), &end, 10);
+      if (*end) bad = true;
+      return r;
+    };
+    auto get_d = [&](const char* k) -> double {
+      const std::string* v = find(k);
+      if (!v || v->empty()) { bad = true; return 0.0; }
+      char* end = nullptr;
+      const double r = std::strtod(v->c_str(), &end);
+      if (*end) bad = true;
+      return r;
+    };
+    mf_options o;
+    if (opt) o = *opt; else mf_options_default(&o);
+    const long long D = get_i("D");
+    const int gen = (int)get_i("generator");
+    const unsigned long long seed = get_u("seed");
+    o.precision = (int32_t)get_i("precision");
+    const long long block = get_i("block");
+    o.storage = (int32_t)get_i("storage");
+    const long long pc = get_i("pairs_cached");
+    o.dvr_L = get_d("dvr_L");
+    o.nvec_hint = (int32_t)get_i("nvec_hint");
+    o.cheb_tol = get_d("cheb_tol");
+    o.lanczos_m = (int32_t)get_i("lanczos_m");
+    o.bounds_pad = get_d("bounds_pad");
+    o.alpha_safety = get_d("alpha_safety");
+    o.f_cache = get_d("f_cache");
+    o.dense_work_limit = get_d("dense_work_limit");
+    o.hermitian_reuse = (int32_t)get_i("hermitian_reuse");
+    o.row_begin = get_i("row_begin");
+    o.row_end = get_i("row_end");
+    o.spin_limit = (int32_t)get_i("spin_limit");
+    const bool hb = get_i("have_bounds") != 0;
+    const double emin = get_d("emin"), emax = get_d("emax");
+    const int planner = (int)get_i("planner");
+    const double s_model = get_d("s_model"), t_meas = get_d("t_measured");
+    o.planner_mode = MF_PLANNER_ANALYTIC;
+    o.model = nullptr;
+    if (bad) return MF_ERR_INVALID;
+    if (D < 2 || D > (int64_t)1 << 31 || (gen != MF_GEN_PHILOX_GUE && gen != MF_GEN_SINC_DVR_HO)) return MF_ERR_INVALID;
+    if (o.precision < MF_PREC_FP64 || o.precision > MF_PREC_BF16X2) return MF_ERR_INVALID;
+    if (block < kTile || block % kTile != 0 || pc < 0) return MF_ERR_INVALID;
+    if (o.storage < MF_STORE_PROCEDURAL || o.storage > MF_STORE_FULL) return MF_ERR_INVALID;
+    if (!(o.dvr_L > 0) || !std::isfinite(o.dvr_L) || !(o.cheb_tol > 0) || o.lanczos_m < 2 ||
+        !(o.alpha_safety > 0 && o.alpha_safety <= 1) || o.nvec_hint < 1 || o.nvec_hint > 64 ||
+        o.hermitian_reuse < -1 || o.hermitian_reuse > 1 || o.spin_limit < 0)
+      return MF_ERR_INVALID;
+    if (o.row_begin != 0 || o.row_end != 0) {
+      if (o.row_begin < 0 || o.row_end <= o.row_begin || o.row_end > D || o.row_begin % kTile != 0 ||
+          (o.row_end % kTile != 0 && o.row_end != D))
+        return MF_ERR_INVALID;
+    }
+    if (hb && !(emax > emin && std::isfinite(emin) && std::isfinite(emax))) return MF_ERR_INVALID;
+    // the recorded block, storage and cache share: no planning, no measurement
+    const double eb = (double)compute_elem_bytes(o.precision);
+    const size_t budget = (size_t)((double)pc * eb * (double)block * (double)block);
+    mf_status st = create_fixed(out, D, gen, seed, block, budget, o);
+    if (st != MF_OK && st != MF_WARN_DENSE_WORK) return st;
+    Plan& p = (*out)->p;
+    if (hb) {  // the recorded bounds: the Chebyshev coefficients come out the same
+      p.emin = emin;
+      p.emax = emax;
+      p.have_bounds = true;
+    }
+    p.planner_used = planner;
+    p.s_model = s_model;
+    p.t_measured = t_meas;
+    p.deserialized = true;
+    p.trials.push_back(std::string("{\"deserialized\": true, \"t_mv\": -1}"));
+    return st;
+  });
+}
+
 mf_status mf_plan_describe(mf_plan_t h, char* buf, size_t len) {
   if (!h || !buf || len == 0) return MF_ERR_INVALID;
   const Plan& p = h->p;
-  char tmp[2048];
+  char tmp[3072];
   const int n = std::snprintf(
       tmp, sizeof(tmp),
       "{\"D\": %lld, \"generator\": \"%s\", \"seed\": %llu, \"precision\": \"%s\", \"block\": %lld, "
@@ -1425,7 +1589,8 @@ mf_status mf_plan_describe(mf_plan_t h, char* buf, size_t len) {
       "\"dvr_cols\": %d, \"n_slot\": %lld, \"n_work\": %lld, \"w_hpsi\": %.6g, \"dense_warn\": %s, "
       "\"dvr_L\": %.17g, \"dvr_dx\": %.17g, \"have_bounds\": %s, \"emin\": %.17g, \"emax\": %.17g, "
       "\"num_sms\": %d, \"sb_nop\": %d, \"sb_dS\": %d, \"spin_limit\": %u, \"last_device_error\": %d, \"tc_walk\": \"%s\", "
-      "\"tch_unit\": %d, \"tch_units\": %lld, \"cache_format\": \"%s\"}",
+      "\"tch_unit\": %d, \"tch_units\": %lld, \"cache_format\": \"%s\", "
+      "\"planner\": %d, \"deserialized\": %s}",
       (long long)p.D, gen_name(p.gen), (unsigned long long)p.seed, prec_name(p.prec), (long long)p.b,
       (long long)p.nblk, (long long)p.npair, store_name(p.storage), p.cache_budget, (long long)p.pairs_cached,
       p.cache_bytes, p.sb_nop ? "sysbath_rows" : (p.use_dvr_window ? "dvr_window" : "herm_tile"), kTile, p.dvr_rows,
@@ -1433,7 +1598,8 @@ mf_status mf_plan_describe(mf_plan_t h, char* buf, size_t len) {
       (long long)p.nslot, (long long)p.nwork, p.w_hpsi, p.dense_warn ? "true" : "false", p.dvr.L, p.dvr.dx,
       p.have_bounds ? "true" : "false", p.emin, p.emax, p.num_sms, p.sb_nop, p.sb_dS, p.spin, p.last_dev_err,
       p.prec != MF_PREC_BF16X2 ? "none" : (p.tch ? "hermitian" : "row_owner"), p.tch_s,
-      (long long)p.tch_nunits, p.tch ? "bf16x2_tiles" : (p.prec == MF_PREC_FP64 ? "complex128" : "complex64"));
+      (long long)p.tch_nunits, p.tch ? "bf16x2_tiles" : (p.prec == MF_PREC_FP64 ? "complex128" : "complex64"),
+      p.planner_used, p.deserialized ? "true" : "false");
   if (n < 0) return MF_ERR_INVALID;
   std::strncpy(buf, tmp, len - 1);
   buf[len - 1] = '\0';

@@ -139,6 +139,7 @@ struct Plan {
   double s_model = 0.0;
   double t_measured = -1.0;
   int32_t planner_used = MF_PLANNER_ANALYTIC;
+  bool deserialized = false;      // created by mf_plan_deserialize (no planning)
   std::vector<std::string> trials;
   // safety estimate (Sec. IV.H)
   double w_hpsi = 0.0;

@@ -126,3 +126,26 @@ def test_every_entry_point_rejects_null_handles_and_bad_arguments(mf):
     bad = {k: v for k, v in checks.items() if v != INV}
     assert not bad, bad
     assert L.mf_batch_destroy(None) == mf.MF_OK
+
+
+def test_plan_deserialize_rejects_malformed_records_without_gpu(mf):
+    """A malformed or out-of-range plan record is refused before anything is
+    allocated (no GPU needed)."""
+    import ctypes
+    L = mf.lib()
+    good = (b"mf_plan v1\nD=4096\ngenerator=0\nseed=1\nprecision=1\nblock=512\nstorage=0\npairs_cached=0\n"
+            b"dvr_L=0x1.4p+6\nnvec_hint=1\ncheb_tol=0x1.ad7f29abcaf48p-24\nlanczos_m=40\nbounds_pad=0x1.999999999999ap-5\n"
+            b"alpha_safety=0x1.ccccccccccccdp-1\nf_cache=0x1.999999999999ap-1\ndense_work_limit=0x1.2309ce54p+43\n"
+            b"hermitian_reuse=-1\nrow_begin=0\nrow_end=0\nspin_limit=0\nhave_bounds=0\nemin=0x0p+0\nemax=0x0p+0\n"
+            b"planner=0\ns_model=0x0p+0\nt_measured=-0x1p+0\nnum_sms=152\n")
+    bad = [b"", b"garbage", b"mf_plan v2\n" + good[11:], good.replace(b"D=4096", b"D=1"),
+           good.replace(b"block=512", b"block=500"), good.replace(b"precision=1", b"precision=7"),
+           good.replace(b"seed=1\n", b""), good.replace(b"cheb_tol=0x1.ad7f29abcaf48p-24", b"cheb_tol=x"),
+           good.replace(b"storage=0", b"storage=5"), good.replace(b"row_end=0", b"row_end=100")]
+    for rec in bad:
+        h = ctypes.c_void_p()
+        st = L.mf_plan_deserialize(ctypes.byref(h), rec, len(rec), None)
+        assert st == mf.MF_ERR_INVALID, rec[:40]
+        assert not h.value
+    assert L.mf_plan_deserialize(None, good, len(good), None) == mf.MF_ERR_INVALID
+    assert L.mf_plan_serialize(None, None, 0, None) == mf.MF_ERR_INVALID
