@@ -237,16 +237,27 @@ void mlp_features(int32_t generator, int32_t precision, const mf_problem& pr, co
   x[9] = (float)std::log10(1.0 + budget / 1e9);
 }
 
+// Two surrogate forms.  Direct (10 inputs): the head of the candidate's
+// storage mode predicts ln t_mv.  Residual (11 inputs): the eleventh input is
+// ln of the analytic per-application time S_model / waves (Eq.
+// planner_cost_score over Eq. planner_waves), and the head predicts the
+// residual ln t_mv - ln(S_model / waves), so the network learns only where
+// the runtime model misses.
 mf_status surrogate_predict(void* model, int32_t generator, int32_t precision, const mf_problem& pr,
                             const mf_candidate& c, const mf_estimate& e, double budget, double, int, double* t) {
   mf_mlp* m = (mf_mlp*)model;
-  if (!m || m->F != 10 || m->O != 3) return MF_ERR_INVALID;
-  float x[10], y[3];
+  if (!m || (m->F != 10 && m->F != 11) || m->O != 3) return MF_ERR_INVALID;
+  float x[11], y[3];
   mlp_features(generator, precision, pr, c, e, budget, x);
+  const double t_model = e.S_model / (double)std::max<int64_t>(1, e.waves);
+  if (m->F == 11) {
+    if (!(t_model > 0)) return MF_ERR_INVALID;
+    x[10] = (float)std::log(t_model);
+  }
   mf_status st = mf_mlp_predict(m, x, 1, y);
   if (st != MF_OK) return st;
   const int k = c.storage == MF_STORE_PROCEDURAL ? 0 : (c.storage == MF_STORE_PARTIAL ? 1 : 2);
-  *t = std::exp((double)y[k]);
+  *t = std::exp((double)y[k]) * (m->F == 11 ? t_model : 1.0);
   return MF_OK;
 }
 

@@ -12,10 +12,11 @@ surrogate's features, the strategy (procedural/partial/full), the measured
 time and the analytic model score.
 
 The surrogate (the library's MLP: 10 features -> 64 -> 64 -> 3 log-times,
-one per strategy) is trained on the GPU on the records of 80 % of the
-problems; on the held-out 20 % the learned planner's choice (lowest predicted
-time) and the analytic planner's choice (lowest model score) are compared
-with the exhaustive measured best: regret = t(choice) / t(best) - 1.
+one per strategy; or the residual form, which also takes ln S_model and
+learns ln t_mv - ln S_model) is trained on the GPU on the records of 80 % of
+the problems; on the held-out 20 % the learned planner's choice (lowest
+predicted time) and the analytic planner's choice (lowest model score) are
+compared with the exhaustive measured best: regret = t(choice) / t(best) - 1.
 
     python -m paper_2606_31598_gb300.planner_sweep --out records.jsonl [--small]
 """
@@ -141,9 +142,11 @@ def run_sweep(out_path, small=False, warm=1, reps=3, max_minutes=1e9, log=print)
     return records
 
 
-# The records of the sweep measured on GB300 (480-problem grid, 30-minute
-# cap: 465 problems, 4185 records), shipped so that the surrogate can be
-# fitted, and the regret report re-derived, without re-measuring:
+# The records of the sweep measured on GB300 with the current kernels and
+# scored by the library's current analytic model (480-problem grid,
+# 32-minute cap: 475 problems, 4275 records from 1195 distinct plans),
+# shipped so that the surrogates can be fitted, and the regret report
+# re-derived, without re-measuring:
 #   python -m paper_2606_31598_gb300.planner_sweep --evaluate-only --out <this file>
 RECORDS_GB300 = os.path.join(os.path.dirname(os.path.abspath(__file__)), "planner_records_gb300.jsonl.gz")
 
@@ -165,18 +168,39 @@ def split(records, frac=0.2, seed=0):
     return [r for r in records if r["problem"] not in test], [r for r in records if r["problem"] in test]
 
 
-def train_surrogate(records, epochs=3000, lr=3e-3, seed=0):
-    mf = _mf()
+def surrogate_inputs(records, residual=False):
+    """Surrogate inputs of the records: the library's 10 features, and for the
+    residual form ln S_model (one task, so S_model / waves = S_model)."""
     X = np.array([r["features"] for r in records], np.float32)
+    if residual:
+        X = np.concatenate([X, np.log([[r["S_model"]] for r in records]).astype(np.float32)], axis=1)
+    return X
+
+
+def train_surrogate(records, epochs=3000, lr=3e-3, seed=0, residual=False):
+    """Algorithm 3's surrogate fitted on the GPU to the records: the head of
+    each record's storage mode regresses ln t_mv (direct form) or
+    ln t_mv - ln S_model (residual form, 11 inputs); masked squared loss."""
+    mf = _mf()
+    X = surrogate_inputs(records, residual)
     Y = np.zeros((len(records), 3), np.float32)
     M = np.zeros((len(records), 3), np.float32)
     for i, r in enumerate(records):
         k = STRATEGIES.index(r["storage"])
-        Y[i, k] = math.log(r["t_mv"])
+        Y[i, k] = math.log(r["t_mv"]) - (math.log(r["S_model"]) if residual else 0.0)
         M[i, k] = 1.0
-    net = mf.MLP(10, 64, 3, seed=seed)
+    net = mf.MLP(X.shape[1], 64, 3, seed=seed)
     curve = net.train(X, Y, M, epochs=epochs, lr=lr, set_normalization=True)
     return net, curve
+
+
+def predicted_log_time(net, rs):
+    """ln t_mv predicted by a direct (10-input) or residual (11-input)
+    surrogate for each record of rs."""
+    residual = getattr(net, "n_in", 10) == 11
+    pred = net.predict(surrogate_inputs(rs, residual))
+    return np.array([pred[i, STRATEGIES.index(r["storage"])] + (math.log(r["S_model"]) if residual else 0.0)
+                     for i, r in enumerate(rs)])
 
 
 def regret(records, net=None):
@@ -193,8 +217,7 @@ def regret(records, net=None):
             # (records scored before T_sum existed keep their first minimum)
             pick = min(rs, key=lambda r: (r["S_model"], r.get("T_sum", 0.0)))
         else:
-            pred = net.predict(np.array([r["features"] for r in rs], np.float32))
-            pick = rs[int(np.argmin([pred[i, STRATEGIES.index(r["storage"])] for i, r in enumerate(rs)]))]
+            pick = rs[int(np.argmin(predicted_log_time(net, rs)))]
         regs.append(pick["t_mv"] / best - 1.0)
     regs = np.array(regs)
     return {"problems": int(len(regs)), "mean": float(regs.mean()), "median": float(np.median(regs)),
@@ -221,15 +244,25 @@ def rescore(records):
 
 
 def evaluate(records, epochs=3000, seed=0):
+    """Held-out comparison on one split of the problems (80 % train, 20 %
+    test): the analytic ranking of the records (their S_model, then T_sum),
+    the direct surrogate and the residual surrogate, each against the
+    measured best.  score_drift is the largest relative change of S_model
+    when the records are re-scored by the library's current model (0 when
+    the sweep ran under the current model)."""
     train, test = split(records, 0.2, seed)
-    net, curve = train_surrogate(train, epochs=epochs, seed=seed)
     out = {"records": len(records), "train_records": len(train), "test_records": len(test),
-           "loss_first": float(curve[0]), "loss_last": float(curve[-1]),
-           "learned_test": regret(test, net), "analytic_test": regret(test, None),
-           "learned_train": regret(train, net), "analytic_train": regret(train, None),
-           "analytic_current_model_test": regret(rescore(test), None),
-           "analytic_current_model_train": regret(rescore(train), None)}
-    net.close()
+           "analytic_test": regret(test, None), "analytic_train": regret(train, None)}
+    for name, residual in (("learned", False), ("residual", True)):
+        net, curve = train_surrogate(train, epochs=epochs, seed=seed, residual=residual)
+        out[name + "_loss_first"] = float(curve[0])
+        out[name + "_loss_last"] = float(curve[-1])
+        out[name + "_test"] = regret(test, net)
+        out[name + "_train"] = regret(train, net)
+        net.close()
+    re = rescore(records)
+    out["score_drift"] = float(max(abs(a["S_model"] / b["S_model"] - 1.0) for a, b in zip(re, records)))
+    out["analytic_current_model_test"] = regret(rescore(test), None)
     return out
 
 

@@ -182,72 +182,76 @@ def test_regret_definition():
     assert {r["problem"] for r in tr}.isdisjoint({r["problem"] for r in te})
 
 
-def test_shipped_gb300_records_give_the_reported_analytic_regret():
-    """The sweep records measured on GB300 ship with the package; the
-    analytic planner's held-out regret recomputed from them (same seed-0
-    split of problems) is the one reported for the sweep, and every problem
-    has the measured best among its candidates."""
+def test_shipped_gb300_records_give_the_reported_analytic_regret(mf):
+    """The sweep records measured on GB300 with the current kernels ship
+    with the package (480-problem grid, cheapest first under a 32-minute
+    cap: 475 problems, 4275 records).  They were scored at sweep time by the
+    library's current Algorithm 1 (re-scoring them with mf_planner_estimate
+    and mf_planner_device_model changes no score), so the analytic regret
+    recomputed from them (seed-0 split of problems) is that of the ranking
+    the library runs, on measurements its rates were not tuned on."""
     from paper_2606_31598_gb300 import planner_sweep as ps
     recs = ps.load(ps.RECORDS_GB300)
-    assert len(recs) == 4185
-    assert len({r["problem"] for r in recs}) == 465
+    assert len(recs) == 4275
+    assert len({r["problem"] for r in recs}) == 475
+    assert all(r["t_mv"] > 0 and len(r["features"]) == 10 for r in recs)
+    assert max(abs(a["S_model"] / b["S_model"] - 1.0) for a, b in zip(ps.rescore(recs), recs)) == 0.0
     train, test = ps.split(recs, 0.2, 0)
     a_test, a_train = ps.regret(test, None), ps.regret(train, None)
-    assert a_test["problems"] == 93 and a_train["problems"] == 372
-    assert abs(a_test["mean"] - 0.11672) < 1e-4 and abs(a_test["max"] - 1.06904) < 1e-4
-    assert abs(a_train["mean"] - 0.07975) < 1e-4
-    assert all(r["t_mv"] > 0 and len(r["features"]) == 10 for r in recs)
+    assert a_test["problems"] == 95 and a_train["problems"] == 380
+    assert abs(a_test["mean"] - 0.0014020) < 1e-6 and abs(a_test["max"] - 0.026763) < 1e-5
+    assert abs(a_train["mean"] - 0.0012458) < 1e-6
 
 
-def test_learned_choice_beats_the_analytic_one_on_the_shipped_records():
-    """Algorithm 3 on the GB300 records, on the CPU: the oracle's FP64 form
-    of the surrogate (10 -> 64 -> 64 -> 3 log-times, masked squared loss,
-    Adam) fitted to the training problems picks, on the 93 held-out
-    problems, plans whose mean regret is well below that of the analytic
-    planner as the sweep scored it (the re-calibrated ranking the library
-    now uses is tested above)."""
-    from oracle import mlp_oracle as MO
-    from paper_2606_31598_gb300 import planner_sweep as ps
-    train, test = ps.split(ps.load(ps.RECORDS_GB300), 0.2, 0)
-    X = np.array([r["features"] for r in train], np.float64)
+def _fit_oracle_surrogate(ps, MO, train, residual, epochs):
+    """Algorithm 3's surrogate in the oracle's FP64 form (10 or 11 inputs ->
+    64 -> 64 -> 3, masked squared loss, Adam) fitted to the records."""
+    X = ps.surrogate_inputs(train, residual).astype(np.float64)
     Y = np.zeros((len(train), 3))
     M = np.zeros((len(train), 3))
     for i, r in enumerate(train):
         k = ps.STRATEGIES.index(r["storage"])
-        Y[i, k] = math.log(r["t_mv"])
+        Y[i, k] = math.log(r["t_mv"]) - (math.log(r["S_model"]) if residual else 0.0)
         M[i, k] = 1.0
-    F, H, O = 10, 64, 3
+    F, H, O = X.shape[1], 64, 3
     rng = np.random.default_rng(0)
     p = np.concatenate([(rng.standard_normal(F * H) / np.sqrt(F)), np.zeros(H),
                         (rng.standard_normal(H * H) / np.sqrt(H)), np.zeros(H),
                         (rng.standard_normal(H * O) / np.sqrt(H)), np.zeros(O)])
     mu, sd = MO.zscore(X)
-    p, curve = MO.train_adam(p, mu, sd, X, Y, M, F, H, O, epochs=800, lr=3e-3)
-    assert curve[-1] < 0.05 * curve[0]
+    p, curve = MO.train_adam(p, mu, sd, X, Y, M, F, H, O, epochs=epochs, lr=3e-3)
 
     class Net:
+        n_in = F
+
         def predict(self, Xq):
-            return MO.forward(p, mu, sd, Xq, F, H, O)[3]
+            return MO.forward(p, mu, sd, np.asarray(Xq, np.float64), F, H, O)[3]
 
-    learned, analytic = ps.regret(test, Net()), ps.regret(test, None)
-    # (fitted here: 0.5 % against 11.7 %; the library's FP32 surrogate after
-    # 3000 epochs on the GPU: 0.24 %)
-    assert learned["mean"] < 0.02 and learned["mean"] < 0.25 * analytic["mean"], (learned, analytic)
+    return Net(), curve
 
 
-def test_library_model_on_the_shipped_records(mf):
-    """Algorithm 1 as the library now ranks (runtime-model throughputs from
-    mf_planner_device_model; ties between equal model scores broken by the
-    total work T_sum), re-scored on every shipped GB300 record: 0.11 %
-    held-out regret (max 2.5 %) and 0.27 % on the training problems.  The
-    sweep's own scores (a 4e11/s Philox generation rate, the FP32 rate for
-    BF16X2, no tie-break) gave 11.7 %; the learned planner trained on the
-    same measurements reached 0.24 % (max 6.8 %)."""
+def test_learned_planners_against_the_current_algorithm_1(mf):
+    """Algorithm 3 against the library's current Algorithm 1 on the fresh
+    GB300 records, held out by problem.  Both surrogate forms -- direct (ln
+    t_mv from the 10 features) and residual (ln S_model as an 11th input,
+    learning ln t_mv - ln S_model) -- fitted for 1500 epochs in the oracle's
+    FP64 form pick plans with lower mean held-out regret than Algorithm 1
+    (0.11 % direct, 0.064 % residual, against 0.140 %) and a smaller largest
+    miss (2.1-2.2 % against 2.7 %).  The margins are at the timing noise of
+    the records: an 800-epoch fit gives 0.18 % and 0.22 %, a 3000-epoch fit
+    0.15 % and 0.057 %, and the library's FP32 GPU fits (3000 epochs) 0.114 %
+    and 0.116 %; so the learned planner matches the re-calibrated analytic
+    one rather than beating it by a margin that would survive re-measuring."""
+    from oracle import mlp_oracle as MO
     from paper_2606_31598_gb300 import planner_sweep as ps
-    recs = ps.load(ps.RECORDS_GB300)
-    train, test = ps.split(recs, 0.2, 0)
-    held, tr = ps.regret(ps.rescore(test), None), ps.regret(ps.rescore(train), None)
-    assert held["mean"] < 0.003 and held["max"] < 0.05 and tr["mean"] < 0.005, (held, tr)
+    train, test = ps.split(ps.load(ps.RECORDS_GB300), 0.2, 0)
+    analytic = ps.regret(test, None)
+    for residual, want in ((False, 0.00111), (True, 0.00064)):
+        net, curve = _fit_oracle_surrogate(ps, MO, train, residual, 1500)
+        assert curve[-1] < 0.002 * curve[0]
+        learned = ps.regret(test, net)
+        assert abs(learned["mean"] - want) < 1e-4, (residual, learned)
+        assert learned["mean"] < analytic["mean"] and learned["max"] < analytic["max"], (residual, learned, analytic)
 
 
 def test_device_model_rejects_bad_input(mf):
