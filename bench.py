@@ -19,7 +19,9 @@ times the CPU oracle on bounded row samples of the same product.
 At N = 1 the line also carries, under "workloads", the other
 configurations, each timed on its own with its roofline, CPU oracle baseline
 and error against the FP64 form: the Philox ensemble at D = 4096 in the FP64
-form (one product and a 32-term step), the 64-vector Philox workload at
+form (one product and a 32-term step), Philox generation at D = 131072 (one
+vector, procedural, with the per-pipe roofline against the pipe rates
+measured in the same run, "pipe_rates"), the 64-vector Philox workload at
 D = 262144 with its 120 GB cache (BF16X2 and FP32 forms, one Chebyshev step)
 and the 256 batched problems (one step).  --headline-only leaves them out.
 """
@@ -378,9 +380,15 @@ def run_mf(args):
             # the other configurations, each with its own timing, roofline,
             # CPU oracle baseline and error (one GPU, after the headline)
             peaks = measured_peaks()
+            rates = mf.mf_pipe_rates(local, stream)
+            line["pipe_rates"] = {"ops_per_s": rates,
+                                  "per_sm_per_clock_at_max_clock": {
+                                      k: v / (props.multi_processor_count * 2.07e9) for k, v in rates.items()},
+                                  "source": "mf_pipe_rates: register-only chains, 8 CTAs x 256 threads per SM"}
             line["workloads"] = {}
             for key, fn in (("philox_D4096_fp64", lambda: sub_small_philox(stream)),
-                            ("philox_D262144_64vec_120GB", lambda: sub_multivector(stream, peaks)),
+                            ("philox_D131072_generation", lambda: sub_philox_generation(stream, rates)),
+                            ("philox_D262144_64vec_120GB", lambda: sub_multivector(stream, peaks, rates)),
                             ("batch_256_problems", lambda: sub_batch(stream))):
                 t0 = time.perf_counter()
                 line["workloads"][key] = fn()
@@ -473,7 +481,53 @@ def sub_small_philox(stream):
                              "sample": "the whole step (one product plus the 32-term step) in FP64 (%.2f s)" % t_cpu}}
 
 
-def sub_multivector(stream, peaks):
+def sub_philox_generation(stream, rates):
+    """Seeded generation at the roofline's finest grain: Philox D = 131072
+    (seed 1), FP32 form, procedural, one vector (seed 3): every canonical
+    entry generated once per product and applied as H and H^dagger.  The
+    roofline is per pipe (operations of the definition over the measured
+    rate of each pipe); error on 16 sampled rows against the oracle's FP32
+    statement, and the CPU baseline is the oracle on those rows."""
+    import torch
+    import paper_2606_31598_gb300 as mf
+    import workloads as W
+    from oracle import oracle as O
+    D = 131072
+    x0 = W.random_state(D, 1, seed=3)
+    x = torch.from_numpy(x0).cuda()
+    y = torch.empty_like(x)
+    plan = mf.Plan(D, mf.MF_GEN_PHILOX_GUE, seed=1, block=2048, precision=mf.MF_PREC_FP32,
+                   storage=mf.MF_STORE_PROCEDURAL, stream=stream)
+    plan.apply(y, x, 1)
+    plan.profile(True)
+    t = events_time(lambda: plan.apply(y, x, 1), 5)
+    kern_ms, kern_n = plan.profile_read()
+    plan.profile(False)
+    plan.sync()
+    per = kern_ms / 1e3 / max(1, kern_n)
+    canon = D * (D + 1) / 2.0
+    rows = np.array([0, 1, 127, 128, 2047, 2048, 65535, 65536, 100000, 131071, 4096, 8191, 31337, 77777, 99999,
+                     120000])
+    got = y[torch.from_numpy(rows).cuda()].cpu().numpy()
+    plan.close()
+    t0 = time.perf_counter()
+    ref = O.apply_rows(O.make_op(O.GEN_PHILOX_GUE, D, seed=1, form=O.FORM_FP32), x0.reshape(D, 1), rows)
+    t_cpu = time.perf_counter() - t0
+    roof = pipe_roofline(canon / per, rates)
+    roof["issue_frac"] = canon / per * PHILOX_INSTR_PER_ENTRY / (152 * 128 * 2.07e9)
+    return {"workload": "Philox GUE D=131072 (seed 1), FP32 form, procedural, 1 vector (seed 3)",
+            "apply_s": t, "kernel_ms": per * 1e3, "entries_per_s": float(D) * D / t,
+            "canonical_entries_per_s": canon / per,
+            "error": {"rows_rel_vs_oracle": float(np.max(np.abs(got.reshape(-1) - ref.reshape(-1))) /
+                                                  np.max(np.abs(ref))),
+                      "measure": "16 sampled output rows against the oracle's FP32 statement"},
+            "roofline": roof,
+            "cpu_baseline": {"value": len(rows) * float(D) / t_cpu, "unit": "entries/s", "cores": cpu_threads(),
+                             "kind": "oracle", "sample": "16 of 131072 output rows of one FP32-form H psi "
+                                                        "(%.2f s), rate extrapolated" % t_cpu}}
+
+
+def sub_multivector(stream, peaks, rates):
     """The 64-vector workload: Philox D = 262144 (seed 1), 64 unit vectors
     (seed 2), block 2048, 120 GB partial cache (3576 of 8256 canonical
     pairs), BF16X2 (tcgen05, Hermitian reuse) and FP32 forms; one Chebyshev
@@ -536,7 +590,11 @@ def sub_multivector(stream, peaks):
     cached = pc * float(B) * B
     t_tc = 24.0 * R * D * D / (peaks["bf16_tflops_sustained"] * 1e12)
     t_hbm = 8.0 * cached / (peaks["hbm_gbs"] * 1e9)
-    t_gen = (canon - cached) * PHILOX_INSTR_PER_ENTRY / (152 * 128 * 2.07e9)
+    # generation: the procedural canonical entries at the per-pipe bound of
+    # the generator (the contraction runs on the tensor cores, so no FP32
+    # apply FMAs are counted)
+    gen = pipe_bound(rates, apply_ffma_per_entry=0)
+    t_gen = (canon - cached) * gen["t_bound"]
     bound = max(t_tc, t_hbm, t_gen)
     tb = res["bf16x2"]["kernel_ms"] / 1e3
     out.update(res)
@@ -545,10 +603,11 @@ def sub_multivector(stream, peaks):
         "t_tensor_s": t_tc, "t_hbm_s": t_hbm, "t_generation_s": t_gen, "achieved_s": tb, "frac": bound / tb,
         "tensor_tflops": 24.0 * R * D * D / tb / 1e12, "peak_tensor_tflops": peaks["bf16_tflops_sustained"],
         "peak_source": peaks["source"],
+        "generation_bound_pipe": gen["bound_pipe"],
         "basis": "tensor: 3 bf16 products x 8 real FLOP x 64 vectors x D^2 at the sustained BF16 peak; hbm: the "
                  "cached canonical entries (8 B each) at the measured copy rate; generation: the procedural "
-                 "canonical entries x %d thread instructions (ncu count of the one-vector generator) at the "
-                 "issue rate 152 x 128 x 2070 MHz" % PHILOX_INSTR_PER_ENTRY}
+                 "canonical entries at the slowest pipe's measured rate (operations of the FP32 Philox "
+                 "definition per entry, mf_pipe_rates)"}
     out["speedup_bf16x2_vs_fp32"] = res["fp32"]["apply_s"] / res["bf16x2"]["apply_s"]
     out["cpu_baseline"] = {"value": len(rows) * float(D) * R / t_cpu, "unit": "entries/s", "cores": cpu_threads(),
                            "kind": "oracle", "sample": "%d of %d output rows of one FP64 H X with 64 vectors "
@@ -762,6 +821,8 @@ def run_philox(args):
     canon = D * (D + 1) / 2.0
     out = {"workload": "Philox GUE D=%d, 1 vector, FP32 form" % D}
     props = torch.cuda.get_device_properties(0)
+    rates = mf.mf_pipe_rates(0, stream)
+    out["pipe_rates"] = rates
     for name, storage, budget in [("procedural", mf.MF_STORE_PROCEDURAL, 0),
                                   ("full_cache", mf.MF_STORE_FULL, int(canon * 8 * 1.02) + (1 << 30))]:
         plan = mf.Plan(D, mf.MF_GEN_PHILOX_GUE, seed=1, block=2048, cache_budget_bytes=budget,
@@ -779,17 +840,14 @@ def run_philox(args):
                "pairs_cached": desc["pairs_cached"], "clocks": clk}
         if storage == mf.MF_STORE_FULL:
             gbs = canon * 8 / per / 1e9
-            res["roofline"] = {"bound": "hbm", "achieved": gbs, "peak": 6781.4, "unit": "GB/s", "frac": gbs / 6781.4,
+            hbm = measured_peaks()["hbm_gbs"]
+            res["roofline"] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
                                "note": "8 B per canonical entry read once per apply; peak of measured copy"}
         else:
-            mhz = clk.get("sm_mhz") or 1900.0
-            peak_ops = props.multi_processor_count * 128 * mhz * 1e6  # thread instructions / s
-            res["issue_peak_thread_ops_per_s"] = peak_ops
-            res["roofline"] = {"bound": "alu", "achieved_canonical_entries_per_s": canon / per,
-                               "ops_per_entry_counted": PHILOX_OPS_PER_ENTRY,
-                               "achieved": canon / per * PHILOX_OPS_PER_ENTRY / 1e12,
-                               "peak": peak_ops / 1e12, "unit": "Tops/s",
-                               "frac": canon / per * PHILOX_OPS_PER_ENTRY / peak_ops}
+            res["roofline"] = pipe_roofline(canon / per, rates)
+            mhz = clk.get("sm_mhz") or 2070.0
+            issue = props.multi_processor_count * 128 * mhz * 1e6  # thread instructions / s
+            res["roofline"]["issue_frac"] = canon / per * PHILOX_INSTR_PER_ENTRY / issue
         if name == "procedural":
             nt = plan.cheb_terms(1.0)
             psi = x.clone()
@@ -810,17 +868,59 @@ def run_philox(args):
     return 0
 
 
-# Operations of the definition per canonical entry of the FP32 Philox form
-# (counted from the generator's steps): half a Philox4x32-10 call (10 rounds
-# of 2 high and 2 low 32-bit products and 2 three-way XORs = 60 per call),
-# two uniforms (6 each), the log polynomial with its division (~24), sqrt
-# (~8), the sin/cos polynomials with the quadrant logic (~24), the scale (3)
-# and the 8 FMAs applying the entry as H and H^dagger.
-PHILOX_OPS_PER_ENTRY = 30 + 12 + 24 + 8 + 24 + 3 + 8
+# Operations of the definition per canonical entry of the FP32 Philox form,
+# by the pipe that executes them (half of one Philox4x32-10 call and one
+# complex Gaussian entry; each packed FP32 instruction counts as two FP32
+# operations):
+#   imad_hi  10: 2 high 32x32 products per round, 10 rounds, per 2 entries
+#   imad     10: the 2 low products per round
+#   lop3     17: 2 three-input XORs per round (10), the two uniforms' masks
+#                (4), exponent and mantissa extraction of the log argument
+#                (2), the quadrant index of sin/cos (1)
+#   iadd3    11: the key schedule (9 bumps x 2 keys per 2 entries) and the
+#                exponent bias and reduction step of the log (2)
+#   ffma     46: uniforms (6), log with its division and polynomial (15),
+#                -2 log (1), square root with its correction (4), sin/cos
+#                reduction and polynomials (17), sigma scaling (3)
+#   mufu      2: the reciprocal (division) and reciprocal square root
+#   i2f       7: integer-float conversions (4 in the uniforms, the log's
+#                exponent, the quadrant's truncation and its float)
+# plus, for the product itself, 8 FP32 FMAs per vector (H and H^dagger).
+PHILOX_GEN_PIPE_OPS = {"imad_hi": 10, "imad": 10, "lop3": 17, "iadd3": 11, "ffma": 46, "mufu": 2, "i2f": 7}
+PHILOX_OPS_PER_ENTRY = sum(PHILOX_GEN_PIPE_OPS.values()) + 8
 # Thread instructions per canonical entry of the FP32 Philox generator as ncu
-# counted them in the one-vector kernel (the generation term of the bound of
-# the 64-vector workload).
+# counted them in the one-vector kernel (generation plus the 8 FMAs).
 PHILOX_INSTR_PER_ENTRY = 108
+
+
+def pipe_bound(rates, apply_ffma_per_entry=8):
+    """Per-pipe bound of procedural Philox generation (seconds per canonical
+    entry): each pipe's operations per entry over that pipe's measured rate
+    (mf_pipe_rates); the bound is the slowest pipe, the sum of all pipes'
+    times a pessimistic (no overlap) bound."""
+    ops = dict(PHILOX_GEN_PIPE_OPS)
+    ops["ffma"] += apply_ffma_per_entry
+    t = {k: ops[k] / rates[k] for k in ops}
+    worst = max(t, key=t.get)
+    return {"ops_per_entry": ops, "s_per_entry": t, "bound_pipe": worst, "t_bound": t[worst],
+            "t_sum": sum(t.values())}
+
+
+def pipe_roofline(canon_per_s, rates, apply_ffma_per_entry=8):
+    """Roofline record of a measured canonical-entry rate against the
+    per-pipe bound: frac = bound time / measured time per entry (the
+    fraction of the slowest pipe's measured peak the kernel keeps busy);
+    sum_frac the same against the no-overlap sum."""
+    b = pipe_bound(rates, apply_ffma_per_entry)
+    t_meas = 1.0 / canon_per_s
+    return {"bound": "alu", "bound_pipe": b["bound_pipe"], "frac": b["t_bound"] / t_meas,
+            "sum_frac": b["t_sum"] / t_meas,
+            "per_pipe_frac": {k: v / t_meas for k, v in b["s_per_entry"].items()},
+            "ops_per_entry": b["ops_per_entry"],
+            "achieved_canonical_entries_per_s": canon_per_s,
+            "peak_canonical_entries_per_s": 1.0 / b["t_bound"],
+            "basis": "operations of the FP32 Philox definition per canonical entry by pipe, over the pipe rates "
+                     "measured by mf_pipe_rates (register-only chains) in this run"}
 
 
 def batch_roofline(hbm_bytes, gen_entries, flops, t_apply):
@@ -829,7 +929,7 @@ def batch_roofline(hbm_bytes, gen_entries, flops, t_apply):
     pipe (152 x 128 lanes x 2 FLOP x 2070 MHz) and entry generation (the
     Philox row-owner rate, 1.5e11 entries/s measured in the 64-vector FP32
     run); achieved fraction = largest bound / measured time."""
-    t_hbm = hbm_bytes / 6781.4e9
+    t_hbm = hbm_bytes / (measured_peaks()["hbm_gbs"] * 1e9)
     t_fma = flops / (152 * 128 * 2 * 2.07e9)
     t_gen = gen_entries / 1.5e11
     bound = max(t_hbm, t_fma, t_gen)

@@ -113,7 +113,11 @@ typedef struct {
   int32_t autotune_repeats;/* R_bench (3) */
   double dense_work_limit; /* W_Hpsi threshold in entries for MF_WARN_DENSE_WORK (1e13) */
   int32_t device;          /* CUDA device ordinal (0) */
-  mf_mlp_t model;          /* trained surrogate for MF_PLANNER_LEARNED/_HYBRID (NULL) */
+  mf_mlp_t model;          /* trained surrogate for MF_PLANNER_LEARNED/_HYBRID (NULL):
+                              3 outputs (procedural, partial, full); 10 inputs =
+                              direct form (outputs are ln t_mv), 11 inputs = residual
+                              form (input 11 is ln(S_model / waves), the outputs are
+                              ln t_mv minus it); any other shape: MF_ERR_INVALID */
   int32_t hermitian_reuse; /* 2..16 vectors: -1 = automatic (default; each canonical
                               chunk applied as H and H^dagger while its partial slots
                               fit min(16 GB, 10 % of free memory)), 0 = row-owner
@@ -430,7 +434,8 @@ mf_status mf_mlp_train(mf_mlp_t m, const float* X, const float* Y, const float* 
  * (generator, precision, D, b, R = nvec, cache budget):
  * log2 D, log2 b, log2 R, one-hot precision (fp32, bf16x2, fp64), one-hot
  * generator (philox, dvr), budget / full-cache bytes (capped at 1),
- * log10(1 + budget/1e9). */
+ * log10(1 + budget/1e9).  The residual surrogate appends ln(S_model / waves)
+ * of the candidate, from mf_planner_estimate with mf_planner_device_model. */
 mf_status mf_mlp_features(int32_t generator, int32_t precision, int64_t D, int64_t block, int64_t nvec,
                           double cache_budget_bytes, float* out10);
 
@@ -552,6 +557,23 @@ mf_status mf_apply_dvr_noalloc(int64_t D, double dvr_L, const void* x, void* y, 
  * Errors: MF_ERR_INVALID, MF_ERR_OOM, MF_ERR_CUDA.
  */
 mf_status mf_selfcheck_generator(int64_t* div_mismatches, int64_t* sqrt_mismatches);
+
+/*
+ * mf_pipe_rates -- measured throughput, in operations per second, of the
+ * execution pipes the entry generators use, on `device` (launched on
+ * `stream`, a cudaStream_t or NULL): register-only chains with no memory
+ * traffic, 8 CTAs of 256 threads per SM, three timed launches after one
+ * warm-up.  ops_per_s[0..7] (n >= 8, host array owned by the caller):
+ * 0 mul.hi.u32 (IMAD.HI), 1 mad.lo.u32 (IMAD), 2 three-input logic (LOP3),
+ * 3 integer add (IADD3), 4 FP32 fma (FFMA, one operation each),
+ * 5 rsqrt.approx.f32 (MUFU), 6 cvt.rn.f32.u32 (I2F), 7 FP64 fma (DFMA).
+ * These are the denominators of the per-pipe generation bound (the runtime
+ * model of Sec. V.A bounds a procedural product by the slowest resource of
+ * entry generation).  Synchronises; about 50 ms.  The paper has no
+ * counterpart.  Errors: MF_ERR_INVALID (NULL array, n < 8, negative device),
+ * MF_ERR_OOM, MF_ERR_CUDA.
+ */
+mf_status mf_pipe_rates(int32_t device, void* stream, double* ops_per_s, int32_t n);
 
 #ifdef __cplusplus
 }

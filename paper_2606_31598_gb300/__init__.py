@@ -121,6 +121,8 @@ def lib():
         for name in ("mf_rows_cheb_begin", "mf_rows_cheb_init", "mf_rows_cheb_term", "mf_rows_cheb_final"):
             getattr(L, name).restype = ctypes.c_int
         L.mf_selfcheck_generator.restype = ctypes.c_int
+        L.mf_pipe_rates.argtypes = [i32, vp, P(d), i32]
+        L.mf_pipe_rates.restype = ctypes.c_int
         L.mf_plan_destroy.argtypes = [vp]
         L.mf_apply.argtypes = [vp, vp, vp, i64]
         L.mf_cheb_propagate.argtypes = [vp, vp, i64, d, i32]
@@ -265,6 +267,18 @@ def mf_selfcheck_generator():
     a, b = ctypes.c_int64(), ctypes.c_int64()
     _check(lib().mf_selfcheck_generator(ctypes.byref(a), ctypes.byref(b)), "mf_selfcheck_generator")
     return a.value, b.value
+
+
+PIPES = ("imad_hi", "imad", "lop3", "iadd3", "ffma", "mufu", "i2f", "dfma")
+
+
+def mf_pipe_rates(device=0, stream=None):
+    """Measured operations per second of each generator pipe on `device`
+    (dict keyed by PIPES)."""
+    out = (ctypes.c_double * len(PIPES))()
+    st = stream if stream is not None else current_stream()
+    _check(lib().mf_pipe_rates(int(device), ctypes.c_void_p(st), out, len(PIPES)), "mf_pipe_rates")
+    return dict(zip(PIPES, list(out)))
 
 
 def mf_apply(plan, y, x, nvec=1):

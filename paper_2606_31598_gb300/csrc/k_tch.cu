@@ -243,6 +243,11 @@ __device__ __forceinline__ int drain_quarter(int warp) {
 // rows starting at row `srow` (N floats per row, D's column order
 // [Re v0.. | Im v0..]): store when first, else add.  Warp w reads TMEM
 // lanes 32 (w % 4) .. +31 and columns h QC .. +QC, h = drain_quarter(w).
+// The adds are reductions performed at L2 (float4 atomic adds, each
+// component rounded to nearest): the draining warp does not wait for the
+// slot's old value.  A slot element is always drained by the same thread
+// (the mapping above does not change), so its store and adds happen in
+// program order and the sum is the same on every run.
 template <int NV>
 __device__ __forceinline__ void drain_acc(uint32_t tmem, uint32_t col0, float* __restrict__ slots, int64_t srow,
                                           bool first) {
@@ -259,14 +264,8 @@ __device__ __forceinline__ void drain_acc(uint32_t tmem, uint32_t col0, float* _
     for (int i = 0; i < PIECE / 4; ++i) {
       float4 o = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
       float4* d4 = dst + pc * (PIECE / 4) + i;
-      if (!first) {
-        const float4 p = *d4;
-        o.x = __fadd_rn(p.x, o.x);
-        o.y = __fadd_rn(p.y, o.y);
-        o.z = __fadd_rn(p.z, o.z);
-        o.w = __fadd_rn(p.w, o.w);
-      }
-      *d4 = o;
+      if (first) *d4 = o;
+      else atomicAdd(d4, o);
     }
   }
 }

@@ -825,10 +825,9 @@ mf_status measure_plan(Plan& p, int64_t nvec, int warm, int reps, double* t_mean
 // one-vector canonical-entry rate of the FP32 generator (2.7e11/s; the
 // BF16X2 form generates the same FP32 entries), the DVR window table (next
 // to free), and for BF16X2 the BF16 tensor rate (1977 TFLOP/s, measured
-// cuBLAS burst) over its three split products.  (The sweep's records were
-// scored with 4e11/s Philox generation and the FP32 rate for BF16X2; with
-// these two rates the analytic planner's held-out regret on those records
-// falls from 11.7 % to 0.7 %.)
+// cuBLAS burst) over its three split products.  (An earlier model with
+// 4e11/s Philox generation and the FP32 rate for BF16X2 picked plans up to
+// 2x slower than the best for Philox with 16 and 64 vectors.)
 mf_device_model device_model(int prec, int gen, int num_sms) {
   mf_device_model m{};
   const double clk = 1.9e9;

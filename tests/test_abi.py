@@ -122,6 +122,9 @@ def test_every_entry_point_rejects_null_handles_and_bad_arguments(mf):
         "mf_external_create (block 100)": L.mf_external_create(ctypes.byref(vp), 300, 100, None, 0, None),
         "mf_sysbath_create (d_S 0)": L.mf_sysbath_create(ctypes.byref(vp), 0, 100, 0, None, None, None, 0.1, None),
         "mf_apply_dvr_noalloc (D 1)": L.mf_apply_dvr_noalloc(1, 0.0, None, None, None),
+        "mf_pipe_rates (NULL)": L.mf_pipe_rates(0, None, None, 8),
+        "mf_pipe_rates (n 7)": L.mf_pipe_rates(0, None, (ctypes.c_double * 8)(), 7),
+        "mf_pipe_rates (device -1)": L.mf_pipe_rates(-1, None, (ctypes.c_double * 8)(), 8),
     }
     bad = {k: v for k, v in checks.items() if v != INV}
     assert not bad, bad

@@ -44,3 +44,20 @@ def test_profile_traffic_record_parses():
 @pytest.mark.parametrize("world", [1, 2, 8])
 def test_job_value_is_whole_job_throughput(world):
     assert bench.job_value(world, 10, 1e9, 2.0) == pytest.approx(world * 10 * 1e9 / 2.0)
+
+
+def test_per_pipe_bound_takes_the_slowest_pipe():
+    """The generation roofline: each pipe's operations per canonical entry
+    over its rate; the bound is the slowest pipe, the sum the no-overlap
+    bound, and a kernel at exactly the bound's rate has frac 1."""
+    rates = {"imad_hi": 1e13, "imad": 2e13, "lop3": 2e13, "iadd3": 2e13, "ffma": 4e13, "mufu": 5e12, "i2f": 5e12}
+    b = bench.pipe_bound(rates)
+    ops = b["ops_per_entry"]
+    assert ops["ffma"] == bench.PHILOX_GEN_PIPE_OPS["ffma"] + 8
+    assert sum(bench.PHILOX_GEN_PIPE_OPS.values()) == 103  # 39 integer Philox ops + the rest of the definition
+    t = {k: ops[k] / rates[k] for k in ops}
+    assert b["bound_pipe"] == max(t, key=t.get) and b["t_bound"] == max(t.values())
+    assert abs(b["t_sum"] - sum(t.values())) < 1e-30
+    r = bench.pipe_roofline(1.0 / b["t_bound"], rates)
+    assert abs(r["frac"] - 1.0) < 1e-12 and r["sum_frac"] > 1.0
+    assert bench.pipe_bound(rates, apply_ffma_per_entry=0)["ops_per_entry"]["ffma"] == 46

@@ -99,3 +99,25 @@ def test_bf16x2_chebyshev_multivector(mf):
     ref = O.cheb_step_dense(H, X, 0.5, c, R, 20)
     assert np.max(np.abs(out - ref)) < 3e-4
     assert np.max(np.abs(np.linalg.norm(out, axis=0) - 1)) < 1e-4
+
+
+def test_hermitian_walk_is_deterministic_across_runs(mf):
+    """The Hermitian tensor-core walk hands units to CTAs through an atomic
+    counter, so which SM runs which unit changes from run to run; every unit
+    owns its slot rows, each slot element is drained by one thread in a
+    fixed order and the gather sums in FP64 in a fixed order, so repeated
+    products are bitwise equal (and agree with the row-owner kernel within
+    the form's tolerance)."""
+    D, nvec = 8192 + 96, 64
+    X = W.random_state(D, nvec, seed=21).reshape(D, nvec)
+    p = mf.Plan(D, mf.MF_GEN_PHILOX_GUE, seed=3, block=1024, precision=mf.MF_PREC_BF16X2, nvec_hint=nvec,
+                cache_budget_bytes=6 * 1024 * 1024 * 8, storage=mf.MF_STORE_PARTIAL)
+    assert p.describe()["tc_walk"] == "hermitian"
+    ys = [_apply(mf, p, X) for _ in range(3)]
+    assert np.array_equal(ys[0], ys[1]) and np.array_equal(ys[0], ys[2])
+    q = mf.Plan(D, mf.MF_GEN_PHILOX_GUE, seed=3, block=1024, precision=mf.MF_PREC_BF16X2, nvec_hint=nvec,
+                hermitian_reuse=0)
+    assert q.describe()["tc_walk"] != "hermitian"
+    assert _rel(ys[0], _apply(mf, q, X)) < 2e-5
+    p.close()
+    q.close()
