@@ -30,11 +30,11 @@
 // ran which unit; tch_gather sums a row's unit partials in FP64 in a fixed
 // order.
 //
-// Roles inside a CTA (768 threads): 22 generator warps fill the A tile
-// region by region and drain the accumulators; one thread of warp 22
+// Roles inside a CTA (640 threads): 18 generator warps fill the A tile
+// region by region and drain the accumulators; one thread of the copy warp
 // streams the operand tiles with bulk asynchronous copies into a ring of
 // NBUF slots, running ahead of the MMAs as far as the ring allows; one
-// thread of warp 23 issues the MMAs (and copies cached tiles into A).  Tiles
+// thread of the MMA warp issues the MMAs (and copies cached tiles into A).  Tiles
 // alternate their fill orientation (column chunks, then row chunks): the
 // product that runs along the fill overlaps it, the other one releases the
 // A regions the next tile fills first, so generation never waits for a
@@ -58,20 +58,23 @@ using namespace ptx;
 
 constexpr int RT = 128;                    // tile edge
 constexpr int KC = 32;                     // K rows per operand copy / columns per chunk of the tile
-constexpr int NGEN = 22;                   // generator warps
+constexpr int NGEN = 18;                   // generator warps
 constexpr int GT = NGEN * 32;              // generator threads
-// The MMA warp and the operand-copy warp share SM sub-partition 3 (warp %
-// 4 == 3), so the MMA warp competes for issue slots with 4 generator warps
-// rather than 5.  Generator warp w is generator number w - (w > 3) - (w > 7).
+// The MMA warp sits in SM sub-partition 3 and the operand-copy warp in
+// sub-partition 2 (warp % 4), each beside 4 generator warps; sub-partitions
+// 0 and 1 hold 5.  Generator warp w is generator number
+// w - (w > LOAD_WARP) - (w > MMA_WARP).  20 warps leave the kernel 96
+// registers per thread (24 warps: 80, with spills).
+constexpr int LOAD_WARP = 2;               // operand-copy warp
 constexpr int MMA_WARP = 3;                // MMA warp (also copies cached tiles into A)
-constexpr int LOAD_WARP = 7;               // operand-copy warp
-constexpr int NTHREADS = (NGEN + 2) * 32;  // 768: 6 warps per SM sub-partition
+constexpr int NTHREADS = (NGEN + 2) * 32;  // 640: 5 warps per SM sub-partition
 constexpr int W = 2;                       // tile rows per band (band accumulators)
 constexpr int SEG = 8;                     // steps between drains of the band accumulators
 constexpr int PLANE = RT * RT * 2;         // one bf16 plane of the tile: 32 KB
 constexpr int A_BYTES = 4 * PLANE;         // 128 KB
 constexpr int PAIRS = RT * RT / 2;         // horizontal entry pairs of a tile
 constexpr int CPAIRS = RT * KC / 2;        // pairs of a 32-column chunk
+constexpr int MAXPR = (CPAIRS + GT - 1) / GT;  // pairs of a region per generator thread (at most)
 constexpr int kMaxSmem = 229376;           // dynamic shared memory this kernel may take
 constexpr uint32_t kDrainSpin = kDefaultSpin;
 
@@ -235,8 +238,8 @@ __device__ __forceinline__ int64_t tile_cache_off(int a, int tj, int64_t slot, i
 // may only read the lanes of its SM sub-partition) and its column quarter
 // 0..3 among the generator warps of that quadrant, or -1 (no drain duty).
 __device__ __forceinline__ int drain_quarter(int warp) {
-  const int h = (warp & 3) == 3 ? (warp >> 2) - 2 : (warp >> 2);
-  return h < 4 ? h : -1;
+  const int h = (warp >> 2) - ((warp & 3) >= 2 ? 1 : 0);
+  return h >= 0 && h < 4 ? h : -1;
 }
 
 // Drain one TMEM accumulator (columns col0 .. col0 + N - 1) into the slot
@@ -549,7 +552,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       // generator warps: a generated tile is filled region by region in its
       // orientation; before writing region q the warps wait until the
       // previous tile has released it.  Thread gt fills pairs gt, gt + GT,
-      // gt + 2 GT (< CPAIRS) of each region: 3 pairs for gt < CPAIRS - 2 GT.
+      // gt + 2 GT, ... (< CPAIRS) of each region: npr of them.
       const int gt = (warp - (warp > MMA_WARP ? 1 : 0) - (warp > LOAD_WARP ? 1 : 0)) * 32 + lane;
       const int npr = (CPAIRS - gt + GT - 1) / GT;
       const bool drainer = drain_quarter(warp) >= 0;
@@ -596,7 +599,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           for (int q = 0; q < 4; ++q) {
             if (tiles > 0 && !(ok = warp_wait(&rel[q], (tiles - 1) & 1u, spin, err, 135, &abort_flag))) break;
 #pragma unroll
-            for (int i = 0; i < 3; ++i)
+            for (int i = 0; i < MAXPR; ++i)
               if (i < npr) {
                 int r, c;
                 region_rc(o, q, gt + GT * i, r, c);
