@@ -602,6 +602,13 @@ def sub_multivector(stream, peaks, rates):
     t_gen = (canon - cached) * gen["t_bound"]
     bound = max(t_tc, t_hbm, t_gen)
     tb = res["bf16x2"]["kernel_ms"] / 1e3
+    # the instruction-shape bound: the Hermitian walk issues N = 2 x 64 = 128
+    # MMAs (M = 128, K = 16): per off-diagonal 128 x 128 tile 8 K steps x 6
+    # split products for H and as many for H^dagger (96), per diagonal tile
+    # 48, at the measured N = 128 instruction rate
+    T = D // 128
+    n_mma = 96.0 * (T * (T + 1) / 2 - T) + 48.0 * T
+    t_tc_shape = n_mma / rates["mma128"] if rates.get("mma128") else None
     out.update(res)
     out["roofline"] = {
         "bound": {t_tc: "tensor", t_hbm: "hbm", t_gen: "generation"}[bound], "t_bound_s": bound,
@@ -609,6 +616,11 @@ def sub_multivector(stream, peaks, rates):
         "tensor_tflops": 24.0 * R * D * D / tb / 1e12, "peak_tensor_tflops": peaks["bf16_tflops_sustained"],
         "peak_source": peaks["source"],
         "generation_bound_pipe": gen["bound_pipe"],
+        "t_tensor_shape_s": t_tc_shape,
+        "frac_of_shape_bound": (max(t_tc_shape, t_hbm, t_gen) / tb) if t_tc_shape else None,
+        "shape_note": "one tcgen05.mma M=128 K=16 instruction takes the same time at N=128 as at N=256 "
+                      "(mf_pipe_rates), so the 64-vector product (N=128) can reach at most half of the dense "
+                      "BF16 rate; t_tensor_shape_s is its MMA instructions at the measured N=128 rate",
         "basis": "tensor: 3 bf16 products x 8 real FLOP x 64 vectors x D^2 at the sustained BF16 peak; hbm: the "
                  "cached canonical entries (8 B each) at the measured copy rate; generation: the procedural "
                  "canonical entries at the slowest pipe's measured rate (operations of the FP32 Philox "

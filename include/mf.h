@@ -566,12 +566,16 @@ mf_status mf_selfcheck_generator(int64_t* div_mismatches, int64_t* sqrt_mismatch
  * warm-up.  ops_per_s[0..7] (n >= 8, host array owned by the caller):
  * 0 mul.hi.u32 (IMAD.HI), 1 mad.lo.u32 (IMAD), 2 three-input logic (LOP3),
  * 3 integer add (IADD3), 4 FP32 fma (FFMA, one operation each),
- * 5 rsqrt.approx.f32 (MUFU), 6 cvt.rn.f32.u32 (I2F), 7 FP64 fma (DFMA).
- * These are the denominators of the per-pipe generation bound (the runtime
- * model of Sec. V.A bounds a procedural product by the slowest resource of
- * entry generation).  Synchronises; about 50 ms.  The paper has no
- * counterpart.  Errors: MF_ERR_INVALID (NULL array, n < 8, negative device),
- * MF_ERR_OOM, MF_ERR_CUDA.
+ * 5 rsqrt.approx.f32 (MUFU), 6 cvt.rn.f32.u32 (I2F), 7 FP64 fma (DFMA);
+ * with n >= 10 also the tensor cores, as tcgen05.mma instructions per second
+ * over the GPU (kind::f16, bf16 operands in shared memory, FP32 accumulator,
+ * M = 128, K = 16, one issuing thread per SM): 8 with N = 128, 9 with
+ * N = 256.  These are the denominators of the per-pipe generation bound and
+ * of the instruction-shape bound of the tensor-core products (the runtime
+ * model of Sec. V.A bounds a product by its slowest resource).  Synchronises;
+ * about 60 ms.  The paper has no counterpart.  Errors: MF_ERR_INVALID (NULL
+ * array, n < 8, negative device), MF_ERR_OOM, MF_ERR_TIMEOUT (an MMA wait
+ * ran out; the GPU stays usable), MF_ERR_CUDA.
  */
 mf_status mf_pipe_rates(int32_t device, void* stream, double* ops_per_s, int32_t n);
 

@@ -269,12 +269,13 @@ def mf_selfcheck_generator():
     return a.value, b.value
 
 
-PIPES = ("imad_hi", "imad", "lop3", "iadd3", "ffma", "mufu", "i2f", "dfma")
+PIPES = ("imad_hi", "imad", "lop3", "iadd3", "ffma", "mufu", "i2f", "dfma", "mma128", "mma256")
 
 
 def mf_pipe_rates(device=0, stream=None):
-    """Measured operations per second of each generator pipe on `device`
-    (dict keyed by PIPES)."""
+    """Measured operations per second of each generator pipe on `device`,
+    and tcgen05 MMA instructions per second (M = 128, K = 16; N = 128 and
+    N = 256) over the GPU (dict keyed by PIPES)."""
     out = (ctypes.c_double * len(PIPES))()
     st = stream if stream is not None else current_stream()
     _check(lib().mf_pipe_rates(int(device), ctypes.c_void_p(st), out, len(PIPES)), "mf_pipe_rates")

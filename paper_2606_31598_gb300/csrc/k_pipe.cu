@@ -19,11 +19,21 @@
 //              of the FP32 form use the same unit)
 //   6 I2F      cvt.rn.f32.u32 (integer-to-float conversion)
 //   7 DFMA     FP64 fused multiply-add
+// and, when the caller asks for them, the 5th-generation tensor cores:
+//   8 MMA128   tcgen05.mma kind::f16 (bf16 operands, FP32 accumulator in
+//              TMEM), M = 128, N = 128, K = 16, both operands in shared
+//              memory (no-swizzle K-major), one issuing thread per SM,
+//              back to back into one accumulator
+//   9 MMA256   the same with N = 256
+// reported as MMA instructions per second over the GPU.  One instruction of
+// either shape takes the same time on GB300, so N = 128 products (64 complex
+// vectors) reach at most half of the dense BF16 rate.
 #include <cuda_runtime.h>
 
 #include <cstdint>
 
 #include "mf_internal.h"
+#include "tc_ptx.cuh"
 
 namespace {
 
@@ -152,6 +162,71 @@ __global__ void __launch_bounds__(kThreads) k_pipe(typename Chain<C, NA>::T* out
   out[blockIdx.x * (int64_t)blockDim.x + threadIdx.x] = s;  // keeps every chain live
 }
 
+// Tensor-core class: operands A (64 KB) and B (64 KB) at the start of the
+// dynamic shared memory; instruction i reads K step i % 8 of a 128-wide K
+// tile (A: 16 row groups of 2048 B, B: N / 8 column groups of 2048 B, so the
+// last byte read is below 128 KB).  Every wait is bounded; a time-out sets
+// *err and the CTA still frees its TMEM.
+constexpr int kMmaSmem = 144 * 1024;  // one CTA per SM
+constexpr int kMmaCols = 256;
+
+template <int N>
+__global__ void __launch_bounds__(128, 1) k_pipe_mma(int nmma, int* err) {
+  using namespace mf::ptx;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ uint64_t bar;
+  __shared__ uint32_t tmem_base;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < 32768; i += 128) reinterpret_cast<uint32_t*>(smem)[i] = 0x3c003c00u ^ (i & 0x00ff00ffu);
+  if (tid == 0) mbar_init(&bar, 1);
+  fence_async_smem();
+  if (tid < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(kMmaCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+  if (tid == 0) {
+    const uint32_t A = smem_u32(smem), B = smem_u32(smem + 65536);
+    constexpr uint32_t idesc = idesc_bf16_m128(N, 0);
+    uint32_t commits = 0;
+    for (int i = 0; i < nmma; ++i) {
+      const uint32_t k = (uint32_t)(i & 7) * 256;
+      mma_bf16(tmem, smem_desc_nosw(A + k, 128, 2048), smem_desc_nosw(B + k, 128, 2048), idesc, i > 0 ? 1u : 0u);
+      if ((i & 31) == 31 || i + 1 == nmma) {
+        mma_commit(&bar);
+        ++commits;
+      }
+    }
+    if (commits > 0 && !mbar_wait(&bar, (commits - 1) & 1u, 1u << 26)) atomicExch(err, 1);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (tid < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kMmaCols) : "memory");
+}
+
+template <int N>
+cudaError_t time_mma(int sms, int* err, cudaStream_t s, cudaEvent_t a, cudaEvent_t e, double* mma_per_s) {
+  auto k = k_pipe_mma<N>;
+  cudaError_t r = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kMmaSmem);
+  if (r != cudaSuccess) return r;
+  const int nmma = 1 << 14;
+  k<<<sms, 128, kMmaSmem, s>>>(256, err);
+  if ((r = cudaGetLastError()) != cudaSuccess) return r;
+  if ((r = cudaEventRecord(a, s)) != cudaSuccess) return r;
+  k<<<sms, 128, kMmaSmem, s>>>(nmma, err);
+  if ((r = cudaEventRecord(e, s)) != cudaSuccess) return r;
+  if ((r = cudaEventSynchronize(e)) != cudaSuccess) return r;
+  float ms = 0.f;
+  if ((r = cudaEventElapsedTime(&ms, a, e)) != cudaSuccess) return r;
+  *mma_per_s = ms > 0.f ? (double)nmma * sms / (ms * 1e-3) : 0.0;
+  return cudaSuccess;
+}
+
 template <int C, int NA>
 cudaError_t time_class(void* out, int blocks, int iters, typename Chain<C, NA>::T m, cudaStream_t s,
                        cudaEvent_t a, cudaEvent_t e, double* ops_per_s) {
@@ -171,7 +246,7 @@ cudaError_t time_class(void* out, int blocks, int iters, typename Chain<C, NA>::
   return cudaSuccess;
 }
 
-mf_status measure(int32_t device, void* stream, double* ops_per_s) {
+mf_status measure(int32_t device, void* stream, double* ops_per_s, bool tensor) {
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return MF_ERR_CUDA;
   const int blocks = sms * kCtasPerSm;
@@ -190,10 +265,19 @@ mf_status measure(int32_t device, void* stream, double* ops_per_s) {
   if (err == cudaSuccess) err = time_class<5, 16>(out, blocks, 512, 0.f, s, a, e, &ops_per_s[5]);
   if (err == cudaSuccess) err = time_class<6, 16>(out, blocks, 512, 0u, s, a, e, &ops_per_s[6]);
   if (err == cudaSuccess) err = time_class<7, 8>(out, blocks, 64, 0.999, s, a, e, &ops_per_s[7]);
+  int timed_out = 0;
+  if (tensor && err == cudaSuccess) {
+    int* d_err = reinterpret_cast<int*>(out);
+    err = cudaMemsetAsync(d_err, 0, sizeof(int), s);
+    if (err == cudaSuccess) err = time_mma<128>(sms, d_err, s, a, e, &ops_per_s[8]);
+    if (err == cudaSuccess) err = time_mma<256>(sms, d_err, s, a, e, &ops_per_s[9]);
+    if (err == cudaSuccess) err = cudaMemcpy(&timed_out, d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  }
   if (a) cudaEventDestroy(a);
   if (e) cudaEventDestroy(e);
   cudaFree(out);
-  return err == cudaSuccess ? MF_OK : MF_ERR_CUDA;
+  if (err != cudaSuccess) return MF_ERR_CUDA;
+  return timed_out ? MF_ERR_TIMEOUT : MF_OK;
 }
 
 }  // namespace
@@ -202,7 +286,7 @@ extern "C" mf_status mf_pipe_rates(int32_t device, void* stream, double* ops_per
   if (!ops_per_s || n < kClasses || device < 0) return MF_ERR_INVALID;
   int prev = 0;
   if (cudaGetDevice(&prev) != cudaSuccess || cudaSetDevice(device) != cudaSuccess) return MF_ERR_CUDA;
-  const mf_status st = measure(device, stream, ops_per_s);
+  const mf_status st = measure(device, stream, ops_per_s, n >= kClasses + 2);
   cudaSetDevice(prev);
   return st;
 }
