@@ -127,10 +127,11 @@ typedef struct {
   int64_t row_end;         /* (Sec. IV.H, row-parallel mode); 0, 0 = all rows; see
                               mf_plan_create */
   int32_t spin_limit;      /* polls of one bounded wait inside the tensor-core kernels
-                              (0 = 2^22, a few hundred ms); when one runs out the kernel
-                              stops, frees its tensor memory and reports MF_ERR_TIMEOUT
-                              (the waits for its own copies and MMAs already issued keep
-                              the 2^22 bound whatever this value) */
+                              (0 = 2^18; a poll suspends at most 5 us, so at most about
+                              1.3 s); when one runs out the kernel stops, frees its
+                              tensor memory and reports MF_ERR_TIMEOUT (the waits for
+                              its own copies and MMAs already issued keep the 2^18
+                              bound whatever this value) */
 } mf_options;
 
 /* Generic planning instance P_mv of Sec. IV.A (Y = A X with A of size

@@ -20,7 +20,9 @@ constexpr int kTile = 128;  // CTA tile edge of the Hermitian (canonical-pair) k
 // Device error word codes: kernels set the word with atomicCAS(word, 0, code)
 // when a bounded wait runs out; the code says which wait (100..199).
 constexpr int kErrTimeoutFirst = 100, kErrTimeoutLast = 199;
-constexpr uint32_t kDefaultSpin = 1u << 22;  // polls of a bounded wait
+// polls of a bounded wait: each poll suspends at most 5 us, so a wait that
+// never completes ends within about 1.3 s
+constexpr uint32_t kDefaultSpin = 1u << 18;
 
 // Host-side fault injection (MF_FAULT="<site>:<n>", see include/mf.h): true
 // when this event of the site is the n-th since the variable took its value.
