@@ -22,8 +22,10 @@ and error against the FP64 form: the Philox ensemble at D = 4096 in the FP64
 form (one product and a 32-term step), Philox generation at D = 131072 (one
 vector, procedural, with the per-pipe roofline against the pipe rates
 measured in the same run, "pipe_rates"), the 64-vector Philox workload at
-D = 262144 with its 120 GB cache (BF16X2 and FP32 forms, one Chebyshev step)
-and the 256 batched problems (one step).  --headline-only leaves them out.
+D = 262144 with its 120 GB cache (BF16X2 and FP32 forms, one Chebyshev step),
+the 256 batched problems (one step) and the planner comparison on the
+shipped sweep records (surrogates trained on the GPU).  --headline-only
+leaves them out.
 """
 import argparse
 import hashlib
@@ -331,6 +333,15 @@ def run_mf(args):
         torch.cuda.synchronize()
         plan16.sync()
         c16 = c16.cpu().numpy()
+        # the same step timed in the BF16X2 form (one vector padded to the
+        # tensor cores' smallest N of 8 vectors)
+        d16 = torch.from_numpy(psi0).to(dev)
+        ev0.record()
+        plan16.cheb_propagate(d16, 1, tau, TERMS)
+        ev1.record()
+        torch.cuda.synchronize()
+        plan16.sync()
+        bf16x2_step_s = ev0.elapsed_time(ev1) / 1e3
         plan16.close()
         err = {"fp32_vs_fp64_form": float(np.linalg.norm(a - b)), "fp32_vs_closed_form": float(np.linalg.norm(a - exact)),
                "bf16x2_vs_fp64_form": float(np.linalg.norm(c16 - b)),
@@ -361,6 +372,7 @@ def run_mf(args):
             "cheb_steps_per_s": world * args.steps / t_job,
             "dt_steps_per_s": world * args.steps / t_job / np.ceil(DT_CONFIG / tau),
             "fp64_form_entries_per_s": fp64_entries_per_s,
+            "bf16x2_form_entries_per_s": entries_per_step / bf16x2_step_s,
             "error": err,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": (achieved / peak) if peak else None, "traffic": traffic,
@@ -389,7 +401,8 @@ def run_mf(args):
             for key, fn in (("philox_D4096_fp64", lambda: sub_small_philox(stream)),
                             ("philox_D131072_generation", lambda: sub_philox_generation(stream, rates)),
                             ("philox_D262144_64vec_120GB", lambda: sub_multivector(stream, peaks, rates)),
-                            ("batch_256_problems", lambda: sub_batch(stream))):
+                            ("batch_256_problems", lambda: sub_batch(stream)),
+                            ("planner_sweep_regret", sub_planner)):
                 t0 = time.perf_counter()
                 line["workloads"][key] = fn()
                 line["workloads"][key]["wall_s"] = time.perf_counter() - t0
@@ -487,8 +500,9 @@ def sub_philox_generation(stream, rates):
     (seed 1), FP32 form, procedural, one vector (seed 3): every canonical
     entry generated once per product and applied as H and H^dagger.  The
     roofline is per pipe (operations of the definition over the measured
-    rate of each pipe); error on 16 sampled rows against the oracle's FP32
-    statement; the CPU baseline is the oracle on 4096 evenly spaced rows."""
+    rate of each pipe); the oracle's FP32 statement of about 4100 rows (tile
+    and block boundaries, and evenly spaced ones) is both the CPU baseline
+    and the error reference."""
     import torch
     import paper_2606_31598_gb300 as mf
     import workloads as W
@@ -507,16 +521,15 @@ def sub_philox_generation(stream, rates):
     plan.sync()
     per = kern_ms / 1e3 / max(1, kern_n)
     canon = D * (D + 1) / 2.0
-    rows = np.array([0, 1, 127, 128, 2047, 2048, 65535, 65536, 100000, 131071, 4096, 8191, 31337, 77777, 99999,
-                     120000])
+    # rows at tile and block boundaries and 4096 evenly spaced ones: the
+    # oracle computes them once, as the CPU baseline and the error reference
+    edge = np.array([0, 1, 127, 128, 2047, 2048, 65535, 65536, 100000, 131071])
+    rows = np.unique(np.concatenate([edge, np.linspace(0, D - 1, 4096).astype(np.int64)]))
     got = y[torch.from_numpy(rows).cuda()].cpu().numpy()
     plan.close()
     op32 = O.make_op(O.GEN_PHILOX_GUE, D, seed=1, form=O.FORM_FP32)
-    ref = O.apply_rows(op32, x0.reshape(D, 1), rows)
-    # CPU baseline: the oracle on 4096 evenly spaced rows (a few seconds)
-    cpu_rows = np.linspace(0, D - 1, 4096).astype(np.int64)
     t0 = time.perf_counter()
-    O.apply_rows(op32, x0.reshape(D, 1), cpu_rows)
+    ref = O.apply_rows(op32, x0.reshape(D, 1), rows)
     t_cpu = time.perf_counter() - t0
     roof = pipe_roofline(canon / per, rates)
     roof["issue_frac"] = canon / per * PHILOX_INSTR_PER_ENTRY / (152 * 128 * 2.07e9)
@@ -525,11 +538,11 @@ def sub_philox_generation(stream, rates):
             "canonical_entries_per_s": canon / per,
             "error": {"rows_rel_vs_oracle": float(np.max(np.abs(got.reshape(-1) - ref.reshape(-1))) /
                                                   np.max(np.abs(ref))),
-                      "measure": "16 sampled output rows against the oracle's FP32 statement"},
+                      "measure": "%d sampled output rows against the oracle's FP32 statement" % len(rows)},
             "roofline": roof,
-            "cpu_baseline": {"value": len(cpu_rows) * float(D) / t_cpu, "unit": "entries/s", "cores": cpu_threads(),
-                             "kind": "oracle", "sample": "4096 of 131072 output rows of one FP32-form H psi "
-                                                        "(%.2f s), rate extrapolated" % t_cpu}}
+            "cpu_baseline": {"value": len(rows) * float(D) / t_cpu, "unit": "entries/s", "cores": cpu_threads(),
+                             "kind": "oracle", "sample": "%d of 131072 output rows of one FP32-form H psi "
+                                                        "(%.2f s), rate extrapolated" % (len(rows), t_cpu)}}
 
 
 def sub_multivector(stream, peaks, rates):
@@ -632,6 +645,50 @@ def sub_multivector(stream, peaks, rates):
     return out
 
 
+def sub_planner():
+    """The planner comparison of Algorithms 1-3 on the GB300 sweep records
+    shipped with the package (475 problems, 4275 candidate plans measured
+    with the current kernels, scored by the library's Algorithm 1): the
+    held-out regret (seed-0 split by problem) of the analytic ranking and of
+    the direct and residual surrogates, trained here on the GPU (3000 Adam
+    epochs each).  CPU baseline: the oracle's FP64 training of the same
+    network, epochs per second over 50 epochs."""
+    import math
+    from oracle import mlp_oracle as MO
+    from paper_2606_31598_gb300 import planner_sweep as ps
+    recs = ps.load(ps.RECORDS_GB300)
+    t0 = time.perf_counter()
+    res = ps.evaluate(recs, epochs=3000)
+    t_fit = time.perf_counter() - t0
+    train, _ = ps.split(recs, 0.2, 0)
+    X = ps.surrogate_inputs(train).astype(np.float64)
+    Y = np.zeros((len(train), 3))
+    M = np.zeros((len(train), 3))
+    for i, r in enumerate(train):
+        k = ps.STRATEGIES.index(r["storage"])
+        Y[i, k] = math.log(r["t_mv"])
+        M[i, k] = 1.0
+    F, H, O = X.shape[1], 64, 3
+    rng = np.random.default_rng(0)
+    p0 = np.concatenate([rng.standard_normal(F * H) / np.sqrt(F), np.zeros(H), rng.standard_normal(H * H) / np.sqrt(H),
+                         np.zeros(H), rng.standard_normal(H * O) / np.sqrt(H), np.zeros(O)])
+    mu, sd = MO.zscore(X)
+    t0 = time.perf_counter()
+    MO.train_adam(p0, mu, sd, X, Y, M, F, H, O, epochs=50, lr=3e-3)
+    t_cpu = time.perf_counter() - t0
+    return {"workload": "planner sweep records (GB300, current kernels): %d problems, %d candidate plans; seed-0 "
+                        "80/20 split by problem" % (len({r["problem"] for r in recs}), len(recs)),
+            "held_out_regret": {"analytic": res["analytic_test"], "learned_direct": res["learned_test"],
+                                "learned_residual": res["residual_test"]},
+            "train_regret": {"analytic": res["analytic_train"], "learned_direct": res["learned_train"],
+                             "learned_residual": res["residual_train"]},
+            "score_drift": res["score_drift"],
+            "fit_s_two_surrogates": t_fit, "gpu_epochs_per_s": 2 * 3000 / t_fit,
+            "cpu_baseline": {"value": 50 / t_cpu, "unit": "epochs/s", "cores": cpu_threads(), "kind": "oracle",
+                             "sample": "50 FP64 Adam epochs of the direct surrogate on the training records "
+                                       "(%.2f s)" % t_cpu}}
+
+
 def sub_batch(stream):
     """256 batched Philox problems (the workload draw: D log-uniform in
     [1024, 32768] rounded to 128, 1..16 vectors, seeds 0..255), plans chosen
@@ -662,9 +719,8 @@ def sub_batch(stream):
     b.propagate(packed, 1.0, 1)
     torch.cuda.synchronize()
     got0 = packed[int(b.offsets[0]):int(b.offsets[1])].cpu().numpy().reshape(Ds[0], nv[0])
-    lo, hi = mf.mf_spectral_bounds(b.plan(0))
-    c, R = 0.5 * (hi + lo), 0.5 * (hi - lo)
-    ref0 = O.cheb_step(O.make_op(O.GEN_PHILOX_GUE, Ds[0], seed=seeds[0], form=O.FORM_FP32), parts[0], 1.0, c, R, nt)
+    NCPU = 4  # problems of the CPU baseline (their bounds, before the batch is closed)
+    bounds = [mf.mf_spectral_bounds(b.plan(i)) for i in range(NCPU)]
     entries = float(sum(D * D * k for D, k in zip(Ds, nv)))
     hbm_bytes = gen_entries = flops = 0.0
     stores = {}
@@ -677,13 +733,20 @@ def sub_batch(stream):
         flops += 8.0 * D * D * k
     n_items, grid = b.info()
     b.close()
+    # CPU baseline: the oracle's Chebyshev step (FP32 form, the batch's
+    # bounds and term count) of the first problems; problem 0's result is
+    # also the error reference
+    applies = nt - 1
     t0 = time.perf_counter()
     cpu_entries = 0.0
-    for i in range(8):
-        O.apply(O.make_op(O.GEN_PHILOX_GUE, Ds[i], seed=seeds[i]), parts[i])
-        cpu_entries += float(Ds[i]) * Ds[i] * nv[i]
+    for i in range(NCPU):
+        lo, hi = bounds[i]
+        ref = O.cheb_step(O.make_op(O.GEN_PHILOX_GUE, Ds[i], seed=seeds[i], form=O.FORM_FP32), parts[i], 1.0,
+                          0.5 * (hi + lo), 0.5 * (hi - lo), nt)
+        if i == 0:
+            ref0 = ref
+        cpu_entries += float(applies) * Ds[i] * Ds[i] * nv[i]
     t_cpu = time.perf_counter() - t0
-    applies = nt - 1
     return {"workload": "256 batched Philox problems, D in [1024, 32768], 1-16 vectors, FP32, autotuned plans",
             "create_s": t_create, "terms_per_step": nt, "step_s": t, "steps_per_s": 1.0 / t,
             "entries_per_s": entries * applies / t, "sum_D2_nvec": entries, "work_items": n_items,
@@ -692,8 +755,8 @@ def sub_batch(stream):
                       "measure": "FP32 form against the oracle's statement of the same form, same bounds/terms"},
             "roofline": batch_roofline(hbm_bytes, gen_entries, flops, t / applies),
             "cpu_baseline": {"value": cpu_entries / t_cpu, "unit": "entries/s", "cores": cpu_threads(),
-                             "kind": "oracle", "sample": "one FP64 product of each of the first 8 problems "
-                                                        "(%.1f s)" % t_cpu}}
+                             "kind": "oracle", "sample": "the FP32-form Chebyshev step of the first %d problems "
+                                                        "(%.1f s)" % (NCPU, t_cpu)}}
 
 
 def time_applies(plan, x, y, nvec, reps):
