@@ -679,7 +679,9 @@ def sub_planner():
     return {"workload": "planner sweep records (GB300, current kernels): %d problems, %d candidate plans; seed-0 "
                         "80/20 split by problem" % (len({r["problem"] for r in recs}), len(recs)),
             "held_out_regret": {"analytic": res["analytic_test"], "learned_direct": res["learned_test"],
-                                "learned_residual": res["residual_test"]},
+                                "learned_residual": res["residual_test"],
+                                "no_planner_procedural_b2048": res["fixed_procedural_test"],
+                                "no_planner_max_cache_b2048": res["fixed_max_cache_test"]},
             "train_regret": {"analytic": res["analytic_train"], "learned_direct": res["learned_train"],
                              "learned_residual": res["residual_train"]},
             "score_drift": res["score_drift"],

@@ -224,6 +224,32 @@ def regret(records, net=None):
             "max": float(regs.max()), "zero_regret_frac": float(np.mean(regs < 1e-9))}
 
 
+def fixed_choice(rs, kind, block=2048):
+    """The plan a caller without a planner would take for one problem:
+    kind "procedural" -- no cache, the block size nearest `block`;
+    kind "max_cache" -- the most cache the budget allows (full, else
+    partial, else procedural) at the block size nearest `block`."""
+    def nearest(cands):
+        return min(cands, key=lambda r: (abs(math.log2(r["block"]) - math.log2(block)), r["block"]))
+    if kind == "procedural":
+        return nearest([r for r in rs if r["storage"] == "procedural"])
+    for st in ("full", "partial", "procedural"):
+        cands = [r for r in rs if r["storage"] == st]
+        if cands:
+            return nearest(cands)
+    raise ValueError(kind)
+
+
+def fixed_regret(records, kind):
+    """regret() of a fixed plan without planning (fixed_choice)."""
+    by = {}
+    for r in records:
+        by.setdefault(r["problem"], []).append(r)
+    regs = np.array([fixed_choice(rs, kind)["t_mv"] / min(r["t_mv"] for r in rs) - 1.0 for rs in by.values()])
+    return {"problems": int(len(regs)), "mean": float(regs.mean()), "median": float(np.median(regs)),
+            "max": float(regs.max()), "zero_regret_frac": float(np.mean(regs < 1e-9))}
+
+
 def rescore(records):
     """The records with S_model recomputed by the library's current analytic
     model (mf_planner_estimate with mf_planner_device_model; host only), so
@@ -263,6 +289,8 @@ def evaluate(records, epochs=3000, seed=0):
     re = rescore(records)
     out["score_drift"] = float(max(abs(a["S_model"] / b["S_model"] - 1.0) for a, b in zip(re, records)))
     out["analytic_current_model_test"] = regret(rescore(test), None)
+    out["fixed_procedural_test"] = fixed_regret(test, "procedural")
+    out["fixed_max_cache_test"] = fixed_regret(test, "max_cache")
     return out
 
 
