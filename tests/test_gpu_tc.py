@@ -33,7 +33,7 @@ def _rel(a, b):
 
 
 @pytest.mark.parametrize("gen", [0, 1])
-@pytest.mark.parametrize("nvec", [1, 8, 16, 64])
+@pytest.mark.parametrize("nvec", [1, 8, 13, 16, 24, 40, 64])
 def test_bf16x2_apply_matches_oracle(mf, gen, nvec):
     D = 1000
     p = mf.Plan(D, gen, seed=3, block=256, precision=mf.MF_PREC_BF16X2)
