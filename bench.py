@@ -398,7 +398,7 @@ def run_mf(args):
                                       k: v / (props.multi_processor_count * 2.07e9) for k, v in rates.items()},
                                   "source": "mf_pipe_rates: register-only chains, 8 CTAs x 256 threads per SM"}
             line["workloads"] = {}
-            for key, fn in (("philox_D4096_fp64", lambda: sub_small_philox(stream)),
+            for key, fn in (("philox_D4096_fp64", lambda: sub_small_philox(stream, rates)),
                             ("philox_D131072_generation", lambda: sub_philox_generation(stream, rates)),
                             ("philox_D262144_64vec_120GB", lambda: sub_multivector(stream, peaks, rates)),
                             ("batch_256_problems", lambda: sub_batch(stream)),
@@ -441,7 +441,16 @@ def events_time(fn, reps):
     return a.elapsed_time(b) / 1e3 / reps
 
 
-def sub_small_philox(stream):
+# FP64 arithmetic operations of the definition per canonical entry of the
+# FP64 Philox form (division and square root counted as one each, so the
+# bound is a lower one): the two uniforms (2 each), the log with its
+# division and 10-term polynomial (18), -2 log (1), the square root (1),
+# sin/cos reduction and two 9-term polynomials (24), sigma scaling (3); plus
+# 8 FP64 FMAs per vector for H and H^dagger.  All run on the FP64 pipe.
+PHILOX64_DFMA_OPS = 2 + 2 + 18 + 1 + 1 + 24 + 3
+
+
+def sub_small_philox(stream, rates=None):
     """Plain method, small size: Philox ensemble D = 4096 (seed 1) in the FP64
     form (complex128), block 512, procedural; one H psi plus one 32-term
     Chebyshev step of t = 1 per step, psi random (seed 1).  GPU and CPU
@@ -486,11 +495,7 @@ def sub_small_philox(stream):
             "error": {"apply_rel_vs_oracle": float(np.max(np.abs(yh - ref_y)) / np.max(np.abs(ref_y))),
                       "step_abs_vs_oracle": float(np.max(np.abs(ph - ref_psi))),
                       "measure": "FP64 form against the CPU oracle's FP64 statement (same bounds and terms)"},
-            "roofline": {"bound": "fp64", "achieved_canonical_entries_per_s": NT * D * (D + 1) / 2.0 / t,
-                         "note": "the FP64 form generates each canonical entry with FP64 Philox-to-Gaussian "
-                                 "arithmetic on GB300's FP64 pipe (DFMA measured at about 1/75 of the FP32 FMA "
-                                 "rate, mf_pipe_rates); %.3f ms per product launch, 8.4e6 canonical entries"
-                                 % (kern_ms / max(1, kern_n))},
+            "roofline": fp64_roofline(D * (D + 1) / 2.0, kern_ms / 1e3 / max(1, kern_n), rates),
             "cpu_baseline": {"value": entries / t_cpu, "unit": "entries/s", "cores": cpu_threads(), "kind": "oracle",
                              "sample": "the whole step (one product plus the 32-term step) in FP64 (%.2f s)" % t_cpu}}
 
@@ -973,6 +978,21 @@ PHILOX_OPS_PER_ENTRY = sum(PHILOX_GEN_PIPE_OPS.values()) + 8
 # Thread instructions per canonical entry of the FP32 Philox generator as ncu
 # counted them in the one-vector kernel (generation plus the 8 FMAs).
 PHILOX_INSTR_PER_ENTRY = 108
+
+
+def fp64_roofline(canon, t_launch, rates):
+    """Roofline of one FP64-form product launch against the measured FP64
+    pipe: the FP64 operations of the definition per canonical entry plus the
+    8 apply FMAs, over the DFMA rate of mf_pipe_rates."""
+    out = {"bound": "fp64", "achieved_canonical_entries_per_s": canon / t_launch, "kernel_s": t_launch,
+           "ops_per_entry": PHILOX64_DFMA_OPS + 8,
+           "note": "FP64 Philox-to-Gaussian arithmetic on GB300's FP64 pipe (about 1/75 of the FP32 FMA rate); "
+                   "division and square root counted as one operation each, so the bound is a lower one"}
+    if rates and rates.get("dfma"):
+        t_bound = canon * (PHILOX64_DFMA_OPS + 8) / rates["dfma"]
+        out.update({"bound_pipe": "dfma", "t_bound_s": t_bound, "frac": t_bound / t_launch,
+                    "peak_dfma_per_s": rates["dfma"]})
+    return out
 
 
 def pipe_bound(rates, apply_ffma_per_entry=8):

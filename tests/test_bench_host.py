@@ -61,3 +61,14 @@ def test_per_pipe_bound_takes_the_slowest_pipe():
     r = bench.pipe_roofline(1.0 / b["t_bound"], rates)
     assert abs(r["frac"] - 1.0) < 1e-12 and r["sum_frac"] > 1.0
     assert bench.pipe_bound(rates, apply_ffma_per_entry=0)["ops_per_entry"]["ffma"] == 46
+
+
+def test_fp64_roofline_counts_the_definition():
+    """The FP64 form's bound: 51 FP64 operations of the definition per
+    canonical entry (two uniforms, log with its division and polynomial,
+    square root, sin/cos polynomials, scaling) plus 8 apply FMAs, over the
+    measured DFMA rate; without rates no fraction is claimed."""
+    assert bench.PHILOX64_DFMA_OPS == 51
+    r = bench.fp64_roofline(1e6, 1e-3, {"dfma": 5.9e10})
+    assert r["ops_per_entry"] == 59 and abs(r["frac"] - 1.0) < 1e-12
+    assert "frac" not in bench.fp64_roofline(1e6, 1e-3, None)
