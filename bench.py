@@ -401,7 +401,7 @@ def run_mf(args):
             for key, fn in (("philox_D4096_fp64", lambda: sub_small_philox(stream, rates)),
                             ("philox_D131072_generation", lambda: sub_philox_generation(stream, rates)),
                             ("philox_D262144_64vec_120GB", lambda: sub_multivector(stream, peaks, rates)),
-                            ("batch_256_problems", lambda: sub_batch(stream)),
+                            ("batch_256_problems", lambda: sub_batch(stream, rates)),
                             ("planner_sweep_regret", sub_planner)):
                 t0 = time.perf_counter()
                 line["workloads"][key] = fn()
@@ -696,7 +696,7 @@ def sub_planner():
                                        "(%.2f s)" % t_cpu}}
 
 
-def sub_batch(stream):
+def sub_batch(stream, rates=None):
     """256 batched Philox problems (the workload draw: D log-uniform in
     [1024, 32768] rounded to 128, 1..16 vectors, seeds 0..255), plans chosen
     per problem by the measured autotuner, FP32 form, one persistent launch
@@ -760,7 +760,7 @@ def sub_batch(stream):
             "persistent_grid": grid, "storage_chosen": stores,
             "error": {"problem0_step_abs_vs_oracle": float(np.max(np.abs(got0 - ref0))),
                       "measure": "FP32 form against the oracle's statement of the same form, same bounds/terms"},
-            "roofline": batch_roofline(hbm_bytes, gen_entries, flops, t / applies),
+            "roofline": batch_roofline(hbm_bytes, gen_entries, flops, t / applies, rates),
             "cpu_baseline": {"value": cpu_entries / t_cpu, "unit": "entries/s", "cores": cpu_threads(),
                              "kind": "oracle", "sample": "the FP32-form Chebyshev step of the first %d problems "
                                                         "(%.1f s)" % (NCPU, t_cpu)}}
@@ -1025,19 +1025,25 @@ def pipe_roofline(canon_per_s, rates, apply_ffma_per_entry=8):
                      "measured by mf_pipe_rates (register-only chains) in this run"}
 
 
-def batch_roofline(hbm_bytes, gen_entries, flops, t_apply):
+def batch_roofline(hbm_bytes, gen_entries, flops, t_apply, rates=None):
     """Lower bounds of one batched product from its three resources, each at
-    its measured or stated peak: HBM (the measured copy rate), the FP32 FMA
-    pipe (152 x 128 lanes x 2 FLOP x 2070 MHz) and entry generation (the
-    Philox row-owner rate, 1.5e11 entries/s measured in the 64-vector FP32
-    run); achieved fraction = largest bound / measured time."""
+    its measured peak: HBM (the measured copy rate), the FP32 FMA pipe (the
+    FFMA rate of mf_pipe_rates, else 152 x 128 lanes x 2070 MHz) and entry
+    generation (the generated entries at the slowest generator pipe of
+    mf_pipe_rates, else the 1.5e11 entries/s of the Philox row-owner kernel);
+    achieved fraction = largest bound / measured time."""
     t_hbm = hbm_bytes / (measured_peaks()["hbm_gbs"] * 1e9)
-    t_fma = flops / (152 * 128 * 2 * 2.07e9)
-    t_gen = gen_entries / 1.5e11
+    if rates and rates.get("ffma"):
+        t_fma = flops / (2.0 * rates["ffma"])
+        t_gen = gen_entries * pipe_bound(rates, apply_ffma_per_entry=0)["t_bound"]
+    else:
+        t_fma = flops / (152 * 128 * 2 * 2.07e9)
+        t_gen = gen_entries / 1.5e11
     bound = max(t_hbm, t_fma, t_gen)
     name = {t_hbm: "hbm", t_fma: "fma", t_gen: "generation"}[bound]
     return {"t_apply_s": t_apply, "t_hbm_s": t_hbm, "t_fma_s": t_fma, "t_gen_s": t_gen, "bound": name,
-            "frac": bound / t_apply, "sum_of_bounds_frac": (t_hbm + t_fma + t_gen) / t_apply}
+            "frac": bound / t_apply, "sum_of_bounds_frac": (t_hbm + t_fma + t_gen) / t_apply,
+            "rates": "measured in this run" if rates else "unit counts"}
 
 
 def run_batch(args):
