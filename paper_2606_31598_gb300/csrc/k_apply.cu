@@ -1,5 +1,5 @@
 // k_apply.cu -- Hermitian canonical-tile generate-and-apply kernel (SIMT,
-// one vector).
+// one vector, and two vectors in the FP32 form).
 //
 // Sec. III.A ("partial caching") and Eq. blockmatvec: each CTA owns one
 // canonical kTile x kTile tile (ti <= tj).  Every canonical entry h_rc
@@ -34,21 +34,27 @@ template <typename C> __device__ __forceinline__ void cmacc(C& acc, const C& h, 
   acc.y = fma(-h.y, x.x, acc.y);
 }
 
-// Procedural part of the Hermitian tile: thread rows r0 + [0, 8), columns
-// c0 + [0, 8); DIAG selects the diagonal tile (entries below the diagonal
-// skipped, the diagonal applied once), the off-diagonal tiles need no test.
-template <typename T, int GEN, bool DIAG>
-__device__ __forceinline__ void proc_tile(typename cplx<T>::t (&yc)[8], const typename cplx<T>::t (&xcv)[8],
-                                          const typename cplx<T>::t* xs_r, typename cplx<T>::t (*red)[kTile + 1],
-                                          int64_t r0, int64_t c0, int ty, int tx, bool active, uint64_t seed,
-                                          T sigma, const dvr_consts& dk) {
+// Procedural part of the Hermitian tile for NV vectors: thread rows
+// r0 + [0, 8), columns c0 + [0, 8); DIAG selects the diagonal tile (entries
+// below the diagonal skipped, the diagonal applied once), the off-diagonal
+// tiles need no test.  x rows are staged [row][NV]; the row sums of vector v
+// go to red[v][tx][row].
+template <typename T, int GEN, bool DIAG, int NV>
+__device__ __forceinline__ void proc_tile(typename cplx<T>::t (&yc)[8][NV], const typename cplx<T>::t (&xcv)[8][NV],
+                                          const typename cplx<T>::t* xs_r,
+                                          typename cplx<T>::t (*red)[16][kTile + 1], int64_t r0, int64_t c0, int ty,
+                                          int tx, bool active, uint64_t seed, T sigma, const dvr_consts& dk) {
   using C = typename cplx<T>::t;
 #pragma unroll 2
   for (int a = 0; a < 8; ++a) {
-    C yra = czero<T>();
+    C yra[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) yra[v] = czero<T>();
     const int64_t r = r0 + a;
     if (active) {
-      const C xa = xs_r[ty * 8 + a];
+      C xa[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) xa[v] = xs_r[(ty * 8 + a) * NV + v];
 #pragma unroll
       for (int pb = 0; pb < 4; ++pb) {
         const int64_t c = c0 + 2 * pb;
@@ -62,72 +68,68 @@ __device__ __forceinline__ void proc_tile(typename cplx<T>::t (&yc)[8], const ty
           h0.y = T(0);
           h1.y = T(0);
         }
-        if (!DIAG) {
-          cmac(yra, h0, xcv[2 * pb]);
-          cmacc(yc[2 * pb], h0, xa);
-          cmac(yra, h1, xcv[2 * pb + 1]);
-          cmacc(yc[2 * pb + 1], h1, xa);
-          continue;
-        }
-        // entry (r, c)
-        if (r < c) {
-          cmac(yra, h0, xcv[2 * pb]);
-          cmacc(yc[2 * pb], h0, xa);
-        } else if (r == c) {
-          cmac(yra, h0, xcv[2 * pb]);
-        }
-        // entry (r, c+1)
-        if (r < c + 1) {
-          cmac(yra, h1, xcv[2 * pb + 1]);
-          cmacc(yc[2 * pb + 1], h1, xa);
-        } else if (r == c + 1) {
-          cmac(yra, h1, xcv[2 * pb + 1]);
+        // entry (r, c), then entry (r, c + 1): applied as H (row sum) and,
+        // strictly above the diagonal, as H^dagger (column sum)
+        const bool up0 = !DIAG || r < c, on0 = DIAG && r == c;
+        const bool up1 = !DIAG || r < c + 1, on1 = DIAG && r == c + 1;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          if (up0 || on0) cmac(yra[v], h0, xcv[2 * pb][v]);
+          if (up0) cmacc(yc[2 * pb][v], h0, xa[v]);
+          if (up1 || on1) cmac(yra[v], h1, xcv[2 * pb + 1][v]);
+          if (up1) cmacc(yc[2 * pb + 1][v], h1, xa[v]);
         }
       }
     }
-    red[tx][ty * 8 + a] = yra;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) red[v][tx][ty * 8 + a] = yra[v];
   }
 }
 
 // ---------------------------------------------------------------------------
-// (1) Hermitian canonical-tile kernel, one vector.
+// (1) Hermitian canonical-tile kernel, NV = 1 or 2 vectors.
 // Thread (ty, tx) of the 16 x 16 grid owns rows ti*128 + ty*8 + [0,8) and
-// columns tj*128 + tx*8 + [0,8): 32 Philox calls, 64 canonical entries.
+// columns tj*128 + tx*8 + [0,8): 32 Philox calls, 64 canonical entries,
+// each applied to the NV vectors as H and as H^dagger.  part is
+// [slot][dpad][NV] (one slot per tile row).
 // ---------------------------------------------------------------------------
-template <typename T, int GEN>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) herm_tile_nv1(const WorkItem* __restrict__ work, int64_t D,
-                                                     int64_t dpad, uint64_t seed, T sigma, dvr_consts dk,
-                                                     const typename cplx<T>::t* __restrict__ xc,
-                                                     typename cplx<T>::t* __restrict__ part,
-                                                     const typename cplx<T>::t* __restrict__ cache,
-                                                     int64_t bstride,
-                                                     const typename cplx<T>::t* __restrict__ hcache) {
+template <typename T, int GEN, int NV>
+__device__ __forceinline__ void herm_tile_body(const WorkItem* __restrict__ work, int64_t D, int64_t dpad, uint64_t seed,
+                                               T sigma, const dvr_consts& dk, const typename cplx<T>::t* __restrict__ xc,
+                                               typename cplx<T>::t* __restrict__ part,
+                                               const typename cplx<T>::t* __restrict__ cache, int64_t bstride,
+                                               const typename cplx<T>::t* __restrict__ hcache) {
   using C = typename cplx<T>::t;
-  __shared__ C xs_r[kTile], xs_c[kTile];
-  __shared__ C red[16][kTile + 1];
+  __shared__ C xs_r[kTile * NV], xs_c[kTile * NV];
+  __shared__ C red[NV][16][kTile + 1];
 
   const WorkItem it = work[blockIdx.x];
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int64_t rt0 = (int64_t)it.ti * kTile, ct0 = (int64_t)it.tj * kTile;
-  if (tid < kTile) {
-    const int64_t r = rt0 + tid;
-    xs_r[tid] = r < D ? xc[r] : czero<T>();
-  } else {
-    const int64_t c = ct0 + tid - kTile;
-    xs_c[tid - kTile] = c < D ? xc[c] : czero<T>();
+  for (int e = tid; e < 2 * kTile * NV; e += 256) {
+    if (e < kTile * NV) {
+      const int64_t r = rt0 + e / NV;
+      xs_r[e] = r < D ? xc[r * NV + e % NV] : czero<T>();
+    } else {
+      const int f = e - kTile * NV;
+      const int64_t c = ct0 + f / NV;
+      xs_c[f] = c < D ? xc[c * NV + f % NV] : czero<T>();
+    }
   }
   __syncthreads();
 
   // column accumulators and column-side x live in registers (indexed only by
-  // unrolled loop counters); the row accumulator is one value per row a,
+  // unrolled loop counters); the row accumulators are NV values per row a,
   // parked in shared memory when the row is done
-  C yc[8], xcv[8];
+  C yc[8][NV], xcv[8][NV];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    yc[q] = czero<T>();
-    xcv[q] = xs_c[tx * 8 + q];
-  }
+  for (int q = 0; q < 8; ++q)
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      yc[q][v] = czero<T>();
+      xcv[q][v] = xs_c[(tx * 8 + q) * NV + v];
+    }
   const bool diag = it.ti == it.tj;
   const int64_t r0 = rt0 + ty * 8, c0 = ct0 + tx * 8;
   const bool active = !(diag && ty > tx);
@@ -156,65 +158,112 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) herm_tile_nv1(con
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         const int a = a2 + u;
-        C yra = czero<T>();
+        C yra[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) yra[v] = czero<T>();
         if (active) {
-          const C xa = xs_r[ty * 8 + a];
+          C xa[NV];
+#pragma unroll
+          for (int v = 0; v < NV; ++v) xa[v] = xs_r[(ty * 8 + a) * NV + v];
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
             const int dr = (ty * 8 + a) - (tx * 8 + q);
-            if (!diag || dr < 0) {
-              cmac(yra, h[u][q], xcv[q]);
-              cmacc(yc[q], h[u][q], xa);
-            } else if (dr == 0) {
-              cmac(yra, h[u][q], xcv[q]);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+              if (!diag || dr < 0) {
+                cmac(yra[v], h[u][q], xcv[q][v]);
+                cmacc(yc[q][v], h[u][q], xa[v]);
+              } else if (dr == 0) {
+                cmac(yra[v], h[u][q], xcv[q][v]);
+              }
             }
           }
         }
-        red[tx][ty * 8 + a] = yra;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) red[v][tx][ty * 8 + a] = yra[v];
       }
     }
   } else if (diag) {
-    proc_tile<T, GEN, true>(yc, xcv, xs_r, red, r0, c0, ty, tx, active, seed, sigma, dk);
+    proc_tile<T, GEN, true, NV>(yc, xcv, xs_r, red, r0, c0, ty, tx, active, seed, sigma, dk);
   } else {
-    proc_tile<T, GEN, false>(yc, xcv, xs_r, red, r0, c0, ty, tx, active, seed, sigma, dk);
+    proc_tile<T, GEN, false, NV>(yc, xcv, xs_r, red, r0, c0, ty, tx, active, seed, sigma, dk);
   }
 
-  // row sums over the 16 column groups, then column sums over the 16 row groups
+  // row sums over the 16 column groups, then column sums over the 16 row
+  // groups; thread tid < 128 NV sums row tid % 128 of vector tid / 128
+  const int row = tid % kTile, vv = tid / kTile;
+  const bool summer = tid < kTile * NV;
   __syncthreads();
   C rs = czero<T>();
-  if (tid < kTile) {
+  if (summer) {
 #pragma unroll
     for (int g = 0; g < 16; ++g) {
-      rs.x += red[g][tid].x;
-      rs.y += red[g][tid].y;
+      rs.x += red[vv][g][row].x;
+      rs.y += red[vv][g][row].y;
     }
   }
   __syncthreads();
 #pragma unroll
-  for (int a = 0; a < 8; ++a) red[ty][tx * 8 + a] = yc[a];
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int v = 0; v < NV; ++v) red[v][ty][tx * 8 + a] = yc[a][v];
   __syncthreads();
-  if (tid < kTile) {
+  if (summer) {
     C cs = czero<T>();
 #pragma unroll
     for (int g = 0; g < 16; ++g) {
-      cs.x += red[g][tid].x;
-      cs.y += red[g][tid].y;
+      cs.x += red[vv][g][row].x;
+      cs.y += red[vv][g][row].y;
     }
     if (diag) {
       rs.x += cs.x;
       rs.y += cs.y;
-      part[(int64_t)it.ti * dpad + rt0 + tid] = rs;
+      part[((int64_t)it.ti * dpad + rt0 + row) * NV + vv] = rs;
     } else {
-      part[(int64_t)it.tj * dpad + rt0 + tid] = rs;  // rows of tile ti, slot tj
-      part[(int64_t)it.ti * dpad + ct0 + tid] = cs;  // rows of tile tj, slot ti
+      part[((int64_t)it.tj * dpad + rt0 + row) * NV + vv] = rs;  // rows of tile ti, slot tj
+      part[((int64_t)it.ti * dpad + ct0 + row) * NV + vv] = cs;  // rows of tile tj, slot ti
     }
   }
 }
 
+template <typename T, int GEN>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) herm_tile_nv1(const WorkItem* __restrict__ work, int64_t D,
+                                                     int64_t dpad, uint64_t seed, T sigma, dvr_consts dk,
+                                                     const typename cplx<T>::t* __restrict__ xc,
+                                                     typename cplx<T>::t* __restrict__ part,
+                                                     const typename cplx<T>::t* __restrict__ cache,
+                                                     int64_t bstride,
+                                                     const typename cplx<T>::t* __restrict__ hcache) {
+  herm_tile_body<T, GEN, 1>(work, D, dpad, seed, sigma, dk, xc, part, cache, bstride, hcache);
+}
+
+// Two vectors: the column sums and column x of both vectors in registers.
+template <typename T, int GEN>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) herm_tile_nv2(const WorkItem* __restrict__ work, int64_t D,
+                                                     int64_t dpad, uint64_t seed, T sigma, dvr_consts dk,
+                                                     const typename cplx<T>::t* __restrict__ xc,
+                                                     typename cplx<T>::t* __restrict__ part,
+                                                     const typename cplx<T>::t* __restrict__ cache,
+                                                     int64_t bstride,
+                                                     const typename cplx<T>::t* __restrict__ hcache) {
+  herm_tile_body<T, GEN, 2>(work, D, dpad, seed, sigma, dk, xc, part, cache, bstride, hcache);
+}
+
 cudaError_t launch_gue_apply(const Plan& p, const void* xc, void* part, int64_t nvec) {
-  if (nvec != 1) return cudaErrorNotSupported;
   const int64_t dpad = p.dpad;
   const unsigned grid = (unsigned)p.nwork;
+  if (nvec == 2 && p.prec == MF_PREC_FP32) {
+    if (p.gen != MF_GEN_SINC_DVR_HO)
+      herm_tile_nv2<float, MF_GEN_PHILOX_GUE><<<grid, 256, 0, p.stream>>>(
+          p.d_work, p.D, dpad, p.seed, p.sigma32, p.dvr, (const float2*)xc, (float2*)part,
+          (const float2*)p.d_cache, p.b, (const float2*)p.d_hblocks);
+    else
+      herm_tile_nv2<float, MF_GEN_SINC_DVR_HO><<<grid, 256, 0, p.stream>>>(
+          p.d_work, p.D, dpad, p.seed, p.sigma32, p.dvr, (const float2*)xc, (float2*)part,
+          (const float2*)p.d_cache, p.b, (const float2*)p.d_hblocks);
+    return cudaGetLastError();
+  }
+  if (nvec != 1) return cudaErrorNotSupported;
   if (p.prec == MF_PREC_FP64) {
     if (p.gen != MF_GEN_SINC_DVR_HO)
       herm_tile_nv1<double, MF_GEN_PHILOX_GUE><<<grid, 256, 0, p.stream>>>(

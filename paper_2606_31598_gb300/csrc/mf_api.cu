@@ -210,6 +210,14 @@ bool use_rows_herm(const Plan& p, int64_t nb) {
 double tch_slot_bytes(const Plan& p, int64_t nb) { return (double)p.tch_rows * 2.0 * (double)nb * 4.0; }
 bool use_tch(const Plan& p, int64_t) { return p.tch; }
 
+// Two vectors in the FP32 form on the canonical-tile kernel (each generated
+// or stored entry applied to both vectors as H and H^dagger from registers),
+// for plans with the tile work list.
+bool use_tile2(const Plan& p, int64_t nvec) {
+  return nvec == 2 && p.prec == MF_PREC_FP32 && p.d_work && !p.use_dvr_window && !p.sliced && !p.sb_nop &&
+         p.opt.hermitian_reuse != 0;
+}
+
 // The DVR window kernel for 2..16 vectors (FP32 form, procedural plans).
 bool use_dvr_mv(const Plan& p, int64_t nvec) {
   return p.use_dvr_window && p.prec == MF_PREC_FP32 && !p.sb_nop && nvec >= 2 && nvec <= 16;
@@ -228,6 +236,7 @@ VecShape shape_for(const Plan& p, int64_t nvec) {
     const DvrRowsShape s = dvr_mv_shape(p.D, nb, p.num_sms);
     return VecShape{nvec, nb, s.nslot, s.dpad};
   }
+  if (use_tile2(p, nvec)) return VecShape{2, 2, p.nslot, p.dpad};
   const int64_t nb = rows_nvec_bucket(nvec);
   if (use_rows_herm(p, nb)) return VecShape{nvec, nb, p.herm_ns + p.ntile, p.ntile * (int64_t)kTile};
   return VecShape{nvec, nb, p.rows_nsplit, p.ntile * (int64_t)kTile};
@@ -302,7 +311,9 @@ mf_status apply_kernel(Plan& p, int64_t nvec) {
   }
   if (fault_hit("launch")) return MF_ERR_CUDA;
   const int64_t nbr = rows_nvec_bucket(nvec);
-  const bool herm = !p.sliced && (nvec > 1 || p.sb_nop) && p.prec != MF_PREC_BF16X2 && use_rows_herm(p, nbr);
+  const bool tile2 = use_tile2(p, nvec);
+  const bool herm =
+      !tile2 && !p.sliced && (nvec > 1 || p.sb_nop) && p.prec != MF_PREC_BF16X2 && use_rows_herm(p, nbr);
   if (herm) {
     const VecShape sh = shape_for(p, nvec);
     MF_CUDA(cudaMemsetAsync(p.d_part, 0, (size_t)sh.nslot * sh.dpad * sh.nb * compute_elem_bytes(p.prec), p.stream));
@@ -317,6 +328,8 @@ mf_status apply_kernel(Plan& p, int64_t nvec) {
     MF_CUDA(launch_tch_apply(p, p.d_xc, p.d_part, p.d_tcb, tc_nvec_bucket(nvec)));
   else if (p.prec == MF_PREC_BF16X2)
     MF_CUDA(launch_tc_apply(p, p.d_xc, p.d_part, p.d_tcb, tc_nvec_bucket(nvec)));
+  else if (tile2)
+    MF_CUDA(launch_gue_apply(p, p.d_xc, p.d_part, 2));
   else if (nvec > 1 && herm)
     MF_CUDA(launch_rows_herm(p, p.d_xc, 0, p.d_part, nbr, 1, nullptr));
   else if (use_dvr_mv(p, nvec))
