@@ -280,6 +280,27 @@ def test_multivector_cache_modes_bit_identical(mf, prec):
     assert np.array_equal(ys[0], ys[1]) and np.array_equal(ys[0], ys[2])
 
 
+@pytest.mark.parametrize("gen,storage", [(0, 0), (0, 1), (0, 2), (1, 2)])
+def test_two_vectors_on_the_tile_kernel(mf, gen, storage):
+    """Two vectors in the FP32 form run on the canonical-tile kernel with both
+    vectors in registers: every column equals the one-vector product bit for
+    bit (same operations in the same order), generated, partially cached and
+    fully cached (and stored DVR blocks) alike, and matches the oracle; the
+    row-owner kernel agrees within the form's tolerance."""
+    D, b = 1000, 256
+    budget = {0: 0, 1: 4 * b * b * 8, 2: 10 * b * b * 8}[storage]
+    X = W.random_state(D, 2, seed=14).reshape(D, 2)
+    p = _plan(mf, D, gen, 1, seed=6, block=b, budget=budget, storage=storage, nvec_hint=2)
+    assert p.describe()["path"] == "herm_tile"
+    Y = _apply(p, X)
+    for v in range(2):
+        assert np.array_equal(Y[:, v], _apply(p, np.ascontiguousarray(X[:, v])))
+    ref = O.apply(O.make_op(gen, D, seed=6, form=O.FORM_FP32), X)
+    assert _relerr(Y, ref) < 2e-5
+    q = _plan(mf, D, gen, 1, seed=6, block=b, budget=budget, storage=storage, nvec_hint=2, hermitian_reuse=0)
+    assert _relerr(_apply(q, X), Y) < 2e-5
+
+
 def test_multivector_matches_single_vector_columns(mf):
     """Each column of the multi-vector product equals the one-vector product."""
     D, nvec = 700, 5
