@@ -47,7 +47,7 @@ def _apply(plan, X):
 
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("budget_pairs", [0, 3, 100])
-@pytest.mark.parametrize("nvec", [1, 3, 16])
+@pytest.mark.parametrize("nvec", [1, 2, 3, 16])
 def test_external_apply_matches_oracle(mf, prec, budget_pairs, nvec):
     D, b = 1000, 256   # 4 x 4 blocks, ragged last block; 10 stored pairs
     dt = np.complex128 if prec == 0 else np.complex64
