@@ -894,36 +894,38 @@ def run_multivector(args):
 
 
 def run_philox(args):
-    """Seeded generation and cached streaming, one vector: the Philox ensemble
-    at D = 131072 (FP32 form) procedural (every canonical entry generated
-    once per apply, used for H and H^dagger) and fully cached (each canonical
-    entry read once from HBM, 8 bytes); Chebyshev steps of dt = 1."""
+    """Seeded generation and cached streaming: the Philox ensemble at
+    D = 131072 (FP32 form), one vector (or --philox-nvec 2), procedural
+    (every canonical entry generated once per apply, used for H and
+    H^dagger) and fully cached (each canonical entry read once from HBM,
+    8 bytes); Chebyshev steps of dt = 1."""
     import torch
     import paper_2606_31598_gb300 as mf
     import workloads as W
-    D = args.philox_dim
+    D, nv = args.philox_dim, args.philox_nvec
     stream = torch.cuda.current_stream().cuda_stream
-    x = torch.from_numpy(W.random_state(D, 1, seed=3)).cuda()
+    x = torch.from_numpy(W.random_state(D, nv, seed=3)).cuda()
     y = torch.empty_like(x)
     canon = D * (D + 1) / 2.0
-    out = {"workload": "Philox GUE D=%d, 1 vector, FP32 form" % D}
+    out = {"workload": "Philox GUE D=%d, %d vector%s, FP32 form" % (D, nv, "s" if nv > 1 else "")}
     props = torch.cuda.get_device_properties(0)
     rates = mf.mf_pipe_rates(0, stream)
     out["pipe_rates"] = rates
     for name, storage, budget in [("procedural", mf.MF_STORE_PROCEDURAL, 0),
                                   ("full_cache", mf.MF_STORE_FULL, int(canon * 8 * 1.02) + (1 << 30))]:
         plan = mf.Plan(D, mf.MF_GEN_PHILOX_GUE, seed=1, block=2048, cache_budget_bytes=budget,
-                       precision=mf.MF_PREC_FP32, storage=storage, stream=stream)
+                       precision=mf.MF_PREC_FP32, storage=storage, stream=stream, nvec_hint=nv)
         desc = plan.describe()
         clock = ClockSampler(0)
         clock.start()
         plan.profile(True)
-        t = time_applies(plan, x, y, 1, args.steps)
+        t = time_applies(plan, x, y, nv, args.steps)
         kern_ms, kern_n = plan.profile_read()
         clk = clock.stop()
         plan.profile(False)
         per = kern_ms / 1e3 / max(1, kern_n)
-        res = {"apply_s": t, "kernel_s": per, "entries_per_s": D * float(D) / t, "canonical_entries_per_s": canon / per,
+        res = {"apply_s": t, "kernel_s": per, "entries_per_s": D * float(D) * nv / t,
+               "canonical_entries_per_s": canon / per,
                "pairs_cached": desc["pairs_cached"], "clocks": clk}
         if storage == mf.MF_STORE_FULL:
             gbs = canon * 8 / per / 1e9
@@ -931,20 +933,21 @@ def run_philox(args):
             res["roofline"] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
                                "note": "8 B per canonical entry read once per apply; peak of measured copy"}
         else:
-            res["roofline"] = pipe_roofline(canon / per, rates)
+            res["roofline"] = pipe_roofline(canon / per, rates, apply_ffma_per_entry=8 * nv)
             mhz = clk.get("sm_mhz") or 2070.0
             issue = props.multi_processor_count * 128 * mhz * 1e6  # thread instructions / s
-            res["roofline"]["issue_frac"] = canon / per * PHILOX_INSTR_PER_ENTRY / issue
+            if nv == 1:  # the ncu instruction count is the one-vector kernel's
+                res["roofline"]["issue_frac"] = canon / per * PHILOX_INSTR_PER_ENTRY / issue
         if name == "procedural":
             nt = plan.cheb_terms(1.0)
             psi = x.clone()
-            plan.cheb_propagate(psi, 1, 1.0, 0)
+            plan.cheb_propagate(psi, nv, 1.0, 0)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
             e0.record()
             for _ in range(args.steps):
-                plan.cheb_propagate(psi, 1, 1.0, 0)
+                plan.cheb_propagate(psi, nv, 1.0, 0)
             e1.record()
             torch.cuda.synchronize()
             res["cheb_steps_per_s"] = args.steps / (e0.elapsed_time(e1) / 1e3)
@@ -1250,6 +1253,7 @@ def main():
     ap.add_argument("--impl", default="mf", choices=["mf", "reference"])
     ap.add_argument("--batch-n", type=int, default=256, help="batch: number of problems")
     ap.add_argument("--philox-dim", type=int, default=131072, help="philox: D")
+    ap.add_argument("--philox-nvec", type=int, default=1, choices=[1, 2], help="philox: vectors")
     ap.add_argument("--batch-budget-gb", type=float, default=200.0, help="batch: shared cache budget")
     ap.add_argument("--sb-ds", type=int, default=4, help="sysbath: system dimension d_S")
     ap.add_argument("--sb-db", type=int, default=65536, help="sysbath: bath dimension d_B")
