@@ -395,7 +395,12 @@ __device__ __forceinline__ void xchunk_copy_async(typename cplx<T>::t* xs, const
   }
 }
 
-template <typename T, int GEN, int NV, int TR, int TV, int NT>
+// KG k-groups: the threads form KG groups, each contracting its KCH / KG
+// columns of every chunk with a TR x TV register tile (rows tr + i RT/TR, so
+// consecutive lanes read consecutive rows); the groups' partial sums are
+// added in group order at the end of the row tile.  Larger register tiles:
+// fewer shared-memory loads per FMA.
+template <typename T, int GEN, int NV, int TR, int TV, int NT, int KG = 1>
 __device__ __forceinline__ void row_tile_async(unsigned char* smem_raw, int64_t R0, int64_t cbeg, int64_t cend,
                                                uint64_t seed, T sigma, const dvr_consts& dk,
                                                const typename cplx<T>::t* __restrict__ xc,
@@ -403,16 +408,20 @@ __device__ __forceinline__ void row_tile_async(unsigned char* smem_raw, int64_t 
                                                const typename cplx<T>::t* __restrict__ cache,
                                                const int64_t* __restrict__ slot_of_pair, int64_t b, int64_t nblk) {
   using C = typename cplx<T>::t;
-  static_assert((RT / TR) * (NV / TV) == NT, "thread blocking must cover the tile");
+  static_assert((RT / TR) * (NV / TV) * KG == NT, "thread blocking must cover the tile");
+  static_assert(KCH % KG == 0 && (NT / KG) % 32 == 0, "a warp belongs to one k-group");
+  static_assert((size_t)(KG - 1) * RT * NV <= (size_t)2 * RT * (KCH + HPAD), "k-group sums fit the chunk buffers");
   constexpr int LD = KCH + HPAD;
+  constexpr int RS = RT / TR;       // row stride of a thread's rows
+  constexpr int KPG = KCH / KG;     // columns of a chunk per k-group
   C* hs0 = reinterpret_cast<C*>(smem_raw);
   C* hs1 = hs0 + RT * LD;
   C* xs0 = hs1 + RT * LD;                         // [KCH][NV]
   C* xs1 = xs0 + KCH * NV;                        // [KCH][NV]
   T* win = reinterpret_cast<T*>(xs1 + KCH * NV);  // [RT + KCH]
   const int tid = threadIdx.x;
-  const int tv = tid % (NV / TV), tr = tid / (NV / TV);
-  const int r0 = tr * TR;
+  const int kg = tid / (NT / KG), lt = tid % (NT / KG);
+  const int tv = lt % (NV / TV), tr = lt / (NV / TV);
   C acc[TR][TV];
 #pragma unroll
   for (int i = 0; i < TR; ++i)
@@ -455,11 +464,11 @@ __device__ __forceinline__ void row_tile_async(unsigned char* smem_raw, int64_t 
         cp_async_commit();
     }
 #pragma unroll 4
-    for (int kk = 0; kk < KCH; ++kk) {
+    for (int kk = kg * KPG; kk < kg * KPG + KPG; ++kk) {
       C h[TR], x[TV];
 #pragma unroll
       for (int i = 0; i < TR; ++i) {
-        h[i] = cur[(r0 + i) * LD + kk];
+        h[i] = cur[(tr + i * RS) * LD + kk];
         if (cj) h[i].y = -h[i].y;
       }
 #pragma unroll
@@ -475,10 +484,33 @@ __device__ __forceinline__ void row_tile_async(unsigned char* smem_raw, int64_t 
     cp_async_wait_all();
     __syncthreads();
   }
+  if constexpr (KG > 1) {
+    // the chunk buffers are free after the last barrier: groups 1.. leave
+    // their sums there, group 0 adds them in group order
+    C* red = hs0;  // [KG - 1][RT][NV]
+    if (kg > 0) {
+#pragma unroll
+      for (int i = 0; i < TR; ++i)
+#pragma unroll
+        for (int j = 0; j < TV; ++j) red[((kg - 1) * RT + tr + i * RS) * NV + tv + j * (NV / TV)] = acc[i][j];
+    }
+    __syncthreads();
+    if (kg > 0) return;
+#pragma unroll
+    for (int g = 1; g < KG; ++g)
+#pragma unroll
+      for (int i = 0; i < TR; ++i)
+#pragma unroll
+        for (int j = 0; j < TV; ++j) {
+          const C v = red[((g - 1) * RT + tr + i * RS) * NV + tv + j * (NV / TV)];
+          acc[i][j].x += v.x;
+          acc[i][j].y += v.y;
+        }
+  }
 #pragma unroll
   for (int i = 0; i < TR; ++i)
 #pragma unroll
-    for (int j = 0; j < TV; ++j) out[(r0 + i) * NV + tv + j * (NV / TV)] = acc[i][j];
+    for (int j = 0; j < TV; ++j) out[(tr + i * RS) * NV + tv + j * (NV / TV)] = acc[i][j];
 }
 
 template <typename T, int NV>
