@@ -464,7 +464,10 @@ mf_status mf_batch_offsets(mf_batch_t b, int64_t* offsets);
  * per-problem term count is used for all); *nterms_out (may be NULL)
  * receives the term count.  Asynchronous. */
 mf_status mf_batch_propagate(mf_batch_t b, void* psi, double dt, int32_t nsteps, int32_t order, int32_t* nterms_out);
-/* The plan of problem i (owned by the batch) and launch facts. */
+/* The plan of problem i (owned by the batch) and launch facts: the
+ * (problem, row tile) work items and the largest persistent grid of the
+ * per-vector-bucket kernels (one persistent kernel per bucket of
+ * max(2, nvec) in {2, 4, 6, 8, 12, 16}, launched side by side each term). */
 mf_status mf_batch_plan(mf_batch_t b, int32_t i, mf_plan_t* plan);
 mf_status mf_batch_info(mf_batch_t b, int32_t* n_items, int32_t* persist_grid);
 

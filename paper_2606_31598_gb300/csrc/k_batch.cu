@@ -43,10 +43,41 @@ struct BatchItem {
 
 namespace {
 
-template <typename T, int GEN>
+// The vector buckets of the batched kernel (rows_nvec_bucket of max(2, nvec)).
+constexpr int kBuckets = 6;
+constexpr int kBucketNV[kBuckets] = {2, 4, 6, 8, 12, 16};
+
+// One row tile of a problem of bucket NB.  Register tiles (rows x vectors)
+// and k-groups per bucket: the FP32 form takes 2 x 2 to 4 x 6 complex tiles
+// in packed FP32 pairs over 2 to 8 k-groups (chosen by timing each bucket
+// over a full cache); the FP64 form keeps one k-group (its registers are the
+// limit).
+template <typename T, int GEN, int NB>
+__device__ __forceinline__ void batch_tile(unsigned char* smem_raw, const BatchProb& P, int64_t R0) {
+  using C = typename cplx<T>::t;
+  const C* xc = (const C*)P.xc;
+  const C* cache = (const C*)P.cache;
+  C* out = (C*)P.part + R0 * P.nb;
+  if constexpr (sizeof(T) == 4) {
+    constexpr int TR = NB == 2 ? 2 : NB == 4 ? 4 : NB == 6 ? 2 : NB == 8 ? 4 : NB == 12 ? 2 : 4;
+    constexpr int TV = NB == 2 ? 2 : NB == 4 ? 4 : NB == 6 ? 6 : NB == 8 ? 4 : NB == 12 ? 6 : 4;
+    constexpr int KG = NB == 2 ? 4 : NB == 4 ? 8 : NB == 6 ? 4 : NB == 8 ? 4 : 2;
+    row_tile_async_f32<GEN, NB, TR, TV, 256, KG>(smem_raw, R0, 0, P.D, P.seed, P.sigma32, P.dk, (const float2*)xc,
+                                                 (float2*)out, (const float2*)cache, P.slot, P.b, P.nblk);
+  } else {
+    constexpr int TR = NB <= 6 ? 1 : 2;
+    constexpr int TV = NB == 2 ? 1 : NB == 4 ? 2 : NB == 6 ? 3 : NB == 8 ? 2 : NB == 12 ? 3 : 4;
+    row_tile_async<T, GEN, NB, TR, TV, 256>(smem_raw, R0, 0, P.D, P.seed, (T)P.sigma64, P.dk, xc, out, cache, P.slot,
+                                            P.b, P.nblk);
+  }
+}
+
+// Persistent kernel of one bucket: drains its (problem, row tile) items,
+// most expensive first, through an atomic counter.  One kernel per bucket
+// (launched side by side) keeps each bucket's register allocation its own.
+template <typename T, int GEN, int NB>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_batch_apply(const BatchItem* __restrict__ items, int n_items,
                                                      const BatchProb* __restrict__ probs, int* __restrict__ counter) {
-  using C = typename cplx<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_item;
   for (;;) {
@@ -56,46 +87,52 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_batch_apply(con
     __syncthreads();
     if (it >= n_items) break;
     const BatchItem w = items[it];
-    const BatchProb& P = probs[w.prob];
-    const int64_t R0 = (int64_t)w.tile * rows::RT;
-    const T sigma = sizeof(T) == 4 ? (T)P.sigma32 : (T)P.sigma64;
-    const C* xc = (const C*)P.xc;
-    const C* cache = (const C*)P.cache;
-    // register tiles (rows x vectors) and k-groups per vector bucket: the
-    // FP32 form runs 2 CTAs per SM with up to 128 registers and takes 4 x 2
-    // to 4 x 4 complex tiles split over 2 to 8 k-groups (fewer shared-memory
-    // loads per FMA: 92.7 -> 82.4 ms per product of the 256-problem batch
-    // against 1 x 1 to 2 x 4 tiles at 3 CTAs per SM); the FP64 form keeps one
-    // k-group (its registers are the limit)
-    constexpr bool F = sizeof(T) == 4;
-    C* out = (C*)P.part + R0 * P.nb;
-    switch (P.nb) {
-      case 2:
-        if constexpr (F) row_tile_async<T, GEN, 2, 4, 2, 256, 8>(smem_raw, R0, 0, P.D, P.seed, sigma, P.dk, xc, out, cache, P.slot, P.b, P.nblk);
-        else row_tile_async<T, GEN, 2, 1, 1, 256>(smem_raw, R0, 0, P.D, P.seed, sigma, P.dk, xc, out, cache, P.slot, P.b, P.nblk);
-        break;
-      case 4:
-        if constexpr (F) row_tile_async<T, GEN, 4, 2, 4, 256, 4>(smem_raw, R0, 0, P.D, P.seed, sigma, P.dk, xc, out, cache, P.slot, P.b, P.nblk);
-        else row_tile_async<T, GEN, 4, 1, 2, 256>(smem_raw, R0, 0, P.D, P.seed, sigma, P.dk, xc, out, cache, P.slot, P.b, P.nblk);
-        break;
-      case 6:
-        if constexpr (F) row_tile_async<T, GEN, 6, 4, 3, 256, 4>(smem_raw, R0, 0, P.D, P.seed, sigma, P.dk, xc, out, cache, P.slot, P.b, P.nblk);
-        else row_tile_async<T, GEN, 6, 1, 3, 256>(smem_raw, R0, 0, P.D, P.seed, sigma, P.dk, xc, out, cache, P.slot, P.b, P.nblk);
-        break;
-      case 8:
-        if constexpr (F) row_tile_async<T, GEN, 8, 4, 4, 256, 4>(smem_raw, R0, 0, P.D, P.seed, sigma, P.dk, xc, out, cache, P.slot, P.b, P.nblk);
-        else row_tile_async<T, GEN, 8, 2, 2, 256>(smem_raw, R0, 0, P.D, P.seed, sigma, P.dk, xc, out, cache, P.slot, P.b, P.nblk);
-        break;
-      case 12:
-        if constexpr (F) row_tile_async<T, GEN, 12, 4, 3, 256, 2>(smem_raw, R0, 0, P.D, P.seed, sigma, P.dk, xc, out, cache, P.slot, P.b, P.nblk);
-        else row_tile_async<T, GEN, 12, 2, 3, 256>(smem_raw, R0, 0, P.D, P.seed, sigma, P.dk, xc, out, cache, P.slot, P.b, P.nblk);
-        break;
-      default:
-        if constexpr (F) row_tile_async<T, GEN, 16, 4, 4, 256, 2>(smem_raw, R0, 0, P.D, P.seed, sigma, P.dk, xc, out, cache, P.slot, P.b, P.nblk);
-        else row_tile_async<T, GEN, 16, 2, 4, 256>(smem_raw, R0, 0, P.D, P.seed, sigma, P.dk, xc, out, cache, P.slot, P.b, P.nblk);
-        break;
+    batch_tile<T, GEN, NB>(smem_raw, probs[w.prob], (int64_t)w.tile * rows::RT);
+  }
+}
+
+template <typename T, int GEN>
+using BatchKernel = void (*)(const BatchItem*, int, const BatchProb*, int*);
+
+template <typename T, int GEN>
+BatchKernel<T, GEN> batch_kernel(int k) {
+  switch (k) {
+    case 0: return k_batch_apply<T, GEN, 2>;
+    case 1: return k_batch_apply<T, GEN, 4>;
+    case 2: return k_batch_apply<T, GEN, 6>;
+    case 3: return k_batch_apply<T, GEN, 8>;
+    case 4: return k_batch_apply<T, GEN, 12>;
+    default: return k_batch_apply<T, GEN, 16>;
+  }
+}
+
+template <typename T>
+size_t batch_smem(int k) {
+  if constexpr (sizeof(T) == 4) {
+    switch (k) {
+      case 0: return rows_smem_bytes_f32<2>();
+      case 1: return rows_smem_bytes_f32<4>();
+      case 2: return rows_smem_bytes_f32<6>();
+      case 3: return rows_smem_bytes_f32<8>();
+      case 4: return rows_smem_bytes_f32<12>();
+      default: return rows_smem_bytes_f32<16>();
+    }
+  } else {
+    switch (k) {
+      case 0: return rows_smem_bytes_async<double, 2>();
+      case 1: return rows_smem_bytes_async<double, 4>();
+      case 2: return rows_smem_bytes_async<double, 6>();
+      case 3: return rows_smem_bytes_async<double, 8>();
+      case 4: return rows_smem_bytes_async<double, 12>();
+      default: return rows_smem_bytes_async<double, 16>();
     }
   }
+}
+
+int bucket_index(int64_t nb) {
+  for (int k = 0; k < kBuckets; ++k)
+    if (kBucketNV[k] == nb) return k;
+  return kBuckets - 1;
 }
 
 // q_cur = psi, acc = J0 psi, xc = compute copy (padding zero); grid.y = problem
@@ -188,13 +225,20 @@ struct mf_batch {
   std::vector<int64_t> offsets;  // element offsets of each problem in the packed vector
   int32_t gen = 0, prec = MF_PREC_FP32;
   int num_sms = 0, persist_grid = 0;
-  size_t smem = 0;
   cudaStream_t user = nullptr, own = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   BatchProb* d_probs = nullptr;
   BatchItem* d_items = nullptr;
   int n_items = 0;
-  int* d_counter = nullptr;
+  int* d_counter = nullptr;  // one per bucket
+  // per bucket: its items d_items[begin[k] .. begin[k + 1]), dynamic shared
+  // memory, persistent grid, and a side stream (the buckets' kernels run side
+  // by side: fork from own, join back)
+  int begin[kBuckets + 1] = {};
+  size_t smem[kBuckets] = {};
+  int grid[kBuckets] = {};
+  cudaStream_t side[kBuckets] = {};
+  cudaEvent_t ev_fork = nullptr, ev_join[kBuckets] = {};
   int64_t max_elems = 0;
   // captured propagation and the arguments it was captured for
   cudaGraphExec_t graph = nullptr;
@@ -214,6 +258,11 @@ void batch_release(mf_batch* b) {
   if (b->d_counter) cudaFree(b->d_counter);
   if (b->ev_in) cudaEventDestroy(b->ev_in);
   if (b->ev_out) cudaEventDestroy(b->ev_out);
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  for (int k = 0; k < kBuckets; ++k) {
+    if (b->ev_join[k]) cudaEventDestroy(b->ev_join[k]);
+    if (b->side[k]) cudaStreamDestroy(b->side[k]);
+  }
   if (b->own) cudaStreamDestroy(b->own);
   delete b;
 }
@@ -222,15 +271,21 @@ unsigned grid_x(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int6
 
 template <typename T>
 cudaError_t launch_batch_apply(mf_batch* b, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), s);
-  if (e != cudaSuccess) return e;
-  if (b->gen == MF_GEN_PHILOX_GUE)
-    k_batch_apply<T, MF_GEN_PHILOX_GUE><<<b->persist_grid, 256, b->smem, s>>>(b->d_items, b->n_items, b->d_probs,
-                                                                              b->d_counter);
-  else
-    k_batch_apply<T, MF_GEN_SINC_DVR_HO><<<b->persist_grid, 256, b->smem, s>>>(b->d_items, b->n_items, b->d_probs,
-                                                                               b->d_counter);
-  return cudaGetLastError();
+  cudaError_t e = cudaMemsetAsync(b->d_counter, 0, kBuckets * sizeof(int), s);
+  if (e == cudaSuccess) e = cudaEventRecord(b->ev_fork, s);
+  for (int k = 0; k < kBuckets && e == cudaSuccess; ++k) {
+    const int n = b->begin[k + 1] - b->begin[k];
+    if (n == 0) continue;
+    e = cudaStreamWaitEvent(b->side[k], b->ev_fork, 0);
+    if (e != cudaSuccess) break;
+    auto kern = b->gen == MF_GEN_PHILOX_GUE ? batch_kernel<T, MF_GEN_PHILOX_GUE>(k)
+                                            : batch_kernel<T, MF_GEN_SINC_DVR_HO>(k);
+    kern<<<b->grid[k], 256, b->smem[k], b->side[k]>>>(b->d_items + b->begin[k], n, b->d_probs, b->d_counter + k);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev_join[k], b->side[k]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->ev_join[k], 0);
+  }
+  return e;
 }
 
 // Enqueue nsteps Chebyshev steps of nterms terms on stream s.
@@ -278,10 +333,17 @@ mf_status mf_batch_create(mf_batch_t* out, int32_t nprob, const int64_t* D, cons
         cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, o.device) != cudaSuccess ||
         cudaStreamCreateWithFlags(&b->own, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess) {
       batch_release(b);
       return MF_ERR_CUDA;
     }
+    for (int k = 0; k < kBuckets; ++k)
+      if (cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&b->ev_join[k], cudaEventDisableTiming) != cudaSuccess) {
+        batch_release(b);
+        return MF_ERR_CUDA;
+      }
     // cache budget shared in proportion to each problem's full canonical cache
     const double eb = o.precision == MF_PREC_FP64 ? 16.0 : 8.0;
     double total_full = 0.0;
@@ -309,48 +371,56 @@ mf_status mf_batch_create(mf_batch_t* out, int32_t nprob, const int64_t* D, cons
       b->offsets.push_back(b->offsets.back() + D[i] * nvec[i]);
       b->max_elems = std::max<int64_t>(b->max_elems, D[i] * rows_nvec_bucket(std::max<int32_t>(2, nvec[i])));
     }
-    // work list: every (problem, row tile), most expensive first
+    // work lists: every (problem, row tile), by vector bucket, each bucket's
+    // most expensive first
     std::vector<BatchItem> items;
     std::vector<double> cost;
+    std::vector<int> bucket;
     for (int32_t i = 0; i < nprob; ++i) {
       const Plan& P = b->plans[i]->p;
+      const int64_t nb = rows_nvec_bucket(std::max<int32_t>(2, nvec[i]));
       for (int64_t t = 0; t < P.ntile; ++t) {
         items.push_back(BatchItem{i, (int32_t)t});
-        cost.push_back((double)P.D * (double)rows_nvec_bucket(std::max<int32_t>(2, nvec[i])));
+        cost.push_back((double)P.D * (double)nb);
+        bucket.push_back(bucket_index(nb));
       }
     }
     std::vector<size_t> idx(items.size());
     for (size_t k = 0; k < idx.size(); ++k) idx[k] = k;
-    std::stable_sort(idx.begin(), idx.end(), [&](size_t a, size_t c) { return cost[a] > cost[c]; });
+    std::stable_sort(idx.begin(), idx.end(), [&](size_t a, size_t c) {
+      return bucket[a] != bucket[c] ? bucket[a] < bucket[c] : cost[a] > cost[c];
+    });
     std::vector<BatchItem> sorted;
     for (size_t k : idx) sorted.push_back(items[k]);
+    for (int k = 0; k <= kBuckets; ++k) b->begin[k] = 0;
+    for (int bk : bucket) ++b->begin[bk + 1];
+    for (int k = 0; k < kBuckets; ++k) b->begin[k + 1] += b->begin[k];
     b->n_items = (int)sorted.size();
-    b->smem = o.precision == MF_PREC_FP64 ? rows_smem_bytes_async<double, 16>() : rows_smem_bytes_async<float, 16>();
     cudaError_t e = dev_malloc((void**)&b->d_items, sorted.size() * sizeof(BatchItem));
     if (e == cudaSuccess)
       e = cudaMemcpy(b->d_items, sorted.data(), sorted.size() * sizeof(BatchItem), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = dev_malloc((void**)&b->d_counter, sizeof(int));
+    if (e == cudaSuccess) e = dev_malloc((void**)&b->d_counter, kBuckets * sizeof(int));
     if (e == cudaSuccess) e = dev_malloc((void**)&b->d_probs, (size_t)nprob * sizeof(BatchProb));
-    // persistent grid: resident CTAs per SM x SMs
-    int per_sm = 0;
-    if (e == cudaSuccess) {
-      if (o.precision == MF_PREC_FP64) {
-        auto k = generator == MF_GEN_PHILOX_GUE ? k_batch_apply<double, MF_GEN_PHILOX_GUE>
-                                                : k_batch_apply<double, MF_GEN_SINC_DVR_HO>;
-        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, b->smem);
-      } else {
-        auto k = generator == MF_GEN_PHILOX_GUE ? k_batch_apply<float, MF_GEN_PHILOX_GUE>
-                                                : k_batch_apply<float, MF_GEN_SINC_DVR_HO>;
-        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, b->smem);
-      }
+    // persistent grid per bucket: resident CTAs per SM x SMs, at most its items
+    for (int k = 0; k < kBuckets && e == cudaSuccess; ++k) {
+      const bool f64 = o.precision == MF_PREC_FP64;
+      b->smem[k] = f64 ? batch_smem<double>(k) : batch_smem<float>(k);
+      const void* kern =
+          f64 ? (generator == MF_GEN_PHILOX_GUE ? (const void*)batch_kernel<double, MF_GEN_PHILOX_GUE>(k)
+                                                : (const void*)batch_kernel<double, MF_GEN_SINC_DVR_HO>(k))
+              : (generator == MF_GEN_PHILOX_GUE ? (const void*)batch_kernel<float, MF_GEN_PHILOX_GUE>(k)
+                                                : (const void*)batch_kernel<float, MF_GEN_SINC_DVR_HO>(k));
+      int per_sm = 0;
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem[k]);
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, b->smem[k]);
+      const int n = b->begin[k + 1] - b->begin[k];
+      b->grid[k] = std::max(1, std::min(std::max(1, per_sm) * b->num_sms, n));
+      b->persist_grid = std::max(b->persist_grid, b->grid[k]);
     }
     if (e != cudaSuccess) {
       batch_release(b);
       return e == cudaErrorMemoryAllocation ? MF_ERR_OOM : MF_ERR_CUDA;
     }
-    b->persist_grid = std::max(1, per_sm) * b->num_sms;
     *out = b;
     return MF_OK;
   });

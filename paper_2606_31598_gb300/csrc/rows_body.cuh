@@ -89,24 +89,23 @@ __device__ __forceinline__ void chunk_store(typename cplx<T>::t* hs, const typen
   }
 }
 
-// Generate H[R0 : R0+RT, c0 : c0+KCH] into hs[RT][KCH+HPAD]: canonical
-// entries from the Philox ensemble (conjugates below the diagonal) or DVR
-// entries from a window table.
-template <typename T, int GEN, int NT>
+// Generate H[R0 : R0+RT, c0 : c0+W] into hs[RT][LD] (W = KCH and LD =
+// KCH+HPAD unless given): canonical entries from the Philox ensemble
+// (conjugates below the diagonal) or DVR entries from a window table.
+template <typename T, int GEN, int NT, int LD = KCH + HPAD, int W = KCH>
 __device__ __forceinline__ void fill_chunk_gen(typename cplx<T>::t* hs, T* win, int64_t R0, int64_t c0,
                                                uint64_t seed, T sigma, const dvr_consts& dk) {
   using C = typename cplx<T>::t;
   const int tid = threadIdx.x;
-  constexpr int LD = KCH + HPAD;
   if (GEN == MF_GEN_SINC_DVR_HO) {
-    // window table: T(k) for k = r - c in (R0 - c0 - KCH, R0 - c0 + RT)
-    const long long kmin = (long long)(R0 - c0) - (KCH - 1);
-    for (int j = tid; j < RT + KCH - 1; j += NT) win[j] = dvr_T(dk, kmin + j, T());
+    // window table: T(k) for k = r - c in (R0 - c0 - W, R0 - c0 + RT)
+    const long long kmin = (long long)(R0 - c0) - (W - 1);
+    for (int j = tid; j < RT + W - 1; j += NT) win[j] = dvr_T(dk, kmin + j, T());
     __syncthreads();
-    for (int e = tid; e < RT * KCH; e += NT) {
-      const int r = e / KCH, c = e % KCH;
+    for (int e = tid; e < RT * W; e += NT) {
+      const int r = e / W, c = e % W;
       C h;
-      h.x = win[r - c + KCH - 1];
+      h.x = win[r - c + W - 1];
       h.y = T(0);
       hs[r * LD + c] = h;
     }
@@ -114,17 +113,17 @@ __device__ __forceinline__ void fill_chunk_gen(typename cplx<T>::t* hs, T* win, 
   }
   if (c0 >= R0 + RT) {
     // strictly above the diagonal: canonical pairs along rows
-    for (int e = tid; e < RT * (KCH / 2); e += NT) {
-      const int r = e / (KCH / 2), pc = e % (KCH / 2);
+    for (int e = tid; e < RT * (W / 2); e += NT) {
+      const int r = e / (W / 2), pc = e % (W / 2);
       C h0, h1;
       gue_pair<T>(seed, sigma, (uint32_t)(R0 + r), (uint32_t)((c0 >> 1) + pc), h0, h1);
       hs[r * LD + 2 * pc] = h0;
       hs[r * LD + 2 * pc + 1] = h1;
     }
-  } else if (c0 + KCH <= R0) {
+  } else if (c0 + W <= R0) {
     // strictly below: H[r][c] = conj(H[c][r]); canonical row c holds the
     // pair of columns (rows here) r = 2p, 2p + 1
-    for (int e = tid; e < KCH * (RT / 2); e += NT) {
+    for (int e = tid; e < W * (RT / 2); e += NT) {
       const int c = e / (RT / 2), pr = e % (RT / 2);
       C h0, h1;
       gue_pair<T>(seed, sigma, (uint32_t)(c0 + c), (uint32_t)((R0 >> 1) + pr), h0, h1);
@@ -134,8 +133,8 @@ __device__ __forceinline__ void fill_chunk_gen(typename cplx<T>::t* hs, T* win, 
       hs[(2 * pr + 1) * LD + c] = h1;
     }
   } else {
-    for (int e = tid; e < RT * KCH; e += NT) {
-      const int r = e / KCH, c = e % KCH;
+    for (int e = tid; e < RT * W; e += NT) {
+      const int r = e / W, c = e % W;
       hs[r * LD + c] = gue_entry<T>(seed, sigma, R0 + r, c0 + c);
     }
   }
@@ -342,24 +341,35 @@ __device__ __forceinline__ void cp_async_elem(void* dst, const void* src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-template <typename T, int NT>
+template <typename T, int NT, int LD = KCH + HPAD, int W = KCH>
 __device__ __forceinline__ void chunk_copy_async(typename cplx<T>::t* hb, int64_t slot, bool transposed, int64_t R0,
                                                  int64_t c0, const typename cplx<T>::t* __restrict__ cache,
                                                  const typename cplx<T>::t* __restrict__ hcache, int64_t b) {
   using C = typename cplx<T>::t;
-  constexpr int LD = KCH + HPAD;
   const int tid = threadIdx.x;
   const int64_t n = blk_of(R0, b), m = blk_of(c0, b);
   const C* blk = slot >= 0 ? cache + slot * b * b : hcache + (-2 - slot) * b * b;
-  static_assert(NT % KCH == 0 && NT % RT == 0, "element strides must be whole rows");
-  if (!transposed) {
-    // element e = tid + i NT: row e / KCH advances by NT / KCH, column fixed
-    const int r = tid / KCH, c = tid % KCH;
+  static_assert(NT % W == 0 && NT % RT == 0, "element strides must be whole rows");
+  constexpr int EPP = 16 / (int)sizeof(C);  // elements per 16-byte piece
+  if (!transposed && EPP == 2 && LD % 2 == 0) {
+    // 16-byte pieces: staged rows start on 16-byte boundaries (LD even) and
+    // so do the stored ones (even columns of a block whose side is a
+    // multiple of 128); piece p = tid + i NT: row p / (W / 2)
+    constexpr int PPR = W / 2;
+    const int r = tid / PPR, c = 2 * (tid % PPR);
     const C* src = blk + (R0 + r - n * b) * b + (c0 + c - m * b);
     C* dst = hb + r * LD + c;
-    const int64_t sstep = (int64_t)(NT / KCH) * b;
+    const int64_t sstep = (int64_t)(NT / PPR) * b;
 #pragma unroll 4
-    for (int i = 0; i < RT * KCH / NT; ++i) cp_async_elem<(int)sizeof(C)>(dst + i * (NT / KCH) * LD, src + i * sstep);
+    for (int i = 0; i < RT * PPR / NT; ++i) cp_async_elem<16>(dst + i * (NT / PPR) * LD, src + i * sstep);
+  } else if (!transposed) {
+    // element e = tid + i NT: row e / W advances by NT / W, column fixed
+    const int r = tid / W, c = tid % W;
+    const C* src = blk + (R0 + r - n * b) * b + (c0 + c - m * b);
+    C* dst = hb + r * LD + c;
+    const int64_t sstep = (int64_t)(NT / W) * b;
+#pragma unroll 4
+    for (int i = 0; i < RT * W / NT; ++i) cp_async_elem<(int)sizeof(C)>(dst + i * (NT / W) * LD, src + i * sstep);
   } else {
     // element e = tid + i NT: row e % RT fixed, column e / RT advances by NT / RT
     const int r = tid % RT, c = tid / RT;
@@ -367,21 +377,21 @@ __device__ __forceinline__ void chunk_copy_async(typename cplx<T>::t* hb, int64_
     C* dst = hb + r * LD + c;
     const int64_t sstep = (int64_t)(NT / RT) * b;
 #pragma unroll 4
-    for (int i = 0; i < RT * KCH / NT; ++i) cp_async_elem<(int)sizeof(C)>(dst + i * (NT / RT), src + i * sstep);
+    for (int i = 0; i < RT * W / NT; ++i) cp_async_elem<(int)sizeof(C)>(dst + i * (NT / RT), src + i * sstep);
   }
   cp_async_commit();
 }
 
-// Rows c0 .. c0+KCH-1 of X (NV vectors each, contiguous and 16-byte aligned
-// since c0 is a multiple of KCH and NV is even) into xs[KCH][NV] in 16-byte
+// Rows c0 .. c0+W-1 of X (NV vectors each, contiguous and 16-byte aligned
+// since c0 is a multiple of W and NV is even) into xs[W][NV] in 16-byte
 // pieces; rows at or past cend are zero-filled by plain stores.
-template <typename T, int NV, int NT>
+template <typename T, int NV, int NT, int W = KCH>
 __device__ __forceinline__ void xchunk_copy_async(typename cplx<T>::t* xs, const typename cplx<T>::t* __restrict__ xc,
                                                   int64_t c0, int64_t cend) {
   using C = typename cplx<T>::t;
   static_assert(NV % 2 == 0, "a 16-byte piece must not straddle two rows");
   constexpr int EPP = 16 / (int)sizeof(C);  // elements per piece
-  constexpr int NP = KCH * NV / EPP;
+  constexpr int NP = W * NV / EPP;
   const C* src = xc + c0 * NV;
   for (int pc = threadIdx.x; pc < NP; pc += NT) {
     const int e = pc * EPP;
@@ -511,6 +521,187 @@ __device__ __forceinline__ void row_tile_async(unsigned char* smem_raw, int64_t 
   for (int i = 0; i < TR; ++i)
 #pragma unroll
     for (int j = 0; j < TV; ++j) out[(tr + i * RS) * NV + tv + j * (NV / TV)] = acc[i][j];
+}
+
+// ---------------------------------------------------------------------------
+// FP32 form of row_tile_async: a ring of S stages of W-column chunks, so
+// that S - 1 chunks (stored entries and rows of X) are in flight while one
+// is contracted -- two 32-column buffers kept too few bytes in flight per SM
+// to overlap the stream of stored entries with the contraction.  The staged
+// rows have an even pitch (W + 2 complex, 16-byte aligned): a thread reads the
+// entries of two consecutive columns in one 16-byte load and its TV
+// contiguous vectors (tv TV .. tv TV + TV - 1) in 16-byte pieces; stored
+// chunks that are not transposed are copied in 16-byte pieces.  The product
+// is taken in packed FP32 pairs: A += (h_r, h_r) x and B += (h_i, h_i) x over
+// the row tile, Y = A + i B at its end (the conjugate of a transposed chunk
+// negates h_i, a compile-time branch of the contraction).
+// ---------------------------------------------------------------------------
+constexpr int F32_W = 32;  // columns per staged chunk
+constexpr int F32_S = 2;   // stages of the ring
+
+template <int W>
+__host__ __device__ constexpr int f32_ld() { return W + 2; }
+
+// A[i][j] += h_i x_j (real parts of h, or all of h for the real DVR entries)
+// and B[i][j] += h_i^im x_j over the column pairs kk0 .. kk0 + KPG - 1 of the
+// staged chunk (h_i^im negated when CJ).
+template <int GEN, int NV, int TR, int TV, int KPG, int LD, bool CJ>
+__device__ __forceinline__ void contract_f32(float2 (&A)[TR][TV], float2 (&B)[TR][TV], const float2* __restrict__ hrow,
+                                             const float2* __restrict__ xcol, int kk0) {
+  constexpr int RS = RT / TR;
+#pragma unroll (KPG <= 4 ? 2 : 1)
+  for (int kk = kk0; kk < kk0 + KPG; kk += 2) {
+    float4 h[TR];
+#pragma unroll
+    for (int i = 0; i < TR; ++i) h[i] = *reinterpret_cast<const float4*>(hrow + i * RS * LD + kk);
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      float4 x[TV / 2];
+#pragma unroll
+      for (int m = 0; m < TV / 2; ++m) x[m] = *reinterpret_cast<const float4*>(xcol + (kk + q) * NV + 2 * m);
+#pragma unroll
+      for (int i = 0; i < TR; ++i) {
+        const float hr = q ? h[i].z : h[i].x, hi = q ? h[i].w : h[i].y;
+        const float2 hrr = make_float2(hr, hr);
+        const float2 hii = CJ ? make_float2(-hi, -hi) : make_float2(hi, hi);
+#pragma unroll
+        for (int m = 0; m < TV / 2; ++m) {
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const float2 xv = u ? make_float2(x[m].z, x[m].w) : make_float2(x[m].x, x[m].y);
+            A[i][2 * m + u] = __ffma2_rn(hrr, xv, A[i][2 * m + u]);
+            if constexpr (GEN != MF_GEN_SINC_DVR_HO) B[i][2 * m + u] = __ffma2_rn(hii, xv, B[i][2 * m + u]);
+          }
+        }
+      }
+    }
+  }
+}
+
+// The generation of a chunk out of line: it is the rare path of the ring
+// (stored chunks are the common one), and inlined it would hold registers
+// across the whole contraction.
+template <int GEN, int NT, int LD, int W>
+__device__ __noinline__ void fill_chunk_gen_f32(float2* hs, float* win, int64_t R0, int64_t c0, uint64_t seed,
+                                                float sigma, dvr_consts dk) {
+  fill_chunk_gen<float, GEN, NT, LD, W>(hs, win, R0, c0, seed, sigma, dk);
+}
+
+template <int GEN, int NV, int TR, int TV, int NT, int KG = 1, int W = F32_W, int S = F32_S>
+__device__ __forceinline__ void row_tile_async_f32(unsigned char* smem_raw, int64_t R0, int64_t cbeg, int64_t cend,
+                                                   uint64_t seed, float sigma, const dvr_consts& dk,
+                                                   const float2* __restrict__ xc, float2* __restrict__ out,
+                                                   const float2* __restrict__ cache,
+                                                   const int64_t* __restrict__ slot_of_pair, int64_t b, int64_t nblk) {
+  using C = float2;
+  constexpr int LD = f32_ld<W>();
+  constexpr int RS = RT / TR;
+  constexpr int KPG = W / KG;
+  static_assert((RT / TR) * (NV / TV) * KG == NT, "thread blocking must cover the tile");
+  static_assert(W % (2 * KG) == 0 && (NT / KG) % 32 == 0, "a warp belongs to one k-group, column pairs");
+  static_assert(TV % 2 == 0 && NV % TV == 0, "vectors in 16-byte pieces");
+  static_assert(S >= 2 && S <= 32 && 128 % W == 0, "a ring of whole chunks inside one stored block");
+  static_assert((size_t)(KG - 1) * RT * NV <= (size_t)S * RT * LD, "k-group sums fit the chunk ring");
+  C* hs = reinterpret_cast<C*>(smem_raw);                // [S][RT][LD]
+  C* xs = hs + S * RT * LD;                              // [S][W][NV]
+  float* win = reinterpret_cast<float*>(xs + S * W * NV);  // [RT + W]
+  const int tid = threadIdx.x;
+  const int kg = tid / (NT / KG), lt = tid % (NT / KG);
+  const int tv = lt % (NV / TV), tr = lt / (NV / TV);
+  C A[TR][TV], B[TR][TV];
+#pragma unroll
+  for (int i = 0; i < TR; ++i)
+#pragma unroll
+    for (int j = 0; j < TV; ++j) A[i][j] = B[i][j] = zc<float>();
+  if (cbeg >= cend) return;
+  const int64_t nch = (cend - cbeg + W - 1) / W;
+  uint32_t conj = 0;  // bit s: the chunk in stage s was read transposed (conjugate on use)
+  // the stored block of the current column block: looked up once per block,
+  // not per chunk (a dependent global load in front of every copy otherwise)
+  int64_t blk_m = -1, sl = -1;
+  bool t = false;
+  // chunk q into stage q % S: one cp.async group per chunk (empty past the
+  // end); a generated chunk is written by plain stores, visible after the
+  // barrier that precedes its use
+  auto issue = [&](int64_t q) {
+    const int st = (int)(q % S);
+    if (q >= nch) {
+      cp_async_commit();
+      return;
+    }
+    const int64_t c0 = cbeg + q * W;
+    if (cache && blk_of(c0, b) != blk_m) {
+      blk_m = blk_of(c0, b);
+      sl = chunk_slot(R0, c0, cache, nullptr, slot_of_pair, b, nblk, t);
+    }
+    xchunk_copy_async<float, NV, NT, W>(xs + st * W * NV, xc, c0, cend);
+    if (sl != -1) {
+      chunk_copy_async<float, NT, LD, W>(hs + st * RT * LD, sl, t, R0, c0, cache, nullptr, b);
+      conj = t ? (conj | (1u << st)) : (conj & ~(1u << st));
+    } else {
+      cp_async_commit();
+      fill_chunk_gen_f32<GEN, NT, LD, W>(hs + st * RT * LD, win, R0, c0, seed, sigma, dk);
+      conj &= ~(1u << st);
+    }
+  };
+#pragma unroll 1
+  for (int q = 0; q < S - 1; ++q) issue(q);
+#pragma unroll 1
+  for (int64_t k = 0; k < nch; ++k) {
+    // chunk k has landed (for this thread's copies; the barrier for all
+    // threads'), and the stage of chunk k - 1 is free for chunk k + S - 1
+    asm volatile("cp.async.wait_group %0;" ::"n"(S - 2) : "memory");
+    __syncthreads();
+    issue(k + S - 1);
+    const int st = (int)(k % S);
+    const C* hrow = hs + st * RT * LD + tr * LD;
+    const C* xcol = xs + st * W * NV + tv * TV;
+    if ((conj >> st) & 1u)
+      contract_f32<GEN, NV, TR, TV, KPG, LD, true>(A, B, hrow, xcol, kg * KPG);
+    else
+      contract_f32<GEN, NV, TR, TV, KPG, LD, false>(A, B, hrow, xcol, kg * KPG);
+  }
+  cp_async_wait_all();
+  __syncthreads();  // every thread is done with the ring
+  if constexpr (GEN != MF_GEN_SINC_DVR_HO) {
+#pragma unroll
+    for (int i = 0; i < TR; ++i)
+#pragma unroll
+      for (int j = 0; j < TV; ++j) {
+        A[i][j].x -= B[i][j].y;
+        A[i][j].y += B[i][j].x;
+      }
+  }
+  if constexpr (KG > 1) {
+    C* red = hs;  // [KG - 1][RT][NV]
+    if (kg > 0) {
+#pragma unroll
+      for (int i = 0; i < TR; ++i)
+#pragma unroll
+        for (int j = 0; j < TV; ++j) red[((kg - 1) * RT + tr + i * RS) * NV + tv * TV + j] = A[i][j];
+    }
+    __syncthreads();
+    if (kg > 0) return;
+#pragma unroll
+    for (int g = 1; g < KG; ++g)
+#pragma unroll
+      for (int i = 0; i < TR; ++i)
+#pragma unroll
+        for (int j = 0; j < TV; ++j) {
+          const C v = red[((g - 1) * RT + tr + i * RS) * NV + tv * TV + j];
+          A[i][j].x += v.x;
+          A[i][j].y += v.y;
+        }
+  }
+#pragma unroll
+  for (int i = 0; i < TR; ++i)
+#pragma unroll
+    for (int j = 0; j < TV; ++j) out[(tr + i * RS) * NV + tv * TV + j] = A[i][j];
+}
+
+template <int NV, int W = F32_W, int S = F32_S>
+__host__ __device__ constexpr size_t rows_smem_bytes_f32() {
+  return sizeof(float2) * ((size_t)S * RT * f32_ld<W>() + (size_t)S * W * NV) + sizeof(float) * (RT + W);
 }
 
 template <typename T, int NV>
