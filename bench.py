@@ -1059,7 +1059,12 @@ def run_batch(args):
     import torch
     import paper_2606_31598_gb300 as mf
     import workloads as W
-    probs = W.batch_problems(args.batch_n)
+    if args.batch_uniform:
+        # uniform problems (D, vectors, count): one vector bucket, for profiling
+        D, k, n = (int(v) for v in args.batch_uniform.split(","))
+        probs = [(D, k, i) for i in range(n)]
+    else:
+        probs = W.batch_problems(args.batch_n)
     Ds = [p[0] for p in probs]
     nv = [p[1] for p in probs]
     seeds = [p[2] for p in probs]
@@ -1108,7 +1113,8 @@ def run_batch(args):
     torch.cuda.synchronize()
     t_seq = time.perf_counter() - t1
     applies = args.steps * (nt - 1)
-    out = {"workload": "%d batched Philox problems, D in [1024, 32768], 1-16 vectors, FP32" % len(Ds),
+    what = ("D = %d, %d vectors each" % (Ds[0], nv[0])) if args.batch_uniform else "D in [1024, 32768], 1-16 vectors"
+    out = {"workload": "%d batched Philox problems, %s, FP32" % (len(Ds), what),
            "sum_D2_nvec": entries, "terms_per_step": nt, "create_s": t_create, "work_items": n_items,
            "persistent_grid": grid, "storage_chosen": stores,
            "batched": {"steps_per_s": args.steps / t_batch, "entries_per_s": entries * applies / t_batch},
@@ -1252,6 +1258,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mf", choices=["mf", "reference"])
     ap.add_argument("--batch-n", type=int, default=256, help="batch: number of problems")
+    ap.add_argument("--batch-uniform", default="", help="batch: 'D,nvec,count' uniform problems instead of the draw")
     ap.add_argument("--philox-dim", type=int, default=131072, help="philox: D")
     ap.add_argument("--philox-nvec", type=int, default=1, choices=[1, 2], help="philox: vectors")
     ap.add_argument("--batch-budget-gb", type=float, default=200.0, help="batch: shared cache budget")
