@@ -729,14 +729,18 @@ def sub_batch(stream, rates=None):
     NCPU = 4  # problems of the CPU baseline (their bounds, before the batch is closed)
     bounds = [mf.mf_spectral_bounds(b.plan(i)) for i in range(NCPU)]
     entries = float(sum(D * D * k for D, k in zip(Ds, nv)))
-    hbm_bytes = gen_entries = flops = 0.0
+    hbm_bytes = hbm_bytes_once = gen_entries = flops = 0.0
+    n_herm = 0
     stores = {}
     for i, (D, k) in enumerate(zip(Ds, nv)):
         d = mf.mf_plan_describe(b.plan(i))
         stores[d["storage"]] = stores.get(d["storage"], 0) + 1
         cached = min(float(D) * D, 2.0 * d["pairs_cached"] * d["block"] ** 2)
-        hbm_bytes += 8.0 * cached
-        gen_entries += float(D) * D - cached
+        herm = b.hermitian(i)
+        n_herm += herm
+        hbm_bytes += (4.0 if herm else 8.0) * cached
+        hbm_bytes_once += 4.0 * cached
+        gen_entries += (0.5 if herm else 1.0) * (float(D) * D - cached)
         flops += 8.0 * D * D * k
     n_items, grid = b.info()
     b.close()
@@ -757,10 +761,10 @@ def sub_batch(stream, rates=None):
     return {"workload": "256 batched Philox problems, D in [1024, 32768], 1-16 vectors, FP32, autotuned plans",
             "create_s": t_create, "terms_per_step": nt, "step_s": t, "steps_per_s": 1.0 / t,
             "entries_per_s": entries * applies / t, "sum_D2_nvec": entries, "work_items": n_items,
-            "persistent_grid": grid, "storage_chosen": stores,
+            "persistent_grid": grid, "storage_chosen": stores, "hermitian_reuse_problems": n_herm,
             "error": {"problem0_step_abs_vs_oracle": float(np.max(np.abs(got0 - ref0))),
                       "measure": "FP32 form against the oracle's statement of the same form, same bounds/terms"},
-            "roofline": batch_roofline(hbm_bytes, gen_entries, flops, t / applies, rates),
+            "roofline": batch_roofline(hbm_bytes, gen_entries, flops, t / applies, rates, hbm_bytes_once),
             "cpu_baseline": {"value": cpu_entries / t_cpu, "unit": "entries/s", "cores": cpu_threads(),
                              "kind": "oracle", "sample": "the FP32-form Chebyshev step of the first %d problems "
                                                         "(%.1f s)" % (NCPU, t_cpu)}}
@@ -1028,13 +1032,17 @@ def pipe_roofline(canon_per_s, rates, apply_ffma_per_entry=8):
                      "measured by mf_pipe_rates (register-only chains) in this run"}
 
 
-def batch_roofline(hbm_bytes, gen_entries, flops, t_apply, rates=None):
+def batch_roofline(hbm_bytes, gen_entries, flops, t_apply, rates=None, hbm_bytes_once=None):
     """Lower bounds of one batched product from its three resources, each at
     its measured peak: HBM (the measured copy rate), the FP32 FMA pipe (the
     FFMA rate of mf_pipe_rates, else 152 x 128 lanes x 2070 MHz) and entry
     generation (the generated entries at the slowest generator pipe of
     mf_pipe_rates, else the 1.5e11 entries/s of the Philox row-owner kernel);
-    achieved fraction = largest bound / measured time."""
+    achieved fraction = largest bound / measured time.  hbm_bytes are the
+    stored bytes the chosen forms read (a stored pair once in the
+    Hermitian-reuse form, twice in the row-owner form); hbm_bytes_once, if
+    given, every stored pair read once (the bound of canonical-pair reuse for
+    every problem), reported beside it."""
     t_hbm = hbm_bytes / (measured_peaks()["hbm_gbs"] * 1e9)
     if rates and rates.get("ffma"):
         t_fma = flops / (2.0 * rates["ffma"])
@@ -1044,9 +1052,14 @@ def batch_roofline(hbm_bytes, gen_entries, flops, t_apply, rates=None):
         t_gen = gen_entries / 1.5e11
     bound = max(t_hbm, t_fma, t_gen)
     name = {t_hbm: "hbm", t_fma: "fma", t_gen: "generation"}[bound]
-    return {"t_apply_s": t_apply, "t_hbm_s": t_hbm, "t_fma_s": t_fma, "t_gen_s": t_gen, "bound": name,
-            "frac": bound / t_apply, "sum_of_bounds_frac": (t_hbm + t_fma + t_gen) / t_apply,
-            "rates": "measured in this run" if rates else "unit counts"}
+    out = {"t_apply_s": t_apply, "t_hbm_s": t_hbm, "t_fma_s": t_fma, "t_gen_s": t_gen, "bound": name,
+           "frac": bound / t_apply, "sum_of_bounds_frac": (t_hbm + t_fma + t_gen) / t_apply,
+           "rates": "measured in this run" if rates else "unit counts"}
+    if hbm_bytes_once is not None:
+        t_once = hbm_bytes_once / (measured_peaks()["hbm_gbs"] * 1e9)
+        out["t_hbm_pairs_once_s"] = t_once
+        out["frac_of_pairs_once_bound"] = max(t_once, t_fma, t_gen) / t_apply
+    return out
 
 
 def run_batch(args):
@@ -1088,16 +1101,21 @@ def run_batch(args):
     t_batch = e0.elapsed_time(e1) / 1e3
     stores = {}
     entries = 0.0
-    hbm_bytes = 0.0     # cached entries read per product (each stored pair as H and as H^dagger)
-    gen_entries = 0.0   # entries generated per product
-    flops = 0.0         # 8 real FLOP per entry and vector
+    hbm_bytes = 0.0       # stored bytes read per product by the chosen forms
+    hbm_bytes_once = 0.0  # every stored pair read once
+    gen_entries = 0.0     # entries generated per product
+    flops = 0.0           # 8 real FLOP per entry and vector
+    n_herm = 0
     for i, (D, k) in enumerate(zip(Ds, nv)):
         d = mf.mf_plan_describe(b.plan(i))
         stores[d["storage"]] = stores.get(d["storage"], 0) + 1
         entries += float(D) * D * k
         cached = min(float(D) * D, 2.0 * d["pairs_cached"] * d["block"] ** 2)
-        hbm_bytes += 8.0 * cached
-        gen_entries += float(D) * D - cached
+        herm = b.hermitian(i)
+        n_herm += herm
+        hbm_bytes += (4.0 if herm else 8.0) * cached
+        hbm_bytes_once += 4.0 * cached
+        gen_entries += (0.5 if herm else 1.0) * (float(D) * D - cached)
         flops += 8.0 * D * D * k
     # the same problems one by one through their own plans (same term count;
     # the plans run on the batch's stream, so time with device syncs)
@@ -1116,11 +1134,11 @@ def run_batch(args):
     what = ("D = %d, %d vectors each" % (Ds[0], nv[0])) if args.batch_uniform else "D in [1024, 32768], 1-16 vectors"
     out = {"workload": "%d batched Philox problems, %s, FP32" % (len(Ds), what),
            "sum_D2_nvec": entries, "terms_per_step": nt, "create_s": t_create, "work_items": n_items,
-           "persistent_grid": grid, "storage_chosen": stores,
+           "persistent_grid": grid, "storage_chosen": stores, "hermitian_reuse_problems": n_herm,
            "batched": {"steps_per_s": args.steps / t_batch, "entries_per_s": entries * applies / t_batch},
            "sequential": {"steps_per_s": args.steps / t_seq, "entries_per_s": entries * applies / t_seq},
            "speedup_batched_vs_sequential": t_seq / t_batch,
-           "roofline": batch_roofline(hbm_bytes, gen_entries, flops, t_batch / applies),
+           "roofline": batch_roofline(hbm_bytes, gen_entries, flops, t_batch / applies, None, hbm_bytes_once),
            "max_diff_batched_vs_sequential": float(max((packed[int(b.offsets[i]):int(b.offsets[i + 1])]
                                                         - seq[i].reshape(-1)).abs().max() for i in range(len(Ds))))}
     print(json.dumps(out))

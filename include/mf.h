@@ -466,10 +466,17 @@ mf_status mf_batch_offsets(mf_batch_t b, int64_t* offsets);
 mf_status mf_batch_propagate(mf_batch_t b, void* psi, double dt, int32_t nsteps, int32_t order, int32_t* nterms_out);
 /* The plan of problem i (owned by the batch) and launch facts: the
  * (problem, row tile) work items and the largest persistent grid of the
- * per-vector-bucket kernels (one persistent kernel per bucket of
- * max(2, nvec) in {2, 4, 6, 8, 12, 16}, launched side by side each term). */
+ * per-list kernels (one persistent kernel per vector bucket of max(2, nvec)
+ * in {2, 4, 6, 8, 12, 16} and form, launched side by side each term). */
 mf_status mf_batch_plan(mf_batch_t b, int32_t i, mf_plan_t* plan);
 mf_status mf_batch_info(mf_batch_t b, int32_t* n_items, int32_t* persist_grid);
+/* Form of problem i's batched product (Sec. III.A canonical-pair reuse):
+ * *hermitian = 1 when each stored canonical chunk is read once and applied
+ * as H and as H^dagger (FP32 problems of 1-6 vectors whose 1 + ntile slots
+ * of partial rows could be allocated; the slots are summed in tile order by
+ * the update), 0 for the row-owner form (each stored entry read as H and as
+ * H^dagger by the two row tiles).  MF_ERR_INVALID for a bad handle or i. */
+mf_status mf_batch_form(mf_batch_t b, int32_t i, int32_t* hermitian);
 
 /* Wait for the plan's stream and report the device error word: MF_OK, or
  * MF_ERR_TIMEOUT when a bounded wait ran out (codes 100..199, see

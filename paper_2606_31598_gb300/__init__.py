@@ -160,8 +160,9 @@ def lib():
         L.mf_batch_propagate.argtypes = [vp, vp, d, i32, i32, P(i32)]
         L.mf_batch_plan.argtypes = [vp, i32, P(vp)]
         L.mf_batch_info.argtypes = [vp, P(i32), P(i32)]
+        L.mf_batch_form.argtypes = [vp, i32, P(i32)]
         for name in ("mf_batch_create", "mf_batch_destroy", "mf_batch_offsets", "mf_batch_propagate",
-                     "mf_batch_plan", "mf_batch_info"):
+                     "mf_batch_plan", "mf_batch_info", "mf_batch_form"):
             getattr(L, name).restype = ctypes.c_int
         for name in ("mf_planner_estimate", "mf_plan_trials", "mf_mlp_create", "mf_mlp_destroy", "mf_mlp_param_count",
                      "mf_mlp_get_params", "mf_mlp_set_params", "mf_mlp_predict", "mf_mlp_loss_grad", "mf_mlp_train",
@@ -497,6 +498,12 @@ class Batch:
         h = ctypes.c_void_p()
         _check(lib().mf_batch_plan(self.handle, int(i), ctypes.byref(h)), "mf_batch_plan")
         return h
+
+    def hermitian(self, i):
+        """True when problem i takes the Hermitian-reuse form of the batched product."""
+        h = ctypes.c_int32()
+        _check(lib().mf_batch_form(self.handle, int(i), ctypes.byref(h)), "mf_batch_form")
+        return bool(h.value)
 
     def info(self):
         a, b = ctypes.c_int32(), ctypes.c_int32()

@@ -22,6 +22,8 @@ namespace mf {
 
 struct BatchProb {
   int64_t D, ntile, b, nblk, nv, nb;
+  int64_t herm;  // Hermitian-reuse form: part holds 1 + ntile slots of dpad rows
+  int64_t dpad;
   uint64_t seed;
   float sigma32;
   double sigma64;
@@ -43,9 +45,15 @@ struct BatchItem {
 
 namespace {
 
-// The vector buckets of the batched kernel (rows_nvec_bucket of max(2, nvec)).
-constexpr int kBuckets = 6;
-constexpr int kBucketNV[kBuckets] = {2, 4, 6, 8, 12, 16};
+// The work lists of the batched kernel: the row-owner form per vector bucket
+// (rows_nvec_bucket of max(2, nvec)) and the Hermitian-reuse form (FP32, few
+// vectors, where the stored bytes bound the product) for buckets 2, 4 and 6
+// (at 8 vectors the row-owner form is faster: 16.7 vs 17.6 ms for 38
+// problems of D = 16384).
+constexpr int kOwnerBuckets = 6;
+constexpr int kBuckets = 9;
+constexpr int kBucketNV[kBuckets] = {2, 4, 6, 8, 12, 16, 2, 4, 6};
+constexpr bool kBucketHerm[kBuckets] = {false, false, false, false, false, false, true, true, true};
 
 // One row tile of a problem of bucket NB.  Register tiles (rows x vectors)
 // and k-groups per bucket: the FP32 form takes 2 x 2 to 4 x 6 complex tiles
@@ -91,6 +99,36 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_batch_apply(con
   }
 }
 
+// Hermitian-reuse form (FP32): row tile I sweeps the upper band, owner rows
+// to slot 0, the chunks' H^dagger rows to slot 1 + I.
+template <int GEN, int NB>
+__device__ __forceinline__ void batch_tile_herm(unsigned char* smem_raw, const BatchProb& P, int64_t ti) {
+  constexpr int TR = NB == 4 ? 4 : 2;
+  constexpr int TV = NB;
+  constexpr int KG = NB == 4 ? 8 : 4;
+  const int64_t R0 = ti * rows::RT;
+  float2* part = (float2*)P.part;
+  row_tile_herm_f32<GEN, NB, TR, TV, 256, KG>(smem_raw, R0, P.D, P.seed, P.sigma32, P.dk, (const float2*)P.xc,
+                                              part + R0 * NB, part + (1 + ti) * P.dpad * NB, P.dpad,
+                                              (const float2*)P.cache, P.slot, P.b, P.nblk);
+}
+
+template <typename T, int GEN, int NB>
+__global__ void __launch_bounds__(256, 2) k_batch_herm(const BatchItem* __restrict__ items, int n_items,
+                                                       const BatchProb* __restrict__ probs, int* __restrict__ counter) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_item;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int it = s_item;
+    __syncthreads();
+    if (it >= n_items) break;
+    const BatchItem w = items[it];
+    if constexpr (sizeof(T) == 4) batch_tile_herm<GEN, NB>(smem_raw, probs[w.prob], (int64_t)w.tile);
+  }
+}
+
 template <typename T, int GEN>
 using BatchKernel = void (*)(const BatchItem*, int, const BatchProb*, int*);
 
@@ -102,7 +140,10 @@ BatchKernel<T, GEN> batch_kernel(int k) {
     case 2: return k_batch_apply<T, GEN, 6>;
     case 3: return k_batch_apply<T, GEN, 8>;
     case 4: return k_batch_apply<T, GEN, 12>;
-    default: return k_batch_apply<T, GEN, 16>;
+    case 5: return k_batch_apply<T, GEN, 16>;
+    case 6: return k_batch_herm<T, GEN, 2>;
+    case 7: return k_batch_herm<T, GEN, 4>;
+    default: return k_batch_herm<T, GEN, 6>;
   }
 }
 
@@ -115,7 +156,10 @@ size_t batch_smem(int k) {
       case 2: return rows_smem_bytes_f32<6>();
       case 3: return rows_smem_bytes_f32<8>();
       case 4: return rows_smem_bytes_f32<12>();
-      default: return rows_smem_bytes_f32<16>();
+      case 5: return rows_smem_bytes_f32<16>();
+      case 6: return herm_smem_bytes_f32<2>();
+      case 7: return herm_smem_bytes_f32<4>();
+      default: return herm_smem_bytes_f32<6>();
     }
   } else {
     switch (k) {
@@ -129,10 +173,10 @@ size_t batch_smem(int k) {
   }
 }
 
-int bucket_index(int64_t nb) {
+int bucket_index(int64_t nb, bool herm) {
   for (int k = 0; k < kBuckets; ++k)
-    if (kBucketNV[k] == nb) return k;
-  return kBuckets - 1;
+    if (kBucketNV[k] == nb && kBucketHerm[k] == herm) return k;
+  return kOwnerBuckets - 1;
 }
 
 // q_cur = psi, acc = J0 psi, xc = compute copy (padding zero); grid.y = problem
@@ -175,6 +219,15 @@ __global__ void k_batch_update(const BatchProb* __restrict__ probs, int parity, 
     const int64_t row = e / P.nv, v = e % P.nv, ci = row * P.nb + v;
     const C pv = part[ci];
     double yr = (double)pv.x, yi = (double)pv.y;
+    if (P.herm) {
+      // the H^dagger rows from the row tiles above this row's, in tile order
+      const int64_t tile = row / rows::RT;
+      for (int64_t s2 = 1; s2 <= tile; ++s2) {
+        const C ps = part[s2 * P.dpad * P.nb + ci];
+        yr += (double)ps.x;
+        yi += (double)ps.y;
+      }
+    }
     const double2 q = qc[e];
     if (gen_dvr) {
       const double V = dvr_V(P.dk, row);
@@ -240,6 +293,8 @@ struct mf_batch {
   cudaStream_t side[kBuckets] = {};
   cudaEvent_t ev_fork = nullptr, ev_join[kBuckets] = {};
   int64_t max_elems = 0;
+  // Hermitian-reuse problems: their 1 + ntile slots of dpad rows (owned)
+  std::vector<void*> hbuf;
   // captured propagation and the arguments it was captured for
   cudaGraphExec_t graph = nullptr;
   double g_dt = 0.0;
@@ -253,6 +308,8 @@ namespace {
 void batch_release(mf_batch* b) {
   if (b->graph) cudaGraphExecDestroy(b->graph);
   for (auto p : b->plans) mf_plan_destroy(p);
+  for (void* h : b->hbuf)
+    if (h) cudaFree(h);
   if (b->d_probs) cudaFree(b->d_probs);
   if (b->d_items) cudaFree(b->d_items);
   if (b->d_counter) cudaFree(b->d_counter);
@@ -371,18 +428,33 @@ mf_status mf_batch_create(mf_batch_t* out, int32_t nprob, const int64_t* D, cons
       b->offsets.push_back(b->offsets.back() + D[i] * nvec[i]);
       b->max_elems = std::max<int64_t>(b->max_elems, D[i] * rows_nvec_bucket(std::max<int32_t>(2, nvec[i])));
     }
-    // work lists: every (problem, row tile), by vector bucket, each bucket's
-    // most expensive first
+    // Hermitian-reuse form for the FP32 problems of buckets 2, 4 and 6 (their
+    // products are bound by the stored bytes, which it halves) when their
+    // 1 + ntile slots can be allocated; the row-owner form otherwise
+    b->hbuf.assign(nprob, nullptr);
+    for (int32_t i = 0; i < nprob && o.precision == MF_PREC_FP32; ++i) {
+      const Plan& P = b->plans[i]->p;
+      const int64_t nb = rows_nvec_bucket(std::max<int32_t>(2, nvec[i]));
+      if (nb > 6) continue;
+      const size_t bytes = (size_t)(1 + P.ntile) * (size_t)(P.ntile * rows::RT) * (size_t)nb * sizeof(float2);
+      if (dev_malloc(&b->hbuf[i], bytes) != cudaSuccess) {
+        cudaGetLastError();
+        b->hbuf[i] = nullptr;
+      }
+    }
+    // work lists: every (problem, row tile), by vector bucket and form, each
+    // list's most expensive first
     std::vector<BatchItem> items;
     std::vector<double> cost;
     std::vector<int> bucket;
     for (int32_t i = 0; i < nprob; ++i) {
       const Plan& P = b->plans[i]->p;
       const int64_t nb = rows_nvec_bucket(std::max<int32_t>(2, nvec[i]));
+      const bool herm = b->hbuf[i] != nullptr;
       for (int64_t t = 0; t < P.ntile; ++t) {
         items.push_back(BatchItem{i, (int32_t)t});
-        cost.push_back((double)P.D * (double)nb);
-        bucket.push_back(bucket_index(nb));
+        cost.push_back((double)(herm ? P.D - t * rows::RT : P.D) * (double)nb);
+        bucket.push_back(bucket_index(nb, herm));
       }
     }
     std::vector<size_t> idx(items.size());
@@ -480,7 +552,9 @@ mf_status mf_batch_propagate(mf_batch_t b, void* psi, double dt, int32_t nsteps,
         q.sigma64 = P.sigma64;
         q.dk = P.dvr;
         q.xc = P.d_xc;
-        q.part = P.d_part;
+        q.herm = b->hbuf[i] != nullptr;
+        q.dpad = P.ntile * rows::RT;
+        q.part = q.herm ? b->hbuf[i] : P.d_part;
         q.cache = P.pairs_cached > 0 ? P.d_cache : nullptr;
         q.slot = P.d_pair_slot;
         q.q[0] = P.d_q[0];
@@ -532,6 +606,12 @@ mf_status mf_batch_propagate(mf_batch_t b, void* psi, double dt, int32_t nsteps,
 mf_status mf_batch_plan(mf_batch_t b, int32_t i, mf_plan_t* plan) {
   if (!b || !plan || i < 0 || i >= (int32_t)b->plans.size()) return MF_ERR_INVALID;
   *plan = b->plans[i];
+  return MF_OK;
+}
+
+mf_status mf_batch_form(mf_batch_t b, int32_t i, int32_t* hermitian) {
+  if (!b || !hermitian || i < 0 || i >= (int32_t)b->plans.size()) return MF_ERR_INVALID;
+  *hermitian = b->hbuf[i] != nullptr;
   return MF_OK;
 }
 

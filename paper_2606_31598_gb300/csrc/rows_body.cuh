@@ -699,6 +699,188 @@ __device__ __forceinline__ void row_tile_async_f32(unsigned char* smem_raw, int6
     for (int j = 0; j < TV; ++j) out[(tr + i * RS) * NV + tv * TV + j] = A[i][j];
 }
 
+// ---------------------------------------------------------------------------
+// Hermitian-reuse form of the FP32 ring tile (Sec. III.A canonical-pair
+// reuse) for few vectors, where the stored bytes bound the product: row tile
+// I sweeps only the upper band, columns [128 I, D), so every stored chunk is
+// read once (always in its stored orientation) and applied twice -- as H to
+// the tile's rows (register tiles, as row_tile_async_f32) and, for chunks
+// strictly above the diagonal tile, as H^dagger to the chunk's W rows:
+// Y[c][v] = sum_r conj(H[r][c]) X[r][v].  The H^dagger sum runs over the
+// tile's rows in P parts of threads (CT = 1 column x NV vectors each, in
+// packed FP32 pairs: A' += (h_r, h_r) x, B' += (h_i, h_i) x, conj(h) x =
+// A' - i B'); the parts are added in fixed order after the next barrier and
+// written to slot 1 + I of the chunk's rows: outd + (I * dpad + c) NV.  The
+// owner rows go to out as in row_tile_async_f32.  Every slot that the
+// reduction reads is written once per product.
+// ---------------------------------------------------------------------------
+template <int NV>
+struct HermF32 {
+  static constexpr int TPP = F32_W;      // threads per part: one column each, all NV vectors
+  static constexpr int P = 256 / TPP;    // parts (256 threads)
+  static constexpr int RP = RT / P;      // rows per part
+  static constexpr int O = F32_W * NV;   // outputs per chunk
+};
+
+template <int NV, int W = F32_W, int S = F32_S>
+__host__ __device__ constexpr size_t herm_smem_bytes_f32() {
+  return sizeof(float2) * ((size_t)S * RT * f32_ld<W>() + (size_t)S * W * NV + (size_t)RT * NV +
+                           2 * (size_t)HermF32<NV>::P * HermF32<NV>::O) +
+         sizeof(float) * (RT + W);
+}
+
+template <int GEN, int NV, int TR, int TV, int NT, int KG>
+__device__ __forceinline__ void row_tile_herm_f32(unsigned char* smem_raw, int64_t R0, int64_t D, uint64_t seed,
+                                                  float sigma, const dvr_consts& dk, const float2* __restrict__ xc,
+                                                  float2* __restrict__ out, float2* __restrict__ outd, int64_t dpad,
+                                                  const float2* __restrict__ cache,
+                                                  const int64_t* __restrict__ slot_of_pair, int64_t b, int64_t nblk) {
+  using C = float2;
+  constexpr int W = F32_W, S = F32_S;
+  constexpr int LD = f32_ld<W>();
+  constexpr int RS = RT / TR;
+  constexpr int KPG = W / KG;
+  using HP = HermF32<NV>;
+  constexpr int P = HP::P, RP = HP::RP, O = HP::O;
+  static_assert(NT == 256 && S == 2, "the part layout assumes 256 threads and two stages");
+  static_assert((RT / TR) * (NV / TV) * KG == NT, "thread blocking must cover the tile");
+  static_assert(W % (2 * KG) == 0 && (NT / KG) % 32 == 0, "a warp belongs to one k-group, column pairs");
+  static_assert(TV % 2 == 0 && NV % TV == 0 && NV % 2 == 0, "vectors in 16-byte pieces");
+  static_assert((size_t)(KG - 1) * RT * NV <= (size_t)S * RT * LD, "k-group sums fit the chunk ring");
+  C* hs = reinterpret_cast<C*>(smem_raw);   // [S][RT][LD]
+  C* xs = hs + S * RT * LD;                 // [S][W][NV]
+  C* xr = xs + S * W * NV;                  // [RT][NV]: the tile's rows of X
+  C* red = xr + RT * NV;                    // [2][P][O]: H^dagger parts
+  float* win = reinterpret_cast<float*>(red + 2 * P * O);  // [RT + W]
+  const int tid = threadIdx.x;
+  const int kg = tid / (NT / KG), lt = tid % (NT / KG);
+  const int tv = lt % (NV / TV), tr = lt / (NV / TV);
+  const int dp = tid / HP::TPP, dc = tid % HP::TPP;  // H^dagger part and column
+  C A[TR][TV], B[TR][TV];
+#pragma unroll
+  for (int i = 0; i < TR; ++i)
+#pragma unroll
+    for (int j = 0; j < TV; ++j) A[i][j] = B[i][j] = zc<float>();
+  const int64_t cbeg = R0;
+  const int64_t nch = (D - cbeg + W - 1) / W;
+  // the tile's rows of X (zero past D), in the first copy group
+  for (int pc = tid; pc < RT * NV / 2; pc += NT) {
+    const int e = 2 * pc;
+    if (R0 + e / NV < D)
+      cp_async_elem<16>(xr + e, xc + R0 * NV + e);
+    else
+      xr[e] = xr[e + 1] = zc<float>();
+  }
+  int64_t blk_m = -1, sl = -1;
+  bool t = false;
+  auto issue = [&](int64_t q) {
+    const int st = (int)(q % S);
+    if (q >= nch) {
+      cp_async_commit();
+      return;
+    }
+    const int64_t c0 = cbeg + q * W;
+    if (cache && blk_of(c0, b) != blk_m) {
+      blk_m = blk_of(c0, b);
+      sl = chunk_slot(R0, c0, cache, nullptr, slot_of_pair, b, nblk, t);  // c0 >= R0: never transposed
+    }
+    xchunk_copy_async<float, NV, NT, W>(xs + st * W * NV, xc, c0, D);
+    if (sl != -1) {
+      chunk_copy_async<float, NT, LD, W>(hs + st * RT * LD, sl, false, R0, c0, cache, nullptr, b);
+    } else {
+      cp_async_commit();
+      fill_chunk_gen_f32<GEN, NT, LD, W>(hs + st * RT * LD, win, R0, c0, seed, sigma, dk);
+    }
+  };
+  // H^dagger parts of chunk q (in red[q % 2]) added in part order and stored
+  auto drain = [&](int64_t q) {
+    const C* rq = red + (q % 2) * P * O;
+    const int64_t c0 = cbeg + q * W;
+    for (int o = tid; o < O; o += NT) {
+      C v = rq[o];
+#pragma unroll
+      for (int p2 = 1; p2 < P; ++p2) {
+        v.x += rq[p2 * O + o].x;
+        v.y += rq[p2 * O + o].y;
+      }
+      outd[(c0 + o / NV) * NV + o % NV] = v;
+    }
+  };
+  issue(0);
+  for (int64_t k = 0; k < nch; ++k) {
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+    const int64_t c0 = cbeg + k * W;
+    if (k > 0 && c0 - W >= R0 + RT) drain(k - 1);
+    issue(k + 1);
+    const int st = (int)(k % S);
+    const C* hst = hs + st * RT * LD;
+    contract_f32<GEN, NV, TR, TV, KPG, LD, false>(A, B, hst + tr * LD, xs + st * W * NV + tv * TV, kg * KPG);
+    if (c0 >= R0 + RT) {
+      // Y[c][v] over this part's rows: A' += h_r x, B' += h_i x
+      C Ad[NV], Bd[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Ad[v] = Bd[v] = zc<float>();
+#pragma unroll 4
+      for (int r = dp * RP; r < dp * RP + RP; ++r) {
+        const C h = hst[r * LD + dc];
+        const float2 hrr = make_float2(h.x, h.x), hii = make_float2(h.y, h.y);
+#pragma unroll
+        for (int m = 0; m < NV / 2; ++m) {
+          const float4 x4 = *reinterpret_cast<const float4*>(xr + r * NV + 2 * m);
+          const float2 x0 = make_float2(x4.x, x4.y), x1 = make_float2(x4.z, x4.w);
+          Ad[2 * m] = __ffma2_rn(hrr, x0, Ad[2 * m]);
+          Ad[2 * m + 1] = __ffma2_rn(hrr, x1, Ad[2 * m + 1]);
+          if constexpr (GEN != MF_GEN_SINC_DVR_HO) {
+            Bd[2 * m] = __ffma2_rn(hii, x0, Bd[2 * m]);
+            Bd[2 * m + 1] = __ffma2_rn(hii, x1, Bd[2 * m + 1]);
+          }
+        }
+      }
+      C* rq = red + (k % 2) * P * O + dp * O + dc * NV;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) rq[v] = make_float2(Ad[v].x + Bd[v].y, Ad[v].y - Bd[v].x);
+    }
+  }
+  cp_async_wait_all();
+  __syncthreads();  // every thread is done with the ring and the last parts
+  if (nch > 0 && cbeg + (nch - 1) * W >= R0 + RT) drain(nch - 1);
+  if constexpr (GEN != MF_GEN_SINC_DVR_HO) {
+#pragma unroll
+    for (int i = 0; i < TR; ++i)
+#pragma unroll
+      for (int j = 0; j < TV; ++j) {
+        A[i][j].x -= B[i][j].y;
+        A[i][j].y += B[i][j].x;
+      }
+  }
+  if constexpr (KG > 1) {
+    C* kred = hs;  // [KG - 1][RT][NV]
+    if (kg > 0) {
+#pragma unroll
+      for (int i = 0; i < TR; ++i)
+#pragma unroll
+        for (int j = 0; j < TV; ++j) kred[((kg - 1) * RT + tr + i * RS) * NV + tv * TV + j] = A[i][j];
+    }
+    __syncthreads();
+    if (kg > 0) return;
+#pragma unroll
+    for (int g = 1; g < KG; ++g)
+#pragma unroll
+      for (int i = 0; i < TR; ++i)
+#pragma unroll
+        for (int j = 0; j < TV; ++j) {
+          const C v = kred[((g - 1) * RT + tr + i * RS) * NV + tv * TV + j];
+          A[i][j].x += v.x;
+          A[i][j].y += v.y;
+        }
+  }
+#pragma unroll
+  for (int i = 0; i < TR; ++i)
+#pragma unroll
+    for (int j = 0; j < TV; ++j) out[(tr + i * RS) * NV + tv * TV + j] = A[i][j];
+}
+
 template <int NV, int W = F32_W, int S = F32_S>
 __host__ __device__ constexpr size_t rows_smem_bytes_f32() {
   return sizeof(float2) * ((size_t)S * RT * f32_ld<W>() + (size_t)S * W * NV) + sizeof(float) * (RT + W);

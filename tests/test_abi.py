@@ -116,6 +116,7 @@ def test_every_entry_point_rejects_null_handles_and_bad_arguments(mf):
         "mf_batch_offsets": L.mf_batch_offsets(None, None),
         "mf_batch_plan": L.mf_batch_plan(None, 0, ctypes.byref(vp)),
         "mf_batch_info": L.mf_batch_info(None, None, None),
+        "mf_batch_form": L.mf_batch_form(None, 0, ctypes.byref(i32)),
         "mf_batch_create (no problems)": L.mf_batch_create(ctypes.byref(vp), 0, None, None, None, 0, 0, None),
         "mf_mlp_param_count": L.mf_mlp_param_count(None, ctypes.byref(i64)),
         "mf_mlp_predict": L.mf_mlp_predict(None, None, 1, None),

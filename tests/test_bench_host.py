@@ -72,3 +72,16 @@ def test_fp64_roofline_counts_the_definition():
     r = bench.fp64_roofline(1e6, 1e-3, {"dfma": 5.9e10})
     assert r["ops_per_entry"] == 59 and abs(r["frac"] - 1.0) < 1e-12
     assert "frac" not in bench.fp64_roofline(1e6, 1e-3, None)
+
+
+def test_batch_roofline_reports_the_pairs_once_bound():
+    """The batched roofline takes the stored bytes the chosen forms read and,
+    beside it, the bound with every stored pair read once (half the
+    row-owner bytes)."""
+    import bench
+    r = bench.batch_roofline(8e9, 0.0, 1e9, 2e-3, None, 4e9)
+    hbm = bench.measured_peaks()["hbm_gbs"] * 1e9
+    assert abs(r["t_hbm_s"] - 8e9 / hbm) < 1e-12 and abs(r["t_hbm_pairs_once_s"] - 4e9 / hbm) < 1e-12
+    assert r["bound"] == "hbm" and abs(r["frac"] - (8e9 / hbm) / 2e-3) < 1e-9
+    assert abs(r["frac_of_pairs_once_bound"] - max(4e9 / hbm, r["t_fma_s"]) / 2e-3) < 1e-9
+    assert "t_hbm_pairs_once_s" not in bench.batch_roofline(8e9, 0.0, 1e9, 2e-3)

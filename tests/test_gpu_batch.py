@@ -34,6 +34,10 @@ def test_batch_matches_per_problem_and_oracle(mf, prec, tol, cache):
     b = mf.Batch(Ds, nv, seeds, mf.MF_GEN_PHILOX_GUE, cache_budget_bytes=budget, precision=prec,
                  storage={"none": mf.MF_STORE_PROCEDURAL, "partial": mf.MF_STORE_PARTIAL,
                           "full": mf.MF_STORE_FULL}[cache])
+    # FP32 problems of 1-6 vectors take the Hermitian-reuse form (each stored
+    # or generated canonical chunk applied as H and as H^dagger), the others
+    # the row-owner form
+    assert [b.hermitian(i) for i in range(len(Ds))] == [prec == 1 and k <= 6 for k in nv]
     cached = [mf.mf_plan_describe(b.plan(i))["pairs_cached"] for i in range(len(Ds))]
     npair = [mf.mf_plan_describe(b.plan(i))["n_pair"] for i in range(len(Ds))]
     if cache == "none":
@@ -88,3 +92,28 @@ def test_batch_dvr_and_workload_draw(mf):
         c, R = 0.5 * (emax + emin), 0.5 * (emax - emin)
         ref = O.cheb_step(O.make_op(O.GEN_SINC_DVR_HO, D), parts[i], 1e-4, c, R, 12)
         assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < 1e-11
+
+
+@pytest.mark.parametrize("cache", ["none", "full"])
+def test_batch_dvr_fp32_both_forms(mf, cache):
+    """DVR problems in the FP32 form: 1-6 vectors on the Hermitian-reuse form
+    (real symmetric entries: H^dagger = H^T), 8 and 12 on the row-owner form; ragged
+    D (a partial last chunk and row tile), generated or stored chunks."""
+    Ds = [1000, 300, 1536, 777, 640]
+    nv = [1, 6, 4, 12, 8]
+    full = sum(8 * D * D for D in Ds)
+    b = mf.Batch(Ds, nv, list(range(5)), mf.MF_GEN_SINC_DVR_HO, precision=mf.MF_PREC_FP32,
+                 cache_budget_bytes=0 if cache == "none" else 4 * full,
+                 storage=mf.MF_STORE_PROCEDURAL if cache == "none" else mf.MF_STORE_FULL)
+    assert [b.hermitian(i) for i in range(5)] == [True, True, True, False, False]
+    parts = [W.random_state(D, k, seed=20 + i).reshape(D, k) for i, (D, k) in enumerate(zip(Ds, nv))]
+    d = torch.from_numpy(np.concatenate([p.ravel() for p in parts])).cuda()
+    b.propagate(d, 1e-4, 1, 12)
+    torch.cuda.synchronize()
+    out = d.cpu().numpy()
+    for i, (D, k) in enumerate(zip(Ds, nv)):
+        got = out[b.offsets[i]:b.offsets[i + 1]].reshape(D, k)
+        emin, emax = mf.mf_spectral_bounds(b.plan(i))
+        c, R = 0.5 * (emax + emin), 0.5 * (emax - emin)
+        ref = O.cheb_step(O.make_op(O.GEN_SINC_DVR_HO, D, form=O.FORM_FP32), parts[i], 1e-4, c, R, 12)
+        assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < 2e-5, (i, np.max(np.abs(got - ref)))
