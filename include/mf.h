@@ -472,8 +472,9 @@ mf_status mf_batch_plan(mf_batch_t b, int32_t i, mf_plan_t* plan);
 mf_status mf_batch_info(mf_batch_t b, int32_t* n_items, int32_t* persist_grid);
 /* Form of problem i's batched product (Sec. III.A canonical-pair reuse):
  * *hermitian = 1 when each stored canonical chunk is read once and applied
- * as H and as H^dagger (FP32 problems of 1-6 vectors whose 1 + ntile slots
- * of partial rows could be allocated; the slots are summed in tile order by
+ * as H and as H^dagger (FP32 problems of 1-6 vectors, in problem order
+ * while their slots of 1 + ntile partial rows fit together in a tenth of the
+ * device memory free after the plans; the slots are summed in tile order by
  * the update), 0 for the row-owner form (each stored entry read as H and as
  * H^dagger by the two row tiles).  MF_ERR_INVALID for a bad handle or i. */
 mf_status mf_batch_form(mf_batch_t b, int32_t i, int32_t* hermitian);

@@ -429,14 +429,24 @@ mf_status mf_batch_create(mf_batch_t* out, int32_t nprob, const int64_t* D, cons
       b->max_elems = std::max<int64_t>(b->max_elems, D[i] * rows_nvec_bucket(std::max<int32_t>(2, nvec[i])));
     }
     // Hermitian-reuse form for the FP32 problems of buckets 2, 4 and 6 (their
-    // products are bound by the stored bytes, which it halves) when their
-    // 1 + ntile slots can be allocated; the row-owner form otherwise
+    // products are bound by the stored bytes, which it halves) while the
+    // slots of 1 + ntile partial rows fit, all together, in a tenth of the
+    // memory free after the plans (they grow as D^2 / 128 per vector); the
+    // row-owner form otherwise
     b->hbuf.assign(nprob, nullptr);
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+      cudaGetLastError();
+      free_b = 0;
+    }
+    size_t slot_room = free_b / 10;
     for (int32_t i = 0; i < nprob && o.precision == MF_PREC_FP32; ++i) {
       const Plan& P = b->plans[i]->p;
       const int64_t nb = rows_nvec_bucket(std::max<int32_t>(2, nvec[i]));
       if (nb > 6) continue;
       const size_t bytes = (size_t)(1 + P.ntile) * (size_t)(P.ntile * rows::RT) * (size_t)nb * sizeof(float2);
+      if (bytes > slot_room) continue;
+      slot_room -= bytes;
       if (dev_malloc(&b->hbuf[i], bytes) != cudaSuccess) {
         cudaGetLastError();
         b->hbuf[i] = nullptr;
