@@ -54,8 +54,50 @@ static cudaError_t launch_rows_t(const Plan& p, const void* xc, void* part) {
   return cudaGetLastError();
 }
 
+// FP32 form with 32 or 64 vectors (blocks in HBM or generated): the ring
+// tile of the batched kernel -- two staged 32-column chunks copied by
+// cp.async while the previous one is contracted, two columns per 16-byte
+// shared load, the complex product in packed FP32 pairs (A += (h_r, h_r) x,
+// B += (h_i, h_i) x, Y = A + iB) -- on 4 x 4 complex register tiles.
+template <int GEN, int NV, int NT>
+__global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) rows_simt_f32(int64_t D, int64_t dpad, int64_t ksplit_cols,
+                                                               uint64_t seed, float sigma, dvr_consts dk,
+                                                               const float2* __restrict__ xc,
+                                                               float2* __restrict__ part,
+                                                               const float2* __restrict__ cache,
+                                                               const int64_t* __restrict__ slot_of_pair, int64_t b,
+                                                               int64_t nblk, int64_t tile0) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int64_t R0 = (tile0 + (int64_t)blockIdx.x) * RT;
+  const int64_t cbeg = (int64_t)blockIdx.y * ksplit_cols;
+  const int64_t cend = cbeg + ksplit_cols < D ? cbeg + ksplit_cols : D;
+  row_tile_async_f32<GEN, NV, 4, 4, NT, 1>(smem_raw, R0, cbeg, cend, seed, sigma, dk, xc,
+                                           part + ((int64_t)blockIdx.y * dpad + R0 - tile0 * RT) * NV, cache,
+                                           slot_of_pair, b, nblk);
+}
+
+template <int GEN, int NV, int NT>
+static cudaError_t launch_rows_f32(const Plan& p, const void* xc, void* part) {
+  static_assert((RT / 4) * (NV / 4) == NT, "4 x 4 tiles cover the row tile");
+  const size_t sm = rows_smem_bytes_f32<NV>();
+  auto k = rows_simt_f32<GEN, NV, NT>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  const int64_t ntiles = p.sliced ? p.slice_nt : p.ntile;
+  dim3 grid((unsigned)ntiles, (unsigned)p.rows_nsplit);
+  k<<<grid, NT, sm, p.stream>>>(p.D, ntiles * (int64_t)kTile, p.rows_split_cols, p.seed, p.sigma32, p.dvr,
+                                (const float2*)xc, (float2*)part, (const float2*)p.d_cache, p.d_pair_slot, p.b,
+                                p.nblk, p.sliced ? p.slice_t0 : 0);
+  return cudaGetLastError();
+}
+
 template <typename T, int GEN>
 static cudaError_t launch_rows_g(const Plan& p, const void* xc, void* part, int64_t nvec) {
+  if constexpr (sizeof(T) == 4) {
+    // host-resident blocks take the synchronous tile (it reads them in place)
+    if (!p.d_hblocks && nvec == 32) return launch_rows_f32<GEN, 32, 256>(p, xc, part);
+    if (!p.d_hblocks && nvec == 64) return launch_rows_f32<GEN, 64, 512>(p, xc, part);
+  }
   // (RT/TR) * (NV/TV) threads
   switch (nvec) {
     case 2: return launch_rows_t<T, GEN, 2, 1, 1, 256>(p, xc, part);

@@ -240,7 +240,7 @@ def test_bad_calls_rejected(mf):
 # --------------------------------------------------------- multi-vector ----
 @pytest.mark.parametrize("gen", [0, 1])
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("nvec", [2, 3, 16, 64])
+@pytest.mark.parametrize("nvec", [2, 3, 16, 32, 64])
 def test_multivector_apply_matches_oracle(mf, gen, prec, nvec):
     """Y = H X (Eq. generic_multivector) by the row-owner kernels, ragged D."""
     D = 1000
@@ -268,9 +268,13 @@ def test_multivector_row_owner_and_hermitian_reuse_agree(mf, prec):
         assert _relerr(y, ref) < (1e-12 if prec == 0 else 2e-5)
 
 
-@pytest.mark.parametrize("prec", [0, 1])
-def test_multivector_cache_modes_bit_identical(mf, prec):
-    D, b, nvec = 1000, 256, 8
+@pytest.mark.parametrize("prec,nvec", [(0, 8), (1, 8), (1, 32), (1, 64)])
+def test_multivector_cache_modes_bit_identical(mf, prec, nvec):
+    """Generated, partially and fully cached block pairs give the same
+    product bit for bit (8 vectors: the Hermitian-reuse kernel; 32 and 64 in
+    the FP32 form: the row-owner ring tile, stored chunks read in both
+    orientations)."""
+    D, b = 1000, 256
     eb = 16 if prec == 0 else 8
     X = W.random_state(D, nvec, seed=3)
     ys = []
