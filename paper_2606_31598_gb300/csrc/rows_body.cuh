@@ -531,7 +531,8 @@ __device__ __forceinline__ void row_tile_async(unsigned char* smem_raw, int64_t 
 // rows have an even pitch (W + 2 complex, 16-byte aligned): a thread reads the
 // entries of two consecutive columns in one 16-byte load and its TV
 // contiguous vectors (tv TV .. tv TV + TV - 1) in 16-byte pieces; stored
-// chunks that are not transposed are copied in 16-byte pieces.  The product
+// chunks are copied in 16-byte pieces, those read transposed kept in their
+// stored orientation (two 8-byte loads per row and column pair).  The product
 // is taken in packed FP32 pairs: A += (h_r, h_r) x and B += (h_i, h_i) x over
 // the row tile, Y = A + i B at its end (the conjugate of a transposed chunk
 // negates h_i, a compile-time branch of the contraction).
@@ -546,14 +547,23 @@ __host__ __device__ constexpr int f32_ld() { return W + 2; }
 // and B[i][j] += h_i^im x_j over the column pairs kk0 .. kk0 + KPG - 1 of the
 // staged chunk (h_i^im negated when CJ).
 template <int GEN, int NV, int TR, int TV, int KPG, int LD, bool CJ>
-__device__ __forceinline__ void contract_f32(float2 (&A)[TR][TV], float2 (&B)[TR][TV], const float2* __restrict__ hrow,
-                                             const float2* __restrict__ xcol, int kk0) {
+__device__ __forceinline__ void contract_f32(float2 (&A)[TR][TV], float2 (&B)[TR][TV], const float2* __restrict__ hst,
+                                             int tr, const float2* __restrict__ xcol, int kk0) {
   constexpr int RS = RT / TR;
 #pragma unroll (KPG <= 4 ? 2 : 1)
   for (int kk = kk0; kk < kk0 + KPG; kk += 2) {
+    // h[i] = (H[r][kk], H[r][kk + 1]) of row r = tr + i RS: one 16-byte
+    // load from a row-major chunk, two 8-byte loads from a transposed one
     float4 h[TR];
 #pragma unroll
-    for (int i = 0; i < TR; ++i) h[i] = *reinterpret_cast<const float4*>(hrow + i * RS * LD + kk);
+    for (int i = 0; i < TR; ++i) {
+      if constexpr (CJ) {
+        const float2 a = hst[kk * RT + tr + i * RS], c = hst[(kk + 1) * RT + tr + i * RS];
+        h[i] = make_float4(a.x, a.y, c.x, c.y);
+      } else {
+        h[i] = *reinterpret_cast<const float4*>(hst + (tr + i * RS) * LD + kk);
+      }
+    }
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       float4 x[TV / 2];
@@ -576,6 +586,27 @@ __device__ __forceinline__ void contract_f32(float2 (&A)[TR][TV], float2 (&B)[TR
       }
     }
   }
+}
+
+// A stored chunk read transposed (stored rows c0 .. c0 + W - 1 of the block
+// pair hold H[c][r] for the tile's rows r) copied as it is stored, hb[c][r]
+// with a pitch of RT, in 16-byte pieces (two rows r, r + 1 of one stored row;
+// R0 + r is even and a stored block's side a multiple of 128).
+template <int NT, int W>
+__device__ __forceinline__ void chunk_copy_async_t(float2* hb, int64_t slot, int64_t R0, int64_t c0,
+                                                   const float2* __restrict__ cache, int64_t b) {
+  constexpr int PPR = RT / 2;  // pieces per stored row
+  static_assert((PPR * W) % NT == 0 && NT % PPR == 0, "pieces in whole passes");
+  const int tid = threadIdx.x;
+  const int64_t n = blk_of(R0, b), m = blk_of(c0, b);
+  const float2* blk = cache + slot * b * b;
+  const int c = tid / PPR, pr = tid % PPR;
+  const float2* src = blk + (c0 + c - m * b) * b + (R0 + 2 * pr - n * b);
+  float2* dst = hb + c * RT + 2 * pr;
+  const int64_t sstep = (int64_t)(NT / PPR) * b;
+#pragma unroll 4
+  for (int i = 0; i < PPR * W / NT; ++i) cp_async_elem<16>(dst + i * (NT / PPR) * RT, src + i * sstep);
+  cp_async_commit();
 }
 
 // The generation of a chunk out of line: it is the rare path of the ring
@@ -635,9 +666,12 @@ __device__ __forceinline__ void row_tile_async_f32(unsigned char* smem_raw, int6
       sl = chunk_slot(R0, c0, cache, nullptr, slot_of_pair, b, nblk, t);
     }
     xchunk_copy_async<float, NV, NT, W>(xs + st * W * NV, xc, c0, cend);
-    if (sl != -1) {
-      chunk_copy_async<float, NT, LD, W>(hs + st * RT * LD, sl, t, R0, c0, cache, nullptr, b);
-      conj = t ? (conj | (1u << st)) : (conj & ~(1u << st));
+    if (sl != -1 && t) {
+      chunk_copy_async_t<NT, W>(hs + st * RT * LD, sl, R0, c0, cache, b);
+      conj |= 1u << st;
+    } else if (sl != -1) {
+      chunk_copy_async<float, NT, LD, W>(hs + st * RT * LD, sl, false, R0, c0, cache, nullptr, b);
+      conj &= ~(1u << st);
     } else {
       cp_async_commit();
       fill_chunk_gen_f32<GEN, NT, LD, W>(hs + st * RT * LD, win, R0, c0, seed, sigma, dk);
@@ -654,12 +688,12 @@ __device__ __forceinline__ void row_tile_async_f32(unsigned char* smem_raw, int6
     __syncthreads();
     issue(k + S - 1);
     const int st = (int)(k % S);
-    const C* hrow = hs + st * RT * LD + tr * LD;
+    const C* hst = hs + st * RT * LD;
     const C* xcol = xs + st * W * NV + tv * TV;
     if ((conj >> st) & 1u)
-      contract_f32<GEN, NV, TR, TV, KPG, LD, true>(A, B, hrow, xcol, kg * KPG);
+      contract_f32<GEN, NV, TR, TV, KPG, LD, true>(A, B, hst, tr, xcol, kg * KPG);
     else
-      contract_f32<GEN, NV, TR, TV, KPG, LD, false>(A, B, hrow, xcol, kg * KPG);
+      contract_f32<GEN, NV, TR, TV, KPG, LD, false>(A, B, hst, tr, xcol, kg * KPG);
   }
   cp_async_wait_all();
   __syncthreads();  // every thread is done with the ring
@@ -815,7 +849,7 @@ __device__ __forceinline__ void row_tile_herm_f32(unsigned char* smem_raw, int64
     issue(k + 1);
     const int st = (int)(k % S);
     const C* hst = hs + st * RT * LD;
-    contract_f32<GEN, NV, TR, TV, KPG, LD, false>(A, B, hst + tr * LD, xs + st * W * NV + tv * TV, kg * KPG);
+    contract_f32<GEN, NV, TR, TV, KPG, LD, false>(A, B, hst, tr, xs + st * W * NV + tv * TV, kg * KPG);
     if (c0 >= R0 + RT) {
       // Y[c][v] over this part's rows: A' += h_r x, B' += h_i x
       C Ad[NV], Bd[NV];
