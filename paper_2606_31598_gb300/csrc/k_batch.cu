@@ -46,14 +46,25 @@ struct BatchItem {
 namespace {
 
 // The work lists of the batched kernel: the row-owner form per vector bucket
-// (rows_nvec_bucket of max(2, nvec)) and the Hermitian-reuse form (FP32, few
+// (batch_nvec_bucket of max(2, nvec)) and the Hermitian-reuse form (FP32, few
 // vectors, where the stored bytes bound the product) for buckets 2, 4 and 6
 // (at 8 vectors the row-owner form is faster: 16.7 vs 17.6 ms for 38
 // problems of D = 16384).
-constexpr int kOwnerBuckets = 6;
-constexpr int kBuckets = 9;
-constexpr int kBucketNV[kBuckets] = {2, 4, 6, 8, 12, 16, 2, 4, 6};
-constexpr bool kBucketHerm[kBuckets] = {false, false, false, false, false, false, true, true, true};
+// The batch pads a problem's vectors to the next of 2, 4, ..., 16 (10 and 14
+// too: 9-10 vectors on the 10-wide tile take 17.8 ms where the 12-wide one
+// takes 20.8, 13-14 on the 14-wide 24.9 where the 16-wide takes 27.2, for 38
+// problems of D = 16384); the plan's workspace, sized for its row-kernel
+// bucket (at least as many vectors), holds the batch's layout.
+constexpr int kOwnerBuckets = 8;
+constexpr int kBuckets = 11;
+constexpr int kBucketNV[kBuckets] = {2, 4, 6, 8, 10, 12, 14, 16, 2, 4, 6};
+constexpr bool kBucketHerm[kBuckets] = {false, false, false, false, false, false, false, false, true, true, true};
+
+int64_t batch_nvec_bucket(int64_t nvec) {
+  for (int k = 0; k < kOwnerBuckets; ++k)
+    if (nvec <= kBucketNV[k]) return kBucketNV[k];
+  return kBucketNV[kOwnerBuckets - 1];
+}
 
 // One row tile of a problem of bucket NB.  Register tiles (rows x vectors)
 // and k-groups per bucket: the FP32 form takes 2 x 2 to 4 x 6 complex tiles
@@ -67,14 +78,14 @@ __device__ __forceinline__ void batch_tile(unsigned char* smem_raw, const BatchP
   const C* cache = (const C*)P.cache;
   C* out = (C*)P.part + R0 * P.nb;
   if constexpr (sizeof(T) == 4) {
-    constexpr int TR = NB == 2 ? 2 : NB == 4 ? 4 : NB == 6 ? 2 : NB == 8 ? 4 : NB == 12 ? 2 : 4;
-    constexpr int TV = NB == 2 ? 2 : NB == 4 ? 4 : NB == 6 ? 6 : NB == 8 ? 4 : NB == 12 ? 6 : 4;
-    constexpr int KG = NB == 2 ? 4 : NB == 4 ? 8 : NB == 6 ? 4 : NB == 8 ? 4 : 2;
+    constexpr int TR = NB == 2 ? 2 : NB == 4 ? 4 : NB == 6 ? 2 : NB == 8 ? 4 : NB == 10 ? 2 : NB == 12 ? 2 : NB == 14 ? 1 : 4;
+    constexpr int TV = NB == 2 ? 2 : NB == 4 ? 4 : NB == 6 ? 6 : NB == 8 ? 4 : NB == 10 ? 10 : NB == 12 ? 6 : NB == 14 ? 14 : 4;
+    constexpr int KG = NB == 2 ? 4 : NB == 4 ? 8 : NB == 6 ? 4 : NB == 8 ? 4 : NB == 10 ? 4 : 2;
     row_tile_async_f32<GEN, NB, TR, TV, 256, KG>(smem_raw, R0, 0, P.D, P.seed, P.sigma32, P.dk, (const float2*)xc,
                                                  (float2*)out, (const float2*)cache, P.slot, P.b, P.nblk);
   } else {
-    constexpr int TR = NB <= 6 ? 1 : 2;
-    constexpr int TV = NB == 2 ? 1 : NB == 4 ? 2 : NB == 6 ? 3 : NB == 8 ? 2 : NB == 12 ? 3 : 4;
+    constexpr int TR = NB <= 6 || NB == 10 || NB == 14 ? 1 : 2;
+    constexpr int TV = NB == 2 ? 1 : NB == 4 ? 2 : NB == 6 ? 3 : NB == 8 ? 2 : NB == 10 ? 5 : NB == 12 ? 3 : NB == 14 ? 7 : 4;
     row_tile_async<T, GEN, NB, TR, TV, 256>(smem_raw, R0, 0, P.D, P.seed, (T)P.sigma64, P.dk, xc, out, cache, P.slot,
                                             P.b, P.nblk);
   }
@@ -139,10 +150,12 @@ BatchKernel<T, GEN> batch_kernel(int k) {
     case 1: return k_batch_apply<T, GEN, 4>;
     case 2: return k_batch_apply<T, GEN, 6>;
     case 3: return k_batch_apply<T, GEN, 8>;
-    case 4: return k_batch_apply<T, GEN, 12>;
-    case 5: return k_batch_apply<T, GEN, 16>;
-    case 6: return k_batch_herm<T, GEN, 2>;
-    case 7: return k_batch_herm<T, GEN, 4>;
+    case 4: return k_batch_apply<T, GEN, 10>;
+    case 5: return k_batch_apply<T, GEN, 12>;
+    case 6: return k_batch_apply<T, GEN, 14>;
+    case 7: return k_batch_apply<T, GEN, 16>;
+    case 8: return k_batch_herm<T, GEN, 2>;
+    case 9: return k_batch_herm<T, GEN, 4>;
     default: return k_batch_herm<T, GEN, 6>;
   }
 }
@@ -155,10 +168,12 @@ size_t batch_smem(int k) {
       case 1: return rows_smem_bytes_f32<4>();
       case 2: return rows_smem_bytes_f32<6>();
       case 3: return rows_smem_bytes_f32<8>();
-      case 4: return rows_smem_bytes_f32<12>();
-      case 5: return rows_smem_bytes_f32<16>();
-      case 6: return herm_smem_bytes_f32<2>();
-      case 7: return herm_smem_bytes_f32<4>();
+      case 4: return rows_smem_bytes_f32<10>();
+      case 5: return rows_smem_bytes_f32<12>();
+      case 6: return rows_smem_bytes_f32<14>();
+      case 7: return rows_smem_bytes_f32<16>();
+      case 8: return herm_smem_bytes_f32<2>();
+      case 9: return herm_smem_bytes_f32<4>();
       default: return herm_smem_bytes_f32<6>();
     }
   } else {
@@ -167,7 +182,9 @@ size_t batch_smem(int k) {
       case 1: return rows_smem_bytes_async<double, 4>();
       case 2: return rows_smem_bytes_async<double, 6>();
       case 3: return rows_smem_bytes_async<double, 8>();
-      case 4: return rows_smem_bytes_async<double, 12>();
+      case 4: return rows_smem_bytes_async<double, 10>();
+      case 5: return rows_smem_bytes_async<double, 12>();
+      case 6: return rows_smem_bytes_async<double, 14>();
       default: return rows_smem_bytes_async<double, 16>();
     }
   }
@@ -442,7 +459,7 @@ mf_status mf_batch_create(mf_batch_t* out, int32_t nprob, const int64_t* D, cons
     size_t slot_room = free_b / 10;
     for (int32_t i = 0; i < nprob && o.precision == MF_PREC_FP32; ++i) {
       const Plan& P = b->plans[i]->p;
-      const int64_t nb = rows_nvec_bucket(std::max<int32_t>(2, nvec[i]));
+      const int64_t nb = batch_nvec_bucket(std::max<int32_t>(2, nvec[i]));
       if (nb > 6) continue;
       const size_t bytes = (size_t)(1 + P.ntile) * (size_t)(P.ntile * rows::RT) * (size_t)nb * sizeof(float2);
       if (bytes > slot_room) continue;
@@ -459,7 +476,7 @@ mf_status mf_batch_create(mf_batch_t* out, int32_t nprob, const int64_t* D, cons
     std::vector<int> bucket;
     for (int32_t i = 0; i < nprob; ++i) {
       const Plan& P = b->plans[i]->p;
-      const int64_t nb = rows_nvec_bucket(std::max<int32_t>(2, nvec[i]));
+      const int64_t nb = batch_nvec_bucket(std::max<int32_t>(2, nvec[i]));
       const bool herm = b->hbuf[i] != nullptr;
       for (int64_t t = 0; t < P.ntile; ++t) {
         items.push_back(BatchItem{i, (int32_t)t});
@@ -556,7 +573,7 @@ mf_status mf_batch_propagate(mf_batch_t b, void* psi, double dt, int32_t nsteps,
         q.nblk = P.nblk;
         q.nv = b->offsets[i + 1] - b->offsets[i];
         q.nv /= P.D;
-        q.nb = rows_nvec_bucket(std::max<int64_t>(2, q.nv));
+        q.nb = batch_nvec_bucket(std::max<int64_t>(2, q.nv));
         q.seed = P.seed;
         q.sigma32 = P.sigma32;
         q.sigma64 = P.sigma64;

@@ -25,9 +25,9 @@ def test_batch_matches_per_problem_and_oracle(mf, prec, tol, cache):
     pairs (partial) and stored pairs only (full); ragged D leaves a partial
     last chunk of columns and a partial last row tile."""
     # (a partial cache needs at least two block pairs: no D = 130 there)
-    Ds = [1000, 2048, 700, 130 if cache != "partial" else 1200, 1536]
-    nv = [1, 3, 16, 2, 5]
-    seeds = [0, 1, 2, 3, 4]
+    Ds = [1000, 2048, 700, 130 if cache != "partial" else 1200, 1536, 900]
+    nv = [1, 3, 16, 2, 5, 9]
+    seeds = [0, 1, 2, 3, 4, 5]
     eb = 16 if prec == 0 else 8
     full = sum(eb * D * D for D in Ds)  # every block pair, with headroom
     budget = {"none": 0, "partial": full // 5, "full": 4 * full}[cache]
@@ -97,15 +97,16 @@ def test_batch_dvr_and_workload_draw(mf):
 @pytest.mark.parametrize("cache", ["none", "full"])
 def test_batch_dvr_fp32_both_forms(mf, cache):
     """DVR problems in the FP32 form: 1-6 vectors on the Hermitian-reuse form
-    (real symmetric entries: H^dagger = H^T), 8 and 12 on the row-owner form; ragged
+    (real symmetric entries: H^dagger = H^T), 8, 10, 12 and 14 on the row-owner form (10 and 14
+    on the batch's own 10- and 14-wide tiles); ragged
     D (a partial last chunk and row tile), generated or stored chunks."""
-    Ds = [1000, 300, 1536, 777, 640]
-    nv = [1, 6, 4, 12, 8]
+    Ds = [1000, 300, 1536, 777, 640, 520, 260]
+    nv = [1, 6, 4, 12, 8, 10, 14]
     full = sum(8 * D * D for D in Ds)
-    b = mf.Batch(Ds, nv, list(range(5)), mf.MF_GEN_SINC_DVR_HO, precision=mf.MF_PREC_FP32,
+    b = mf.Batch(Ds, nv, list(range(7)), mf.MF_GEN_SINC_DVR_HO, precision=mf.MF_PREC_FP32,
                  cache_budget_bytes=0 if cache == "none" else 4 * full,
                  storage=mf.MF_STORE_PROCEDURAL if cache == "none" else mf.MF_STORE_FULL)
-    assert [b.hermitian(i) for i in range(5)] == [True, True, True, False, False]
+    assert [b.hermitian(i) for i in range(7)] == [True, True, True, False, False, False, False]
     parts = [W.random_state(D, k, seed=20 + i).reshape(D, k) for i, (D, k) in enumerate(zip(Ds, nv))]
     d = torch.from_numpy(np.concatenate([p.ravel() for p in parts])).cuda()
     b.propagate(d, 1e-4, 1, 12)
