@@ -4,10 +4,12 @@
 // independent problems need no communication, so on one GPU they share the
 // SMs.  Every problem is a plan of its own (block size and cache chosen by
 // its planner, bounds by Lanczos, Chebyshev coefficients for its own R*dt);
-// one persistent kernel per Chebyshev term drains a work list of
-// (problem, 128-row tile) items through an atomic counter, so problems of
-// uneven D and vector count balance across the SMs, and the whole
-// propagation -- every step and term -- is captured once in a CUDA graph.
+// each Chebyshev term forks one persistent kernel per work list (vector
+// bucket and form: row-owner, or Hermitian-reuse for the FP32 problems of
+// 1-6 vectors) onto side streams, each draining its (problem, 128-row tile)
+// items through an atomic counter, so problems of uneven D and vector count
+// balance across the SMs; the whole propagation -- every step and term --
+// is captured once in a CUDA graph.
 #include <cuda_runtime.h>
 
 #include <algorithm>
