@@ -524,10 +524,11 @@ __device__ __forceinline__ void row_tile_async(unsigned char* smem_raw, int64_t 
 }
 
 // ---------------------------------------------------------------------------
-// FP32 form of row_tile_async: a ring of S stages of W-column chunks, so
-// that S - 1 chunks (stored entries and rows of X) are in flight while one
-// is contracted -- two 32-column buffers kept too few bytes in flight per SM
-// to overlap the stream of stored entries with the contraction.  The staged
+// FP32 form of row_tile_async: a ring of S stages of W-column chunks, S - 1
+// chunks (stored entries and rows of X) in flight while one is contracted
+// (two stages of 32 columns: deeper rings of 16- or 32-column chunks timed
+// 1-8 % slower, the contraction and not the copies' latency being what the
+// ring waits for).  The staged
 // rows have an even pitch (W + 2 complex, 16-byte aligned): a thread reads the
 // entries of two consecutive columns in one 16-byte load and its TV
 // contiguous vectors (tv TV .. tv TV + TV - 1) in 16-byte pieces; stored
